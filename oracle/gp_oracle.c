@@ -1,0 +1,716 @@
+/*
+ * gp_oracle.c -- plain, slow, obviously-correct CPU oracle for stack-based
+ * genetic-programming fitness evaluation (Sathia, Ganesh, Nanditale,
+ * "Accelerating Genetic Programming using GPUs", arXiv 2110.11226).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * execute this file: only tests/, __graft_entry__.smoke() and the CPU
+ * baseline leg of bench.py use it.  It shares no code, header, table or
+ * constant with the CUDA library; its op numbering and node layout are
+ * written out here on their own and a test checks them against the
+ * library's public header.
+ *
+ * Passages followed (section / equation of the paper):
+ *   - Program = prefix (Polish) list of nodes, evaluated with a stack by a
+ *     reverse scan of the list (Sec. III-A).
+ *   - Functions have arity <= 2 (Sec. III); a stack of size m evaluates a
+ *     tree of depth m-1 (Sec. III-C2, hoisted crossover), the stack size is
+ *     20.
+ *   - Fitness = weighted loss of the predictions against y, reduced per
+ *     program (Sec. III-C3): MAE, MSE, RMSE, logistic loss.
+ *   - Tournament selection: k Philox draws per tournament, best adjusted
+ *     fitness wins, adjusted = raw + c * len (Sec. III-C1, Eqs. parsimony
+ *     and fitness); Philox4x32-10 from Salmon et al. 2011 (Sec. III-B).
+ *
+ * Readings where the paper is silent (each listed in the design doc):
+ *   - first pop of a binary function is its LEFT operand;
+ *   - protected operators with threshold 0.001f, compared as |x| < thr:
+ *     div -> 1, inv -> 0, log -> 0, sqrt takes |x|; exp/sin/cos/tan plain;
+ *   - weighted means normalised by sum(w); RMSE = sqrt(weighted MSE);
+ *   - log-loss on sigmoid(p): c*|p| + log1p(exp(-|p|)), c = 1-y if p>=0
+ *     else y, with the c*|p| term dropped when c == 0;
+ *   - tournament draws with replacement, index = (u * n) >> 32, ties go to
+ *     the earliest draw, NaN counts as the worst fitness.
+ *
+ * Everything is FP64 unless a function says FP32 ("_f32" evaluates every
+ * operation rounded to float with the C library's float functions; it is
+ * the reference for bit-exact checks of the IEEE operators).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <float.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---- node layout and op numbering (the library's input format) ---------- */
+typedef struct {
+    int16_t op;   /* opcode, see below                                  */
+    int16_t feat; /* feature (column) index for a variable terminal     */
+    float c;      /* value of a constant terminal                       */
+} ora_node;
+
+enum {
+    ORA_CONST = 0, ORA_VAR = 1,
+    ORA_ADD = 2, ORA_SUB = 3, ORA_MUL = 4, ORA_DIV = 5,
+    ORA_SQRT = 6, ORA_LOG = 7, ORA_EXP = 8, ORA_SIN = 9, ORA_COS = 10,
+    ORA_TAN = 11, ORA_ABS = 12, ORA_NEG = 13, ORA_INV = 14,
+    ORA_NOPS = 15
+};
+
+enum { ORA_MAE = 0, ORA_MSE = 1, ORA_RMSE = 2, ORA_LOGLOSS = 3 };
+
+#define ORA_MAX_STACK 20
+#define ORA_MAX_LEN 255
+#define ORA_MAX_CONSTS 16
+
+/* status codes of ora_validate */
+enum {
+    ORA_OK = 0, ORA_BAD_LENGTH = 1, ORA_BAD_OP = 2, ORA_BAD_FEATURE = 3,
+    ORA_UNDERFLOW = 4, ORA_LEFTOVER = 5, ORA_TOO_DEEP = 6
+};
+
+static const float ORA_THR = 0.001f;
+
+static const char *const ora_names[ORA_NOPS] = {
+    "const", "var", "add", "sub", "mul", "div", "sqrt", "log", "exp",
+    "sin", "cos", "tan", "abs", "neg", "inv"};
+
+const char *ora_op_name(int op) {
+    return (op >= 0 && op < ORA_NOPS) ? ora_names[op] : "";
+}
+
+int ora_op_arity(int op) {
+    if (op == ORA_CONST || op == ORA_VAR) return 0;
+    if (op >= ORA_ADD && op <= ORA_DIV) return 2;
+    if (op >= ORA_SQRT && op <= ORA_INV) return 1;
+    return -1;
+}
+
+int ora_num_ops(void) { return ORA_NOPS; }
+
+/* ---- validation: the reverse scan's stack high-water mark ------------- */
+/* Returns a status code; *hw receives the largest stack height reached. */
+int ora_validate(const ora_node *p, int len, int n_feat, int *hw) {
+    int sp = 0, mx = 0;
+    if (hw) *hw = 0;
+    if (len < 1 || len > ORA_MAX_LEN) return ORA_BAD_LENGTH;
+    for (int j = len - 1; j >= 0; --j) {
+        int a = ora_op_arity(p[j].op);
+        if (a < 0) return ORA_BAD_OP;
+        if (p[j].op == ORA_VAR && (p[j].feat < 0 || p[j].feat >= n_feat))
+            return ORA_BAD_FEATURE;
+        if (a == 0) {
+            sp += 1;
+        } else {
+            if (sp < a) return ORA_UNDERFLOW;
+            sp -= a - 1;
+        }
+        if (sp > mx) mx = sp;
+    }
+    if (hw) *hw = mx;
+    if (sp != 1) return ORA_LEFTOVER;
+    if (mx > ORA_MAX_STACK) return ORA_TOO_DEEP;
+    return ORA_OK;
+}
+
+/* ---- the function set, FP64 ------------------------------------------- */
+static double fn1_64(int op, double a) {
+    const double thr = (double)ORA_THR;
+    switch (op) {
+    case ORA_SQRT: return sqrt(fabs(a));
+    case ORA_LOG:  return fabs(a) < thr ? 0.0 : log(fabs(a));
+    case ORA_EXP:  return exp(a);
+    case ORA_SIN:  return sin(a);
+    case ORA_COS:  return cos(a);
+    case ORA_TAN:  return tan(a);
+    case ORA_ABS:  return fabs(a);
+    case ORA_NEG:  return -a;
+    case ORA_INV:  return fabs(a) < thr ? 0.0 : 1.0 / a;
+    }
+    return NAN;
+}
+
+/* a = left operand (first pop), b = right operand (second pop) */
+static double fn2_64(int op, double a, double b) {
+    const double thr = (double)ORA_THR;
+    switch (op) {
+    case ORA_ADD: return a + b;
+    case ORA_SUB: return a - b;
+    case ORA_MUL: return a * b;
+    case ORA_DIV: return fabs(b) < thr ? 1.0 : a / b;
+    }
+    return NAN;
+}
+
+/* ---- the function set, FP32 (every step rounded to float) ------------- */
+static float fn1_32(int op, float a) {
+    switch (op) {
+    case ORA_SQRT: return sqrtf(fabsf(a));
+    case ORA_LOG:  return fabsf(a) < ORA_THR ? 0.0f : logf(fabsf(a));
+    case ORA_EXP:  return expf(a);
+    case ORA_SIN:  return sinf(a);
+    case ORA_COS:  return cosf(a);
+    case ORA_TAN:  return tanf(a);
+    case ORA_ABS:  return fabsf(a);
+    case ORA_NEG:  return -a;
+    case ORA_INV:  return fabsf(a) < ORA_THR ? 0.0f : 1.0f / a;
+    }
+    return NAN;
+}
+
+static float fn2_32(int op, float a, float b) {
+    switch (op) {
+    case ORA_ADD: return a + b;
+    case ORA_SUB: return a - b;
+    case ORA_MUL: return a * b;
+    case ORA_DIV: return fabsf(b) < ORA_THR ? 1.0f : a / b;
+    }
+    return NAN;
+}
+
+/* ---- one program on one row: reverse scan of the prefix list ---------- */
+/* X is column-major: X[f * ld + row].  Returns 0 or a status code; the
+ * stack is as long as the program so any well-formed list evaluates. */
+static int eval_row64(const ora_node *p, int len, const float *X, int64_t ld,
+                      int64_t row, double *out) {
+    double st[ORA_MAX_LEN + 1];
+    int sp = 0;
+    if (len < 1 || len > ORA_MAX_LEN) return ORA_BAD_LENGTH;
+    for (int j = len - 1; j >= 0; --j) {
+        int op = p[j].op, a = ora_op_arity(op);
+        if (a < 0) return ORA_BAD_OP;
+        if (op == ORA_CONST) {
+            st[sp++] = (double)p[j].c;
+        } else if (op == ORA_VAR) {
+            st[sp++] = (double)X[(int64_t)p[j].feat * ld + row];
+        } else if (a == 1) {
+            if (sp < 1) return ORA_UNDERFLOW;
+            st[sp - 1] = fn1_64(op, st[sp - 1]);
+        } else {
+            if (sp < 2) return ORA_UNDERFLOW;
+            double left = st[sp - 1], right = st[sp - 2];
+            sp -= 1;
+            st[sp - 1] = fn2_64(op, left, right);
+        }
+    }
+    if (sp != 1) return ORA_LEFTOVER;
+    *out = st[0];
+    return ORA_OK;
+}
+
+static int eval_row32(const ora_node *p, int len, const float *X, int64_t ld,
+                      int64_t row, float *out) {
+    float st[ORA_MAX_LEN + 1];
+    int sp = 0;
+    if (len < 1 || len > ORA_MAX_LEN) return ORA_BAD_LENGTH;
+    for (int j = len - 1; j >= 0; --j) {
+        int op = p[j].op, a = ora_op_arity(op);
+        if (a < 0) return ORA_BAD_OP;
+        if (op == ORA_CONST) {
+            st[sp++] = p[j].c;
+        } else if (op == ORA_VAR) {
+            st[sp++] = X[(int64_t)p[j].feat * ld + row];
+        } else if (a == 1) {
+            if (sp < 1) return ORA_UNDERFLOW;
+            st[sp - 1] = fn1_32(op, st[sp - 1]);
+        } else {
+            if (sp < 2) return ORA_UNDERFLOW;
+            float left = st[sp - 1], right = st[sp - 2];
+            sp -= 1;
+            st[sp - 1] = fn2_32(op, left, right);
+        }
+    }
+    if (sp != 1) return ORA_LEFTOVER;
+    *out = st[0];
+    return ORA_OK;
+}
+
+/* Predictions of every program on rows [row0, row0 + n_eval):
+ * out[p * n_eval + i].  A malformed program gives NaN on every row; its
+ * status goes to status[p] when status is not NULL. */
+void ora_predict64(const ora_node *progs, const int32_t *offsets, int n_progs,
+                   const float *X, int64_t ld, int64_t row0, int64_t n_eval,
+                   double *out, int32_t *status, int n_threads) {
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int p = 0; p < n_progs; ++p) {
+        const ora_node *prog = progs + offsets[p];
+        int len = offsets[p + 1] - offsets[p];
+        int st = ORA_OK;
+        for (int64_t i = 0; i < n_eval; ++i) {
+            double v = NAN;
+            int s = eval_row64(prog, len, X, ld, row0 + i, &v);
+            if (s) { st = s; v = NAN; }
+            out[(int64_t)p * n_eval + i] = v;
+        }
+        if (status) status[p] = st;
+    }
+}
+
+void ora_predict32(const ora_node *progs, const int32_t *offsets, int n_progs,
+                   const float *X, int64_t ld, int64_t row0, int64_t n_eval,
+                   float *out, int n_threads) {
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int p = 0; p < n_progs; ++p) {
+        const ora_node *prog = progs + offsets[p];
+        int len = offsets[p + 1] - offsets[p];
+        for (int64_t i = 0; i < n_eval; ++i) {
+            float v = NAN;
+            if (eval_row32(prog, len, X, ld, row0 + i, &v)) v = NAN;
+            out[(int64_t)p * n_eval + i] = v;
+        }
+    }
+}
+
+/* ---- running error bound of an FP32 evaluation ------------------------ *
+ * Alongside the FP64 value v of every node this carries e, a first-order
+ * bound on |v32 - v| for an evaluation that rounds each operation to
+ * float and whose library functions err by at most ulps_fn units in the
+ * last place.  Flags:
+ *   1 = a protected operator's threshold test may decide differently in
+ *       FP32 than in FP64 (the operand lies within e of the threshold);
+ *   2 = an intermediate leaves the float range or becomes non-finite, or
+ *       the bound itself is meaningless (tan near a pole, error larger
+ *       than the operand of a division).
+ * Textbook rules (Higham, "Accuracy and Stability of Numerical
+ * Algorithms", 2nd ed., Ch. 2-3): |fl(x op y) - (x op y)| <= u |x op y|,
+ * u = 2^-24, plus propagation of operand errors through first
+ * derivatives. */
+typedef struct { double v, e; int flags; } ora_ve;
+
+static const double U32 = 5.9604644775390625e-08;   /* 2^-24 */
+static const double ETA32 = 7.006492321624085e-46;  /* 2^-150: underflow */
+
+static ora_ve ve_round(ora_ve r, double ulps) {
+    /* rounding (or a library function's error) of the computed result,
+     * |fl(x) - x| <= u|x| + eta with eta covering gradual underflow */
+    double mag = fabs(r.v) + r.e;
+    r.e += ulps * 2.0 * U32 * mag + ulps * 2.0 * ETA32;
+    if (!isfinite(r.v) || fabs(r.v) > (double)FLT_MAX || !isfinite(r.e))
+        r.flags |= 2;
+    return r;
+}
+
+static ora_ve ve_fn1(int op, ora_ve a, double ulps_fn) {
+    const double thr = (double)ORA_THR;
+    ora_ve r;
+    r.flags = a.flags;
+    r.v = fn1_64(op, a.v);
+    double av = fabs(a.v);
+    switch (op) {
+    case ORA_ABS: case ORA_NEG:
+        r.e = a.e;
+        return r; /* exact operations */
+    case ORA_SQRT:
+        r.e = (av > 0.0) ? fmin(a.e / sqrt(av), sqrt(a.e)) : sqrt(a.e);
+        return ve_round(r, 0.5);
+    case ORA_LOG:
+        if (fabs(av - thr) <= a.e) r.flags |= 1;
+        if (av < thr) { r.e = 0.0; return r; }
+        r.e = (a.e < av) ? -log1p(-a.e / av) : INFINITY;
+        if (!(a.e < av)) r.flags |= 2;
+        return ve_round(r, ulps_fn);
+    case ORA_INV:
+        if (fabs(av - thr) <= a.e) r.flags |= 1;
+        if (av < thr) { r.e = 0.0; return r; }
+        if (a.e < av) r.e = a.e / (av * (av - a.e));
+        else { r.e = INFINITY; r.flags |= 2; }
+        return ve_round(r, 0.5);
+    case ORA_EXP:
+        r.e = fabs(r.v) * expm1(a.e);
+        return ve_round(r, ulps_fn);
+    case ORA_SIN: case ORA_COS:
+        r.e = fmin(a.e, 2.0);
+        return ve_round(r, ulps_fn);
+    case ORA_TAN: {
+        double d = a.e * (1.0 + r.v * r.v);
+        if (d > 0.1 * (1.0 + fabs(r.v))) { d = INFINITY; r.flags |= 2; }
+        r.e = 2.0 * d; /* factor 2 covers the curvature over [a-e, a+e] */
+        return ve_round(r, ulps_fn);
+    }
+    }
+    r.e = INFINITY;
+    r.flags |= 2;
+    return r;
+}
+
+static ora_ve ve_fn2(int op, ora_ve a, ora_ve b) {
+    const double thr = (double)ORA_THR;
+    ora_ve r;
+    r.flags = a.flags | b.flags;
+    r.v = fn2_64(op, a.v, b.v);
+    switch (op) {
+    case ORA_ADD: case ORA_SUB:
+        r.e = a.e + b.e;
+        return ve_round(r, 0.5);
+    case ORA_MUL:
+        r.e = fabs(a.v) * b.e + fabs(b.v) * a.e + a.e * b.e;
+        return ve_round(r, 0.5);
+    case ORA_DIV: {
+        double bv = fabs(b.v);
+        if (fabs(bv - thr) <= b.e) r.flags |= 1;
+        if (bv < thr) { r.e = 0.0; return r; }
+        if (b.e < bv) r.e = (a.e + fabs(r.v) * b.e) / (bv - b.e);
+        else { r.e = INFINITY; r.flags |= 2; }
+        return ve_round(r, 0.5);
+    }
+    }
+    r.e = INFINITY;
+    r.flags |= 2;
+    return r;
+}
+
+static int eval_row_bound(const ora_node *p, int len, const float *X,
+                          int64_t ld, int64_t row, double ulps_fn,
+                          ora_ve *out) {
+    ora_ve st[ORA_MAX_LEN + 1];
+    int sp = 0;
+    if (len < 1 || len > ORA_MAX_LEN) return ORA_BAD_LENGTH;
+    for (int j = len - 1; j >= 0; --j) {
+        int op = p[j].op, a = ora_op_arity(op);
+        if (a < 0) return ORA_BAD_OP;
+        if (op == ORA_CONST || op == ORA_VAR) {
+            ora_ve t;
+            t.v = (op == ORA_CONST) ? (double)p[j].c
+                                    : (double)X[(int64_t)p[j].feat * ld + row];
+            t.e = 0.0; /* inputs are floats: exact in both precisions */
+            t.flags = isfinite(t.v) ? 0 : 2;
+            st[sp++] = t;
+        } else if (a == 1) {
+            if (sp < 1) return ORA_UNDERFLOW;
+            st[sp - 1] = ve_fn1(op, st[sp - 1], ulps_fn);
+        } else {
+            if (sp < 2) return ORA_UNDERFLOW;
+            ora_ve left = st[sp - 1], right = st[sp - 2];
+            sp -= 1;
+            st[sp - 1] = ve_fn2(op, left, right);
+        }
+    }
+    if (sp != 1) return ORA_LEFTOVER;
+    *out = st[0];
+    return ORA_OK;
+}
+
+void ora_predict_bound(const ora_node *progs, const int32_t *offsets,
+                       int n_progs, const float *X, int64_t ld, int64_t row0,
+                       int64_t n_eval, double ulps_fn, double *out_v,
+                       double *out_e, uint8_t *out_flags, int n_threads) {
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int p = 0; p < n_progs; ++p) {
+        const ora_node *prog = progs + offsets[p];
+        int len = offsets[p + 1] - offsets[p];
+        for (int64_t i = 0; i < n_eval; ++i) {
+            ora_ve r;
+            int64_t k = (int64_t)p * n_eval + i;
+            if (eval_row_bound(prog, len, X, ld, row0 + i, ulps_fn, &r)) {
+                r.v = NAN; r.e = INFINITY; r.flags = 2;
+            }
+            out_v[k] = r.v;
+            out_e[k] = r.e;
+            out_flags[k] = (uint8_t)r.flags;
+        }
+    }
+}
+
+/* ---- fitness ------------------------------------------------------------ */
+/* Per-row loss of prediction p against target y (Sec. III-C3 metric list;
+ * the formulas are the weighted-mean readings stated in the header). */
+double ora_loss(int metric, double p, double y) {
+    switch (metric) {
+    case ORA_MAE: return fabs(p - y);
+    case ORA_MSE: case ORA_RMSE: return (p - y) * (p - y);
+    case ORA_LOGLOSS: {
+        double ap = fabs(p);
+        double c = (p >= 0.0) ? 1.0 - y : y;
+        double lin = (c == 0.0) ? 0.0 : c * ap;
+        return lin + log1p(exp(-ap));
+    }
+    }
+    return NAN;
+}
+
+/* Fitness of every program over rows [row0, row0 + n_eval):
+ *   MAE/MSE/logloss = sum_i w_i l_i / sum_i w_i, RMSE = sqrt(MSE).
+ * w == NULL means all weights 1.  Returns 0, or -1 for a bad metric or a
+ * zero total weight.  A malformed program gets NaN and status[p] != 0. */
+int ora_fitness(const ora_node *progs, const int32_t *offsets, int n_progs,
+                const float *X, int64_t ld, const float *y, const float *w,
+                int metric, int64_t row0, int64_t n_eval, double *out_fit,
+                int32_t *status, int n_threads) {
+    if (metric < ORA_MAE || metric > ORA_LOGLOSS) return -1;
+    double sw = 0.0;
+    for (int64_t i = 0; i < n_eval; ++i) sw += w ? (double)w[row0 + i] : 1.0;
+    if (!(sw != 0.0)) return -1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int p = 0; p < n_progs; ++p) {
+        const ora_node *prog = progs + offsets[p];
+        int len = offsets[p + 1] - offsets[p];
+        double se = 0.0;
+        int st = ORA_OK;
+        for (int64_t i = 0; i < n_eval && st == ORA_OK; ++i) {
+            double v;
+            int64_t r = row0 + i;
+            st = eval_row64(prog, len, X, ld, r, &v);
+            if (st) break;
+            double wi = w ? (double)w[r] : 1.0;
+            se += wi * ora_loss(metric, v, (double)y[r]);
+        }
+        double f = NAN;
+        if (st == ORA_OK) {
+            f = se / sw;
+            if (metric == ORA_RMSE) f = sqrt(f);
+        }
+        out_fit[p] = f;
+        if (status) status[p] = st;
+    }
+    return 0;
+}
+
+/* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------- *
+ * Round: with the 32x32->64 products of counter words 0 and 2 by the two
+ * multipliers, the new counter is (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2),
+ * hi(M0*c0) ^ c3 ^ k1, lo(M0*c0)); the key advances by the two Weyl
+ * constants between rounds; ten rounds. */
+void ora_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                       uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Draw j of tournament t: counter (j/4, t, offset lo, offset hi), key
+ * (seed lo, seed hi), output word j%4, index = (u * n_progs) >> 32. */
+int64_t ora_tournament_draw(uint64_t seed, uint64_t offset, int64_t t, int j,
+                            int n_progs) {
+    uint32_t ctr[4] = {(uint32_t)(j >> 2), (uint32_t)t, (uint32_t)offset,
+                       (uint32_t)(offset >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    ora_philox4x32_10(ctr, key, o);
+    return (int64_t)(((uint64_t)o[j & 3] * (uint64_t)n_progs) >> 32);
+}
+
+/* Tournament selection (Sec. III-C1).  adjusted = raw + c*len when smaller
+ * is better (Eqs. parsimony, fitness), raw - c*len when greater is better.
+ * The winner is the draw with the strictly best adjusted fitness; the
+ * first such draw wins ties; NaN is the worst value.  lengths may be NULL
+ * (no penalty). */
+int ora_tournament(const float *fitness, const int32_t *lengths, int n_progs,
+                   int64_t n_tourn, int k, float parsimony,
+                   int greater_is_better, uint64_t seed, uint64_t offset,
+                   int32_t *out_idx) {
+    if (n_progs < 1 || k < 1 || n_tourn < 0) return -1;
+    for (int64_t t = 0; t < n_tourn; ++t) {
+        int best = -1;
+        double best_adj = 0.0;
+        for (int j = 0; j < k; ++j) {
+            int i = (int)ora_tournament_draw(seed, offset, t, j, n_progs);
+            double pen = lengths ? (double)parsimony * (double)lengths[i] : 0.0;
+            double raw = (double)fitness[i];
+            double adj;
+            if (greater_is_better) {
+                adj = raw - pen;
+                if (isnan(adj)) adj = -INFINITY;
+            } else {
+                adj = raw + pen;
+                if (isnan(adj)) adj = INFINITY;
+            }
+            int better;
+            if (best < 0) better = 1;
+            else if (greater_is_better) better = adj > best_adj;
+            else better = adj < best_adj;
+            if (better) { best = i; best_adj = adj; }
+        }
+        out_idx[t] = best;
+    }
+    return 0;
+}
+
+/* ---- reverse mode: gradient of fitness w.r.t. the constants ----------- *
+ * A tape of node values from the reverse scan, then adjoints pushed from
+ * the root down in prefix order; constant k (k-th CONST node in prefix
+ * order) collects the adjoint of its node.  Derivative of a protected
+ * operator is 0 on its protected branch. */
+static double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+static double dloss(int metric, double p, double y) {
+    switch (metric) {
+    case ORA_MAE: return sgn(p - y);
+    case ORA_MSE: case ORA_RMSE: return 2.0 * (p - y);
+    case ORA_LOGLOSS: {
+        double s = (p >= 0.0) ? 1.0 / (1.0 + exp(-p))
+                              : exp(p) / (1.0 + exp(p));
+        return s - y;
+    }
+    }
+    return NAN;
+}
+
+int ora_count_consts(const ora_node *p, int len) {
+    int n = 0;
+    for (int j = 0; j < len; ++j) n += (p[j].op == ORA_CONST);
+    return n;
+}
+
+/* grad[p * 16 + k] = d fitness_p / d c_k, fit[p] = fitness_p.  Returns 0,
+ * -1 (bad metric / zero weight) or -2 (a program with more than 16
+ * constants; its row of grad is NaN). */
+int ora_const_grad(const ora_node *progs, const int32_t *offsets,
+                   int n_progs, const float *X, int64_t ld, const float *y,
+                   const float *w, int metric, int64_t row0, int64_t n_eval,
+                   double *grad, double *fit, int n_threads) {
+    if (metric < ORA_MAE || metric > ORA_LOGLOSS) return -1;
+    double sw = 0.0;
+    for (int64_t i = 0; i < n_eval; ++i) sw += w ? (double)w[row0 + i] : 1.0;
+    if (!(sw != 0.0)) return -1;
+    int rc = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic) reduction(min : rc)
+#endif
+    for (int p = 0; p < n_progs; ++p) {
+        const ora_node *prog = progs + offsets[p];
+        int len = offsets[p + 1] - offsets[p];
+        double g[ORA_MAX_CONSTS];
+        int kslot[ORA_MAX_LEN];
+        for (int k = 0; k < ORA_MAX_CONSTS; ++k) g[k] = 0.0;
+        int nc = 0, bad = 0;
+        if (len < 1 || len > ORA_MAX_LEN) bad = 1;
+        for (int j = 0; j < len && !bad; ++j) {
+            kslot[j] = -1;
+            if (prog[j].op == ORA_CONST) {
+                if (nc >= ORA_MAX_CONSTS) { bad = 2; break; }
+                kslot[j] = nc++;
+            }
+        }
+        double se = 0.0;
+        for (int64_t i = 0; i < n_eval && !bad; ++i) {
+            int64_t r = row0 + i;
+            double val[ORA_MAX_LEN], adj[ORA_MAX_LEN];
+            int left[ORA_MAX_LEN], right[ORA_MAX_LEN];
+            int pos[ORA_MAX_LEN + 1], sp = 0;
+            /* forward: reverse scan; the stack holds node positions */
+            for (int j = len - 1; j >= 0 && !bad; --j) {
+                int op = prog[j].op, a = ora_op_arity(op);
+                left[j] = right[j] = -1;
+                if (a < 0) { bad = 1; break; }
+                if (op == ORA_CONST) val[j] = (double)prog[j].c;
+                else if (op == ORA_VAR)
+                    val[j] = (double)X[(int64_t)prog[j].feat * ld + r];
+                else if (a == 1) {
+                    if (sp < 1) { bad = 1; break; }
+                    left[j] = pos[--sp];
+                    val[j] = fn1_64(op, val[left[j]]);
+                } else {
+                    if (sp < 2) { bad = 1; break; }
+                    left[j] = pos[--sp];
+                    right[j] = pos[--sp];
+                    val[j] = fn2_64(op, val[left[j]], val[right[j]]);
+                }
+                pos[sp++] = j;
+            }
+            if (bad || sp != 1) { bad = 1; break; }
+            double pr = val[0], yi = (double)y[r];
+            double wi = w ? (double)w[r] : 1.0;
+            se += wi * ora_loss(metric, pr, yi);
+            /* backward: prefix order, parents before children */
+            for (int j = 0; j < len; ++j) adj[j] = 0.0;
+            adj[0] = wi * dloss(metric, pr, yi);
+            const double thr = (double)ORA_THR;
+            for (int j = 0; j < len; ++j) {
+                int op = prog[j].op;
+                double aj = adj[j];
+                if (op == ORA_CONST) { g[kslot[j]] += aj; continue; }
+                if (op == ORA_VAR) continue;
+                double u = val[left[j]];
+                double du = 0.0, dv = 0.0;
+                switch (op) {
+                case ORA_ADD: du = 1.0; dv = 1.0; break;
+                case ORA_SUB: du = 1.0; dv = -1.0; break;
+                case ORA_MUL: du = val[right[j]]; dv = u; break;
+                case ORA_DIV: {
+                    double v = val[right[j]];
+                    if (fabs(v) < thr) { du = 0.0; dv = 0.0; }
+                    else { du = 1.0 / v; dv = -u / (v * v); }
+                    break;
+                }
+                case ORA_SQRT: du = (u == 0.0) ? 0.0 : sgn(u) / (2.0 * sqrt(fabs(u))); break;
+                case ORA_LOG:  du = (fabs(u) < thr) ? 0.0 : 1.0 / u; break;
+                case ORA_EXP:  du = val[j]; break;
+                case ORA_SIN:  du = cos(u); break;
+                case ORA_COS:  du = -sin(u); break;
+                case ORA_TAN:  du = 1.0 + val[j] * val[j]; break;
+                case ORA_ABS:  du = sgn(u); break;
+                case ORA_NEG:  du = -1.0; break;
+                case ORA_INV:  du = (fabs(u) < thr) ? 0.0 : -1.0 / (u * u); break;
+                }
+                adj[left[j]] = aj * du;
+                if (right[j] >= 0) adj[right[j]] = aj * dv;
+            }
+        }
+        if (bad) {
+            for (int k = 0; k < ORA_MAX_CONSTS; ++k) grad[p * ORA_MAX_CONSTS + k] = NAN;
+            if (fit) fit[p] = NAN;
+            if (bad == 2) rc = -2;
+            continue;
+        }
+        double f = se / sw, scale = 1.0 / sw;
+        if (metric == ORA_RMSE) {
+            f = sqrt(f);
+            scale = (f > 0.0) ? scale / (2.0 * f) : 0.0;
+        }
+        for (int k = 0; k < ORA_MAX_CONSTS; ++k)
+            grad[p * ORA_MAX_CONSTS + k] = (k < nc) ? g[k] * scale : 0.0;
+        if (fit) fit[p] = f;
+    }
+    return rc;
+}
+
+/* ---- Adam (Kingma & Ba 2015, Algorithm 1), one step on n parameters --- */
+void ora_adam(double *theta, const double *g, double *m, double *v, int64_t n,
+              int step, double lr, double beta1, double beta2, double eps) {
+    double b1t = 1.0 - pow(beta1, (double)step);
+    double b2t = 1.0 - pow(beta2, (double)step);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+        double mh = m[i] / b1t, vh = v[i] / b2t;
+        theta[i] -= lr * mh / (sqrt(vh) + eps);
+    }
+}
+
+int ora_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,73 @@
+"""The oracle's pins catch plausible mistakes (CPU only).
+
+Each case plants one mistake in a temporary copy of oracle/gp_oracle.c,
+builds it, and runs tests/test_oracle_pins.py against the copy: the pins
+must fail.  Nothing here touches the real oracle or a GPU.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "gp_oracle.c")
+
+MUTANTS = {
+    "operand_order": ("double left = st[sp - 1], right = st[sp - 2];",
+                      "double left = st[sp - 2], right = st[sp - 1];"),
+    "fp32_operand_order": ("float left = st[sp - 1], right = st[sp - 2];",
+                           "float left = st[sp - 2], right = st[sp - 1];"),
+    "div_protect_value": ("case ORA_DIV: return fabs(b) < thr ? 1.0 : a / b;",
+                          "case ORA_DIV: return fabs(b) < thr ? 0.0 : a / b;"),
+    "threshold_inclusive": ("case ORA_DIV: return fabs(b) < thr ? 1.0 : a / b;",
+                            "case ORA_DIV: return fabs(b) <= thr ? 1.0 : a / b;"),
+    "sqrt_no_abs": ("case ORA_SQRT: return sqrt(fabs(a));", "case ORA_SQRT: return sqrt(a);"),
+    "dropped_weight": ("se += wi * ora_loss(metric, v, (double)y[r]);",
+                       "se += ora_loss(metric, v, (double)y[r]);"),
+    "rmse_no_root": ("if (metric == ORA_RMSE) f = sqrt(f);", "if (0) f = sqrt(f);"),
+    "logloss_label_swap": ("double c = (p >= 0.0) ? 1.0 - y : y;",
+                           "double c = (p >= 0.0) ? y : 1.0 - y;"),
+    "philox_9_rounds": ("for (int r = 0; r < 10; ++r) {", "for (int r = 0; r < 9; ++r) {"),
+    "draw_word": ("(uint64_t)o[j & 3]", "(uint64_t)o[0]"),
+    "tie_to_last": ("else better = adj < best_adj;", "else better = adj <= best_adj;"),
+    "stack_bound_off_by_one": ("if (mx > ORA_MAX_STACK) return ORA_TOO_DEEP;",
+                               "if (mx >= ORA_MAX_STACK) return ORA_TOO_DEEP;"),
+    "dsub_sign": ("case ORA_SUB: du = 1.0; dv = -1.0; break;",
+                  "case ORA_SUB: du = 1.0; dv = 1.0; break;"),
+    "dmae_sign": ("case ORA_MAE: return sgn(p - y);", "case ORA_MAE: return sgn(y - p);"),
+    "dcos_sign": ("case ORA_COS:  du = -sin(u); break;", "case ORA_COS:  du = sin(u); break;"),
+    "adam_no_bias_correction": ("double mh = m[i] / b1t, vh = v[i] / b2t;",
+                                "double mh = m[i], vh = v[i] / b2t;"),
+    "bound_drops_mul_term": ("r.e = fabs(a.v) * b.e + fabs(b.v) * a.e + a.e * b.e;",
+                             "r.e = fabs(a.v) * b.e + a.e * b.e;"),
+}
+
+
+def _run_mutant(name, tmp):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    d = os.path.join(tmp, name)
+    os.makedirs(d, exist_ok=True)
+    c = os.path.join(d, "m.c")
+    so = os.path.join(d, "m.so")
+    open(c, "w").write(src.replace(old, new))
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                    "-ffp-contract=off", c, "-o", so, "-lm"], check=True)
+    env = dict(os.environ, GP_ORACLE_SO=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode
+
+
+def test_pins_catch_planted_mistakes(tmp_path):
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+        results = list(ex.map(lambda n: _run_mutant(n, str(tmp_path)), MUTANTS))
+    survived = [n for n, rc in results if rc == 0]
+    assert not survived, f"mutants not caught by the pins: {survived}"
