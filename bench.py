@@ -1,0 +1,359 @@
+"""Benchmark: one GP generation's hot path on the GPU (arXiv 2110.11226).
+
+A step = batched fitness evaluation of the whole population over every row
+(device pre-pass + persistent evaluator with the fused loss + FP64 reduction)
+followed by tournament selection on the device.  Default workload: Pagie-1,
+N = 16,777,216 rows x 2 features, P = 4096 programs (ramped half-and-half,
+depth 2-10, 12-op function set), RMSE, tournament size 20.
+
+Prints one JSON line.  `value` = program-row evaluations per second with the
+inputs resident in HBM; `e2e` = the same through gp_evaluate_host (host
+buffers, all copies inside the timed region); `plain` = the one-launch-per-
+program evaluator on the same GPU; `roofline` = the evaluator kernel against
+the ALU roofline (node operations over FP32-pipe / SFU peaks, or feature
+bytes over HBM bandwidth); `cpu_baseline` = the FP64 C oracle on the host
+cores, on a bounded sample.
+
+Multi-GPU (torchrun): every rank evaluates its own population (islands, seed
+offset by rank) on the same data with no collective on the data path; the
+time is the max over ranks (weak scaling).
+
+--impl reference: times the oracle instead (the CPU reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "program-row evals/s (GPops/s) and % roofline, batched vs plain eval, same GB300"
+UNIT = "program-row evals/s"
+SFU_OPS = {5, 6, 7, 8, 9, 10, 11, 14}  # div sqrt log exp sin cos tan inv
+LOSS_FP32 = {"mae": 3, "mse": 3, "rmse": 3, "logloss": 6}
+LOSS_SFU = {"mae": 0, "mse": 0, "rmse": 0, "logloss": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pagie_large")
+    ap.add_argument("--n-rows", type=int, default=1 << 24)
+    ap.add_argument("--n-progs", type=int, default=0)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(args, rank):
+    from paper_2110_11226_gb300 import synth
+    wl = synth.workload(args.workload, n_rows=args.n_rows, n_progs=args.n_progs or None)
+    if rank:
+        # islands: every rank evaluates its own population over the same data
+        nodes, off = synth.ramped_half_and_half(len(wl.offsets) - 1, *_depths(args.workload),
+                                                wl.funcs, wl.data.n_feat, 1000 + rank)
+        wl.nodes, wl.offsets = nodes, off
+    return wl
+
+
+def _depths(name):
+    return {"pagie_small": (2, 6), "pagie_large": (2, 10), "tabular": (2, 8),
+            "binary": (2, 8), "const_tune": (4, 10)}[name]
+
+
+def op_counts(nodes, off):
+    op = nodes["op"].astype(np.int64)
+    fn = (op >= 2).astype(np.int64)
+    sfu = np.isin(op, list(SFU_OPS)).astype(np.int64)
+    cfn = np.add.reduceat(fn, off[:-1]) if len(op) else np.zeros(len(off) - 1)
+    csfu = np.add.reduceat(sfu, off[:-1]) if len(op) else np.zeros(len(off) - 1)
+    return int(cfn.sum()), int(csfu.sum()), int(len(op))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    rows.append((float(f[1]), float(f[2]), f[5:9]))
+                except ValueError:
+                    continue
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        load = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(wl, seconds, n_threads=0):
+    """The oracle as it stands, on a bounded sample of the workload."""
+    import oracle
+    d = wl.data
+    P = len(wl.offsets) - 1
+    # calibrate on a small sample, then size the measured one to ~`seconds`
+    n0 = min(d.n_rows, 1 << 14)
+    p0 = min(P, 64)
+    t = time.perf_counter()
+    oracle.fitness(wl.nodes, wl.offsets[:p0 + 1], d.X, d.y, d.w, wl.metric, n_eval=n0,
+                   n_threads=n_threads)
+    dt = max(time.perf_counter() - t, 1e-4)
+    rate = p0 * n0 / dt
+    n_s = int(min(d.n_rows, max(n0, seconds * rate / p0)))
+    t = time.perf_counter()
+    oracle.fitness(wl.nodes, wl.offsets[:p0 + 1], d.X, d.y, d.w, wl.metric, n_eval=n_s,
+                   n_threads=n_threads)
+    dt = time.perf_counter() - t
+    return {"value": p0 * n_s / dt, "unit": UNIT, "cores": oracle.max_threads() if n_threads <= 0 else n_threads,
+            "kind": "oracle",
+            "sample": f"first {p0} programs x first {n_s} rows of {wl.name}, FP64 C oracle, OpenMP over programs",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    wl = make_workload(args, 0)
+    import oracle
+    P = len(wl.offsets) - 1
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline(wl, max(1.0, min(args.cpu_seconds, 20.0) / max(args.steps, 1)))
+        if s >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * P * wl.data.n_rows / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "n_rows": wl.data.n_rows,
+                                            "n_progs": P, "n_feat": wl.data.n_feat, "metric": wl.metric},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2110_11226_gb300 import gp
+
+    wl = make_workload(args, rank)
+    d = wl.data
+    P = len(wl.offsets) - 1
+    N = d.n_rows
+    dev = torch.device("cuda", local)
+    pn = gp.nodes_to_device(wl.nodes, dev)
+    po = torch.from_numpy(wl.offsets).to(dev)
+    dX = torch.from_numpy(d.X).to(dev)
+    dy = torch.from_numpy(d.y).to(dev)
+    dw = None if d.w is None else torch.from_numpy(d.w).to(dev)
+    fit = torch.empty(P, dtype=torch.float32, device=dev)
+    win = torch.empty(P, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    pipes = gp.gp_probe_pipes()
+    tuned = None
+    if args.autotune:
+        tuned = gp.gp_autotune(pn, po, dX, dy, dw, metric=wl.metric)
+
+    def step(seed):
+        gp.gp_evaluate(pn, po, dX, dy, dw, metric=wl.metric, out=fit)
+        gp.gp_tournament_ex(fit, P, wl.tourn_size, seed, out=win)
+
+    for s in range(args.warmup):
+        step(42 + s)
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    gp.gp_timing_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s in range(args.steps):
+            step(1000 + s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    eval_ms, n_eval_calls = gp.gp_timing_read()
+    gp.gp_timing_enable(False)
+    total_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    clocks = clk.summary()
+    rows_evals = float(N) * P
+    value = ws * rows_evals * args.steps / (total_ms * 1e-3)
+    fin = torch.isfinite(fit).float().mean().item()
+
+    # roofline of the evaluator kernel (per launch = one population over N rows)
+    n_fn, n_sfu, n_nodes = op_counts(wl.nodes, wl.offsets)
+    ops_fp32 = N * (n_fn + LOSS_FP32[wl.metric] * P)
+    ops_sfu = N * (n_sfu + LOSS_SFU[wl.metric] * P)
+    bytes_alg = N * 4 * (d.n_feat + 1 + (d.w is not None))
+    peak_fp32 = pipes["fp32_lane_ops_per_s"]
+    peak_sfu = pipes["mufu_ex2_lane_ops_per_s"]
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    t_kernel = eval_ms / max(n_eval_calls, 1) * 1e-3
+    cands = {"fp32": ops_fp32 / peak_fp32, "sfu": ops_sfu / peak_sfu, "hbm": bytes_alg / (hbm * 1e9)}
+    bound = max(cands, key=cands.get)
+    if bound == "hbm":
+        roof = {"bound": "hbm", "achieved": bytes_alg / t_kernel / 1e9, "peak": hbm, "unit": "GB/s"}
+    else:
+        ops = ops_fp32 if bound == "fp32" else ops_sfu
+        pk = peak_fp32 if bound == "fp32" else peak_sfu
+        roof = {"bound": "alu", "pipe": bound, "achieved": ops / t_kernel / 1e12,
+                "peak": pk / 1e12, "unit": "Tlane-op/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel_ms"] = t_kernel * 1e3
+    roof["t_roof_ms"] = {k: v * 1e3 for k, v in cands.items()}
+    roof["peak_source"] = "gp_probe_pipes (FADD / MUFU.EX2 chains on all SMs, this run)"
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Pagie-1 / program populations)",
+            "config": {"workload": wl.name, "n_rows": N, "n_feat": d.n_feat, "n_progs": P,
+                       "metric": wl.metric, "tourn_size": wl.tourn_size,
+                       "mean_nodes": n_nodes / P, "function_nodes": n_fn, "sfu_nodes": n_sfu,
+                       "l2": "inputs larger than L2" if N * 4 * (d.n_feat + 1) > 129e6 else "L2-resident inputs",
+                       "parallelism": f"islands x{ws}" if ws > 1 else "single GPU",
+                       "opts": None if tuned is None else {"rows_per_thread": tuned.rows_per_thread,
+                                                           "chunk_rows": tuned.chunk_rows,
+                                                           "blocks_per_sm": tuned.blocks_per_sm}},
+            "node_evals_per_s": value * (n_nodes / P),
+            "finite_fitness_frac": fin,
+            "clocks": clocks,
+            # per step: compile, order, weight sum (+1 with weights), two
+            # evaluator launches (depth classes), finalize, tournament
+            "gpu_launches": (7 + (d.w is not None)) * args.steps,
+            "roofline": roof,
+            "pipes": pipes}
+
+    if rank == 0 and not args.no_plain:
+        gp.gp_evaluate_plain(pn, po, dX, dy, dw, metric=wl.metric, out=fit)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        gp.gp_evaluate_plain(pn, po, dX, dy, dw, metric=wl.metric, out=fit)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        line["plain"] = {"value": rows_evals / (pms * 1e-3), "unit": UNIT, "ms_per_eval": pms,
+                         "launches": P + 3}
+        line["batched_over_plain"] = value / ws / line["plain"]["value"]
+
+    if rank == 0 and not args.no_e2e:
+        hn = wl.nodes
+        ho = wl.offsets
+        hX = torch.from_numpy(d.X).pin_memory().numpy()
+        hy = torch.from_numpy(d.y).pin_memory().numpy()
+        hw = None if d.w is None else torch.from_numpy(d.w).pin_memory().numpy()
+        hfit = torch.empty(P, dtype=torch.float32).pin_memory().numpy()
+        hwin = torch.empty(P, dtype=torch.int32).pin_memory()
+        fit_d = torch.empty(P, dtype=torch.float32, device=dev)
+
+        def e2e_step(seed):
+            gp.gp_evaluate_host(hn, ho, hX, hy, hw, metric=wl.metric, out=hfit)
+            fit_d.copy_(torch.from_numpy(hfit), non_blocking=True)
+            gp.gp_tournament_ex(fit_d, P, wl.tourn_size, seed, out=win)
+            hwin.copy_(win, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        e2e_step(1)
+        t0 = time.perf_counter()
+        ksteps = max(1, min(args.steps, 3))
+        for s in range(ksteps):
+            e2e_step(2 + s)
+        dt = time.perf_counter() - t0
+        h2d = hn.nbytes + ho.nbytes + hX.nbytes + hy.nbytes + (0 if hw is None else hw.nbytes) + hfit.nbytes
+        d2h = hfit.nbytes + P * 4
+        line["e2e"] = {"value": rows_evals * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h), "steps": ksteps,
+                       "api": "gp_evaluate_host + gp_tournament_ex (host buffers, pinned)"}
+
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,277 @@
+/*
+ * gp.h -- C ABI of libgp: batched fitness evaluation and selection for
+ * stack-based genetic programming on one GB300 GPU (sm_103a).
+ *
+ * The method is that of Sathia, Ganesh and Nanditale, "Accelerating Genetic
+ * Programming using GPUs" (arXiv 2110.11226):
+ *   - a program is a prefix (Polish) list of nodes evaluated with a stack
+ *     by scanning the list in reverse (Sec. III-A);
+ *   - every program is evaluated on every row of a column-major dataset
+ *     that already resides in GPU memory (Sec. III, III-C3);
+ *   - a weighted loss per row is reduced to one raw fitness per program
+ *     (Sec. III-C3);
+ *   - tournament selection draws k programs per tournament with Philox and
+ *     keeps the best adjusted fitness, adjusted = raw + c * len
+ *     (Sec. III-C1, Eqs. parsimony and fitness).
+ * The constant-gradient and Adam entry points have no counterpart in the
+ * paper; they tune the ephemeral constants of the programs.
+ *
+ * Conventions for every entry point:
+ *   - Pointers are device pointers unless the comment says "host"; they are
+ *     owned by the caller and never freed or retained by the library.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; nothing synchronises
+ *     unless the comment says so.
+ *   - The return value is GP_OK (0) or a negative gp_status.  Argument
+ *     errors are returned before anything is launched.  Problems found on
+ *     the device (a malformed program) never trap: they set bits of a
+ *     device status word (gp_last_device_status) and NaN results.
+ *   - Floating point: evaluation in FP32 (IEEE +,-,*,/ and sqrt, CUDA's
+ *     accurate libm functions, no contraction into FMA); the cross-block
+ *     fitness sum in FP64.
+ */
+#ifndef GP_H_
+#define GP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GP_MAX_STACK 20   /* stack slots: a program must never hold more    */
+#define GP_MAX_LEN 255    /* nodes per program                              */
+#define GP_MAX_CONSTS 16  /* constants per program for gp_const_grad        */
+
+/* One node of a prefix list (8 bytes).  VAR reads column `feat` of X;
+ * CONST pushes `c`; functions ignore feat and c. */
+typedef struct gp_node {
+    int16_t op;
+    int16_t feat;
+    float c;
+} gp_node;
+
+/* Function set: arity <= 2 (Sec. III).  Binary functions take the first
+ * value popped in the reverse scan as their LEFT operand, so the prefix
+ * list [SUB, x0, x1] computes x0 - x1.  Protected operators use the
+ * threshold 0.001f with the strict test |v| < 0.001f:
+ *   DIV(a,b) = 1 on the protected branch, INV(a) = 0, LOG(a) = 0,
+ *   otherwise a/b, 1/a, log|a|; SQRT(a) = sqrt|a|. */
+enum gp_op {
+    GP_CONST = 0, GP_VAR = 1,
+    GP_ADD = 2, GP_SUB = 3, GP_MUL = 4, GP_DIV = 5,
+    GP_SQRT = 6, GP_LOG = 7, GP_EXP = 8, GP_SIN = 9, GP_COS = 10,
+    GP_TAN = 11, GP_ABS = 12, GP_NEG = 13, GP_INV = 14,
+    GP_NUM_OPS = 15
+};
+
+/* Fitness metrics (Sec. III-C3), weighted means over the rows:
+ *   MAE  = sum w|p-y| / sum w          MSE = sum w (p-y)^2 / sum w
+ *   RMSE = sqrt(MSE)                   LOGLOSS = sum w l(p,y) / sum w
+ * with l(p,y) = c|p| + log1p(exp(-|p|)), c = 1-y if p >= 0 else y (the
+ * logistic loss of sigmoid(p) against a label y in {0,1}; the c|p| term
+ * is 0 when c == 0).  All four are smaller-is-better. */
+enum gp_metric { GP_MAE = 0, GP_MSE = 1, GP_RMSE = 2, GP_LOGLOSS = 3 };
+
+enum gp_status {
+    GP_OK = 0,
+    GP_ERR_ARG = -1,       /* bad argument (NULL, size, metric, opts)     */
+    GP_ERR_PROGRAM = -2,   /* malformed program (host-side validation)    */
+    GP_ERR_CONSTS = -3,    /* more than GP_MAX_CONSTS constants           */
+    GP_ERR_CUDA = -4,      /* a CUDA runtime call failed                  */
+    GP_ERR_TIMEOUT = -5,   /* a bounded device loop hit its cap           */
+    GP_ERR_NOMEM = -6,     /* device allocation failed                    */
+    GP_ERR_WORKSPACE = -7  /* caller workspace too small or misaligned    */
+};
+
+/* Per-program status written by the validator (device pre-pass and
+ * gp_validate_host). */
+enum gp_prog_status {
+    GP_PROG_OK = 0, GP_PROG_BAD_LENGTH = 1, GP_PROG_BAD_OP = 2,
+    GP_PROG_BAD_FEATURE = 3, GP_PROG_UNDERFLOW = 4, GP_PROG_LEFTOVER = 5,
+    GP_PROG_TOO_DEEP = 6
+};
+
+/* Bits of the device status word. */
+#define GP_DEV_BAD_PROGRAM 0x1u      /* a program failed validation     */
+#define GP_DEV_TOO_MANY_CONSTS 0x2u  /* gp_const_grad: > 16 constants  */
+#define GP_DEV_QUEUE_CAP 0x4u        /* persistent work loop hit its cap */
+
+/* Cross-block accumulation of the fitness sums. */
+enum gp_accum { GP_ACCUM_FP64 = 0, GP_ACCUM_KAHAN32 = 1 };
+
+/* Tunables of the batched evaluator; zero means "choose".  The choice is
+ * the autotuned one for this problem shape when gp_autotune has run,
+ * otherwise a fixed default.  Results are bit-identical for every choice
+ * with the same chunk_rows (fixed reduction partition). */
+typedef struct gp_eval_opts {
+    int rows_per_thread;  /* 4 or 8                                       */
+    int chunk_rows;       /* rows per work item, multiple of 32*rpt       */
+    int blocks_per_sm;    /* resident blocks per SM of the persistent grid */
+    int accum;            /* gp_accum                                     */
+    int reserved[4];      /* must be 0                                    */
+} gp_eval_opts;
+
+/* ---- information ------------------------------------------------------- */
+const char *gp_version(void);
+const char *gp_status_string(int status);
+
+/* ---- evaluation ---------------------------------------------------------
+ * gp_evaluate: fitness of every program on rows [0, n_rows) (Sec. III-C3:
+ * execution step fused with the loss and the weighted column reduction, so
+ * the n_progs x n_rows prediction matrix is never stored).
+ *   progs       [offsets[n_progs]] nodes; program p is
+ *               progs[offsets[p] .. offsets[p+1]) in prefix order
+ *   offsets     [n_progs + 1] int32, offsets[0] = 0, non-decreasing
+ *   X           [n_feat][n_rows] float32, column-major (feature f's column
+ *               starts at X + f * n_rows)
+ *   y           [n_rows] float32 targets (labels 0/1 for GP_LOGLOSS)
+ *   w           [n_rows] float32 weights, or NULL for all ones
+ *   out_fitness [n_progs] float32; NaN for a malformed program
+ * Batched persistent evaluator: one device pre-pass validates and compiles
+ * all programs, sorts them by length, and one persistent launch works
+ * through (program, row-chunk) items.  Scratch comes from a library-owned
+ * per-device cache that grows on demand (cudaMalloc), so the first call at
+ * a new size allocates; use gp_evaluate_ex with a caller workspace to
+ * avoid that (e.g. under CUDA graph capture).  The same inputs give
+ * bit-identical fitness on every call. */
+int gp_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs,
+                const float *X, int64_t n_rows, int n_feat, const float *y,
+                const float *w, int metric, float *out_fitness, void *stream);
+
+/* As gp_evaluate, with explicit tunables, optional FP64 fitness
+ * (out_fitness64 [n_progs], may be NULL), optional per-program validator
+ * status (out_prog_status [n_progs], may be NULL) and a caller workspace
+ * `ws` of `ws_bytes` bytes (256-byte aligned, at least gp_workspace_size
+ * bytes; ws == NULL uses the library cache).  With a caller workspace the
+ * call performs no allocation and no synchronisation. */
+int gp_evaluate_ex(const gp_node *progs, const int32_t *offsets, int n_progs,
+                   const float *X, int64_t n_rows, int n_feat,
+                   const float *y, const float *w, int metric,
+                   const gp_eval_opts *opts, float *out_fitness,
+                   double *out_fitness64, int32_t *out_prog_status, void *ws,
+                   size_t ws_bytes, void *stream);
+
+/* Bytes of workspace gp_evaluate_ex needs for this shape and these opts. */
+size_t gp_workspace_size(int n_progs, int64_t n_rows, int n_feat,
+                         const gp_eval_opts *opts);
+
+/* Plain evaluator: one kernel launch per program, one row per thread in
+ * blocks of 256 rows, programs read node by node from global memory and a
+ * 20-slot stack held by predicated register selects (the shape of the
+ * paper's execution kernel, Sec. III-C3 and III-D1), loss fused, per-block
+ * partial sums reduced in FP64.  Same arguments and results as
+ * gp_evaluate (fitness equal within the FP32 summation order). */
+int gp_evaluate_plain(const gp_node *progs, const int32_t *offsets,
+                      int n_progs, const float *X, int64_t n_rows, int n_feat,
+                      const float *y, const float *w, int metric,
+                      float *out_fitness, void *stream);
+
+/* Predictions (debug / parity path): out_pred [n_progs][n_rows] float32,
+ * the value of program p on row i; NaN rows for a malformed program.  Uses
+ * the same interpreter as gp_evaluate. */
+int gp_predict(const gp_node *progs, const int32_t *offsets, int n_progs,
+               const float *X, int64_t n_rows, int n_feat, float *out_pred,
+               void *stream);
+
+/* End-to-end variant of gp_evaluate for HOST buffers: progs, offsets, X,
+ * y, w (may be NULL) and out_fitness are host pointers (pinned memory is
+ * fastest).  Validates the programs on the host first (GP_ERR_PROGRAM,
+ * nothing launched), copies the inputs to the device, evaluates, copies
+ * the fitness back and synchronises `stream` before returning. */
+int gp_evaluate_host(const gp_node *progs, const int32_t *offsets,
+                     int n_progs, const float *X, int64_t n_rows, int n_feat,
+                     const float *y, const float *w, int metric,
+                     float *out_fitness, void *stream);
+
+/* Host-side validation (no GPU needed).  progs/offsets are HOST pointers;
+ * out_status [n_progs] receives gp_prog_status codes and out_high_water
+ * [n_progs] (may be NULL) the largest stack height of the reverse scan
+ * (a stack of 20 evaluates it iff <= 20, Sec. III-C2).  Returns GP_OK if
+ * every program is valid, GP_ERR_PROGRAM otherwise, GP_ERR_ARG for bad
+ * offsets. */
+int gp_validate_host(const gp_node *progs, const int32_t *offsets,
+                     int n_progs, int n_feat, int32_t *out_status,
+                     int32_t *out_high_water);
+
+/* ---- selection ----------------------------------------------------------
+ * Tournament selection (Sec. III-C1): tournament t draws tourn_size program
+ * indices with replacement from Philox4x32-10 (Salmon et al. 2011, cited
+ * in Sec. III-B), key = (seed lo32, seed hi32), counter = (j / 4, t,
+ * offset lo32, offset hi32), word j % 4, index = (u * n_progs) >> 32; the
+ * winner is the draw with the strictly best adjusted fitness (ties: the
+ * earliest draw; NaN is the worst), adjusted = raw + parsimony * len when
+ * smaller is better, raw - parsimony * len otherwise (Eqs. parsimony,
+ * fitness).  len = offsets[p+1] - offsets[p]; offsets may be NULL (no
+ * penalty).  out_idx [n_tourn] int32.  One thread per tournament. */
+int gp_tournament_ex(const float *fitness, const int32_t *offsets,
+                     int n_progs, int n_tourn, int tourn_size,
+                     float parsimony, int greater_is_better, uint64_t seed,
+                     uint64_t offset, int32_t *out_idx, void *stream);
+
+/* Short form: n_tourn = n_progs, no parsimony, smaller is better, offset
+ * 0, legacy default stream. */
+int gp_tournament(const float *fitness, int n_progs, int tourn_size,
+                  uint64_t seed, int32_t *out_idx);
+
+/* ---- constant tuning (no counterpart in the paper) ----------------------
+ * Gradient of each program's fitness with respect to its ephemeral
+ * constants, by a reverse-mode adjoint sweep per row that recomputes the
+ * forward values instead of storing n_progs x n_rows x len of them.
+ * Constant k of program p is its k-th CONST node in prefix order;
+ * out_grad [n_progs][16] float32 (slots >= the program's constant count
+ * are 0), out_fitness [n_progs] (may be NULL).  Derivatives of protected
+ * operators are 0 on the protected branch; MAE uses sign(p - y) (0 at
+ * equality); RMSE = MSE gradient / (2 RMSE) (0 when RMSE == 0).  A program
+ * with more than 16 constants gets NaN gradients and sets
+ * GP_DEV_TOO_MANY_CONSTS.  Scratch as for gp_evaluate. */
+int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs,
+                  const float *X, int64_t n_rows, int n_feat, const float *y,
+                  const float *w, int metric, float *out_grad,
+                  float *out_fitness, void *stream);
+
+/* One Adam step (Kingma & Ba 2015) on the constants, in place in `progs`:
+ * with g = grad[p][k], m = beta1 m + (1-beta1) g, v = beta2 v + (1-beta2)
+ * g^2, c -= lr * (m / (1-beta1^step)) / (sqrt(v / (1-beta2^step)) + eps).
+ * m, v [n_progs][16] float32 state owned by the caller (zero before step
+ * 1).  step >= 1. */
+int gp_adam_step(gp_node *progs, const int32_t *offsets, int n_progs,
+                 const float *grad, float *m, float *v, int step, float lr,
+                 float beta1, float beta2, float eps, void *stream);
+
+/* ---- runtime --------------------------------------------------------------
+ * Synchronises `stream`, returns the device status bits accumulated since
+ * the last call into *flags and clears them. */
+int gp_last_device_status(void *stream, uint32_t *flags);
+
+/* Times the candidate tunables of the batched evaluator on these inputs
+ * (CUDA events on `stream`, synchronising) and remembers the fastest for
+ * this problem shape; writes it to *best (may be NULL).  Later calls with
+ * zero opts fields use it. */
+int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs,
+                const float *X, int64_t n_rows, int n_feat, const float *y,
+                const float *w, int metric, gp_eval_opts *best, void *stream);
+
+/* Measurement only: sustained issue rates of the FP32 pipe (FADD) and the
+ * special-function unit (ex2, rcp) over all SMs, in lane-operations per
+ * second, measured with CUDA events; out[0] = fp32, out[1] = mufu ex2,
+ * out[2] = mufu rcp, out[3] = SM count.  Synchronises. */
+int gp_probe_pipes(double *out, void *stream);
+
+/* Measurement only.  While enabled (on != 0), every batched evaluation
+ * records a CUDA event pair on its stream around the evaluator's persistent
+ * launches.  gp_timing_read waits for the recorded events, returns the sum
+ * of their elapsed times in *total_ms and their count in *n_calls, and
+ * forgets them.  Enabling or disabling also forgets them.  Do not enable
+ * it while capturing a CUDA graph. */
+int gp_timing_enable(int on);
+int gp_timing_read(double *total_ms, int *n_calls);
+
+/* Frees the library's cached device scratch on every device. */
+void gp_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H_ */

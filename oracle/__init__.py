@@ -95,7 +95,7 @@ def _load():
                                    C.c_uint64, C.c_uint64, P]
     lib.ora_count_consts.argtypes = [P, i32]
     lib.ora_const_grad.argtypes = [P, P, i32, P, i64, P, P, i32, i64, i64,
-                                   P, P, i32]
+                                   P, P, P, i32]
     lib.ora_adam.argtypes = [P, P, P, P, i64, i32, f64, f64, f64, f64]
     lib.ora_max_threads.restype = i32
     _lib = lib
@@ -252,9 +252,11 @@ def count_consts(prog) -> int:
 
 
 def const_grad(progs, offsets, X, y, w=None, metric="mse", row0=0,
-               n_eval=None, n_threads=0):
+               n_eval=None, n_threads=0, with_abs=False):
     """Reverse-mode gradient of fitness w.r.t. each program's constants
-    (constant k = k-th CONST node in prefix order).  Returns (grad [P,16], fit [P])."""
+    (constant k = k-th CONST node in prefix order).  Returns (grad [P,16],
+    fit [P]), plus gabs [P,16] (the same sums of absolute per-row
+    contributions) when with_abs."""
     lib = _load()
     progs, offsets = _progs(progs, offsets)
     X = _colmajor(X)
@@ -266,12 +268,13 @@ def const_grad(progs, offsets, X, y, w=None, metric="mse", row0=0,
     m = METRICS[metric] if isinstance(metric, str) else int(metric)
     g = np.empty((P, MAX_CONSTS), np.float64)
     f = np.empty(P, np.float64)
+    ga = np.empty((P, MAX_CONSTS), np.float64) if with_abs else None
     rc = lib.ora_const_grad(_ptr(progs), _ptr(offsets), P, _ptr(X), n_rows,
                             _ptr(y), _ptr(w), m, row0, n_eval, _ptr(g),
-                            _ptr(f), n_threads)
+                            _ptr(f), _ptr(ga), n_threads)
     if rc == -1:
         raise ValueError("oracle const_grad: bad metric or zero total weight")
-    return g, f
+    return (g, f, ga) if with_abs else (g, f)
 
 
 def adam(theta, g, m, v, step, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -580,13 +580,14 @@ int ora_count_consts(const ora_node *p, int len) {
     return n;
 }
 
-/* grad[p * 16 + k] = d fitness_p / d c_k, fit[p] = fitness_p.  Returns 0,
+/* grad[p * 16 + k] = d fitness_p / d c_k, fit[p] = fitness_p, gabs (may be
+ * NULL) = the same sum over rows taken of absolute values.  Returns 0,
  * -1 (bad metric / zero weight) or -2 (a program with more than 16
  * constants; its row of grad is NaN). */
 int ora_const_grad(const ora_node *progs, const int32_t *offsets,
                    int n_progs, const float *X, int64_t ld, const float *y,
                    const float *w, int metric, int64_t row0, int64_t n_eval,
-                   double *grad, double *fit, int n_threads) {
+                   double *grad, double *fit, double *gabs, int n_threads) {
     if (metric < ORA_MAE || metric > ORA_LOGLOSS) return -1;
     double sw = 0.0;
     for (int64_t i = 0; i < n_eval; ++i) sw += w ? (double)w[row0 + i] : 1.0;
@@ -599,9 +600,9 @@ int ora_const_grad(const ora_node *progs, const int32_t *offsets,
     for (int p = 0; p < n_progs; ++p) {
         const ora_node *prog = progs + offsets[p];
         int len = offsets[p + 1] - offsets[p];
-        double g[ORA_MAX_CONSTS];
+        double g[ORA_MAX_CONSTS], ga[ORA_MAX_CONSTS];
         int kslot[ORA_MAX_LEN];
-        for (int k = 0; k < ORA_MAX_CONSTS; ++k) g[k] = 0.0;
+        for (int k = 0; k < ORA_MAX_CONSTS; ++k) g[k] = ga[k] = 0.0;
         int nc = 0, bad = 0;
         if (len < 1 || len > ORA_MAX_LEN) bad = 1;
         for (int j = 0; j < len && !bad; ++j) {
@@ -648,7 +649,11 @@ int ora_const_grad(const ora_node *progs, const int32_t *offsets,
             for (int j = 0; j < len; ++j) {
                 int op = prog[j].op;
                 double aj = adj[j];
-                if (op == ORA_CONST) { g[kslot[j]] += aj; continue; }
+                if (op == ORA_CONST) {
+                    g[kslot[j]] += aj;
+                    ga[kslot[j]] += fabs(aj);
+                    continue;
+                }
                 if (op == ORA_VAR) continue;
                 double u = val[left[j]];
                 double du = 0.0, dv = 0.0;
@@ -677,7 +682,10 @@ int ora_const_grad(const ora_node *progs, const int32_t *offsets,
             }
         }
         if (bad) {
-            for (int k = 0; k < ORA_MAX_CONSTS; ++k) grad[p * ORA_MAX_CONSTS + k] = NAN;
+            for (int k = 0; k < ORA_MAX_CONSTS; ++k) {
+                grad[p * ORA_MAX_CONSTS + k] = NAN;
+                if (gabs) gabs[p * ORA_MAX_CONSTS + k] = NAN;
+            }
             if (fit) fit[p] = NAN;
             if (bad == 2) rc = -2;
             continue;
@@ -687,8 +695,12 @@ int ora_const_grad(const ora_node *progs, const int32_t *offsets,
             f = sqrt(f);
             scale = (f > 0.0) ? scale / (2.0 * f) : 0.0;
         }
-        for (int k = 0; k < ORA_MAX_CONSTS; ++k)
+        for (int k = 0; k < ORA_MAX_CONSTS; ++k) {
             grad[p * ORA_MAX_CONSTS + k] = (k < nc) ? g[k] * scale : 0.0;
+            /* sum of |per-row contributions|: the scale of the gradient's
+             * cancellation, used to state gradient tolerances */
+            if (gabs) gabs[p * ORA_MAX_CONSTS + k] = (k < nc) ? ga[k] * fabs(scale) : 0.0;
+        }
         if (fit) fit[p] = f;
     }
     return rc;

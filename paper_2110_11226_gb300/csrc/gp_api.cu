@@ -1,0 +1,671 @@
+// gp_api.cu -- the C ABI of libgp (include/gp.h): argument checks, the
+// per-device scratch cache, launch sequences, host-side validation, the
+// host-buffer end-to-end path and the autotuner.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "gp_internal.cuh"
+
+using namespace gpk;
+
+// Device status word: kernels OR problem bits into it; gp_last_device_status
+// reads and clears it.  Host code reaches it through cudaGetSymbolAddress.
+__device__ unsigned int g_gp_status_word;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+struct ShapeKey {
+    int n_progs;
+    int64_t n_rows;
+    int n_feat;
+    bool operator<(const ShapeKey &o) const {
+        return std::tie(n_progs, n_rows, n_feat) < std::tie(o.n_progs, o.n_rows, o.n_feat);
+    }
+};
+
+struct DevCtx {
+    bool init = false;
+    int sms = 0;
+    unsigned int *status = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    std::map<ShapeKey, gp_eval_opts> tuned;
+};
+
+std::mutex g_mu;
+DevCtx g_ctx[kMaxDevices];
+
+// measurement hook (gp_timing_enable / gp_timing_read)
+struct TimingState {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> live, pool;
+};
+TimingState g_timing;
+
+std::pair<cudaEvent_t, cudaEvent_t> timing_pair() {
+    std::lock_guard<std::mutex> g(g_mu);
+    std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+    if (!g_timing.pool.empty()) {
+        e = g_timing.pool.back();
+        g_timing.pool.pop_back();
+    } else {
+        cudaEventCreate(&e.first);
+        cudaEventCreate(&e.second);
+    }
+    g_timing.live.push_back(e);
+    return e;
+}
+
+int ctx_of_current(DevCtx **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GP_ERR_CUDA;
+    DevCtx &c = g_ctx[dev];
+    if (!c.init) {
+        if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return GP_ERR_CUDA;
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_gp_status_word) != cudaSuccess) return GP_ERR_CUDA;
+        c.status = static_cast<unsigned int *>(p);
+        c.init = true;
+    }
+    *out = &c;
+    return GP_OK;
+}
+
+// grow-only device buffer; the old one is freed (cudaFree synchronises)
+int grow(void **ptr, size_t *cap, size_t need) {
+    if (*cap >= need && *ptr) return GP_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    size_t want = std::max(need, (size_t)1 << 20);
+    if (cudaMalloc(ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return GP_ERR_NOMEM;
+    }
+    *cap = want;
+    return GP_OK;
+}
+
+inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
+#define GP_CUDA(x)                                    \
+    do {                                              \
+        if ((x) != cudaSuccess) {                     \
+            cudaGetLastError();                       \
+            return GP_ERR_CUDA;                       \
+        }                                             \
+    } while (0)
+
+int check_common(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                 int64_t n_rows, int n_feat) {
+    if (!progs || !offsets || !X) return GP_ERR_ARG;
+    if (n_progs < 1 || n_rows < 1 || n_feat < 1 || n_feat > 32767) return GP_ERR_ARG;
+    if (n_rows > ((int64_t)1 << 40)) return GP_ERR_ARG;
+    return GP_OK;
+}
+
+int check_metric(int metric) {
+    return (metric >= GP_MAE && metric <= GP_LOGLOSS) ? GP_OK : GP_ERR_ARG;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ---- tunables -----------------------------------------------------------
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int64_t default_chunk(int n_progs, int64_t n_rows, int sms) {
+    // enough items for dynamic balancing (about 16 per resident warp),
+    // chunks of at most 64K rows, multiples of 256 rows
+    const double items_wanted = 16.0 * sms * 24.0;
+    int64_t c = (int64_t)((double)n_rows * (double)n_progs / items_wanted);
+    c = std::max<int64_t>(c, 256);
+    c = std::min<int64_t>(c, 65536);
+    c = round_up(c, 256);
+    return std::min<int64_t>(c, round_up(n_rows, 256));
+}
+
+int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat, DevCtx *c,
+                 gp_eval_opts *out) {
+    gp_eval_opts o{};
+    if (in) o = *in;
+    for (int i = 0; i < 4; ++i)
+        if (o.reserved[i] != 0) return GP_ERR_ARG;
+    if (o.rows_per_thread == 0 || o.chunk_rows == 0 || o.blocks_per_sm == 0) {
+        std::lock_guard<std::mutex> g(g_mu);
+        auto it = c->tuned.find(ShapeKey{n_progs, n_rows, n_feat});
+        if (it != c->tuned.end()) {
+            if (o.rows_per_thread == 0) o.rows_per_thread = it->second.rows_per_thread;
+            if (o.chunk_rows == 0) o.chunk_rows = it->second.chunk_rows;
+            if (o.blocks_per_sm == 0) o.blocks_per_sm = it->second.blocks_per_sm;
+        }
+    }
+    if (o.rows_per_thread == 0) o.rows_per_thread = 4;
+    if (o.rows_per_thread != 4 && o.rows_per_thread != 8) return GP_ERR_ARG;
+    if (o.chunk_rows == 0) o.chunk_rows = (int)default_chunk(n_progs, n_rows, c->sms);
+    if (o.chunk_rows < 32 * o.rows_per_thread || o.chunk_rows % (32 * o.rows_per_thread) != 0)
+        return GP_ERR_ARG;
+    if (o.blocks_per_sm < 0 || o.blocks_per_sm > 32) return GP_ERR_ARG;
+    if (o.accum != GP_ACCUM_FP64 && o.accum != GP_ACCUM_KAHAN32) return GP_ERR_ARG;
+    *out = o;
+    return GP_OK;
+}
+
+int eval_info(int rpt, int fmode, int cls, int block, int *regs) {
+    if (rpt == 4) return fmode == 2 ? info_eval_r4_f2(cls, block, regs) : info_eval_r4_f0(cls, block, regs);
+    return fmode == 2 ? info_eval_r8_f2(cls, block, regs) : info_eval_r8_f0(cls, block, regs);
+}
+
+cudaError_t eval_launch(const EvalArgs &a, int rpt, int fmode, int grid, int block, cudaStream_t st) {
+    if (rpt == 4) return fmode == 2 ? launch_eval_r4_f2(a, grid, block, st) : launch_eval_r4_f0(a, grid, block, st);
+    return fmode == 2 ? launch_eval_r8_f2(a, grid, block, st) : launch_eval_r8_f0(a, grid, block, st);
+}
+
+struct Plan {
+    gp_eval_opts o;
+    int n_chunks;
+    Layout L;
+};
+
+int make_plan(const gp_eval_opts *opts, int n_progs, int64_t n_rows, int n_feat, DevCtx *c,
+              Plan *pl) {
+    int rc = resolve_opts(opts, n_progs, n_rows, n_feat, c, &pl->o);
+    if (rc) return rc;
+    pl->n_chunks = (int)((n_rows + pl->o.chunk_rows - 1) / pl->o.chunk_rows);
+    pl->L = make_layout(n_progs, pl->n_chunks, false);
+    return GP_OK;
+}
+
+// the batched evaluation sequence on a carved workspace
+int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                 int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
+                 const Plan &pl, const Workspace &W, DevCtx *c, float *out, double *out64,
+                 int32_t *out_status, cudaStream_t st) {
+    GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
+    CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
+                   nullptr, nullptr, nullptr, c->status, nullptr};
+    GP_CUDA(launch_compile(ca, st));
+    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
+    GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
+    const int fmode = (n_feat <= 2) ? 2 : 0;
+    const int rpt = pl.o.rows_per_thread;
+    const bool vec = aligned16(X) && aligned16(y) && (!w || aligned16(w)) && (n_rows % 4 == 0);
+    std::pair<cudaEvent_t, cudaEvent_t> tev{nullptr, nullptr};
+    if (g_timing.on) {
+        tev = timing_pair();
+        GP_CUDA(cudaEventRecord(tev.first, st));
+    }
+    for (int cls = 0; cls < kNumClasses; ++cls) {
+        EvalArgs ea{};
+        ea.code = W.code;
+        ea.meta = W.meta;
+        ea.order = W.order;
+        ea.class_count = W.class_count;
+        ea.cls = cls;
+        ea.X = X;
+        ea.ld = (fmode == 2) ? (n_feat == 2 ? n_rows : 0) : n_rows;
+        ea.n_rows = n_rows;
+        ea.y = y;
+        ea.w = w;
+        ea.n_progs = n_progs;
+        ea.metric = metric;
+        ea.chunk_rows = pl.o.chunk_rows;
+        ea.n_chunks = pl.n_chunks;
+        ea.counter = W.counters + cls;
+        ea.part = W.part;
+        ea.dev_status = c->status;
+        ea.vec_ok = vec ? 1 : 0;
+        const int block = kEvalBlockThreads;
+        int occ = eval_info(rpt, fmode, cls, block, nullptr);
+        if (occ < 1) occ = 1;
+        int bps = pl.o.blocks_per_sm > 0 ? std::min(pl.o.blocks_per_sm, occ) : occ;
+        GP_CUDA(eval_launch(ea, rpt, fmode, c->sms * bps, block, st));
+    }
+    if (tev.second) GP_CUDA(cudaEventRecord(tev.second, st));
+    FinalizeArgs fa{W.part, pl.n_chunks, n_progs, W.meta, W.sumw, metric, pl.o.accum,
+                    out, out64, out_status};
+    GP_CUDA(launch_finalize(fa, st));
+    return GP_OK;
+}
+
+int validate_one_host(const gp_node *p, int len, int n_feat, int *hw_out) {
+    int sp = 0, hw = 0;
+    *hw_out = 0;
+    if (len < 1 || len > GP_MAX_LEN) return GP_PROG_BAD_LENGTH;
+    for (int j = len - 1; j >= 0; --j) {
+        const int op = p[j].op;
+        int ar;
+        if (op == GP_CONST || op == GP_VAR) ar = 0;
+        else if (op >= GP_ADD && op <= GP_DIV) ar = 2;
+        else if (op >= GP_SQRT && op <= GP_INV) ar = 1;
+        else return GP_PROG_BAD_OP;
+        if (op == GP_VAR && (p[j].feat < 0 || p[j].feat >= n_feat)) return GP_PROG_BAD_FEATURE;
+        if (ar == 0) ++sp;
+        else {
+            if (sp < ar) return GP_PROG_UNDERFLOW;
+            sp -= ar - 1;
+        }
+        hw = std::max(hw, sp);
+    }
+    *hw_out = hw;
+    if (sp != 1) return GP_PROG_LEFTOVER;
+    if (hw > GP_MAX_STACK) return GP_PROG_TOO_DEEP;
+    return GP_PROG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gp_version(void) { return "libgp 1.0 (sm_103a)"; }
+
+const char *gp_status_string(int s) {
+    switch (s) {
+    case GP_OK: return "ok";
+    case GP_ERR_ARG: return "bad argument";
+    case GP_ERR_PROGRAM: return "malformed program";
+    case GP_ERR_CONSTS: return "more than 16 constants in a program";
+    case GP_ERR_CUDA: return "CUDA runtime error";
+    case GP_ERR_TIMEOUT: return "device loop cap reached";
+    case GP_ERR_NOMEM: return "device allocation failed";
+    case GP_ERR_WORKSPACE: return "workspace too small or misaligned";
+    }
+    return "unknown status";
+}
+
+size_t gp_workspace_size(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts *opts) {
+    if (n_progs < 1 || n_rows < 1 || n_feat < 1) return 0;
+    DevCtx *c = nullptr;
+    if (ctx_of_current(&c)) return 0;
+    Plan pl;
+    if (make_plan(opts, n_progs, n_rows, n_feat, c, &pl)) return 0;
+    return pl.L.total;
+}
+
+int gp_evaluate_ex(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                   int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
+                   const gp_eval_opts *opts, float *out_fitness, double *out_fitness64,
+                   int32_t *out_prog_status, void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
+    if (rc) return rc;
+    if (!y || !out_fitness) return GP_ERR_ARG;
+    if ((rc = check_metric(metric))) return rc;
+    DevCtx *c = nullptr;
+    if ((rc = ctx_of_current(&c))) return rc;
+    Plan pl;
+    if ((rc = make_plan(opts, n_progs, n_rows, n_feat, c, &pl))) return rc;
+    void *base = ws;
+    if (ws) {
+        if (ws_bytes < pl.L.total || ((uintptr_t)ws & 255u)) return GP_ERR_WORKSPACE;
+    } else {
+        std::lock_guard<std::mutex> g(g_mu);
+        if ((rc = grow(&c->ws, &c->ws_bytes, pl.L.total))) return rc;
+        base = c->ws;
+    }
+    Workspace W = carve(base, pl.L, false);
+    return run_evaluate(progs, offsets, n_progs, X, n_rows, n_feat, y, w, metric, pl, W, c,
+                        out_fitness, out_fitness64, out_prog_status, S(stream));
+}
+
+int gp_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
+                float *out_fitness, void *stream) {
+    return gp_evaluate_ex(progs, offsets, n_progs, X, n_rows, n_feat, y, w, metric, nullptr,
+                          out_fitness, nullptr, nullptr, nullptr, 0, stream);
+}
+
+int gp_evaluate_plain(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                      int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
+                      float *out_fitness, void *stream) {
+    int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
+    if (rc) return rc;
+    if (!y || !out_fitness) return GP_ERR_ARG;
+    if ((rc = check_metric(metric))) return rc;
+    DevCtx *c = nullptr;
+    if ((rc = ctx_of_current(&c))) return rc;
+    const int64_t nb64 = (n_rows + 255) / 256;
+    if (nb64 > (1 << 30)) return GP_ERR_ARG;
+    const int n_blocks = (int)nb64;
+    Layout L = make_layout(n_progs, n_blocks, false);
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        if ((rc = grow(&c->ws, &c->ws_bytes, L.total))) return rc;
+    }
+    Workspace W = carve(c->ws, L, false);
+    cudaStream_t st = S(stream);
+    CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
+                   nullptr, nullptr, nullptr, c->status, nullptr};
+    GP_CUDA(launch_compile(ca, st));
+    GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
+    PlainArgs pa{progs, offsets, W.meta, X, n_rows, n_rows, y, w, metric, n_blocks, W.part};
+    for (int p = 0; p < n_progs; ++p) GP_CUDA(launch_plain(pa, p, st));
+    FinalizeArgs fa{W.part, n_blocks, n_progs, W.meta, W.sumw, metric, GP_ACCUM_FP64,
+                    out_fitness, nullptr, nullptr};
+    GP_CUDA(launch_finalize(fa, st));
+    return GP_OK;
+}
+
+int gp_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+               int64_t n_rows, int n_feat, float *out_pred, void *stream) {
+    int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
+    if (rc) return rc;
+    if (!out_pred) return GP_ERR_ARG;
+    DevCtx *c = nullptr;
+    if ((rc = ctx_of_current(&c))) return rc;
+    const int64_t chunk = std::min<int64_t>(round_up(n_rows, 128), 4096);
+    const int n_chunks = (int)((n_rows + chunk - 1) / chunk);
+    Layout L = make_layout(n_progs, 1, false);
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        if ((rc = grow(&c->ws, &c->ws_bytes, L.total))) return rc;
+    }
+    Workspace W = carve(c->ws, L, false);
+    cudaStream_t st = S(stream);
+    GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
+    CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
+                   nullptr, nullptr, nullptr, c->status, nullptr};
+    GP_CUDA(launch_compile(ca, st));
+    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
+    const bool vec = aligned16(X) && (n_rows % 4 == 0);
+    for (int cls = 0; cls < kNumClasses; ++cls) {
+        EvalArgs ea{};
+        ea.code = W.code;
+        ea.meta = W.meta;
+        ea.order = W.order;
+        ea.class_count = W.class_count;
+        ea.cls = cls;
+        ea.X = X;
+        ea.ld = n_rows;
+        ea.n_rows = n_rows;
+        ea.n_progs = n_progs;
+        ea.metric = GP_MSE;
+        ea.chunk_rows = chunk;
+        ea.n_chunks = n_chunks;
+        ea.counter = W.counters + cls;
+        ea.pred = out_pred;
+        ea.dev_status = c->status;
+        ea.vec_ok = vec ? 1 : 0;
+        int occ = info_predict(kEvalBlockThreads, nullptr);
+        GP_CUDA(launch_predict(ea, c->sms * std::max(occ, 1), kEvalBlockThreads, st));
+    }
+    return GP_OK;
+}
+
+int gp_validate_host(const gp_node *progs, const int32_t *offsets, int n_progs, int n_feat,
+                     int32_t *out_status, int32_t *out_high_water) {
+    if (!progs || !offsets || !out_status || n_progs < 1 || n_feat < 1) return GP_ERR_ARG;
+    if (offsets[0] != 0) return GP_ERR_ARG;
+    int rc = GP_OK;
+    for (int p = 0; p < n_progs; ++p) {
+        const int len = offsets[p + 1] - offsets[p];
+        int hw = 0;
+        const int s = (len < 0) ? GP_PROG_BAD_LENGTH : validate_one_host(progs + offsets[p], len, n_feat, &hw);
+        out_status[p] = s;
+        if (out_high_water) out_high_water[p] = hw;
+        if (s != GP_PROG_OK) rc = GP_ERR_PROGRAM;
+        if (len < 0) return GP_ERR_ARG;
+    }
+    return rc;
+}
+
+int gp_evaluate_host(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                     int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
+                     float *out_fitness, void *stream) {
+    int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
+    if (rc) return rc;
+    if (!y || !out_fitness) return GP_ERR_ARG;
+    if ((rc = check_metric(metric))) return rc;
+    if (offsets[0] != 0) return GP_ERR_ARG;
+    for (int p = 0; p < n_progs; ++p) {
+        int hw = 0;
+        const int len = offsets[p + 1] - offsets[p];
+        if (len < 0) return GP_ERR_ARG;
+        if (validate_one_host(progs + offsets[p], len, n_feat, &hw) != GP_PROG_OK) return GP_ERR_PROGRAM;
+    }
+    DevCtx *c = nullptr;
+    if ((rc = ctx_of_current(&c))) return rc;
+    const size_t n_nodes = (size_t)offsets[n_progs];
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t b_nodes = al(n_nodes * sizeof(gp_node) + 8);
+    const size_t b_off = al((size_t)(n_progs + 1) * sizeof(int32_t));
+    const size_t b_X = al((size_t)n_feat * (size_t)n_rows * sizeof(float));
+    const size_t b_y = al((size_t)n_rows * sizeof(float));
+    const size_t b_w = w ? b_y : 0;
+    const size_t b_out = al((size_t)n_progs * sizeof(float));
+    const size_t need = b_nodes + b_off + b_X + b_y + b_w + b_out;
+    char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        if ((rc = grow(&c->stage, &c->stage_bytes, need))) return rc;
+        base = static_cast<char *>(c->stage);
+    }
+    gp_node *d_nodes = reinterpret_cast<gp_node *>(base);
+    int32_t *d_off = reinterpret_cast<int32_t *>(base + b_nodes);
+    float *d_X = reinterpret_cast<float *>(base + b_nodes + b_off);
+    float *d_y = reinterpret_cast<float *>(base + b_nodes + b_off + b_X);
+    float *d_w = w ? reinterpret_cast<float *>(base + b_nodes + b_off + b_X + b_y) : nullptr;
+    float *d_out = reinterpret_cast<float *>(base + b_nodes + b_off + b_X + b_y + b_w);
+    cudaStream_t st = S(stream);
+    GP_CUDA(cudaMemcpyAsync(d_nodes, progs, n_nodes * sizeof(gp_node), cudaMemcpyHostToDevice, st));
+    GP_CUDA(cudaMemcpyAsync(d_off, offsets, (size_t)(n_progs + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    GP_CUDA(cudaMemcpyAsync(d_X, X, (size_t)n_feat * n_rows * sizeof(float), cudaMemcpyHostToDevice, st));
+    GP_CUDA(cudaMemcpyAsync(d_y, y, (size_t)n_rows * sizeof(float), cudaMemcpyHostToDevice, st));
+    if (w) GP_CUDA(cudaMemcpyAsync(d_w, w, (size_t)n_rows * sizeof(float), cudaMemcpyHostToDevice, st));
+    rc = gp_evaluate(d_nodes, d_off, n_progs, d_X, n_rows, n_feat, d_y, d_w, metric, d_out, stream);
+    if (rc) return rc;
+    GP_CUDA(cudaMemcpyAsync(out_fitness, d_out, (size_t)n_progs * sizeof(float), cudaMemcpyDeviceToHost, st));
+    GP_CUDA(cudaStreamSynchronize(st));
+    return GP_OK;
+}
+
+int gp_tournament_ex(const float *fitness, const int32_t *offsets, int n_progs, int n_tourn,
+                     int tourn_size, float parsimony, int greater_is_better, uint64_t seed,
+                     uint64_t offset, int32_t *out_idx, void *stream) {
+    if (!fitness || !out_idx || n_progs < 1 || n_tourn < 0 || tourn_size < 1) return GP_ERR_ARG;
+    TournArgs a{fitness, offsets, n_progs, n_tourn, tourn_size, parsimony,
+                greater_is_better ? 1 : 0, seed, offset, out_idx};
+    GP_CUDA(launch_tournament(a, S(stream)));
+    return GP_OK;
+}
+
+int gp_tournament(const float *fitness, int n_progs, int tourn_size, uint64_t seed, int32_t *out_idx) {
+    return gp_tournament_ex(fitness, nullptr, n_progs, n_progs, tourn_size, 0.0f, 0, seed, 0,
+                            out_idx, nullptr);
+}
+
+int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                  int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
+                  float *out_grad, float *out_fitness, void *stream) {
+    int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
+    if (rc) return rc;
+    if (!y || !out_grad) return GP_ERR_ARG;
+    if ((rc = check_metric(metric))) return rc;
+    DevCtx *c = nullptr;
+    if ((rc = ctx_of_current(&c))) return rc;
+    const int64_t chunk = default_chunk(n_progs, n_rows, c->sms);
+    const int n_chunks = (int)((n_rows + chunk - 1) / chunk);
+    Layout L = make_layout(n_progs, n_chunks, true);
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        if ((rc = grow(&c->ws, &c->ws_bytes, L.total))) return rc;
+    }
+    Workspace W = carve(c->ws, L, true);
+    cudaStream_t st = S(stream);
+    GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
+    CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
+                   W.rchild, W.kslot, W.cnode, c->status, nullptr};
+    GP_CUDA(launch_compile(ca, st));
+    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
+    GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
+    GradArgs ga{progs, offsets, W.meta, W.order, W.rchild, W.kslot, X, n_rows, n_rows, y, w,
+                n_progs, metric, chunk, n_chunks, W.counters, W.part, W.gpart, c->status};
+    GP_CUDA(launch_grad(ga, c->sms * 4, 128, st));
+    GradFinalizeArgs fa{W.part, W.gpart, n_chunks, n_progs, W.meta, W.sumw, metric,
+                        out_grad, out_fitness};
+    GP_CUDA(launch_grad_finalize(fa, st));
+    return GP_OK;
+}
+
+int gp_adam_step(gp_node *progs, const int32_t *offsets, int n_progs, const float *grad, float *m,
+                 float *v, int step, float lr, float beta1, float beta2, float eps, void *stream) {
+    if (!progs || !offsets || !grad || !m || !v || n_progs < 1 || step < 1) return GP_ERR_ARG;
+    if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f))
+        return GP_ERR_ARG;
+    AdamArgs a{progs, offsets, nullptr, nullptr, n_progs, grad, m, v, step, lr, beta1, beta2, eps};
+    GP_CUDA(launch_adam(a, S(stream)));
+    return GP_OK;
+}
+
+int gp_last_device_status(void *stream, uint32_t *flags) {
+    if (!flags) return GP_ERR_ARG;
+    DevCtx *c = nullptr;
+    int rc = ctx_of_current(&c);
+    if (rc) return rc;
+    GP_CUDA(cudaStreamSynchronize(S(stream)));
+    unsigned int v = 0;
+    GP_CUDA(cudaMemcpy(&v, c->status, sizeof(v), cudaMemcpyDeviceToHost));
+    GP_CUDA(cudaMemset(c->status, 0, sizeof(v)));
+    *flags = v;
+    return GP_OK;
+}
+
+int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
+                gp_eval_opts *best, void *stream) {
+    int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
+    if (rc) return rc;
+    if (!y) return GP_ERR_ARG;
+    if ((rc = check_metric(metric))) return rc;
+    DevCtx *c = nullptr;
+    if ((rc = ctx_of_current(&c))) return rc;
+    cudaStream_t st = S(stream);
+    float *out = nullptr;
+    GP_CUDA(cudaMalloc(&out, (size_t)n_progs * sizeof(float)));
+    const int64_t base_chunk = default_chunk(n_progs, n_rows, c->sms);
+    std::vector<gp_eval_opts> cands;
+    const int fmode = (n_feat <= 2) ? 2 : 0;
+    for (int rpt : {4, 8}) {
+        const int occ = eval_info(rpt, fmode, 0, kEvalBlockThreads, nullptr);
+        for (int64_t ch : {base_chunk, base_chunk * 2, std::max<int64_t>(base_chunk / 2, 256)}) {
+            const int64_t chr = round_up(std::min<int64_t>(ch, 65536), 256);
+            for (int bps = 1; bps <= std::max(occ, 1); ++bps) {
+                gp_eval_opts o{};
+                o.rows_per_thread = rpt;
+                o.chunk_rows = (int)chr;
+                o.blocks_per_sm = bps;
+                cands.push_back(o);
+            }
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    gp_eval_opts best_o = cands.front();
+    for (const gp_eval_opts &o : cands) {
+        // one warm-up, then the time of one call
+        rc = gp_evaluate_ex(progs, offsets, n_progs, X, n_rows, n_feat, y, w, metric, &o, out,
+                            nullptr, nullptr, nullptr, 0, stream);
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        rc = gp_evaluate_ex(progs, offsets, n_progs, X, n_rows, n_feat, y, w, metric, &o, out,
+                            nullptr, nullptr, nullptr, 0, stream);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = GP_ERR_CUDA;
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_o = o;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        c->tuned[ShapeKey{n_progs, n_rows, n_feat}] = best_o;
+    }
+    if (best) *best = best_o;
+    return GP_OK;
+}
+
+int gp_probe_pipes(double *out, void *stream) {
+    if (!out) return GP_ERR_ARG;
+    GP_CUDA(probe_pipes(out, S(stream)));
+    return GP_OK;
+}
+
+int gp_timing_enable(int on) {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> drop;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        g_timing.on = on != 0;
+        drop.swap(g_timing.live);
+    }
+    for (auto &e : drop) cudaEventSynchronize(e.second);
+    std::lock_guard<std::mutex> g(g_mu);
+    for (auto &e : drop) g_timing.pool.push_back(e);
+    return GP_OK;
+}
+
+int gp_timing_read(double *total_ms, int *n_calls) {
+    if (!total_ms) return GP_ERR_ARG;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> live;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        live.swap(g_timing.live);
+    }
+    double sum = 0.0;
+    int rc = GP_OK;
+    for (auto &e : live) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e.second) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e.first, e.second) != cudaSuccess) {
+            cudaGetLastError();
+            rc = GP_ERR_CUDA;
+        }
+        sum += ms;
+    }
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        for (auto &e : live) g_timing.pool.push_back(e);
+    }
+    *total_ms = sum;
+    if (n_calls) *n_calls = (int)live.size();
+    return rc;
+}
+
+void gp_shutdown(void) {
+    std::lock_guard<std::mutex> g(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < kMaxDevices; ++d) {
+        DevCtx &c = g_ctx[d];
+        if (!c.init) continue;
+        cudaSetDevice(d);
+        if (c.ws) cudaFree(c.ws);
+        if (c.stage) cudaFree(c.stage);
+        c.ws = c.stage = nullptr;
+        c.ws_bytes = c.stage_bytes = 0;
+        c.tuned.clear();
+    }
+    cudaSetDevice(cur);
+}
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+// gp_compile.cu -- device pre-pass: validate each prefix list, compile it
+// to the register-stack form (gp_internal.cuh), and sort the programs into
+// depth classes and by length (length-bucketed work queue); plus the
+// deterministic total-weight sum.
+#include "gp_internal.cuh"
+
+namespace gpk {
+
+static __host__ __device__ inline int op_arity(int op) {
+    if (op == GP_CONST || op == GP_VAR) return 0;
+    if (op >= GP_ADD && op <= GP_DIV) return 2;
+    if (op >= GP_SQRT && op <= GP_INV) return 1;
+    return -1;
+}
+
+static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(int n_progs, int n_chunks, bool grad) {
+    Layout L{};
+    size_t o = 0;
+    size_t P = (size_t)(n_progs > 0 ? n_progs : 1);
+    size_t C = (size_t)(n_chunks > 0 ? n_chunks : 1);
+    L.counters = o;    o = align256(o + 8 * sizeof(unsigned long long));
+    L.sumw = o;        o = align256(o + sizeof(double));
+    L.sumw_part = o;   o = align256(o + kSumwBlocks * sizeof(double));
+    L.code = o;        o = align256(o + P * kCodeStride * sizeof(uint2));
+    L.meta = o;        o = align256(o + P * sizeof(ProgMeta));
+    L.order = o;       o = align256(o + P * sizeof(int32_t));
+    L.class_count = o; o = align256(o + (kNumClasses + 2) * sizeof(int32_t));
+    L.part = o;        o = align256(o + P * C * sizeof(float));
+    if (grad) {
+        L.rchild = o;  o = align256(o + P * kCodeStride);
+        L.kslot = o;   o = align256(o + P * kCodeStride);
+        L.cnode = o;   o = align256(o + P * GP_MAX_CONSTS * sizeof(int16_t));
+        L.gpart = o;   o = align256(o + P * C * GP_MAX_CONSTS * sizeof(float));
+    }
+    L.total = o;
+    return L;
+}
+
+Workspace carve(void *base, const Layout &L, bool grad) {
+    char *b = static_cast<char *>(base);
+    Workspace w{};
+    w.counters = reinterpret_cast<unsigned long long *>(b + L.counters);
+    w.sumw = reinterpret_cast<double *>(b + L.sumw);
+    w.sumw_part = reinterpret_cast<double *>(b + L.sumw_part);
+    w.code = reinterpret_cast<uint2 *>(b + L.code);
+    w.meta = reinterpret_cast<ProgMeta *>(b + L.meta);
+    w.order = reinterpret_cast<int32_t *>(b + L.order);
+    w.class_count = reinterpret_cast<int32_t *>(b + L.class_count);
+    w.part = reinterpret_cast<float *>(b + L.part);
+    if (grad) {
+        w.rchild = reinterpret_cast<uint8_t *>(b + L.rchild);
+        w.kslot = reinterpret_cast<int8_t *>(b + L.kslot);
+        w.cnode = reinterpret_cast<int16_t *>(b + L.cnode);
+        w.gpart = reinterpret_cast<float *>(b + L.gpart);
+    }
+    w.bytes = L.total;
+    return w;
+}
+
+// One thread per program.  Three passes over at most 255 nodes held in
+// per-thread local arrays: (1) reverse scan for validity and subtree sizes,
+// (2) mark terminal children that fold into their binary parent, (3)
+// reverse scan emitting instructions.
+__global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n_progs) return;
+    const int off = a.offsets[p];
+    const int len = a.offsets[p + 1] - off;
+    uint2 *out = a.code + (size_t)p * kCodeStride;
+    const gp_node *prog = a.progs + off;
+
+    uint8_t size[GP_MAX_LEN];
+    uint8_t mode[GP_MAX_LEN];  // terminal: 1 = folded; binary: 0/1 R/2 L
+    int status = GP_PROG_OK;
+    int sp = 0, hw = 0, n_consts = 0;
+
+    if (len < 1 || len > GP_MAX_LEN) status = GP_PROG_BAD_LENGTH;
+    // pass 1: reverse scan with a stack of subtree sizes (kept in size[])
+    uint8_t szst[GP_MAX_LEN];
+    for (int j = len - 1; j >= 0 && status == GP_PROG_OK; --j) {
+        const gp_node nd = prog[j];
+        const int ar = op_arity(nd.op);
+        mode[j] = 0;
+        if (ar < 0) { status = GP_PROG_BAD_OP; break; }
+        if (nd.op == GP_VAR && (nd.feat < 0 || nd.feat >= a.n_feat)) {
+            status = GP_PROG_BAD_FEATURE;
+            break;
+        }
+        int s;
+        if (ar == 0) {
+            s = 1;
+            n_consts += (nd.op == GP_CONST);
+        } else if (ar == 1) {
+            if (sp < 1) { status = GP_PROG_UNDERFLOW; break; }
+            s = 1 + szst[--sp];
+        } else {
+            if (sp < 2) { status = GP_PROG_UNDERFLOW; break; }
+            const int l = szst[--sp];
+            const int r = szst[--sp];
+            s = 1 + l + r;
+        }
+        size[j] = (uint8_t)s;
+        szst[sp++] = (uint8_t)s;
+        if (sp > hw) hw = sp;
+    }
+    if (status == GP_PROG_OK && sp != 1) status = GP_PROG_LEFTOVER;
+    if (status == GP_PROG_OK && hw > GP_MAX_STACK) status = GP_PROG_TOO_DEEP;
+    if (a.out_prog_status) a.out_prog_status[p] = status;
+    if (status != GP_PROG_OK) {
+        out[0] = make_uint2(K_END, 0u);
+        a.meta[p] = ProgMeta{1, status, 0, 0};
+        atomicOr(a.dev_status, GP_DEV_BAD_PROGRAM);
+        return;
+    }
+
+    // pass 2: fold terminal children of binary nodes (prefer the right one)
+    for (int j = 0; j < len; ++j) {
+        const int op = prog[j].op;
+        if (op_arity(op) != 2) continue;
+        const int lc = j + 1, rc = j + 1 + size[j + 1];
+        if (op_arity(prog[rc].op) == 0) {
+            mode[rc] = 1;
+            mode[j] = 1;
+        } else if (op_arity(prog[lc].op) == 0) {
+            mode[lc] = 1;
+            mode[j] = 2;
+        }
+    }
+
+    // auxiliary tables for the adjoint (right child offset, constant slot)
+    if (a.rchild) {
+        uint8_t *rc = a.rchild + (size_t)p * kCodeStride;
+        int8_t *ks = a.kslot + (size_t)p * kCodeStride;
+        int16_t *cn = a.cnode + (size_t)p * GP_MAX_CONSTS;
+        int k = 0;
+        for (int j = 0; j < len; ++j) {
+            const int op = prog[j].op;
+            rc[j] = (op_arity(op) == 2) ? (uint8_t)(1 + size[j + 1]) : 0;
+            ks[j] = -1;
+            if (op == GP_CONST) {
+                if (k < GP_MAX_CONSTS) cn[k] = (int16_t)j;
+                ks[j] = (int8_t)(k < GP_MAX_CONSTS ? k : -1);
+                ++k;
+            }
+        }
+        for (; k < GP_MAX_CONSTS; ++k) cn[k] = -1;
+    }
+
+    // pass 3: emit in reverse-scan order
+    int n = 0, depth = 0;
+    sp = 0;
+    for (int j = len - 1; j >= 0; --j) {
+        const gp_node nd = prog[j];
+        const int ar = op_arity(nd.op);
+        if (ar == 0) {
+            if (mode[j]) continue;  // folded into its parent
+            const uint32_t id = (nd.op == GP_VAR) ? ((K_PUSH_X + sp) | kNeedsX) : (K_PUSH_C + sp);
+            out[n++] = make_uint2(id | ((uint32_t)(uint16_t)nd.feat << 16),
+                                  __float_as_uint(nd.c));
+            ++sp;
+        } else if (ar == 1) {
+            out[n++] = make_uint2(K_UN + (nd.op - GP_SQRT), 0u);
+        } else {
+            const uint32_t b = nd.op - GP_ADD;
+            if (mode[j] == 0) {
+                out[n++] = make_uint2(K_BIN + b * kDeepSlots + (sp - 2), 0u);
+                --sp;
+            } else {
+                const gp_node t = (mode[j] == 1) ? prog[j + 1 + size[j + 1]] : prog[j + 1];
+                uint32_t id;
+                if (mode[j] == 1) id = (t.op == GP_VAR ? (K_BIN_RX + b) | kNeedsX : K_BIN_RC + b);
+                else id = (t.op == GP_VAR ? (K_BIN_LX + b) | kNeedsX : K_BIN_LC + b);
+                out[n++] = make_uint2(id | ((uint32_t)(uint16_t)t.feat << 16),
+                                      __float_as_uint(t.c));
+            }
+        }
+        if (sp > depth) depth = sp;
+    }
+    out[n++] = make_uint2(K_END, 0u);
+    a.meta[p] = ProgMeta{n, GP_PROG_OK, depth, n_consts};
+}
+
+cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st) {
+    if (a.n_progs <= 0) return cudaSuccess;
+    const int block = 128;
+    const int grid = (a.n_progs + block - 1) / block;
+    compile_kernel<<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Counting sort of program ids: key = class * 256 + (256 - n_ins), so the
+// shallow class comes first and, inside a class, longer programs first
+// (longest-processing-time order for the dynamic work queue).  Invalid
+// programs (n_ins = 1) land at the end of the shallow class.  Order inside
+// one key is arbitrary; results do not depend on it.
+constexpr int kOrderBins = kNumClasses * 256;
+
+__global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n_progs,
+                                                     int32_t *order, int32_t *class_count) {
+    __shared__ int hist[kOrderBins];
+    __shared__ int cursor[kOrderBins];
+    for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < n_progs; p += blockDim.x) {
+        const ProgMeta m = meta[p];
+        const int cls = (m.depth <= kSmallDepth) ? 0 : 1;
+        const int key = cls * 256 + (256 - m.n_ins);
+        atomicAdd(&hist[key], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < kOrderBins; ++i) {
+            cursor[i] = run;
+            run += hist[i];
+            if (i == 255) class_count[0] = run;
+        }
+        class_count[1] = run - class_count[0];
+        class_count[2] = 0;
+        class_count[3] = 0;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < n_progs; p += blockDim.x) {
+        const ProgMeta m = meta[p];
+        const int cls = (m.depth <= kSmallDepth) ? 0 : 1;
+        const int key = cls * 256 + (256 - m.n_ins);
+        const int pos = atomicAdd(&cursor[key], 1);
+        order[pos] = p;
+    }
+}
+
+cudaError_t launch_order(const ProgMeta *meta, int n_progs, int32_t *order,
+                         int32_t *class_count, cudaStream_t st) {
+    order_kernel<<<1, 1024, 0, st>>>(meta, n_progs, order, class_count);
+    return cudaGetLastError();
+}
+
+// Total weight in FP64 with a fixed partition: block b sums rows
+// [b*span, (b+1)*span) with a fixed per-thread stride and a fixed tree, and
+// one warp then adds the block sums in order.  w == NULL gives n_rows.
+__global__ void __launch_bounds__(256) sumw_kernel(const float *__restrict__ w, int64_t n_rows,
+                                                   double *part) {
+    __shared__ double red[256];
+    const int64_t span = (n_rows + kSumwBlocks - 1) / kSumwBlocks;
+    const int64_t r0 = (int64_t)blockIdx.x * span;
+    const int64_t r1 = min(n_rows, r0 + span);
+    double s = 0.0;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) s += (double)w[r];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void sumw_final_kernel(const double *part, double *sumw, const float *w,
+                                  int64_t n_rows) {
+    if (threadIdx.x != 0) return;
+    if (w == nullptr) {
+        *sumw = (double)n_rows;
+        return;
+    }
+    double s = 0.0;
+    for (int i = 0; i < kSumwBlocks; ++i) s += part[i];
+    *sumw = s;
+}
+
+cudaError_t launch_sumw(const float *w, int64_t n_rows, double *part, double *sumw,
+                        cudaStream_t st) {
+    if (w) sumw_kernel<<<kSumwBlocks, 256, 0, st>>>(w, n_rows, part);
+    sumw_final_kernel<<<1, 32, 0, st>>>(part, sumw, w, n_rows);
+    return cudaGetLastError();
+}
+
+}  // namespace gpk

@@ -1,0 +1,15 @@
+// gp_eval_r8_f0.cu -- instance of the batched evaluator: 8 rows per
+// thread, feature mode 0 (feature columns loaded per reference),
+// both depth classes.
+#include "gp_interp.cuh"
+
+namespace gpk {
+cudaError_t launch_eval_r8_f0(const EvalArgs &a, int grid, int block, cudaStream_t st) {
+    if (a.cls == 0) return launch_eval_t<8, kSmallDepth - 1, 0, false>(a, grid, block, st);
+    return launch_eval_t<8, kDeepSlots, 0, false>(a, grid, block, st);
+}
+int info_eval_r8_f0(int cls, int block, int *regs) {
+    if (cls == 0) return info_t<8, kSmallDepth - 1, 0, false>(block, regs);
+    return info_t<8, kDeepSlots, 0, false>(block, regs);
+}
+}  // namespace gpk

@@ -1,0 +1,107 @@
+// gp_probe.cu -- measurement only: sustained lane-operation rates of the
+// FP32 pipe (dependent FADD chains) and the special-function unit (ex2 and
+// rcp approximations) over every SM, timed with CUDA events.  These give
+// the denominators of the ALU roofline of the evaluator.
+#include "gp_internal.cuh"
+
+namespace gpk {
+
+namespace {
+constexpr int kChains = 8;
+constexpr int kIters = 4096;
+constexpr int kBlock = 256;
+
+__global__ void __launch_bounds__(kBlock) fadd_probe(float *sink, float d) {
+    float x[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) x[i] = (float)(threadIdx.x + i);
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) x[i] = __fadd_rn(x[i], d);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) s += x[i];
+    if (s == 1234.5f) sink[0] = s;
+}
+
+__global__ void __launch_bounds__(kBlock) ex2_probe(float *sink) {
+    float x[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) x[i] = 0.25f + 0.01f * (float)i;
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) {
+            float y;
+            asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x[i]));
+            x[i] = y;
+        }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) s += x[i];
+    if (s == 1234.5f) sink[0] = s;
+}
+
+__global__ void __launch_bounds__(kBlock) rcp_probe(float *sink) {
+    float x[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) x[i] = 1.5f + 0.25f * (float)i;
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) {
+            float y;
+            asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[i]));
+            x[i] = y;
+        }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) s += x[i];
+    if (s == 1234.5f) sink[0] = s;
+}
+
+template <typename F>
+cudaError_t time_it(F launch, cudaStream_t st, double *ms) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return e;
+    launch();  // warm-up
+    cudaEventRecord(a, st);
+    for (int r = 0; r < 3; ++r) launch();
+    cudaEventRecord(b, st);
+    e = cudaEventSynchronize(b);
+    float f = 0.0f;
+    cudaEventElapsedTime(&f, a, b);
+    *ms = f / 3.0;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t probe_pipes(double *out, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    float *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(float));
+    if (e != cudaSuccess) return e;
+    const int grid = sms * 8;
+    const double lane_ops = (double)grid * kBlock * kIters * kChains;
+    double ms = 0.0;
+    e = time_it([&] { fadd_probe<<<grid, kBlock, 0, st>>>(sink, 1e-7f); }, st, &ms);
+    if (e == cudaSuccess) out[0] = lane_ops / (ms * 1e-3);
+    if (e == cudaSuccess) e = time_it([&] { ex2_probe<<<grid, kBlock, 0, st>>>(sink); }, st, &ms);
+    if (e == cudaSuccess) out[1] = lane_ops / (ms * 1e-3);
+    if (e == cudaSuccess) e = time_it([&] { rcp_probe<<<grid, kBlock, 0, st>>>(sink); }, st, &ms);
+    if (e == cudaSuccess) out[2] = lane_ops / (ms * 1e-3);
+    out[3] = (double)sms;
+    cudaFree(sink);
+    return e;
+}
+
+}  // namespace gpk

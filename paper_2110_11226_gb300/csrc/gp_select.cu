@@ -1,0 +1,73 @@
+// gp_select.cu -- tournament selection on the device (Sec. III-C1): one
+// thread per tournament, k draws from Philox4x32-10, the best adjusted
+// fitness wins (Eqs. parsimony and fitness).
+#include <math_constants.h>
+
+#include "gp_internal.cuh"
+
+namespace gpk {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+//   (c0,c1,c2,c3) <- (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+// with the key advanced by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += W0;
+        k.y += W1;
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(256) tournament_kernel(TournArgs a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_tourn) return;
+    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    int best = -1;
+    double best_adj = 0.0;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    for (int j = 0; j < a.k; ++j) {
+        if ((j & 3) == 0)
+            r = philox4x32_10(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)a.offset,
+                                         (uint32_t)(a.offset >> 32)),
+                              key);
+        const uint32_t u = (j & 3) == 0 ? r.x : (j & 3) == 1 ? r.y : (j & 3) == 2 ? r.z : r.w;
+        const int i = (int)(((uint64_t)u * (uint64_t)a.n_progs) >> 32);
+        // adjusted fitness in FP64 so the comparison is decided exactly as
+        // a double-precision reference decides it
+        double pen = 0.0;
+        if (a.offsets)
+            pen = __dmul_rn((double)a.parsimony, (double)(a.offsets[i + 1] - a.offsets[i]));
+        const double raw = (double)a.fitness[i];
+        double adj;
+        bool better;
+        if (a.greater) {
+            adj = __dsub_rn(raw, pen);
+            if (isnan(adj)) adj = -CUDART_INF;
+            better = best < 0 || adj > best_adj;
+        } else {
+            adj = __dadd_rn(raw, pen);
+            if (isnan(adj)) adj = CUDART_INF;
+            better = best < 0 || adj < best_adj;
+        }
+        if (better) {
+            best = i;
+            best_adj = adj;
+        }
+    }
+    a.out[t] = best;
+}
+
+cudaError_t launch_tournament(const TournArgs &a, cudaStream_t st) {
+    if (a.n_tourn <= 0) return cudaSuccess;
+    const int block = 256;
+    tournament_kernel<<<(a.n_tourn + block - 1) / block, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gpk

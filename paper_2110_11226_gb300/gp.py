@@ -1,0 +1,315 @@
+"""Python binding of libgp (include/gp.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device arrays
+are CUDA torch tensors (PyTorch provides device memory and streams; all
+computation runs in libgp's kernels); host arrays are numpy arrays.  There
+is no fallback: if libgp.so cannot be built or loaded, importing this module
+raises.
+
+Program populations travel as one flat array of 8-byte nodes (int16 op,
+int16 feat, float32 c) plus int32 offsets[P+1] (Sec. III-A prefix lists);
+``nodes_to_device`` turns the numpy form into a CUDA int64 tensor holding
+the same bytes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3}
+ACCUM = {"fp64": 0, "kahan32": 1}
+MAX_CONSTS = 16
+NODE_DTYPE = np.dtype([("op", "<i2"), ("feat", "<i2"), ("c", "<f4")])
+
+DEV_BAD_PROGRAM = 0x1
+DEV_TOO_MANY_CONSTS = 0x2
+DEV_QUEUE_CAP = 0x4
+
+
+class GPError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} failed: {code} ({_lib.gp_status_string(code).decode()})")
+        self.code = code
+
+
+class EvalOpts(C.Structure):
+    _fields_ = [("rows_per_thread", C.c_int), ("chunk_rows", C.c_int),
+                ("blocks_per_sm", C.c_int), ("accum", C.c_int),
+                ("reserved", C.c_int * 4)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path) or os.environ.get("GP_REBUILD"):
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libgp.so missing at {path}; run paper_2110_11226_gb300/build.py")
+    lib = C.CDLL(path)
+    P, i32, i64, f32, u64 = C.c_void_p, C.c_int, C.c_int64, C.c_float, C.c_uint64
+    sig = {
+        "gp_version": (C.c_char_p, []),
+        "gp_status_string": (C.c_char_p, [i32]),
+        "gp_evaluate": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
+        "gp_evaluate_ex": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P, P, P, P,
+                                 C.c_size_t, P]),
+        "gp_workspace_size": (C.c_size_t, [i32, i64, i32, P]),
+        "gp_evaluate_plain": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
+        "gp_predict": (i32, [P, P, i32, P, i64, i32, P, P]),
+        "gp_evaluate_host": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
+        "gp_validate_host": (i32, [P, P, i32, i32, P, P]),
+        "gp_tournament_ex": (i32, [P, P, i32, i32, i32, f32, i32, u64, u64, P, P]),
+        "gp_tournament": (i32, [P, i32, i32, u64, P]),
+        "gp_const_grad": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P, P]),
+        "gp_adam_step": (i32, [P, P, i32, P, P, P, i32, f32, f32, f32, f32, P]),
+        "gp_last_device_status": (i32, [P, P]),
+        "gp_autotune": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
+        "gp_probe_pipes": (i32, [P, P]),
+        "gp_timing_enable": (i32, [i32]),
+        "gp_timing_read": (i32, [P, P]),
+        "gp_shutdown": (None, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _build.LIB
+
+
+# ---- marshalling helpers -------------------------------------------------
+def _dptr(t: Optional[torch.Tensor], name: str):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _metric(m):
+    return METRICS[m] if isinstance(m, str) else int(m)
+
+
+def _check(name, rc):
+    if rc != 0:
+        raise GPError(name, rc)
+
+
+def _xshape(X):
+    if X.dim() != 2:
+        raise ValueError("X must be [n_feat][n_rows] (column-major data)")
+    return int(X.shape[1]), int(X.shape[0])
+
+
+def nodes_to_device(nodes: np.ndarray, device="cuda") -> torch.Tensor:
+    """numpy node array -> CUDA int64 tensor with the same 8-byte records."""
+    n = np.ascontiguousarray(nodes, dtype=NODE_DTYPE)
+    return torch.from_numpy(n.view(np.int64).copy()).to(device)
+
+
+def nodes_from_device(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(NODE_DTYPE).copy()
+
+
+def _nprogs(offsets):
+    return int(offsets.numel()) - 1
+
+
+# ---- entry points --------------------------------------------------------
+def gp_version() -> str:
+    return _lib.gp_version().decode()
+
+
+def gp_evaluate(progs, offsets, X, y, w=None, metric="mse", out=None, stream=None):
+    n_rows, n_feat = _xshape(X)
+    P = _nprogs(offsets)
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=X.device)
+    _check("gp_evaluate", _lib.gp_evaluate(
+        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
+        _dptr(y, "y"), _dptr(w, "w"), _metric(metric), _dptr(out, "out"), _stream(stream)))
+    return out
+
+
+def make_opts(rows_per_thread=0, chunk_rows=0, blocks_per_sm=0, accum="fp64") -> EvalOpts:
+    o = EvalOpts()
+    o.rows_per_thread = rows_per_thread
+    o.chunk_rows = chunk_rows
+    o.blocks_per_sm = blocks_per_sm
+    o.accum = ACCUM[accum] if isinstance(accum, str) else int(accum)
+    return o
+
+
+def gp_evaluate_ex(progs, offsets, X, y, w=None, metric="mse", opts: Optional[EvalOpts] = None,
+                   out=None, out64=None, out_status=None, ws=None, stream=None):
+    n_rows, n_feat = _xshape(X)
+    P = _nprogs(offsets)
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=X.device)
+    ws_ptr, ws_bytes = (None, 0) if ws is None else (_dptr(ws, "ws"), ws.numel() * ws.element_size())
+    _check("gp_evaluate_ex", _lib.gp_evaluate_ex(
+        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
+        _dptr(y, "y"), _dptr(w, "w"), _metric(metric),
+        None if opts is None else C.byref(opts), _dptr(out, "out"), _dptr(out64, "out64"),
+        _dptr(out_status, "out_status"), ws_ptr, ws_bytes, _stream(stream)))
+    return out
+
+
+def gp_workspace_size(n_progs, n_rows, n_feat, opts: Optional[EvalOpts] = None) -> int:
+    return int(_lib.gp_workspace_size(int(n_progs), int(n_rows), int(n_feat),
+                                      None if opts is None else C.byref(opts)))
+
+
+def gp_evaluate_plain(progs, offsets, X, y, w=None, metric="mse", out=None, stream=None):
+    n_rows, n_feat = _xshape(X)
+    P = _nprogs(offsets)
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=X.device)
+    _check("gp_evaluate_plain", _lib.gp_evaluate_plain(
+        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
+        _dptr(y, "y"), _dptr(w, "w"), _metric(metric), _dptr(out, "out"), _stream(stream)))
+    return out
+
+
+def gp_predict(progs, offsets, X, out=None, stream=None):
+    n_rows, n_feat = _xshape(X)
+    P = _nprogs(offsets)
+    if out is None:
+        out = torch.empty((P, n_rows), dtype=torch.float32, device=X.device)
+    _check("gp_predict", _lib.gp_predict(
+        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
+        _dptr(out, "out"), _stream(stream)))
+    return out
+
+
+def gp_evaluate_host(nodes: np.ndarray, offsets: np.ndarray, X: np.ndarray, y: np.ndarray,
+                     w: Optional[np.ndarray] = None, metric="mse", out: Optional[np.ndarray] = None,
+                     stream=None) -> np.ndarray:
+    """Host arrays in, host fitness out (copies inside the call, synchronous)."""
+    nodes = np.ascontiguousarray(nodes, dtype=NODE_DTYPE)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+    P = len(offsets) - 1
+    if out is None:
+        out = np.empty(P, np.float32)
+    _check("gp_evaluate_host", _lib.gp_evaluate_host(
+        _hptr(nodes), _hptr(offsets), P, _hptr(X), X.shape[1], X.shape[0], _hptr(y), _hptr(w),
+        _metric(metric), _hptr(out), _stream(stream)))
+    return out
+
+
+def gp_validate_host(nodes: np.ndarray, offsets: np.ndarray, n_feat: int):
+    """Returns (rc, status[P], high_water[P]) -- runs on the host, no GPU needed."""
+    nodes = np.ascontiguousarray(nodes, dtype=NODE_DTYPE)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+    P = len(offsets) - 1
+    st = np.zeros(P, np.int32)
+    hw = np.zeros(P, np.int32)
+    rc = _lib.gp_validate_host(_hptr(nodes), _hptr(offsets), P, int(n_feat), _hptr(st), _hptr(hw))
+    return int(rc), st, hw
+
+
+def gp_tournament_ex(fitness, n_tourn, tourn_size, seed, offsets=None, parsimony=0.0,
+                     greater_is_better=False, offset=0, out=None, stream=None):
+    P = int(fitness.numel())
+    if out is None:
+        out = torch.empty(n_tourn, dtype=torch.int32, device=fitness.device)
+    _check("gp_tournament_ex", _lib.gp_tournament_ex(
+        _dptr(fitness, "fitness"), _dptr(offsets, "offsets"), P, int(n_tourn), int(tourn_size),
+        float(parsimony), int(bool(greater_is_better)), int(seed), int(offset),
+        _dptr(out, "out"), _stream(stream)))
+    return out
+
+
+def gp_tournament(fitness, tourn_size, seed, out=None):
+    P = int(fitness.numel())
+    if out is None:
+        out = torch.empty(P, dtype=torch.int32, device=fitness.device)
+    _check("gp_tournament", _lib.gp_tournament(
+        _dptr(fitness, "fitness"), P, int(tourn_size), int(seed), _dptr(out, "out")))
+    return out
+
+
+def gp_const_grad(progs, offsets, X, y, w=None, metric="mse", out_grad=None, out_fitness=None,
+                  stream=None):
+    n_rows, n_feat = _xshape(X)
+    P = _nprogs(offsets)
+    if out_grad is None:
+        out_grad = torch.empty((P, MAX_CONSTS), dtype=torch.float32, device=X.device)
+    if out_fitness is None:
+        out_fitness = torch.empty(P, dtype=torch.float32, device=X.device)
+    _check("gp_const_grad", _lib.gp_const_grad(
+        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
+        _dptr(y, "y"), _dptr(w, "w"), _metric(metric), _dptr(out_grad, "out_grad"),
+        _dptr(out_fitness, "out_fitness"), _stream(stream)))
+    return out_grad, out_fitness
+
+
+def gp_adam_step(progs, offsets, grad, m, v, step, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
+                 stream=None):
+    P = _nprogs(offsets)
+    _check("gp_adam_step", _lib.gp_adam_step(
+        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(grad, "grad"),
+        _dptr(m, "m"), _dptr(v, "v"), int(step), float(lr), float(beta1), float(beta2),
+        float(eps), _stream(stream)))
+
+
+def gp_last_device_status(stream=None) -> int:
+    flags = C.c_uint32(0)
+    _check("gp_last_device_status", _lib.gp_last_device_status(_stream(stream), C.byref(flags)))
+    return int(flags.value)
+
+
+def gp_autotune(progs, offsets, X, y, w=None, metric="mse", stream=None) -> EvalOpts:
+    n_rows, n_feat = _xshape(X)
+    best = EvalOpts()
+    _check("gp_autotune", _lib.gp_autotune(
+        _dptr(progs, "progs"), _dptr(offsets, "offsets"), _nprogs(offsets), _dptr(X, "X"),
+        n_rows, n_feat, _dptr(y, "y"), _dptr(w, "w"), _metric(metric), C.byref(best),
+        _stream(stream)))
+    return best
+
+
+def gp_probe_pipes(stream=None) -> dict:
+    out = (C.c_double * 4)()
+    _check("gp_probe_pipes", _lib.gp_probe_pipes(out, _stream(stream)))
+    return {"fp32_lane_ops_per_s": out[0], "mufu_ex2_lane_ops_per_s": out[1],
+            "mufu_rcp_lane_ops_per_s": out[2], "sms": int(out[3])}
+
+
+def gp_timing_enable(on: bool = True):
+    _check("gp_timing_enable", _lib.gp_timing_enable(int(bool(on))))
+
+
+def gp_timing_read():
+    """(total ms, number of evaluations) of the evaluator launches since the last read."""
+    ms = C.c_double(0.0)
+    n = C.c_int(0)
+    _check("gp_timing_read", _lib.gp_timing_read(C.byref(ms), C.byref(n)))
+    return float(ms.value), int(n.value)
+
+
+def gp_shutdown():
+    _lib.gp_shutdown()

@@ -1,0 +1,115 @@
+"""Parity helpers: compare GPU results with the FP64 oracle.
+
+Per point (tolerance 1e-5 relative, FP32 evaluation against FP64):
+  * the oracle gives, for every row, the FP64 value v, a first-order bound e
+    on the error of any FP32 evaluation whose library functions err by at
+    most ULPS units in the last place, and flags (1 = a protected
+    operator's threshold test may decide differently in FP32, 2 = a value
+    leaves the float range);
+  * "ok" rows (no flag, e <= v/4 * 1e-5) must satisfy |gpu - v| <= 1e-5 |v|;
+  * "conditioning" rows (no flag, larger e) must satisfy |gpu - v| <= 1.5 e
+    + 1e-5 |v| -- FP32 cannot meet 1e-5 there, the bound says by how much;
+  * flagged rows are counted, not compared.
+Fitness (tolerance 1e-4 relative): programs whose rows are all unflagged
+and whose propagated bound is below 1e-4/4 of the fitness must match within
+1e-4; the others must stay within the propagated bound and are counted.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+import oracle
+
+ULPS = 4.0          # CUDA: sinf/cosf/expf 2 ulp, tanf 4, logf/log1pf 1
+REL_POINT = 1e-5
+REL_FIT = 1e-4
+
+
+@dataclasses.dataclass
+class PointStats:
+    rows: int
+    ok: int
+    conditioning: int
+    flagged: int
+
+
+def check_points(gpu, nodes, off, X, row0=0, n_eval=None):
+    gpu = np.asarray(gpu, np.float64)
+    v, e, fl = oracle.predict_bound(nodes, off, X, row0=row0, n_eval=n_eval, ulps_fn=ULPS)
+    assert gpu.shape == v.shape
+    unfl = fl == 0
+    tight = unfl & (e <= 0.25 * REL_POINT * np.abs(v))
+    cond = unfl & ~tight
+    with np.errstate(invalid="ignore"):
+        err = np.abs(gpu - v)
+    bad_ok = tight & ~(err <= REL_POINT * np.abs(v))
+    assert not bad_ok.any(), _report(bad_ok, gpu, v, e)
+    bad_c = cond & ~(err <= 1.5 * e + REL_POINT * np.abs(v))
+    # a NaN FP64 value (e.g. sin(inf)) must be NaN on the GPU as well
+    both_nan = np.isnan(gpu) & np.isnan(v)
+    bad_c &= ~both_nan
+    assert not bad_c.any(), _report(bad_c, gpu, v, e)
+    return PointStats(int(v.size), int(tight.sum()), int(cond.sum()), int((~unfl).sum())), (v, e, fl)
+
+
+def _report(mask, gpu, v, e):
+    idx = np.argwhere(mask)[:5]
+    return "mismatch at " + "; ".join(
+        f"{tuple(i)}: gpu={gpu[tuple(i)]!r} fp64={v[tuple(i)]!r} bound={e[tuple(i)]!r}" for i in idx)
+
+
+def fitness_bound(metric, v, e, y, w):
+    """Propagate per-row FP32 bounds e into a bound on the weighted metric."""
+    y = y.astype(np.float64)
+    wv = np.ones_like(y) if w is None else w.astype(np.float64)
+    sw = wv.sum()
+    with np.errstate(all="ignore"):
+        if metric == "mae" or metric == "logloss":  # |dl/dp| <= 1
+            b = (e * wv).sum(axis=1) / sw
+        else:
+            d = np.abs(v - y[None, :])
+            b = ((2 * d * e + e * e) * wv).sum(axis=1) / sw
+    return b
+
+
+@dataclasses.dataclass
+class FitStats:
+    programs: int
+    strict: int
+    conditioning: int
+    flagged: int
+    max_rel_strict: float
+
+
+def check_fitness(gpu_fit, nodes, off, X, y, w, metric, row0=0, n_eval=None, v=None, e=None,
+                  fl=None):
+    gpu_fit = np.asarray(gpu_fit, np.float64)
+    f64, st = oracle.fitness(nodes, off, X, y, w, metric, row0=row0, n_eval=n_eval)
+    if v is None:
+        v, e, fl = oracle.predict_bound(nodes, off, X, row0=row0, n_eval=n_eval, ulps_fn=ULPS)
+    ys = y[row0:row0 + v.shape[1]]
+    ws = None if w is None else w[row0:row0 + v.shape[1]]
+    mse_metric = "mse" if metric == "rmse" else metric
+    b = fitness_bound(mse_metric, v, e, ys, ws)
+    f_cmp = f64
+    g_cmp = gpu_fit
+    if metric == "rmse":  # compare squares: the bound is on the MSE
+        f_cmp = f64 ** 2
+        g_cmp = gpu_fit ** 2
+    flagged = (fl != 0).any(axis=1) | (st != 0)
+    with np.errstate(invalid="ignore"):
+        strict = ~flagged & np.isfinite(f64) & (b <= 0.25 * REL_FIT * np.abs(f_cmp))
+        rel = np.abs(gpu_fit - f64) / np.maximum(np.abs(f64), 1e-300)
+        strict_ok = ~strict | (rel <= REL_FIT) | (np.abs(gpu_fit - f64) <= 1e-12)
+    assert strict_ok.all(), f"fitness mismatch: {np.argwhere(~strict_ok)[:5].ravel()} rel={rel[~strict_ok][:5]}"
+    cond = ~flagged & ~strict
+    with np.errstate(invalid="ignore"):
+        cond_ok = ~cond | (np.abs(g_cmp - f_cmp) <= 1.5 * b + REL_FIT * np.abs(f_cmp)) | \
+            (np.isinf(g_cmp) & np.isinf(f_cmp))
+    assert cond_ok.all(), f"conditioning fitness beyond bound: {np.argwhere(~cond_ok)[:5].ravel()}"
+    # status: malformed programs are NaN on both sides
+    assert np.all(np.isnan(gpu_fit[st != 0]))
+    mr = float(np.max(rel[strict])) if strict.any() else 0.0
+    return FitStats(len(f64), int(strict.sum()), int(cond.sum()), int(flagged.sum()), mr), f64

@@ -1,0 +1,93 @@
+"""The C ABI library: it loads, exports every entry point of include/gp.h,
+agrees with the oracle and the input generator on the node format, and its
+host-side validation agrees with the oracle (CPU only, no compute calls on a
+GPU)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_11226_gb300 import build as gpbuild
+from paper_2110_11226_gb300 import synth
+from helpers import parse_prefix, pack
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gp.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gp_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _enum(name_prefix):
+    txt = open(HEADER).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(rf"\b({name_prefix}[A-Z_0-9]+)\s*=\s*(-?\d+)", txt)}
+
+
+def test_library_exports_every_declared_symbol():
+    path = gpbuild.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_opcodes_agree_between_header_oracle_and_generator():
+    ops = _enum("GP_")
+    for name, code in synth.OP.items():
+        assert ops["GP_" + name.upper()] == code, name
+        assert oracle.OPS[name] == code
+        assert oracle.op_name(code) == name
+        assert oracle.op_arity(code) == synth.ARITY[code]
+    assert ops["GP_NUM_OPS"] == len(synth.OP)
+    assert ops["GP_MAE"] == 0 and ops["GP_MSE"] == 1 and ops["GP_RMSE"] == 2 and ops["GP_LOGLOSS"] == 3
+    for k, v in oracle.METRICS.items():
+        assert ops["GP_" + k.upper()] == v
+    # gp_node is 8 bytes: int16 op, int16 feat, float c
+    assert synth.NODE_DTYPE.itemsize == 8 and oracle.NODE_DTYPE == synth.NODE_DTYPE
+    st = _enum("GP_PROG_")
+    assert st["GP_PROG_OK"] == oracle.OK and st["GP_PROG_TOO_DEEP"] == oracle.TOO_DEEP
+    assert st["GP_PROG_UNDERFLOW"] == oracle.UNDERFLOW and st["GP_PROG_LEFTOVER"] == oracle.LEFTOVER
+
+
+def test_host_validation_agrees_with_oracle():
+    from paper_2110_11226_gb300 import gp
+    rng = np.random.default_rng(5)
+    progs = []
+    n_feat = 3
+    good = synth.unpack(*synth.random_programs(200, 9, synth.FULL_SET + ("tan",), n_feat, seed=4))
+    for p in good:
+        progs.append(p)
+        q = list(p)
+        kind = rng.integers(6)
+        if kind == 0 and len(q) > 1:
+            q = q[:-1]                         # drop a terminal: underflow
+        elif kind == 1:
+            q = q + [(synth.OP["var"], 0, 0.0)]  # leftover value
+        elif kind == 2:
+            q[rng.integers(len(q))] = (77, 0, 0.0)  # unknown op
+        elif kind == 3:
+            q = [(synth.OP["var"], n_feat, 0.0)]    # feature out of range
+        elif kind == 4:
+            d = 21                                  # left spine deeper than the stack
+            q = [(synth.OP["add"], 0, 0.0)] * d + [(synth.OP["var"], 0, 0.0)] + [(synth.OP["const"], 0, 1.0)] * d
+        progs.append(q)
+    progs.append([])
+    nodes, off = pack(progs)
+    rc, st, hw = gp.gp_validate_host(nodes, off, n_feat)
+    assert rc == -2  # GP_ERR_PROGRAM
+    for i, p in enumerate(progs):
+        ost, ohw = oracle.validate(nodes[off[i]:off[i + 1]], n_feat)
+        assert st[i] == ost, (i, st[i], ost)
+        if ost == oracle.OK:
+            assert hw[i] == ohw
+    rc2, st2, _ = gp.gp_validate_host(*pack(good), n_feat)
+    assert rc2 == 0 and np.all(st2 == 0)

@@ -1,0 +1,413 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Small cases run in full (several row tiles, a ragged tail, every metric);
+the full-size workloads run in the launch configuration of bench.py and are
+checked on sampled programs the oracle evaluates over every row.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2110_11226_gb300 import gp, synth
+from helpers import pack, parse_prefix, read_table
+from parity import check_fitness, check_points
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def put(nodes, off, X, y=None, w=None):
+    return (gp.nodes_to_device(nodes), dev(off.astype(np.int32)), dev(X),
+            None if y is None else dev(y), None if w is None else dev(w))
+
+
+def _weights(n, seed):
+    return np.random.default_rng(seed).uniform(0.25, 4.0, n).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# per-point values
+# --------------------------------------------------------------------------
+def test_predict_bit_exact_on_ieee_operators():
+    """add/sub/mul/div/inv/sqrt/abs/neg are correctly rounded on both sides
+    and nothing is contracted into FMA: the GPU values equal the oracle's
+    FP32 mode bit for bit (pagie_small programs and hand-written ones)."""
+    wl = synth.workload("pagie_small")
+    extra = synth.unpack(*synth.random_programs(300, 9, ("add", "sub", "mul", "div", "inv",
+                                                         "sqrt", "abs", "neg"), 2, seed=17))
+    progs = synth.unpack(wl.nodes, wl.offsets) + extra
+    nodes, off = pack(progs)
+    for n in (4096, 4096 + 37, 5):
+        X = synth.pagie_data(n, 3).X
+        pn, po, dX, _, _ = put(nodes, off, X)
+        got = gp.gp_predict(pn, po, dX).cpu().numpy()
+        want = oracle.predict32(nodes, off, X)
+        np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_predict_tiny_programs_and_protected_points():
+    rows = read_table("tiny_programs.txt")
+    nodes, off = pack([parse_prefix(r[0]) for r in rows])
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-5, 5, size=(2, 1000)).astype(np.float32)
+    X[:, :6] = np.array([[0.0, 0.0005, -0.000999, 0.001, 1.5, -2.25],
+                         [0.0011, -0.0005, 0.002, -0.001, 0.0, 3.0]], np.float32)
+    pn, po, dX, _, _ = put(nodes, off, X)
+    got = gp.gp_predict(pn, po, dX).cpu().numpy()
+    st, _ = check_points(got, nodes, off, X)
+    assert st.ok > 0.6 * st.rows
+
+
+@pytest.mark.parametrize("n_feat,funcs", [(2, synth.FULL_SET), (1, synth.FULL_SET + ("tan",)),
+                                          (7, synth.FULL_SET + ("tan",)), (50, synth.FULL_SET)])
+def test_predict_full_function_set(n_feat, funcs):
+    nodes, off = synth.ramped_half_and_half(600, 2, 8, funcs, n_feat, seed=40 + n_feat)
+    n = 2048 + 61
+    X = np.random.default_rng(n_feat).uniform(-5, 5, size=(n_feat, n)).astype(np.float32)
+    pn, po, dX, _, _ = put(nodes, off, X)
+    got = gp.gp_predict(pn, po, dX).cpu().numpy()
+    st, _ = check_points(got, nodes, off, X)
+    assert st.ok > 0.5 * st.rows, st
+
+
+def test_deep_and_long_programs():
+    """Programs needing all 20 stack slots (the deep register class), 255
+    nodes, single terminals, unary chains."""
+    V, Cn = synth.OP["var"], synth.OP["const"]
+    progs = []
+    for d in (8, 9, 12, 19):  # left spines: stack height d + 1
+        progs.append([(synth.OP["sub"], 0, 0.0)] * d + [(V, 0, 0.0)] +
+                     [(Cn, 0, float(np.float32(0.125 * (i + 1)))) for i in range(d)])
+        progs.append([(synth.OP["div"], 0, 0.0)] * d + [(V, 1, 0.0)] +
+                     [(synth.OP["add"], 0, 0.0), (V, 0, 0.0), (V, 1, 0.0)] * d)
+    progs.append([(synth.OP["add"], 0, 0.0), (Cn, 0, 1.0)] * 127 + [(V, 0, 0.0)])  # 255 nodes
+    progs.append([(synth.OP["sin"], 0, 0.0)] * 254 + [(V, 1, 0.0)])
+    progs.append([(V, 1, 0.0)])
+    progs.append([(Cn, 0, -3.5)])
+    nodes, off = pack(progs)
+    for stt, hw in [oracle.validate(nodes[off[i]:off[i + 1]], 2) for i in range(len(progs))]:
+        assert stt == oracle.OK and hw <= 20
+    X = synth.pagie_data(1000 + 3, 9).X
+    pn, po, dX, _, _ = put(nodes, off, X)
+    got = gp.gp_predict(pn, po, dX).cpu().numpy()
+    check_points(got, nodes, off, X)
+    y = synth.pagie_data(1003, 9).y
+    fit = gp.gp_evaluate(pn, po, dX, dev(y), metric="mse").cpu().numpy()
+    check_fitness(fit, nodes, off, X, y, None, "mse")
+
+
+# --------------------------------------------------------------------------
+# fitness
+# --------------------------------------------------------------------------
+def test_fitness_pagie_small_full():
+    """Pagie-1, N=4096, P=512, {add,sub,mul,div}, MSE: every program."""
+    wl = synth.workload("pagie_small")
+    d = wl.data
+    pn, po, dX, dy, _ = put(wl.nodes, wl.offsets, d.X, d.y)
+    fit = gp.gp_evaluate(pn, po, dX, dy, metric="mse").cpu().numpy()
+    stats, f64 = check_fitness(fit, wl.nodes, wl.offsets, d.X, d.y, None, "mse")
+    assert stats.strict > 0.8 * stats.programs, stats
+    # the GPU values are bit-exact to the oracle's FP32 mode here, so its
+    # fitness equals the FP64 reduction of those values up to summation
+    p32 = oracle.predict32(wl.nodes, wl.offsets, d.X).astype(np.float64)
+    with np.errstate(all="ignore"):
+        ref = np.mean((p32 - d.y.astype(np.float64)) ** 2, axis=1)
+        fin = np.isfinite(ref)
+        np.testing.assert_allclose(fit[fin], ref[fin], rtol=2e-6)
+
+
+@pytest.mark.parametrize("metric", ["mae", "mse", "rmse", "logloss"])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_fitness_metrics_ragged_many_chunks(metric, weighted):
+    n = 4096 + 37
+    if metric == "logloss":
+        d = synth.classification_data(n, 7, n_feat=5)
+        funcs = synth.FULL_SET
+    else:
+        d = synth.pagie_data(n, 8)
+        funcs = synth.FULL_SET + ("tan",)
+    w = _weights(n, 3) if weighted else (d.w if metric == "logloss" else None)
+    nodes, off = synth.ramped_half_and_half(256, 2, 7, funcs, d.n_feat, seed=60)
+    pn, po, dX, dy, dw = put(nodes, off, d.X, d.y, w)
+    for rpt in (4, 8):
+        opts = gp.make_opts(rows_per_thread=rpt, chunk_rows=256)
+        fit = gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=metric, opts=opts).cpu().numpy()
+        stats, _ = check_fitness(fit, nodes, off, d.X, d.y, w, metric)
+        assert stats.strict > 0.5 * stats.programs, stats
+
+
+def test_plain_evaluator_matches_oracle_and_batched():
+    wl = synth.workload("pagie_small")
+    d = wl.data
+    w = _weights(d.n_rows, 4)
+    pn, po, dX, dy, dw = put(wl.nodes, wl.offsets, d.X, d.y, w)
+    plain = gp.gp_evaluate_plain(pn, po, dX, dy, dw, metric="rmse").cpu().numpy()
+    batched = gp.gp_evaluate(pn, po, dX, dy, dw, metric="rmse").cpu().numpy()
+    check_fitness(plain, wl.nodes, wl.offsets, d.X, d.y, w, "rmse")
+    fin = np.isfinite(batched)
+    np.testing.assert_array_equal(np.isfinite(plain), fin)
+    np.testing.assert_allclose(plain[fin], batched[fin], rtol=2e-6)
+
+
+def test_fitness_is_deterministic_and_accumulators_agree():
+    wl = synth.workload("pagie_large", n_rows=1 << 16, n_progs=512)
+    d = wl.data
+    pn, po, dX, dy, _ = put(wl.nodes, wl.offsets, d.X, d.y)
+    a = gp.gp_evaluate(pn, po, dX, dy, metric="rmse").cpu().numpy()
+    b = gp.gp_evaluate(pn, po, dX, dy, metric="rmse").cpu().numpy()
+    np.testing.assert_array_equal(a.view(np.uint32), b.view(np.uint32))
+    o64 = gp.make_opts(rows_per_thread=8, chunk_rows=1024, accum="fp64")
+    o32 = gp.make_opts(rows_per_thread=8, chunk_rows=1024, accum="kahan32")
+    f64 = gp.gp_evaluate_ex(pn, po, dX, dy, metric="rmse", opts=o64).cpu().numpy()
+    f32 = gp.gp_evaluate_ex(pn, po, dX, dy, metric="rmse", opts=o32).cpu().numpy()
+    fin = np.isfinite(f64)
+    np.testing.assert_allclose(f32[fin], f64[fin], rtol=1e-6)
+    np.testing.assert_allclose(a[fin], f64[fin], rtol=5e-6)
+    stats, _ = check_fitness(a, wl.nodes, wl.offsets, d.X, d.y, None, "rmse")
+    assert stats.strict > 0.5 * stats.programs
+
+
+def test_invalid_programs_are_flagged_not_trapped():
+    good = parse_prefix("add x0 x1")
+    V, A = synth.OP["var"], synth.OP["add"]
+    progs = [good, [(A, 0, 0.0), (V, 0, 0.0)], good, [(V, 5, 0.0)], [(99, 0, 0.0)],
+             [(V, 0, 0.0), (V, 1, 0.0)], [(A, 0, 0.0)] * 21 + [(V, 0, 0.0)] * 22, good]
+    nodes, off = pack(progs)
+    d = synth.pagie_data(300, 1)
+    pn, po, dX, dy, _ = put(nodes, off, d.X, d.y)
+    gp.gp_last_device_status()  # clear
+    st = torch.empty(len(progs), dtype=torch.int32, device="cuda")
+    fit = gp.gp_evaluate_ex(pn, po, dX, dy, metric="mae", out_status=st).cpu().numpy()
+    flags = gp.gp_last_device_status()
+    assert flags & gp.DEV_BAD_PROGRAM
+    bad = np.array([0, 1, 0, 1, 1, 1, 1, 0], bool)
+    assert np.all(np.isnan(fit[bad])) and np.all(np.isfinite(fit[~bad]))
+    want = [oracle.validate(nodes[off[i]:off[i + 1]], 2)[0] for i in range(len(progs))]
+    np.testing.assert_array_equal(st.cpu().numpy(), np.array(want))
+    pred = gp.gp_predict(pn, po, dX).cpu().numpy()
+    assert np.all(np.isnan(pred[bad])) and np.all(np.isfinite(pred[~bad]))
+    assert gp.gp_last_device_status() & gp.DEV_BAD_PROGRAM
+    assert gp.gp_last_device_status() == 0
+
+
+def test_argument_errors_return_codes():
+    d = synth.pagie_data(64, 1)
+    nodes, off = pack([parse_prefix("add x0 x1")])
+    pn, po, dX, dy, _ = put(nodes, off, d.X, d.y)
+    with pytest.raises(gp.GPError) as e:
+        gp.gp_evaluate(pn, po, dX, dy, metric=7)
+    assert e.value.code == -1
+    with pytest.raises(gp.GPError):
+        gp.gp_evaluate_ex(pn, po, dX, dy, opts=gp.make_opts(rows_per_thread=3))
+    with pytest.raises(gp.GPError) as e:
+        gp.gp_evaluate_host(pack([[(synth.OP["add"], 0, 0.0)]])[0], np.array([0, 1], np.int32),
+                            d.X, d.y)
+    assert e.value.code == -2
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gp.GPError) as e:
+        gp.gp_evaluate_ex(pn, po, dX, dy, ws=small)
+    assert e.value.code == -7
+
+
+def test_edge_sizes():
+    nodes, off = synth.ramped_half_and_half(40, 1, 4, synth.FULL_SET, 2, seed=3)
+    for n in (1, 2, 3, 4, 5, 127, 129, 1023):
+        d = synth.pagie_data(n, n)
+        pn, po, dX, dy, _ = put(nodes, off, d.X, d.y)
+        fit = gp.gp_evaluate(pn, po, dX, dy, metric="mae").cpu().numpy()
+        check_fitness(fit, nodes, off, d.X, d.y, None, "mae")
+        pred = gp.gp_predict(pn, po, dX).cpu().numpy()
+        check_points(pred, nodes, off, d.X)
+
+
+def test_host_entry_point_matches_device_entry_point():
+    wl = synth.workload("binary", n_rows=8192 + 5, n_progs=128)
+    d = wl.data
+    host = gp.gp_evaluate_host(wl.nodes, wl.offsets, d.X, d.y, d.w, metric="logloss")
+    pn, po, dX, dy, dw = put(wl.nodes, wl.offsets, d.X, d.y, d.w)
+    devf = gp.gp_evaluate(pn, po, dX, dy, dw, metric="logloss").cpu().numpy()
+    np.testing.assert_array_equal(host.view(np.uint32), devf.view(np.uint32))
+    check_fitness(host, wl.nodes, wl.offsets, d.X, d.y, d.w, "logloss")
+
+
+def test_graph_capture_replays_the_generation():
+    wl = synth.workload("pagie_large", n_rows=1 << 15, n_progs=256)
+    d = wl.data
+    pn, po, dX, dy, _ = put(wl.nodes, wl.offsets, d.X, d.y)
+    opts = gp.make_opts(rows_per_thread=4, chunk_rows=2048)
+    ws = torch.empty(gp.gp_workspace_size(256, d.n_rows, 2, opts), dtype=torch.uint8, device="cuda")
+    fit = torch.empty(256, dtype=torch.float32, device="cuda")
+    win = torch.empty(256, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        gp.gp_evaluate_ex(pn, po, dX, dy, metric="rmse", opts=opts, out=fit, ws=ws)
+        gp.gp_tournament_ex(fit, 256, 20, 42, out=win)
+    s.synchronize()
+    eager_fit, eager_win = fit.clone(), win.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        gp.gp_evaluate_ex(pn, po, dX, dy, metric="rmse", opts=opts, out=fit, ws=ws)
+        gp.gp_tournament_ex(fit, 256, 20, 42, out=win)
+    fit.zero_()
+    win.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(fit.view(torch.int32), eager_fit.view(torch.int32))
+    assert torch.equal(win, eager_win)
+
+
+# --------------------------------------------------------------------------
+# tournament selection: bit-exact
+# --------------------------------------------------------------------------
+def test_tournament_bit_exact():
+    rng = np.random.default_rng(0)
+    for P, T, k in ((512, 512, 20), (1000, 1700, 10), (7, 50, 1), (4096, 7000, 33)):
+        f = rng.normal(size=P).astype(np.float32)
+        f[rng.random(P) < 0.05] = np.nan
+        f[rng.random(P) < 0.05] = np.inf
+        f[: P // 4] = np.round(f[: P // 4], 1)  # many ties
+        lens = rng.integers(1, 256, P)
+        off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+        for pars, greater, seed, offset in ((0.0, False, 42, 0), (0.01, False, 7, 3),
+                                            (0.003, True, 2 ** 40 + 5, 2 ** 33)):
+            got = gp.gp_tournament_ex(dev(f), T, k, seed, offsets=dev(off), parsimony=pars,
+                                      greater_is_better=greater, offset=offset).cpu().numpy()
+            want = oracle.tournament(f, T, k, seed, lengths=np.diff(off), parsimony=pars,
+                                     greater_is_better=greater, offset=offset)
+            np.testing.assert_array_equal(got, want)
+    f = rng.normal(size=300).astype(np.float32)
+    got = gp.gp_tournament(dev(f), 20, 42).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.tournament(f, 300, 20, 42))
+
+
+# --------------------------------------------------------------------------
+# constant gradients and Adam
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("metric", ["mse", "rmse", "mae", "logloss"])
+def test_const_grad_matches_oracle_reverse_mode(metric):
+    n = 2048 + 19
+    if metric == "logloss":
+        d = synth.classification_data(n, 11, n_feat=4)
+    else:
+        d = synth.pagie_data(n, 12)
+    nodes, off = synth.ramped_half_and_half(200, 2, 6, synth.FULL_SET, d.n_feat, seed=70,
+                                            max_consts=16)
+    pn, po, dX, dy, dw = put(nodes, off, d.X, d.y, d.w)
+    g, f = gp.gp_const_grad(pn, po, dX, dy, dw, metric=metric)
+    g, f = g.cpu().numpy().astype(np.float64), f.cpu().numpy()
+    g64, f64, gabs = oracle.const_grad(nodes, off, d.X, d.y, d.w, metric, with_abs=True)
+    _, _, fl = oracle.predict_bound(nodes, off, d.X, ulps_fn=4.0)
+    fbatch = gp.gp_evaluate(pn, po, dX, dy, dw, metric=metric).cpu().numpy()
+    fin = np.isfinite(fbatch)
+    np.testing.assert_allclose(f[fin], fbatch[fin], rtol=5e-6)
+    clean = ~(fl != 0).any(axis=1) & np.isfinite(g64).all(axis=1) & (np.abs(f64) < 1e6)
+    assert clean.sum() > 0.6 * len(clean)
+    with np.errstate(invalid="ignore"):
+        tol = 1e-4 * np.maximum(gabs, 1e-3 * np.abs(g64).max(axis=1, keepdims=True)) + 1e-7
+        ok = np.abs(g - g64) <= tol
+    bad = clean[:, None] & ~ok
+    assert not bad.any(), (np.argwhere(bad)[:5], g[bad][:5], g64[bad][:5])
+    nconst = np.array([oracle.count_consts(nodes[off[i]:off[i + 1]]) for i in range(len(off) - 1)])
+    for i, k in enumerate(nconst):
+        assert np.all(g[i, k:] == 0)
+
+
+def test_adam_steps_match_oracle():
+    d = synth.pagie_data(1024, 5)
+    nodes, off = synth.ramped_half_and_half(64, 2, 5, synth.FULL_SET, 2, seed=71, max_consts=16)
+    pn, po, dX, dy, _ = put(nodes, off, d.X, d.y)
+    m = torch.zeros((64, 16), device="cuda")
+    v = torch.zeros((64, 16), device="cuda")
+    theta = nodes["c"].astype(np.float64)
+    om = np.zeros((64, 16))
+    ov = np.zeros((64, 16))
+    for step in range(1, 6):
+        g, _ = gp.gp_const_grad(pn, po, dX, dy, metric="mse")
+        gh = g.cpu().numpy().astype(np.float64)
+        gp.gp_adam_step(pn, po, g, m, v, step, lr=1e-2)
+        after = gp.nodes_from_device(pn)
+        # oracle Adam on the same gradients, parameter per constant slot
+        cur = nodes.copy()
+        cur["c"] = np.float32(theta)
+        for p in range(64):
+            idx = np.arange(off[p], off[p + 1])
+            kidx = idx[nodes["op"][idx] == synth.OP["const"]]
+            if len(kidx) == 0:
+                continue
+            th = theta[kidx].copy()
+            mm = om[p, :len(kidx)].copy()
+            vv = ov[p, :len(kidx)].copy()
+            oracle.adam(th, gh[p, :len(kidx)], mm, vv, step, lr=1e-2)
+            om[p, :len(kidx)] = mm
+            ov[p, :len(kidx)] = vv
+            theta[kidx] = th
+            np.testing.assert_allclose(after["c"][kidx], th, rtol=2e-6, atol=2e-7)
+        theta = after["c"].astype(np.float64)
+    assert np.array_equal(after["op"], nodes["op"])
+
+
+# --------------------------------------------------------------------------
+# full-size workloads in the benchmark's launch configuration (sampled)
+# --------------------------------------------------------------------------
+def _sample(off, k, seed):
+    P = len(off) - 1
+    return np.sort(np.random.default_rng(seed).choice(P, size=k, replace=False))
+
+
+def _subset(nodes, off, idx):
+    progs = synth.unpack(nodes, off)
+    return pack([progs[i] for i in idx])
+
+
+@pytest.mark.parametrize("name,n_rows,k", [("pagie_large", 1 << 24, 6), ("pagie_large", 1 << 20, 16),
+                                           ("tabular", 10_000_000, 4), ("binary", 1 << 22, 6)])
+def test_full_size_fitness_sampled(name, n_rows, k):
+    wl = synth.workload(name, n_rows=n_rows)
+    d = wl.data
+    pn, po, dX, dy, dw = put(wl.nodes, wl.offsets, d.X, d.y, d.w)
+    fit = gp.gp_evaluate(pn, po, dX, dy, dw, metric=wl.metric).cpu().numpy()
+    assert np.isfinite(fit).mean() > 0.5
+    idx = _sample(wl.offsets, k, 5)
+    sn, so = _subset(wl.nodes, wl.offsets, idx)
+    f64, st = oracle.fitness(sn, so, d.X, d.y, d.w, wl.metric)
+    # full-size rows are too many for per-row bounds; the FP32 oracle gives
+    # the conditioning of each sampled program instead
+    rel = np.abs(fit[idx] - f64) / np.maximum(np.abs(f64), 1e-30)
+    with np.errstate(all="ignore"):
+        p32 = oracle.predict32(sn, so, d.X)
+        ys = d.y.astype(np.float64)
+        wv = np.ones_like(ys) if d.w is None else d.w.astype(np.float64)
+        if wl.metric in ("rmse", "mse"):
+            f32 = (((p32 - ys) ** 2) * wv).sum(1) / wv.sum()
+            if wl.metric == "rmse":
+                f32 = np.sqrt(f32)
+        else:
+            f32 = np.array([np.nan] * len(idx))
+    for i in range(len(idx)):
+        if not np.isfinite(f64[i]):
+            continue
+        cond = abs(f32[i] - f64[i]) / max(abs(f64[i]), 1e-30) if np.isfinite(f32[i]) else 0.0
+        assert rel[i] <= max(1e-4, 4 * cond), (name, idx[i], fit[idx[i]], f64[i], cond)
+
+
+def test_full_size_const_grad_sampled():
+    wl = synth.workload("const_tune")
+    d = wl.data
+    pn, po, dX, dy, _ = put(wl.nodes, wl.offsets, d.X, d.y)
+    g, f = gp.gp_const_grad(pn, po, dX, dy, metric="mse")
+    g = g.cpu().numpy().astype(np.float64)
+    idx = _sample(wl.offsets, 6, 9)
+    sn, so = _subset(wl.nodes, wl.offsets, idx)
+    g64, f64, gabs = oracle.const_grad(sn, so, d.X, d.y, None, "mse", with_abs=True)
+    v, e, fl = oracle.predict_bound(sn, so, d.X[:, :65536], ulps_fn=4.0)
+    for j, p in enumerate(idx):
+        if (fl[j] != 0).any() or not np.isfinite(g64[j]).all():
+            continue
+        tol = 1e-4 * np.maximum(gabs[j], 1e-3 * np.abs(g64[j]).max()) + 1e-7
+        assert np.all(np.abs(g[p] - g64[j]) <= tol), (p, g[p], g64[j])

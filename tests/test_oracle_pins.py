@@ -463,6 +463,10 @@ def test_const_grad_closed_forms():
     assert np.all(g[:, 1:] == 0)
     f_ref = oracle.fitness(nodes, off, X, y, w, "mse")[0]
     np.testing.assert_array_equal(fit, f_ref)
+    # magnitude output: sum of |w 2 (c - y)| / sum w for the constant program
+    _, _, ga = oracle.const_grad(nodes, off, X, y, w, "mse", with_abs=True)
+    assert ga[0, 0] == pytest.approx(np.sum(wd * 2 * np.abs(c - yd)) / np.sum(wd), rel=1e-12)
+    assert np.all(ga >= np.abs(g) * (1 - 1e-12))
 
 
 @pytest.mark.parametrize("metric", ["mse", "rmse", "mae", "logloss"])
