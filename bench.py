@@ -14,9 +14,11 @@ the ALU roofline (node operations over FP32-pipe / SFU peaks, or feature
 bytes over HBM bandwidth); `cpu_baseline` = the FP64 C oracle on the host
 cores, on a bounded sample.
 
-Multi-GPU (torchrun): every rank evaluates its own population (islands, seed
-offset by rank) on the same data with no collective on the data path; the
-time is the max over ranks (weak scaling).
+Multi-GPU (torchrun): the population is sharded by programs -- every rank
+evaluates its own P programs of a global population of world*P (seed offset
+by rank) on the same data, the fitness shards are all-gathered (selection
+needs all of them), and every rank runs the same world*P tournaments; the
+time is the max over ranks (weak scaling: P per GPU is fixed).
 
 --impl reference: times the oracle instead (the CPU reference arm).
 """
@@ -72,7 +74,7 @@ def make_workload(args, rank):
     from paper_2110_11226_gb300 import synth
     wl = synth.workload(args.workload, n_rows=args.n_rows, n_progs=args.n_progs or None)
     if rank:
-        # islands: every rank evaluates its own population over the same data
+        # program shard of rank r: its own P programs, same data
         nodes, off = synth.ramped_half_and_half(len(wl.offsets) - 1, *_depths(args.workload),
                                                 wl.funcs, wl.data.n_feat, 1000 + rank)
         wl.nodes, wl.offsets = nodes, off
@@ -217,7 +219,8 @@ def main():
     dy = torch.from_numpy(d.y).to(dev)
     dw = None if d.w is None else torch.from_numpy(d.w).to(dev)
     fit = torch.empty(P, dtype=torch.float32, device=dev)
-    win = torch.empty(P, dtype=torch.int32, device=dev)
+    win = torch.empty(ws * P, dtype=torch.int32, device=dev)
+    from paper_2110_11226_gb300.dist import gather_fitness
     stream = torch.cuda.current_stream()
     pipes = gp.gp_probe_pipes()
     tuned = None
@@ -226,7 +229,8 @@ def main():
 
     def step(seed):
         gp.gp_evaluate(pn, po, dX, dy, dw, metric=wl.metric, out=fit)
-        gp.gp_tournament_ex(fit, P, wl.tourn_size, seed, out=win)
+        gfit = gather_fitness(fit) if ws > 1 else fit
+        gp.gp_tournament_ex(gfit, ws * P, wl.tourn_size, seed, out=win)
 
     for s in range(args.warmup):
         step(42 + s)
@@ -290,7 +294,7 @@ def main():
                        "metric": wl.metric, "tourn_size": wl.tourn_size,
                        "mean_nodes": n_nodes / P, "function_nodes": n_fn, "sfu_nodes": n_sfu,
                        "l2": "inputs larger than L2" if N * 4 * (d.n_feat + 1) > 129e6 else "L2-resident inputs",
-                       "parallelism": f"islands x{ws}" if ws > 1 else "single GPU",
+                       "parallelism": f"program shards x{ws} + fitness all-gather" if ws > 1 else "single GPU",
                        "opts": None if tuned is None else {"rows_per_thread": tuned.rows_per_thread,
                                                            "chunk_rows": tuned.chunk_rows,
                                                            "blocks_per_sm": tuned.blocks_per_sm}},
@@ -330,7 +334,7 @@ def main():
             gp.gp_evaluate_host(hn, ho, hX, hy, hw, metric=wl.metric, out=hfit)
             fit_d.copy_(torch.from_numpy(hfit), non_blocking=True)
             gp.gp_tournament_ex(fit_d, P, wl.tourn_size, seed, out=win)
-            hwin.copy_(win, non_blocking=True)
+            hwin.copy_(win[:P], non_blocking=True)
             torch.cuda.current_stream().synchronize()
 
         e2e_step(1)

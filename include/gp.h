@@ -235,7 +235,8 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs,
  * with g = grad[p][k], m = beta1 m + (1-beta1) g, v = beta2 v + (1-beta2)
  * g^2, c -= lr * (m / (1-beta1^step)) / (sqrt(v / (1-beta2^step)) + eps).
  * m, v [n_progs][16] float32 state owned by the caller (zero before step
- * 1).  step >= 1. */
+ * 1).  step >= 1.  A slot whose gradient is not finite keeps its constant
+ * and its m, v unchanged. */
 int gp_adam_step(gp_node *progs, const int32_t *offsets, int n_progs,
                  const float *grad, float *m, float *v, int step, float lr,
                  float beta1, float beta2, float eps, void *stream);

@@ -96,6 +96,8 @@ def _load():
     lib.ora_count_consts.argtypes = [P, i32]
     lib.ora_const_grad.argtypes = [P, P, i32, P, i64, P, P, i32, i64, i64,
                                    P, P, P, i32]
+    lib.ora_const_grad32.argtypes = [P, P, i32, P, i64, P, P, i32, i64, i64,
+                                     P, P, i32]
     lib.ora_adam.argtypes = [P, P, P, P, i64, i32, f64, f64, f64, f64]
     lib.ora_max_threads.restype = i32
     _lib = lib
@@ -275,6 +277,30 @@ def const_grad(progs, offsets, X, y, w=None, metric="mse", row0=0,
     if rc == -1:
         raise ValueError("oracle const_grad: bad metric or zero total weight")
     return (g, f, ga) if with_abs else (g, f)
+
+
+def const_grad32(progs, offsets, X, y, w=None, metric="mse", row0=0,
+                 n_eval=None, n_threads=0):
+    """The reverse mode with every per-row operation in FP32 (sums over rows
+    in FP64): how far FP32 rounding alone moves each gradient.  Returns
+    (grad [P,16], fit [P])."""
+    lib = _load()
+    progs, offsets = _progs(progs, offsets)
+    X = _colmajor(X)
+    y = np.ascontiguousarray(y, np.float32)
+    w = None if w is None else np.ascontiguousarray(w, np.float32)
+    n_rows = X.shape[1]
+    n_eval = n_rows - row0 if n_eval is None else n_eval
+    P = len(offsets) - 1
+    m = METRICS[metric] if isinstance(metric, str) else int(metric)
+    g = np.empty((P, MAX_CONSTS), np.float64)
+    f = np.empty(P, np.float64)
+    rc = lib.ora_const_grad32(_ptr(progs), _ptr(offsets), P, _ptr(X), n_rows,
+                              _ptr(y), _ptr(w), m, row0, n_eval, _ptr(g),
+                              _ptr(f), n_threads)
+    if rc == -1:
+        raise ValueError("oracle const_grad32: bad metric or zero total weight")
+    return g, f
 
 
 def adam(theta, g, m, v, step, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):

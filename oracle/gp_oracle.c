@@ -706,6 +706,147 @@ int ora_const_grad(const ora_node *progs, const int32_t *offsets,
     return rc;
 }
 
+/* The same reverse mode with every per-row operation in FP32 (C library
+ * float functions, derivatives formed in float) and only the sums over
+ * rows in FP64.  Its distance from ora_const_grad measures how much FP32
+ * rounding alone moves each gradient (the gradient's conditioning); it is
+ * the reference the GPU's FP32 adjoint is held to where that distance is
+ * large.  Same arguments and return values as ora_const_grad. */
+static float sgn32(float x) { return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f); }
+
+static float loss32(int metric, float p, float y) {
+    switch (metric) {
+    case ORA_MAE: return fabsf(p - y);
+    case ORA_MSE: case ORA_RMSE: return (p - y) * (p - y);
+    case ORA_LOGLOSS: {
+        float ap = fabsf(p);
+        float c = (p >= 0.0f) ? 1.0f - y : y;
+        float lin = (c == 0.0f) ? 0.0f : c * ap;
+        return lin + log1pf(expf(-ap));
+    }
+    }
+    return NAN;
+}
+
+static float dloss32(int metric, float p, float y) {
+    switch (metric) {
+    case ORA_MAE: return sgn32(p - y);
+    case ORA_MSE: case ORA_RMSE: return 2.0f * (p - y);
+    case ORA_LOGLOSS: {
+        float s = (p >= 0.0f) ? 1.0f / (1.0f + expf(-p)) : expf(p) / (1.0f + expf(p));
+        return s - y;
+    }
+    }
+    return NAN;
+}
+
+int ora_const_grad32(const ora_node *progs, const int32_t *offsets,
+                     int n_progs, const float *X, int64_t ld, const float *y,
+                     const float *w, int metric, int64_t row0, int64_t n_eval,
+                     double *grad, double *fit, int n_threads) {
+    if (metric < ORA_MAE || metric > ORA_LOGLOSS) return -1;
+    double sw = 0.0;
+    for (int64_t i = 0; i < n_eval; ++i) sw += w ? (double)w[row0 + i] : 1.0;
+    if (!(sw != 0.0)) return -1;
+    int rc = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic) reduction(min : rc)
+#endif
+    for (int p = 0; p < n_progs; ++p) {
+        const ora_node *prog = progs + offsets[p];
+        int len = offsets[p + 1] - offsets[p];
+        double g[ORA_MAX_CONSTS];
+        int kslot[ORA_MAX_LEN];
+        for (int k = 0; k < ORA_MAX_CONSTS; ++k) g[k] = 0.0;
+        int nc = 0, bad = 0;
+        if (len < 1 || len > ORA_MAX_LEN) bad = 1;
+        for (int j = 0; j < len && !bad; ++j) {
+            kslot[j] = -1;
+            if (prog[j].op == ORA_CONST) {
+                if (nc >= ORA_MAX_CONSTS) { bad = 2; break; }
+                kslot[j] = nc++;
+            }
+        }
+        double se = 0.0;
+        for (int64_t i = 0; i < n_eval && !bad; ++i) {
+            int64_t r = row0 + i;
+            float val[ORA_MAX_LEN], adj[ORA_MAX_LEN];
+            int left[ORA_MAX_LEN], right[ORA_MAX_LEN];
+            int pos[ORA_MAX_LEN + 1], sp = 0;
+            for (int j = len - 1; j >= 0 && !bad; --j) {
+                int op = prog[j].op, a = ora_op_arity(op);
+                left[j] = right[j] = -1;
+                if (a < 0) { bad = 1; break; }
+                if (op == ORA_CONST) val[j] = prog[j].c;
+                else if (op == ORA_VAR) val[j] = X[(int64_t)prog[j].feat * ld + r];
+                else if (a == 1) {
+                    if (sp < 1) { bad = 1; break; }
+                    left[j] = pos[--sp];
+                    val[j] = fn1_32(op, val[left[j]]);
+                } else {
+                    if (sp < 2) { bad = 1; break; }
+                    left[j] = pos[--sp];
+                    right[j] = pos[--sp];
+                    val[j] = fn2_32(op, val[left[j]], val[right[j]]);
+                }
+                pos[sp++] = j;
+            }
+            if (bad || sp != 1) { bad = 1; break; }
+            float pr = val[0], yi = y[r];
+            float wi = w ? w[r] : 1.0f;
+            se += (double)(wi * loss32(metric, pr, yi));
+            for (int j = 0; j < len; ++j) adj[j] = 0.0f;
+            adj[0] = wi * dloss32(metric, pr, yi);
+            for (int j = 0; j < len; ++j) {
+                int op = prog[j].op;
+                float aj = adj[j];
+                if (op == ORA_CONST) { g[kslot[j]] += (double)aj; continue; }
+                if (op == ORA_VAR) continue;
+                float u = val[left[j]];
+                float du = 0.0f, dv = 0.0f;
+                switch (op) {
+                case ORA_ADD: du = 1.0f; dv = 1.0f; break;
+                case ORA_SUB: du = 1.0f; dv = -1.0f; break;
+                case ORA_MUL: du = val[right[j]]; dv = u; break;
+                case ORA_DIV: {
+                    float v = val[right[j]];
+                    if (fabsf(v) < ORA_THR) { du = 0.0f; dv = 0.0f; }
+                    else { du = 1.0f / v; dv = -(val[j] / v); }
+                    break;
+                }
+                case ORA_SQRT: du = (u == 0.0f) ? 0.0f : sgn32(u) / (2.0f * val[j]); break;
+                case ORA_LOG:  du = (fabsf(u) < ORA_THR) ? 0.0f : 1.0f / u; break;
+                case ORA_EXP:  du = val[j]; break;
+                case ORA_SIN:  du = cosf(u); break;
+                case ORA_COS:  du = -sinf(u); break;
+                case ORA_TAN:  du = 1.0f + val[j] * val[j]; break;
+                case ORA_ABS:  du = sgn32(u); break;
+                case ORA_NEG:  du = -1.0f; break;
+                case ORA_INV:  du = (fabsf(u) < ORA_THR) ? 0.0f : -(val[j] * val[j]); break;
+                }
+                adj[left[j]] = aj * du;
+                if (right[j] >= 0) adj[right[j]] = aj * dv;
+            }
+        }
+        if (bad) {
+            for (int k = 0; k < ORA_MAX_CONSTS; ++k) grad[p * ORA_MAX_CONSTS + k] = NAN;
+            if (fit) fit[p] = NAN;
+            if (bad == 2) rc = -2;
+            continue;
+        }
+        double f = se / sw, scale = 1.0 / sw;
+        if (metric == ORA_RMSE) {
+            f = sqrt(f);
+            scale = (f > 0.0) ? scale / (2.0 * f) : 0.0;
+        }
+        for (int k = 0; k < ORA_MAX_CONSTS; ++k)
+            grad[p * ORA_MAX_CONSTS + k] = (k < nc) ? g[k] * scale : 0.0;
+        if (fit) fit[p] = f;
+    }
+    return rc;
+}
+
 /* ---- Adam (Kingma & Ba 2015, Algorithm 1), one step on n parameters --- */
 void ora_adam(double *theta, const double *g, double *m, double *v, int64_t n,
               int step, double lr, double beta1, double beta2, double eps) {

@@ -26,6 +26,7 @@
 #pragma once
 
 #include "gp_internal.cuh"
+#include "gp_math.cuh"
 
 namespace gpk {
 
@@ -155,14 +156,17 @@ __global__ void __launch_bounds__(kEvalBlock) eval_kernel(const EvalArgs a) {
 #pragma unroll
             for (int j = 0; j < RPT; ++j) t[j] = 0.0f;
 
+            // One indirect dispatch per instruction.  Operand-fetch cases are
+            // a few register moves and jump to the operation bodies below,
+            // each of which exists once, so the hot code stays small.
             uint2 ins = cbuf[0];
             for (int pc = 0; pc < m.n_ins; ++pc) {
                 const uint2 nx = cbuf[pc + 1];
                 const uint32_t op = ins.x & 0xffu;
-                const int feat = (int)(ins.x >> 16);
                 const float c = __uint_as_float(ins.y);
                 float u[RPT];
                 if (ins.x & kNeedsX) {
+                    const int feat = (int)(ins.x >> 16);
                     if (FMODE == 2) {
 #pragma unroll
                         for (int j = 0; j < RPT; ++j) u[j] = feat ? x1[j] : x0[j];
@@ -170,36 +174,25 @@ __global__ void __launch_bounds__(kEvalBlock) eval_kernel(const EvalArgs a) {
                         load_rows<RPT>(u, a.X + (int64_t)feat * a.ld, r0, re, vec);
                     }
                 }
-                bool done = false;
                 switch (op) {
+#define GP_SPILL(k)                                                             \
+    if constexpr (k > 0 && k <= MAXD) {                                         \
+        _Pragma("unroll") for (int j = 0; j < RPT; ++j) s[k > 0 ? k - 1 : 0][j] = t[j]; \
+    }
 #define GP_PUSH(k)                                                              \
-    case K_PUSH_X + k:                                                          \
-    case K_PUSH_C + k:                                                          \
-        if constexpr (k <= MAXD) {                                              \
-            if constexpr (k > 0) {                                              \
-                _Pragma("unroll") for (int j = 0; j < RPT; ++j) s[k > 0 ? k - 1 : 0][j] = t[j]; \
-            }                                                                   \
-            if (op == K_PUSH_X + k) {                                           \
-                _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = u[j];    \
-            } else {                                                            \
-                _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = c;       \
-            }                                                                   \
-        }                                                                       \
-        break;
+    case K_PUSH_X + k: GP_SPILL(k) goto L_TU;                                   \
+    case K_PUSH_C + k: GP_SPILL(k) goto L_TC;
                     GP_R20(GP_PUSH)
 #undef GP_PUSH
-#define GP_BIN(b, fn)                                                           \
-    GP_R19(GP_BIN_##b)
-#define GP_BINK(b, fn, k)                                                       \
-    case K_BIN + b * kDeepSlots + k:                                            \
-        if constexpr (k < MAXD) {                                               \
-            _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = fn(t[j], s[k < MAXD ? k : 0][j]); \
-        }                                                                       \
-        break;
-#define GP_BIN_0(k) GP_BINK(0, f_add, k)
-#define GP_BIN_1(k) GP_BINK(1, f_sub, k)
-#define GP_BIN_2(k) GP_BINK(2, f_mul, k)
-#define GP_BIN_3(k) GP_BINK(3, f_div, k)
+#undef GP_SPILL
+#define GP_FETCH(k)                                                             \
+    if constexpr (k < MAXD) {                                                   \
+        _Pragma("unroll") for (int j = 0; j < RPT; ++j) u[j] = s[k < MAXD ? k : 0][j]; \
+    }
+#define GP_BIN_0(k) case K_BIN + 0 * kDeepSlots + k: GP_FETCH(k) goto L_ADD;
+#define GP_BIN_1(k) case K_BIN + 1 * kDeepSlots + k: GP_FETCH(k) goto L_SUB;
+#define GP_BIN_2(k) case K_BIN + 2 * kDeepSlots + k: GP_FETCH(k) goto L_MUL;
+#define GP_BIN_3(k) case K_BIN + 3 * kDeepSlots + k: GP_FETCH(k) goto L_DIV;
                     GP_R19(GP_BIN_0)
                     GP_R19(GP_BIN_1)
                     GP_R19(GP_BIN_2)
@@ -208,48 +201,59 @@ __global__ void __launch_bounds__(kEvalBlock) eval_kernel(const EvalArgs a) {
 #undef GP_BIN_1
 #undef GP_BIN_2
 #undef GP_BIN_3
-#undef GP_BINK
-#undef GP_BIN
+#undef GP_FETCH
+                    case K_BIN_RX + 0: case K_BIN_LX + 0: goto L_ADD;
+                    case K_BIN_RX + 1: goto L_SUB;
+                    case K_BIN_LX + 1: goto L_RSUB;
+                    case K_BIN_RX + 2: case K_BIN_LX + 2: goto L_MUL;
+                    case K_BIN_RX + 3: goto L_DIV;
+                    case K_BIN_LX + 3: goto L_RDIV;
+                    case K_BIN_RC + 0: case K_BIN_LC + 0: goto L_ADDC;
+                    case K_BIN_RC + 1: goto L_SUBC;
+                    case K_BIN_LC + 1: goto L_RSUBC;
+                    case K_BIN_RC + 2: case K_BIN_LC + 2: goto L_MULC;
+                    case K_BIN_RC + 3: goto L_DIVC;
+                    case K_BIN_LC + 3: goto L_RDIVC;
 #define GP_UN(i, fn)                                                            \
     case K_UN + i:                                                              \
         _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = fn(t[j]);        \
-        break;
+        goto L_NEXT;
                     GP_UN(0, f_sqrt)
                     GP_UN(1, f_log)
                     GP_UN(2, f_exp)
-                    GP_UN(3, f_sin)
-                    GP_UN(4, f_cos)
-                    GP_UN(5, f_tan)
+                    GP_UN(3, gp_sin)
+                    GP_UN(4, gp_cos)
+                    GP_UN(5, gp_tan)
                     GP_UN(6, f_abs)
                     GP_UN(7, f_neg)
                     GP_UN(8, f_inv)
 #undef GP_UN
-#define GP_FOLD(b, fn)                                                          \
-    case K_BIN_RX + b:                                                          \
-        _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = fn(t[j], u[j]);  \
-        break;                                                                  \
-    case K_BIN_RC + b:                                                          \
-        _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = fn(t[j], c);     \
-        break;                                                                  \
-    case K_BIN_LX + b:                                                          \
-        _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = fn(u[j], t[j]);  \
-        break;                                                                  \
-    case K_BIN_LC + b:                                                          \
-        _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = fn(c, t[j]);     \
-        break;
-                    GP_FOLD(0, f_add)
-                    GP_FOLD(1, f_sub)
-                    GP_FOLD(2, f_mul)
-                    GP_FOLD(3, f_div)
-#undef GP_FOLD
                     default:
-                        done = true;  // K_END
-                        break;
+                        goto L_END;  // K_END
                 }
-                if (done) break;
+#define GP_BODY(label, expr)                                                    \
+    label:                                                                      \
+        _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = expr;            \
+        goto L_NEXT;
+                GP_BODY(L_TU, u[j])
+                GP_BODY(L_TC, c)
+                GP_BODY(L_ADD, f_add(t[j], u[j]))
+                GP_BODY(L_SUB, f_sub(t[j], u[j]))
+                GP_BODY(L_RSUB, f_sub(u[j], t[j]))
+                GP_BODY(L_MUL, f_mul(t[j], u[j]))
+                GP_BODY(L_DIV, f_div(t[j], u[j]))
+                GP_BODY(L_RDIV, f_div(u[j], t[j]))
+                GP_BODY(L_ADDC, f_add(t[j], c))
+                GP_BODY(L_SUBC, f_sub(t[j], c))
+                GP_BODY(L_RSUBC, f_sub(c, t[j]))
+                GP_BODY(L_MULC, f_mul(t[j], c))
+                GP_BODY(L_DIVC, f_div(t[j], c))
+                GP_BODY(L_RDIVC, f_div(c, t[j]))
+#undef GP_BODY
+            L_NEXT:
                 ins = nx;
             }
-
+        L_END:
             if (PRED) {
                 float *dst = a.pred + (size_t)p * a.n_rows;
 #pragma unroll

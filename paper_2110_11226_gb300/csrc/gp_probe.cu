@@ -22,13 +22,14 @@ __global__ void __launch_bounds__(kBlock) fadd_probe(float *sink, float d) {
     float s = 0.0f;
 #pragma unroll
     for (int i = 0; i < kChains; ++i) s += x[i];
-    if (s == 1234.5f) sink[0] = s;
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kBlock) ex2_probe(float *sink) {
+// chains start from runtime values so that nothing can be folded at compile time
+__global__ void __launch_bounds__(kBlock) ex2_probe(float *sink, float d) {
     float x[kChains];
 #pragma unroll
-    for (int i = 0; i < kChains; ++i) x[i] = 0.25f + 0.01f * (float)i;
+    for (int i = 0; i < kChains; ++i) x[i] = d * (float)(threadIdx.x + 3 * i + 1);
     for (int it = 0; it < kIters; ++it) {
 #pragma unroll
         for (int i = 0; i < kChains; ++i) {
@@ -40,13 +41,13 @@ __global__ void __launch_bounds__(kBlock) ex2_probe(float *sink) {
     float s = 0.0f;
 #pragma unroll
     for (int i = 0; i < kChains; ++i) s += x[i];
-    if (s == 1234.5f) sink[0] = s;
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kBlock) rcp_probe(float *sink) {
+__global__ void __launch_bounds__(kBlock) rcp_probe(float *sink, float d) {
     float x[kChains];
 #pragma unroll
-    for (int i = 0; i < kChains; ++i) x[i] = 1.5f + 0.25f * (float)i;
+    for (int i = 0; i < kChains; ++i) x[i] = 1.0f + d * (float)(threadIdx.x + 3 * i + 1);
     for (int it = 0; it < kIters; ++it) {
 #pragma unroll
         for (int i = 0; i < kChains; ++i) {
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kBlock) rcp_probe(float *sink) {
     float s = 0.0f;
 #pragma unroll
     for (int i = 0; i < kChains; ++i) s += x[i];
-    if (s == 1234.5f) sink[0] = s;
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 template <typename F>
@@ -88,16 +89,16 @@ cudaError_t probe_pipes(double *out, cudaStream_t st) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     float *sink = nullptr;
-    cudaError_t e = cudaMalloc(&sink, sizeof(float));
-    if (e != cudaSuccess) return e;
     const int grid = sms * 8;
+    cudaError_t e = cudaMalloc(&sink, sizeof(float) * grid * kBlock);
+    if (e != cudaSuccess) return e;
     const double lane_ops = (double)grid * kBlock * kIters * kChains;
     double ms = 0.0;
     e = time_it([&] { fadd_probe<<<grid, kBlock, 0, st>>>(sink, 1e-7f); }, st, &ms);
     if (e == cudaSuccess) out[0] = lane_ops / (ms * 1e-3);
-    if (e == cudaSuccess) e = time_it([&] { ex2_probe<<<grid, kBlock, 0, st>>>(sink); }, st, &ms);
+    if (e == cudaSuccess) e = time_it([&] { ex2_probe<<<grid, kBlock, 0, st>>>(sink, 1e-3f); }, st, &ms);
     if (e == cudaSuccess) out[1] = lane_ops / (ms * 1e-3);
-    if (e == cudaSuccess) e = time_it([&] { rcp_probe<<<grid, kBlock, 0, st>>>(sink); }, st, &ms);
+    if (e == cudaSuccess) e = time_it([&] { rcp_probe<<<grid, kBlock, 0, st>>>(sink, 1e-3f); }, st, &ms);
     if (e == cudaSuccess) out[2] = lane_ops / (ms * 1e-3);
     out[3] = (double)sms;
     cudaFree(sink);

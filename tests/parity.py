@@ -98,7 +98,22 @@ def check_fitness(gpu_fit, nodes, off, X, y, w, metric, row0=0, n_eval=None, v=N
     if metric == "rmse":  # compare squares: the bound is on the MSE
         f_cmp = f64 ** 2
         g_cmp = gpu_fit ** 2
-    flagged = (fl != 0).any(axis=1) | (st != 0)
+    # FP32 range of the loss itself: a weighted row loss, or the sum of a
+    # chunk's losses, beyond the float range is +inf on the GPU while the
+    # FP64 oracle stays finite (all losses are >= 0, so the total bounds
+    # every partial sum)
+    FMAX = float(np.finfo(np.float32).max)
+    with np.errstate(all="ignore"):
+        yy = ys.astype(np.float64)[None, :]
+        if metric == "mae":
+            rl = np.abs(v - yy)
+        elif metric == "logloss":
+            rl = np.abs(v) + np.log(2.0)
+        else:
+            rl = (v - yy) ** 2
+        wl = rl if ws is None else rl * ws.astype(np.float64)[None, :]
+        loss_range = (np.nanmax(wl, axis=1) > 0.5 * FMAX) | (np.nansum(wl, axis=1) > 0.5 * FMAX)
+    flagged = (fl != 0).any(axis=1) | (st != 0) | loss_range
     with np.errstate(invalid="ignore"):
         strict = ~flagged & np.isfinite(f64) & (b <= 0.25 * REL_FIT * np.abs(f_cmp))
         rel = np.abs(gpu_fit - f64) / np.maximum(np.abs(f64), 1e-300)

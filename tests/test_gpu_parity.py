@@ -302,20 +302,62 @@ def test_const_grad_matches_oracle_reverse_mode(metric):
     g, f = gp.gp_const_grad(pn, po, dX, dy, dw, metric=metric)
     g, f = g.cpu().numpy().astype(np.float64), f.cpu().numpy()
     g64, f64, gabs = oracle.const_grad(nodes, off, d.X, d.y, d.w, metric, with_abs=True)
+    g32, _ = oracle.const_grad32(nodes, off, d.X, d.y, d.w, metric)
     _, _, fl = oracle.predict_bound(nodes, off, d.X, ulps_fn=4.0)
     fbatch = gp.gp_evaluate(pn, po, dX, dy, dw, metric=metric).cpu().numpy()
     fin = np.isfinite(fbatch)
     np.testing.assert_allclose(f[fin], fbatch[fin], rtol=5e-6)
-    clean = ~(fl != 0).any(axis=1) & np.isfinite(g64).all(axis=1) & (np.abs(f64) < 1e6)
-    assert clean.sum() > 0.6 * len(clean)
-    with np.errstate(invalid="ignore"):
-        tol = 1e-4 * np.maximum(gabs, 1e-3 * np.abs(g64).max(axis=1, keepdims=True)) + 1e-7
-        ok = np.abs(g - g64) <= tol
-    bad = clean[:, None] & ~ok
-    assert not bad.any(), (np.argwhere(bad)[:5], g[bad][:5], g64[bad][:5])
+    extra = _mae_flip_tol(nodes, off, d, metric)
+    strict, cond = _grad_check(g, g64, g32, gabs, fl, extra)
+    assert strict > 0.6 * len(g64), (strict, cond)
     nconst = np.array([oracle.count_consts(nodes[off[i]:off[i + 1]]) for i in range(len(off) - 1)])
     for i, k in enumerate(nconst):
         assert np.all(g[i, k:] == 0)
+
+
+def _mae_flip_tol(nodes, off, d, metric):
+    """MAE's gradient uses sign(p - y): on rows where |p - y| is within
+    twice the FP32 value bound the sign may differ between FP32 and FP64,
+    which moves the gradient by up to twice those rows' absolute
+    contributions.  Returns that amount per (program, constant)."""
+    P = len(off) - 1
+    if metric != "mae":
+        return np.zeros((P, 16))
+    v, e, _ = oracle.predict_bound(nodes, off, d.X, ulps_fn=4.0)
+    w = np.ones(d.n_rows, np.float32) if d.w is None else d.w
+    out = np.zeros((P, 16))
+    for p in range(P):
+        risk = np.abs(v[p] - d.y) <= 2 * e[p] + 1e-30
+        if not risk.any():
+            continue
+        wr = np.where(risk, w, 0).astype(np.float32)
+        sn, so = pack([synth.unpack(nodes, off)[p]])
+        _, _, ga = oracle.const_grad(sn, so, d.X, d.y, wr, "mae", with_abs=True)
+        out[p] = 2 * ga[0] * wr.sum() / w.sum()
+    return out
+
+
+def _grad_check(g, g64, g32, gabs, fl, extra=None):
+    """Gradient tolerance: 1e-4 of the gradient's scale (the sum of absolute
+    per-row contributions) where FP32 rounding alone moves the oracle's
+    gradient by less than a quarter of that; elsewhere the gradient is
+    ill-conditioned in FP32 and the GPU must stay within ten times the
+    deviation of the oracle's FP32 adjoint.  Programs with flagged rows
+    (protected-branch flips, float range) are not compared."""
+    usable = ~(fl != 0).any(axis=1) & np.isfinite(g64).all(axis=1) & np.isfinite(g32).all(axis=1)
+    with np.errstate(invalid="ignore"):
+        tol = 1e-4 * np.maximum(gabs, 1e-3 * np.abs(g64).max(axis=1, keepdims=True)) + 1e-7
+        if extra is not None:
+            tol = tol + extra
+        dev32 = np.abs(g32 - g64)
+        well = usable & (dev32 <= 0.25 * tol).all(axis=1)
+        ill = usable & ~well
+        err = np.abs(g - g64)
+    bad = well[:, None] & ~(err <= tol)
+    assert not bad.any(), (np.argwhere(bad)[:5], g[bad][:5], g64[bad][:5])
+    bad2 = ill[:, None] & ~(err <= 10.0 * dev32 + tol)
+    assert not bad2.any(), (np.argwhere(bad2)[:5], g[bad2][:5], g64[bad2][:5], g32[bad2][:5])
+    return int(well.sum()), int(ill.sum())
 
 
 def test_adam_steps_match_oracle():
@@ -340,14 +382,18 @@ def test_adam_steps_match_oracle():
             kidx = idx[nodes["op"][idx] == synth.OP["const"]]
             if len(kidx) == 0:
                 continue
-            th = theta[kidx].copy()
-            mm = om[p, :len(kidx)].copy()
-            vv = ov[p, :len(kidx)].copy()
-            oracle.adam(th, gh[p, :len(kidx)], mm, vv, step, lr=1e-2)
-            om[p, :len(kidx)] = mm
-            ov[p, :len(kidx)] = vv
-            theta[kidx] = th
-            np.testing.assert_allclose(after["c"][kidx], th, rtol=2e-6, atol=2e-7)
+            # a slot whose gradient is not finite keeps its constant and state
+            fin = np.isfinite(gh[p, :len(kidx)])
+            kf = kidx[fin]
+            th = theta[kf].copy()
+            mm = om[p, :len(kidx)][fin].copy()
+            vv = ov[p, :len(kidx)][fin].copy()
+            oracle.adam(th, gh[p, :len(kidx)][fin], mm, vv, step, lr=1e-2)
+            om[p, np.flatnonzero(fin)] = mm
+            ov[p, np.flatnonzero(fin)] = vv
+            theta[kf] = th
+            np.testing.assert_allclose(after["c"][kf], th, rtol=2e-6, atol=2e-7)
+            np.testing.assert_array_equal(after["c"][kidx[~fin]], cur["c"][kidx[~fin]])
         theta = after["c"].astype(np.float64)
     assert np.array_equal(after["op"], nodes["op"])
 
@@ -376,24 +422,33 @@ def test_full_size_fitness_sampled(name, n_rows, k):
     idx = _sample(wl.offsets, k, 5)
     sn, so = _subset(wl.nodes, wl.offsets, idx)
     f64, st = oracle.fitness(sn, so, d.X, d.y, d.w, wl.metric)
-    # full-size rows are too many for per-row bounds; the FP32 oracle gives
-    # the conditioning of each sampled program instead
-    rel = np.abs(fit[idx] - f64) / np.maximum(np.abs(f64), 1e-30)
+    # full-size rows are too many for per-row bounds; the oracle's FP32 mode
+    # gives the conditioning of each sampled program instead (the loss of
+    # its FP32 values, summed in FP64)
     with np.errstate(all="ignore"):
-        p32 = oracle.predict32(sn, so, d.X)
-        ys = d.y.astype(np.float64)
-        wv = np.ones_like(ys) if d.w is None else d.w.astype(np.float64)
+        rel = np.abs(fit[idx] - f64) / np.maximum(np.abs(f64), 1e-30)
+        p32 = oracle.predict32(sn, so, d.X).astype(np.float64)
+        ys = d.y.astype(np.float64)[None, :]
+        wv = np.ones(d.n_rows) if d.w is None else d.w.astype(np.float64)
         if wl.metric in ("rmse", "mse"):
-            f32 = (((p32 - ys) ** 2) * wv).sum(1) / wv.sum()
-            if wl.metric == "rmse":
-                f32 = np.sqrt(f32)
+            rl = (p32 - ys) ** 2
+        elif wl.metric == "mae":
+            rl = np.abs(p32 - ys)
         else:
-            f32 = np.array([np.nan] * len(idx))
+            ap = np.abs(p32)
+            c = np.where(p32 >= 0, 1.0 - ys, ys)
+            rl = np.where(c == 0, 0.0, c * ap) + np.log1p(np.exp(-ap))
+        f32 = (rl * wv).sum(1) / wv.sum()
+        if wl.metric == "rmse":
+            f32 = np.sqrt(f32)
+    checked = 0
     for i in range(len(idx)):
-        if not np.isfinite(f64[i]):
-            continue
-        cond = abs(f32[i] - f64[i]) / max(abs(f64[i]), 1e-30) if np.isfinite(f32[i]) else 0.0
+        if not np.isfinite(f64[i]) or not np.isfinite(f32[i]):
+            continue  # FP32 range: the float evaluation itself overflows
+        cond = abs(f32[i] - f64[i]) / max(abs(f64[i]), 1e-30)
         assert rel[i] <= max(1e-4, 4 * cond), (name, idx[i], fit[idx[i]], f64[i], cond)
+        checked += 1
+    assert checked >= len(idx) // 2
 
 
 def test_full_size_const_grad_sampled():
@@ -405,9 +460,7 @@ def test_full_size_const_grad_sampled():
     idx = _sample(wl.offsets, 6, 9)
     sn, so = _subset(wl.nodes, wl.offsets, idx)
     g64, f64, gabs = oracle.const_grad(sn, so, d.X, d.y, None, "mse", with_abs=True)
-    v, e, fl = oracle.predict_bound(sn, so, d.X[:, :65536], ulps_fn=4.0)
-    for j, p in enumerate(idx):
-        if (fl[j] != 0).any() or not np.isfinite(g64[j]).all():
-            continue
-        tol = 1e-4 * np.maximum(gabs[j], 1e-3 * np.abs(g64[j]).max()) + 1e-7
-        assert np.all(np.abs(g[p] - g64[j]) <= tol), (p, g[p], g64[j])
+    g32, _ = oracle.const_grad32(sn, so, d.X, d.y, None, "mse")
+    _, _, fl = oracle.predict_bound(sn, so, d.X, ulps_fn=4.0)
+    strict, cond = _grad_check(g[idx], g64, g32, gabs, fl)
+    assert strict + cond >= 3, (strict, cond)
