@@ -104,10 +104,11 @@ enum gp_accum { GP_ACCUM_FP64 = 0, GP_ACCUM_KAHAN32 = 1 };
 /* Tunables of the batched evaluator; zero means "choose".  The choice is
  * the autotuned one for this problem shape when gp_autotune has run,
  * otherwise a fixed default.  Results are bit-identical for every choice
- * with the same chunk_rows (fixed reduction partition). */
+ * with the same rows_per_thread and chunk_rows (fixed reduction
+ * partition); blocks_per_sm never changes them. */
 typedef struct gp_eval_opts {
-    int rows_per_thread;  /* 4 or 8                                       */
-    int chunk_rows;       /* rows per work item, multiple of 32*rpt       */
+    int rows_per_thread;  /* 4 or 8 (default 8)                           */
+    int chunk_rows;       /* rows per work item, multiple of 256          */
     int blocks_per_sm;    /* resident blocks per SM of the persistent grid */
     int accum;            /* gp_accum                                     */
     int reserved[4];      /* must be 0                                    */

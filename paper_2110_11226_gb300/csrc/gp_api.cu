@@ -129,7 +129,7 @@ int64_t default_chunk(int n_progs, int64_t n_rows, int sms) {
     // chunks of at most 64K rows, multiples of 256 rows
     const double items_wanted = 16.0 * sms * 24.0;
     int64_t c = (int64_t)((double)n_rows * (double)n_progs / items_wanted);
-    c = std::max<int64_t>(c, 256);
+    c = std::max<int64_t>(c, 1024);  // a block's 8 warps x 128 rows
     c = std::min<int64_t>(c, 65536);
     c = round_up(c, 256);
     return std::min<int64_t>(c, round_up(n_rows, 256));
@@ -150,11 +150,10 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
             if (o.blocks_per_sm == 0) o.blocks_per_sm = it->second.blocks_per_sm;
         }
     }
-    if (o.rows_per_thread == 0) o.rows_per_thread = 4;
+    if (o.rows_per_thread == 0) o.rows_per_thread = 8;
     if (o.rows_per_thread != 4 && o.rows_per_thread != 8) return GP_ERR_ARG;
     if (o.chunk_rows == 0) o.chunk_rows = (int)default_chunk(n_progs, n_rows, c->sms);
-    if (o.chunk_rows < 32 * o.rows_per_thread || o.chunk_rows % (32 * o.rows_per_thread) != 0)
-        return GP_ERR_ARG;
+    if (o.chunk_rows < 256 || o.chunk_rows % 256 != 0) return GP_ERR_ARG;
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 32) return GP_ERR_ARG;
     if (o.accum != GP_ACCUM_FP64 && o.accum != GP_ACCUM_KAHAN32) return GP_ERR_ARG;
     *out = o;
@@ -225,11 +224,15 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
         ea.part = W.part;
         ea.dev_status = c->status;
         ea.vec_ok = vec ? 1 : 0;
+        // the deep class keeps 4 rows per thread (its 19-slot stack would
+        // otherwise leave room for one block per SM); the same chunk
+        // partition serves both
+        const int rpt_c = (cls == 0) ? rpt : 4;
         const int block = kEvalBlockThreads;
-        int occ = eval_info(rpt, fmode, cls, block, nullptr);
+        int occ = eval_info(rpt_c, fmode, cls, block, nullptr);
         if (occ < 1) occ = 1;
         int bps = pl.o.blocks_per_sm > 0 ? std::min(pl.o.blocks_per_sm, occ) : occ;
-        GP_CUDA(eval_launch(ea, rpt, fmode, c->sms * bps, block, st));
+        GP_CUDA(eval_launch(ea, rpt_c, fmode, c->sms * bps, block, st));
     }
     if (tev.second) GP_CUDA(cudaEventRecord(tev.second, st));
     FinalizeArgs fa{W.part, pl.n_chunks, n_progs, W.meta, W.sumw, metric, pl.o.accum,
@@ -362,7 +365,7 @@ int gp_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const 
     if (!out_pred) return GP_ERR_ARG;
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
-    const int64_t chunk = std::min<int64_t>(round_up(n_rows, 128), 4096);
+    const int64_t chunk = std::min<int64_t>(round_up(n_rows, 256), 4096);
     const int n_chunks = (int)((n_rows + chunk - 1) / chunk);
     Layout L = make_layout(n_progs, 1, false);
     {
@@ -556,7 +559,7 @@ int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs, const
     const int fmode = (n_feat <= 2) ? 2 : 0;
     for (int rpt : {4, 8}) {
         const int occ = eval_info(rpt, fmode, 0, kEvalBlockThreads, nullptr);
-        for (int64_t ch : {base_chunk, base_chunk * 2, std::max<int64_t>(base_chunk / 2, 256)}) {
+        for (int64_t ch : {base_chunk, std::max<int64_t>(base_chunk / 4, 1024)}) {
             const int64_t chr = round_up(std::min<int64_t>(ch, 65536), 256);
             for (int bps = 1; bps <= std::max(occ, 1); ++bps) {
                 gp_eval_opts o{};

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
     if (status == GP_PROG_OK && hw > GP_MAX_STACK) status = GP_PROG_TOO_DEEP;
     if (a.out_prog_status) a.out_prog_status[p] = status;
     if (status != GP_PROG_OK) {
-        out[0] = make_uint2(K_END, 0u);
+        out[0] = make_uint2(make_ins(OP_END, SRC_NONE, false, 0, 0), 0u);
         a.meta[p] = ProgMeta{1, status, 0, 0};
         atomicOr(a.dev_status, GP_DEV_BAD_PROGRAM);
         return;
@@ -156,29 +156,33 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
         const int ar = op_arity(nd.op);
         if (ar == 0) {
             if (mode[j]) continue;  // folded into its parent
-            const uint32_t id = (nd.op == GP_VAR) ? ((K_PUSH_X + sp) | kNeedsX) : (K_PUSH_C + sp);
-            out[n++] = make_uint2(id | ((uint32_t)(uint16_t)nd.feat << 16),
+            const uint32_t src = (nd.op == GP_VAR) ? SRC_X : SRC_C;
+            const bool spill = sp > 0;  // the old top goes to slot sp-1
+            out[n++] = make_uint2(make_ins(OP_PUSH, src, spill, spill ? sp - 1 : 0,
+                                           (uint32_t)(uint16_t)nd.feat),
                                   __float_as_uint(nd.c));
             ++sp;
         } else if (ar == 1) {
-            out[n++] = make_uint2(K_UN + (nd.op - GP_SQRT), 0u);
+            out[n++] = make_uint2(make_ins(OP_SQRT + (nd.op - GP_SQRT), SRC_NONE, false, 0, 0), 0u);
         } else {
-            const uint32_t b = nd.op - GP_ADD;
+            const uint32_t b = nd.op - GP_ADD;  // add, sub, mul, div
+            const uint32_t fwd[4] = {OP_ADD, OP_SUB, OP_MUL, OP_DIV};
+            const uint32_t rev[4] = {OP_ADD, OP_RSUB, OP_MUL, OP_RDIV};
             if (mode[j] == 0) {
-                out[n++] = make_uint2(K_BIN + b * kDeepSlots + (sp - 2), 0u);
+                // right operand in slot sp-2, left operand is t
+                out[n++] = make_uint2(make_ins(fwd[b], SRC_SLOT, false, sp - 2, 0), 0u);
                 --sp;
             } else {
                 const gp_node t = (mode[j] == 1) ? prog[j + 1 + size[j + 1]] : prog[j + 1];
-                uint32_t id;
-                if (mode[j] == 1) id = (t.op == GP_VAR ? (K_BIN_RX + b) | kNeedsX : K_BIN_RC + b);
-                else id = (t.op == GP_VAR ? (K_BIN_LX + b) | kNeedsX : K_BIN_LC + b);
-                out[n++] = make_uint2(id | ((uint32_t)(uint16_t)t.feat << 16),
+                const uint32_t src = (t.op == GP_VAR) ? SRC_X : SRC_C;
+                const uint32_t op = (mode[j] == 1) ? fwd[b] : rev[b];
+                out[n++] = make_uint2(make_ins(op, src, false, 0, (uint32_t)(uint16_t)t.feat),
                                       __float_as_uint(t.c));
             }
         }
         if (sp > depth) depth = sp;
     }
-    out[n++] = make_uint2(K_END, 0u);
+    out[n++] = make_uint2(make_ins(OP_END, SRC_NONE, false, 0, 0), 0u);
     a.meta[p] = ProgMeta{n, GP_PROG_OK, depth, n_consts};
 }
 

@@ -1,6 +1,6 @@
-// gp_eval_r4_f0.cu -- instance of the batched evaluator: 4 rows per
+// gp_eval_r4_f0.cu -- instances of the batched evaluator: 4 rows per
 // thread, feature mode 0 (feature columns loaded per reference),
-// both depth classes.
+// both depth classes (7 or 19 shared-memory stack slots).
 #include "gp_interp.cuh"
 
 namespace gpk {

@@ -1,6 +1,6 @@
-// gp_eval_r8_f2.cu -- instance of the batched evaluator: 8 rows per
+// gp_eval_r8_f2.cu -- instances of the batched evaluator: 8 rows per
 // thread, feature mode 2 (columns 0 and 1 held in registers),
-// both depth classes.
+// both depth classes (7 or 19 shared-memory stack slots).
 #include "gp_interp.cuh"
 
 namespace gpk {

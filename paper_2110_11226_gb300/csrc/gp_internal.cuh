@@ -1,20 +1,22 @@
 // gp_internal.cuh -- definitions shared by the translation units of libgp.
 //
 // Compiled program form.  The device pre-pass turns each prefix list into a
-// sequence of register-stack instructions, in reverse-scan order (Sec.
-// III-A: the list is evaluated by scanning it from the end).  The top of
-// the stack lives in a register array `t`; deeper values in a register
-// array `s[slot]`.  Each instruction names its slot at compile time so the
-// interpreter can address registers with constant indices:
-//   PUSH_X(k)/PUSH_C(k)  stack height k before the push: s[k-1] = t (k>0),
-//                        t = X[feat] / c
-//   BIN(op, k)           t = op(t, s[k])      (left = t, first pop)
-//   UN(op)               t = op(t)
-//   BIN_RX/RC(op)        t = op(t, X[feat] / c)  right child is a terminal
-//   BIN_LX/LC(op)        t = op(X[feat] / c, t)  left child is a terminal
-//   END
-// The folded forms evaluate the same operations on the same operands as
-// the plain reverse scan, so every result is bit-identical to it.
+// sequence of stack-machine instructions in reverse-scan order (Sec. III-A:
+// the list is evaluated by scanning it from the end).  The top of the stack
+// lives in registers (t); deeper values live in a per-warp shared-memory
+// stack whose slot numbers the pre-pass resolves, so the interpreter's code
+// has one body per operation and no per-slot variants.  An instruction is
+//   op    what to do with t and the operand u:
+//         PUSH (t = u), t+u, t-u, u-t, t*u, div(t,u), div(u,t), f(t) for the
+//         nine unary functions, END
+//   src   where u comes from: nothing, a stack slot (popped), X[feat], c
+//   spill save t to stack slot `slot` first (a push onto a non-empty stack)
+// A binary node whose right child is a terminal takes that terminal as u
+// (t = f(t, u)); failing that, one whose left child is a terminal takes it
+// as u with the reversed operation (t = f(u, t)); otherwise the right
+// operand sits in a stack slot.  These forms evaluate the same operations on
+// the same operands as the plain reverse scan, so every result is
+// bit-identical to it.
 #pragma once
 
 #include <cstdint>
@@ -26,23 +28,23 @@ namespace gpk {
 
 constexpr int kCodeStride = 256;   // instructions per program (255 + END)
 constexpr int kEvalBlockThreads = 256;  // threads per block of the evaluator
-constexpr uint32_t kNeedsX = 0x100u;  // instruction bit 8: reads X[feat]
 constexpr int kDeepSlots = GP_MAX_STACK - 1;  // s[0..18]
 constexpr float kThr = 0.001f;     // protected-operator threshold
 
-// instruction ids (low 8 bits of ins.x; feature index in the high 16 bits)
+// instruction word x: op in bits 0-4, src in bits 5-6, spill in bit 7,
+// stack slot in bits 8-15, feature index in bits 16-31; word y: constant
 enum : uint32_t {
-    K_PUSH_X = 0,                     // + k, k = 0..19
-    K_PUSH_C = 20,                    // + k
-    K_BIN = 40,                       // + b*19 + k, b = op - GP_ADD (0..3)
-    K_UN = K_BIN + 4 * kDeepSlots,    // 116 + (op - GP_SQRT), 9 unary ops
-    K_BIN_RX = K_UN + 9,              // 125 + b
-    K_BIN_RC = K_BIN_RX + 4,          // 129 + b
-    K_BIN_LX = K_BIN_RC + 4,          // 133 + b
-    K_BIN_LC = K_BIN_LX + 4,          // 137 + b
-    K_END = K_BIN_LC + 4,             // 141
-    K_COUNT = K_END + 1
+    OP_PUSH = 0, OP_ADD = 1, OP_SUB = 2, OP_RSUB = 3, OP_MUL = 4, OP_DIV = 5,
+    OP_RDIV = 6, OP_SQRT = 7, OP_LOG = 8, OP_EXP = 9, OP_SIN = 10, OP_COS = 11,
+    OP_TAN = 12, OP_ABS = 13, OP_NEG = 14, OP_INV = 15, OP_END = 16
 };
+enum : uint32_t { SRC_NONE = 0, SRC_SLOT = 1, SRC_X = 2, SRC_C = 3 };
+constexpr uint32_t kSpill = 0x80u;
+
+__host__ __device__ constexpr uint32_t make_ins(uint32_t op, uint32_t src, bool spill,
+                                                uint32_t slot, uint32_t feat) {
+    return op | (src << 5) | (spill ? kSpill : 0u) | (slot << 8) | (feat << 16);
+}
 
 // per-program metadata written by the pre-pass
 struct ProgMeta {
@@ -53,8 +55,8 @@ struct ProgMeta {
 };
 
 // depth classes: programs whose compiled stack fits kSmallDepth run in a
-// kernel instance with fewer deep register slots
-constexpr int kSmallDepth = 8;     // s[0..6] + t
+// kernel instance with a smaller shared-memory stack (more blocks per SM)
+constexpr int kSmallDepth = 8;     // 7 stack slots + t
 constexpr int kNumClasses = 2;
 
 // Workspace carved out of one device allocation (all offsets 256-aligned).
