@@ -151,7 +151,8 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
         }
     }
     if (o.rows_per_thread == 0) o.rows_per_thread = 8;
-    if (o.rows_per_thread != 4 && o.rows_per_thread != 8) return GP_ERR_ARG;
+    if (o.rows_per_thread != 4 && o.rows_per_thread != 8 && o.rows_per_thread != 16)
+        return GP_ERR_ARG;
     if (o.chunk_rows == 0) o.chunk_rows = (int)default_chunk(n_progs, n_rows, c->sms);
     if (o.chunk_rows < 256 || o.chunk_rows % 256 != 0) return GP_ERR_ARG;
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 32) return GP_ERR_ARG;
@@ -162,12 +163,14 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
 
 int eval_info(int rpt, int fmode, int cls, int block, int *regs) {
     if (rpt == 4) return fmode == 2 ? info_eval_r4_f2(cls, block, regs) : info_eval_r4_f0(cls, block, regs);
-    return fmode == 2 ? info_eval_r8_f2(cls, block, regs) : info_eval_r8_f0(cls, block, regs);
+    if (rpt == 8) return fmode == 2 ? info_eval_r8_f2(cls, block, regs) : info_eval_r8_f0(cls, block, regs);
+    return fmode == 2 ? info_eval_r16_f2(cls, block, regs) : info_eval_r16_f0(cls, block, regs);
 }
 
 cudaError_t eval_launch(const EvalArgs &a, int rpt, int fmode, int grid, int block, cudaStream_t st) {
     if (rpt == 4) return fmode == 2 ? launch_eval_r4_f2(a, grid, block, st) : launch_eval_r4_f0(a, grid, block, st);
-    return fmode == 2 ? launch_eval_r8_f2(a, grid, block, st) : launch_eval_r8_f0(a, grid, block, st);
+    if (rpt == 8) return fmode == 2 ? launch_eval_r8_f2(a, grid, block, st) : launch_eval_r8_f0(a, grid, block, st);
+    return fmode == 2 ? launch_eval_r16_f2(a, grid, block, st) : launch_eval_r16_f0(a, grid, block, st);
 }
 
 struct Plan {
@@ -557,7 +560,7 @@ int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs, const
     const int64_t base_chunk = default_chunk(n_progs, n_rows, c->sms);
     std::vector<gp_eval_opts> cands;
     const int fmode = (n_feat <= 2) ? 2 : 0;
-    for (int rpt : {4, 8}) {
+    for (int rpt : {4, 8, 16}) {
         const int occ = eval_info(rpt, fmode, 0, kEvalBlockThreads, nullptr);
         for (int64_t ch : {base_chunk, std::max<int64_t>(base_chunk / 4, 1024)}) {
             const int64_t chr = round_up(std::min<int64_t>(ch, 65536), 256);

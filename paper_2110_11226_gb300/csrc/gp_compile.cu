@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
     if (status == GP_PROG_OK && hw > GP_MAX_STACK) status = GP_PROG_TOO_DEEP;
     if (a.out_prog_status) a.out_prog_status[p] = status;
     if (status != GP_PROG_OK) {
-        out[0] = make_uint2(make_ins(OP_END, SRC_NONE, false, 0, 0), 0u);
+        out[0] = make_uint2(make_ins(OP_END, 0, 0), 0u);
         a.meta[p] = ProgMeta{1, status, 0, 0};
         atomicOr(a.dev_status, GP_DEV_BAD_PROGRAM);
         return;
@@ -156,33 +156,35 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
         const int ar = op_arity(nd.op);
         if (ar == 0) {
             if (mode[j]) continue;  // folded into its parent
-            const uint32_t src = (nd.op == GP_VAR) ? SRC_X : SRC_C;
+            const bool x = nd.op == GP_VAR;
             const bool spill = sp > 0;  // the old top goes to slot sp-1
-            out[n++] = make_uint2(make_ins(OP_PUSH, src, spill, spill ? sp - 1 : 0,
-                                           (uint32_t)(uint16_t)nd.feat),
+            const uint32_t op = spill ? (x ? OP_PUSH_X_SP : OP_PUSH_C_SP) : (x ? OP_PUSH_X : OP_PUSH_C);
+            out[n++] = make_uint2(make_ins(op, spill ? sp - 1 : 0, (uint32_t)(uint16_t)nd.feat),
                                   __float_as_uint(nd.c));
             ++sp;
         } else if (ar == 1) {
-            out[n++] = make_uint2(make_ins(OP_SQRT + (nd.op - GP_SQRT), SRC_NONE, false, 0, 0), 0u);
+            out[n++] = make_uint2(make_ins(OP_SQRT + (nd.op - GP_SQRT), 0, 0), 0u);
         } else {
-            const uint32_t b = nd.op - GP_ADD;  // add, sub, mul, div
-            const uint32_t fwd[4] = {OP_ADD, OP_SUB, OP_MUL, OP_DIV};
-            const uint32_t rev[4] = {OP_ADD, OP_RSUB, OP_MUL, OP_RDIV};
+            const int b = nd.op - GP_ADD;  // add, sub, mul, div
             if (mode[j] == 0) {
                 // right operand in slot sp-2, left operand is t
-                out[n++] = make_uint2(make_ins(fwd[b], SRC_SLOT, false, sp - 2, 0), 0u);
+                const uint32_t ops[4] = {OP_ADD_S, OP_SUB_S, OP_MUL_S, OP_DIV_S};
+                out[n++] = make_uint2(make_ins(ops[b], sp - 2, 0), 0u);
                 --sp;
             } else {
                 const gp_node t = (mode[j] == 1) ? prog[j + 1 + size[j + 1]] : prog[j + 1];
-                const uint32_t src = (t.op == GP_VAR) ? SRC_X : SRC_C;
-                const uint32_t op = (mode[j] == 1) ? fwd[b] : rev[b];
-                out[n++] = make_uint2(make_ins(op, src, false, 0, (uint32_t)(uint16_t)t.feat),
+                const int x = (t.op == GP_VAR) ? 0 : 1;  // X or C variant
+                // right terminal: t = op(t, u); left terminal: t = op(u, t)
+                const uint32_t fwd[4] = {OP_ADD_X, OP_SUB_X, OP_MUL_X, OP_DIV_X};
+                const uint32_t rev[4] = {OP_ADD_X, OP_RSUB_X, OP_MUL_X, OP_RDIV_X};
+                const uint32_t op = ((mode[j] == 1) ? fwd[b] : rev[b]) + x;
+                out[n++] = make_uint2(make_ins(op, 0, (uint32_t)(uint16_t)t.feat),
                                       __float_as_uint(t.c));
             }
         }
         if (sp > depth) depth = sp;
     }
-    out[n++] = make_uint2(make_ins(OP_END, SRC_NONE, false, 0, 0), 0u);
+    out[n++] = make_uint2(make_ins(OP_END, 0, 0), 0u);
     a.meta[p] = ProgMeta{n, GP_PROG_OK, depth, n_consts};
 }
 

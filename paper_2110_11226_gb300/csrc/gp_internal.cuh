@@ -4,19 +4,22 @@
 // sequence of stack-machine instructions in reverse-scan order (Sec. III-A:
 // the list is evaluated by scanning it from the end).  The top of the stack
 // lives in registers (t); deeper values live in a per-warp shared-memory
-// stack whose slot numbers the pre-pass resolves, so the interpreter's code
-// has one body per operation and no per-slot variants.  An instruction is
-//   op    what to do with t and the operand u:
-//         PUSH (t = u), t+u, t-u, u-t, t*u, div(t,u), div(u,t), f(t) for the
-//         nine unary functions, END
-//   src   where u comes from: nothing, a stack slot (popped), X[feat], c
-//   spill save t to stack slot `slot` first (a push onto a non-empty stack)
-// A binary node whose right child is a terminal takes that terminal as u
-// (t = f(t, u)); failing that, one whose left child is a terminal takes it
-// as u with the reversed operation (t = f(u, t)); otherwise the right
-// operand sits in a stack slot.  These forms evaluate the same operations on
-// the same operands as the plain reverse scan, so every result is
-// bit-identical to it.
+// stack whose slot numbers the pre-pass resolves.  Each instruction is one
+// of 30 operations that name their operand source, so the interpreter's
+// only branch per instruction is one switch:
+//   PUSH_X / PUSH_C        t = X[feat] / c
+//   PUSH_X_SP / PUSH_C_SP  stack[slot] = t first (push onto a non-empty stack)
+//   op_S                   t = op(t, stack[slot])      (right operand popped)
+//   op_X / op_C            t = op(t, X[feat] / c)      (right child a terminal)
+//   RSUB_*, RDIV_*         t = op(X[feat] / c, t)      (left child a terminal)
+//   unary                  t = f(t)
+//   END
+// A binary node whose right child is a terminal takes it inline; failing
+// that, one whose left child is a terminal takes it inline with the
+// reversed operation (add and mul commute exactly in IEEE arithmetic);
+// otherwise its right operand sits in a stack slot.  These forms evaluate
+// the same operations on the same operands as the plain reverse scan, so
+// every result is bit-identical to it.
 #pragma once
 
 #include <cstdint>
@@ -31,19 +34,20 @@ constexpr int kEvalBlockThreads = 256;  // threads per block of the evaluator
 constexpr int kDeepSlots = GP_MAX_STACK - 1;  // s[0..18]
 constexpr float kThr = 0.001f;     // protected-operator threshold
 
-// instruction word x: op in bits 0-4, src in bits 5-6, spill in bit 7,
-// stack slot in bits 8-15, feature index in bits 16-31; word y: constant
+// instruction word x: op in bits 0-4, stack slot in bits 8-15, feature
+// index in bits 16-31; word y: the constant
 enum : uint32_t {
-    OP_PUSH = 0, OP_ADD = 1, OP_SUB = 2, OP_RSUB = 3, OP_MUL = 4, OP_DIV = 5,
-    OP_RDIV = 6, OP_SQRT = 7, OP_LOG = 8, OP_EXP = 9, OP_SIN = 10, OP_COS = 11,
-    OP_TAN = 12, OP_ABS = 13, OP_NEG = 14, OP_INV = 15, OP_END = 16
+    OP_PUSH_X = 0, OP_PUSH_C = 1, OP_PUSH_X_SP = 2, OP_PUSH_C_SP = 3,
+    OP_ADD_S = 4, OP_SUB_S = 5, OP_MUL_S = 6, OP_DIV_S = 7,
+    OP_ADD_X = 8, OP_ADD_C = 9, OP_SUB_X = 10, OP_SUB_C = 11,
+    OP_RSUB_X = 12, OP_RSUB_C = 13, OP_MUL_X = 14, OP_MUL_C = 15,
+    OP_DIV_X = 16, OP_DIV_C = 17, OP_RDIV_X = 18, OP_RDIV_C = 19,
+    OP_SQRT = 20, OP_LOG = 21, OP_EXP = 22, OP_SIN = 23, OP_COS = 24,
+    OP_TAN = 25, OP_ABS = 26, OP_NEG = 27, OP_INV = 28, OP_END = 29
 };
-enum : uint32_t { SRC_NONE = 0, SRC_SLOT = 1, SRC_X = 2, SRC_C = 3 };
-constexpr uint32_t kSpill = 0x80u;
 
-__host__ __device__ constexpr uint32_t make_ins(uint32_t op, uint32_t src, bool spill,
-                                                uint32_t slot, uint32_t feat) {
-    return op | (src << 5) | (spill ? kSpill : 0u) | (slot << 8) | (feat << 16);
+__host__ __device__ constexpr uint32_t make_ins(uint32_t op, uint32_t slot, uint32_t feat) {
+    return op | (slot << 8) | (feat << 16);
 }
 
 // per-program metadata written by the pre-pass
@@ -140,6 +144,8 @@ GP_EVAL_INSTANCE(4, 2)
 GP_EVAL_INSTANCE(4, 0)
 GP_EVAL_INSTANCE(8, 2)
 GP_EVAL_INSTANCE(8, 0)
+GP_EVAL_INSTANCE(16, 2)
+GP_EVAL_INSTANCE(16, 0)
 #undef GP_EVAL_INSTANCE
 cudaError_t launch_predict(const EvalArgs &a, int grid, int block,
                            cudaStream_t st);

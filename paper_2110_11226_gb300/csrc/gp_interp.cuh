@@ -17,11 +17,12 @@
 // coalesced loads from the column-major X).  The top of the stack is the
 // register array t[RPT]; deeper values sit in the warp's slice of a
 // shared-memory stack, one float4 per (slot, group of 4 rows, lane), so a
-// push or pop is one or two conflict-free 16-byte accesses per lane.  The
-// dispatch has 17 cases, one per operation: measured on this GPU, the cost
-// of an interpreter's dispatch grows with the number of distinct code
-// locations it jumps between, so the operand source (stack slot, X column,
-// constant) and the spill are handled by shared code before the switch.
+// push or pop is one or two conflict-free 16-byte accesses per lane.  Each
+// instruction costs one switch (30 cases) and nothing else that branches:
+// measured on this GPU, an interpreter's dispatch latency grows with every
+// dependent branch per instruction (about 20-40 cycles each) and with the
+// number of distinct code locations it jumps between, so operand source and
+// spill are part of the operation code rather than separate tests.
 //
 // After a sub-tile each lane turns its RPT predictions into weighted losses
 // (the fused form of the paper's matrix-vector loss step) and adds them into
@@ -37,8 +38,10 @@
 
 namespace gpk {
 
-constexpr int kEvalBlock = kEvalBlockThreads;
-constexpr int kEvalWarps = kEvalBlock / 32;
+// warps per block: 8, or 4 at 16 rows per thread (its shared-memory stack
+// is twice as large per warp)
+template <int RPT>
+__host__ __device__ constexpr int eval_warps() { return RPT >= 16 ? 4 : 8; }
 
 // ---- the function set (FP32, IEEE operators, no contraction) -----------
 __device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b); }
@@ -107,90 +110,113 @@ __device__ __forceinline__ float4 *stack_at(float4 *stk, uint32_t slot, int q) {
 
 // Runs one compiled program over RPT rows per lane; returns the top of the
 // stack in t.  stk = this warp's stack slice, already offset by the lane.
-template <int RPT, int FMODE>
+// The instruction buffer ends with OP_END up to its last entry, so the loop
+// ends within kCodeStride + 1 steps whatever the buffer holds; op values
+// that name no operation act as OP_END and stack slots are clamped to the
+// stack, so no instruction word can make it run away or leave its memory.
+template <int RPT, int NSLOT, int FMODE>
 __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restrict__ cbuf,
-                                          int n_ins, const float (&x0)[RPT],
-                                          const float (&x1)[RPT], const float *__restrict__ X,
-                                          int64_t ld, int64_t r0, int64_t re, bool vec,
-                                          float4 *stk) {
+                                          const float (&x0)[RPT], const float (&x1)[RPT],
+                                          const float *__restrict__ X, int64_t ld, int64_t r0,
+                                          int64_t re, bool vec, float4 *stk) {
 #pragma unroll
     for (int j = 0; j < RPT; ++j) t[j] = 0.0f;
+    int pc = 0;
     uint2 ins = cbuf[0];
-    for (int pc = 0; pc < n_ins; ++pc) {
-        const uint2 nx = cbuf[pc + 1];
+#pragma unroll 1
+    for (;;) {
+        const uint2 nx = cbuf[min(pc + 1, kCodeStride)];
+        ++pc;
         const uint32_t w = ins.x;
-        const uint32_t op = w & 31u;
-        const uint32_t src = (w >> 5) & 3u;
-        const uint32_t slot = (w >> 8) & 255u;
         const float c = __uint_as_float(ins.y);
-        if (w & kSpill) {
-#pragma unroll
-            for (int q = 0; q < RPT / 4; ++q)
-                *stack_at<RPT>(stk, slot, q) = make_float4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]);
-        }
-        float u[RPT];
-        if (src == SRC_SLOT) {
-#pragma unroll
-            for (int q = 0; q < RPT / 4; ++q) {
-                const float4 v = *stack_at<RPT>(stk, slot, q);
-                u[4 * q] = v.x;
-                u[4 * q + 1] = v.y;
-                u[4 * q + 2] = v.z;
-                u[4 * q + 3] = v.w;
-            }
-        } else if (src == SRC_X) {
-            const int feat = (int)(w >> 16);
-            if (FMODE == 2) {
-#pragma unroll
-                for (int j = 0; j < RPT; ++j) u[j] = feat ? x1[j] : x0[j];
-            } else {
-                load_rows<RPT>(u, X + (int64_t)feat * ld, r0, re, vec);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < RPT; ++j) u[j] = c;
-        }
-#define GP_OP(code, expr)                                                       \
-    case code:                                                                  \
-        _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = expr;            \
-        break;
-        bool done = false;
-        switch (op) {
-            GP_OP(OP_PUSH, u[j])
-            GP_OP(OP_ADD, f_add(t[j], u[j]))
-            GP_OP(OP_SUB, f_sub(t[j], u[j]))
-            GP_OP(OP_RSUB, f_sub(u[j], t[j]))
-            GP_OP(OP_MUL, f_mul(t[j], u[j]))
-            GP_OP(OP_DIV, f_div(t[j], u[j]))
-            GP_OP(OP_RDIV, f_div(u[j], t[j]))
-            GP_OP(OP_SQRT, f_sqrt(t[j]))
-            GP_OP(OP_LOG, f_log(t[j]))
-            GP_OP(OP_EXP, f_exp(t[j]))
-            GP_OP(OP_SIN, gp_sin(t[j]))
-            GP_OP(OP_COS, gp_cos(t[j]))
-            GP_OP(OP_TAN, gp_tan(t[j]))
-            GP_OP(OP_ABS, f_abs(t[j]))
-            GP_OP(OP_NEG, f_neg(t[j]))
-            GP_OP(OP_INV, f_inv(t[j]))
-            default:
-                done = true;  // OP_END
-                break;
-        }
-#undef GP_OP
-        if (done) break;
         ins = nx;
+// operand helpers: stack slot, X column, constant
+#define GP_SLOT_LOAD(u)                                                         \
+    {                                                                           \
+        const uint32_t sl = min((w >> 8) & 255u, (uint32_t)NSLOT - 1u);         \
+        _Pragma("unroll") for (int q = 0; q < RPT / 4; ++q) {                   \
+            const float4 v = *stack_at<RPT>(stk, sl, q);                        \
+            u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w; \
+        }                                                                       \
     }
+#define GP_SPILL()                                                              \
+    {                                                                           \
+        const uint32_t sl = min((w >> 8) & 255u, (uint32_t)NSLOT - 1u);         \
+        _Pragma("unroll") for (int q = 0; q < RPT / 4; ++q)                     \
+            *stack_at<RPT>(stk, sl, q) = make_float4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]); \
+    }
+#define GP_X_LOAD(u)                                                            \
+    {                                                                           \
+        const int feat = (int)(w >> 16);                                        \
+        if (FMODE == 2) {                                                       \
+            _Pragma("unroll") for (int j = 0; j < RPT; ++j) u[j] = feat ? x1[j] : x0[j]; \
+        } else {                                                                \
+            load_rows<RPT>(u, X + (int64_t)feat * ld, r0, re, vec);             \
+        }                                                                       \
+    }
+#define GP_T(expr) _Pragma("unroll") for (int j = 0; j < RPT; ++j) t[j] = expr;
+#define GP_U_C(u) _Pragma("unroll") for (int j = 0; j < RPT; ++j) u[j] = c;
+        float u[RPT];
+        switch (w & 31u) {
+            case OP_PUSH_X: GP_X_LOAD(u) GP_T(u[j]) break;
+            case OP_PUSH_C: GP_T(c) break;
+            case OP_PUSH_X_SP: GP_SPILL() GP_X_LOAD(u) GP_T(u[j]) break;
+            case OP_PUSH_C_SP: GP_SPILL() GP_T(c) break;
+            case OP_ADD_S: GP_SLOT_LOAD(u) GP_T(f_add(t[j], u[j])) break;
+            case OP_SUB_S: GP_SLOT_LOAD(u) GP_T(f_sub(t[j], u[j])) break;
+            case OP_MUL_S: GP_SLOT_LOAD(u) GP_T(f_mul(t[j], u[j])) break;
+            case OP_DIV_S: GP_SLOT_LOAD(u) goto div_tu;
+            case OP_ADD_X: GP_X_LOAD(u) GP_T(f_add(t[j], u[j])) break;
+            case OP_ADD_C: GP_T(f_add(t[j], c)) break;
+            case OP_SUB_X: GP_X_LOAD(u) GP_T(f_sub(t[j], u[j])) break;
+            case OP_SUB_C: GP_T(f_sub(t[j], c)) break;
+            case OP_RSUB_X: GP_X_LOAD(u) GP_T(f_sub(u[j], t[j])) break;
+            case OP_RSUB_C: GP_T(f_sub(c, t[j])) break;
+            case OP_MUL_X: GP_X_LOAD(u) GP_T(f_mul(t[j], u[j])) break;
+            case OP_MUL_C: GP_T(f_mul(t[j], c)) break;
+            case OP_DIV_X: GP_X_LOAD(u) goto div_tu;
+            case OP_DIV_C: GP_U_C(u) goto div_tu;
+            case OP_RDIV_X: GP_X_LOAD(u) goto div_ut;
+            case OP_RDIV_C: GP_U_C(u) goto div_ut;
+            case OP_SQRT: GP_T(f_sqrt(t[j])) break;
+            case OP_LOG: GP_T(f_log(t[j])) break;
+            case OP_EXP: GP_T(f_exp(t[j])) break;
+            case OP_SIN:
+            case OP_COS:
+            case OP_TAN: trig_rows<RPT>(t, (int)(w & 31u) - OP_SIN); break;
+            case OP_ABS: GP_T(f_abs(t[j])) break;
+            case OP_NEG: GP_T(f_neg(t[j])) break;
+            case OP_INV: GP_T(f_inv(t[j])) break;
+            default:  // OP_END and anything that is not an operation
+                goto done;
+        }
+        continue;
+        // division has one body per operand order, shared by its operand cases
+    div_tu:
+        GP_T(f_div(t[j], u[j]))
+        continue;
+    div_ut:
+        GP_T(f_div(u[j], t[j]))
+#undef GP_T
+#undef GP_U_C
+#undef GP_X_LOAD
+#undef GP_SPILL
+#undef GP_SLOT_LOAD
+    }
+done:;
 }
 
 // shared memory of one block: the program's instructions, then the stack
 template <int RPT, int NSLOT>
 constexpr size_t eval_smem_bytes() {
     return (size_t)(kCodeStride + 1) * sizeof(uint2) +
-           (size_t)kEvalWarps * NSLOT * (RPT / 4) * 32 * sizeof(float4);
+           (size_t)eval_warps<RPT>() * NSLOT * (RPT / 4) * 32 * sizeof(float4);
 }
 
 template <int RPT, int NSLOT, int FMODE, bool PRED>
-__global__ void __launch_bounds__(kEvalBlock) eval_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(eval_warps<RPT>() * 32) eval_kernel(const EvalArgs a) {
+    constexpr int kEvalWarps = eval_warps<RPT>();
+    constexpr int kEvalBlock = kEvalWarps * 32;
     extern __shared__ float4 smem_eval[];
     uint2 *cbuf = reinterpret_cast<uint2 *>(smem_eval);
     float4 *stack_all = smem_eval + ((kCodeStride + 1) * sizeof(uint2) + 15) / 16;
@@ -230,8 +256,10 @@ __global__ void __launch_bounds__(kEvalBlock) eval_kernel(const EvalArgs a) {
             __syncthreads();  // s_item is rewritten at the top
             continue;
         }
-        for (int i = threadIdx.x; i < m.n_ins; i += kEvalBlock)
-            cbuf[i] = a.code[(size_t)p * kCodeStride + i];
+        // the program, then OP_END up to and including the last entry
+        for (int i = threadIdx.x; i <= kCodeStride; i += kEvalBlock)
+            cbuf[i] = (i < m.n_ins) ? a.code[(size_t)p * kCodeStride + i]
+                                    : make_uint2(make_ins(OP_END, 0, 0), 0u);
         __syncthreads();
 
         float ks = 0.0f, kc = 0.0f;
@@ -251,7 +279,7 @@ __global__ void __launch_bounds__(kEvalBlock) eval_kernel(const EvalArgs a) {
                 for (int j = 0; j < RPT; ++j) x0[j] = x1[j] = 0.0f;
             }
             float t[RPT];
-            interpret<RPT, FMODE>(t, cbuf, m.n_ins, x0, x1, a.X, a.ld, r0, re, vec, stk);
+            interpret<RPT, NSLOT, FMODE>(t, cbuf, x0, x1, a.X, a.ld, r0, re, vec, stk);
             if (PRED) {
                 float *dst = a.pred + (size_t)p * a.n_rows;
 #pragma unroll
@@ -293,7 +321,7 @@ cudaError_t launch_eval_t(const EvalArgs &a, int grid, int block, cudaStream_t s
     auto k = eval_kernel<RPT, NSLOT, FMODE, PRED>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kEvalBlock, smem, st>>>(a);
+    k<<<grid, eval_warps<RPT>() * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -308,7 +336,8 @@ int info_t(int block, int *regs) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kEvalBlock, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, eval_warps<RPT>() * 32, smem) != cudaSuccess)
+        return 0;
     return n;
 }
 

@@ -29,14 +29,14 @@ constexpr float kS0 = -0.166666672f, kS1 = 0.00833332911f, kS2 = -0.000198393129
 constexpr float kC0 = 0.0416666679f, kC1 = -0.00138888834f, kC2 = 2.47994594e-05f,
                 kC3 = -2.72057548e-07f;
 
-static __device__ __noinline__ float gp_sin_slow(float x) { return sinf(x); }
-static __device__ __noinline__ float gp_cos_slow(float x) { return cosf(x); }
-static __device__ __noinline__ float gp_tan_slow(float x) { return tanf(x); }
-
-// r = x - j pi/2 with j = rint(x 2/pi); q = j
+// r = x - j pi/2 with j the integer nearest x 2/pi, q = j mod 4.  Adding
+// 1.5 * 2^23 rounds to an integer in the FMA pipe, and for |j| < 2^22 the
+// two's-complement low bits of that sum's encoding are j's low bits.
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
 __device__ __forceinline__ float trig_reduce(float x, int &q) {
-    const float j = rintf(__fmul_rn(x, kTwoOverPi));
-    q = (int)j;
+    const float jm = __fmaf_rn(x, kTwoOverPi, kRoundMagic);
+    const float j = __fsub_rn(jm, kRoundMagic);
+    q = __float_as_int(jm);
     float r = __fmaf_rn(-j, kPio2Hi, x);
     r = __fmaf_rn(-j, kPio2Mid, r);
     r = __fmaf_rn(-j, kPio2Lo, r);
@@ -58,34 +58,49 @@ __device__ __forceinline__ float cos_poly(float s) {
     return __fmaf_rn(p, s, 1.0f);
 }
 
-// quadrant q (mod 4) of x = q pi/2 + r: sin x = sin r, cos r, -sin r, -cos r
-__device__ __forceinline__ float gp_sin(float x) {
-    if (!(fabsf(x) < kTrigFast)) return gp_sin_slow(x);
-    int q;
-    const float r = trig_reduce(x, q);
-    const float s = __fmul_rn(r, r);
-    const float v = (q & 1) ? cos_poly(s) : sin_poly(r, s);
-    return (q & 2) ? -v : v;
+static __device__ __noinline__ float trig_slow(float x, int kind) {
+    return kind == 0 ? sinf(x) : (kind == 1 ? cosf(x) : tanf(x));
 }
 
-__device__ __forceinline__ float gp_cos(float x) {
-    if (!(fabsf(x) < kTrigFast)) return gp_cos_slow(x);
-    int q;
-    const float r = trig_reduce(x, q);
-    const float s = __fmul_rn(r, r);
-    q += 1;
-    const float v = (q & 1) ? cos_poly(s) : sin_poly(r, s);
-    return (q & 2) ? -v : v;
-}
-
-// tan x = sin r / cos r (q even) or -cos r / sin r (q odd)
-__device__ __forceinline__ float gp_tan(float x) {
-    if (!(fabsf(x) < kTrigFast)) return gp_tan_slow(x);
-    int q;
-    const float r = trig_reduce(x, q);
-    const float s = __fmul_rn(r, r);
-    const float sn = sin_poly(r, s), cs = cos_poly(s);
-    return (q & 1) ? -__fdiv_rn(cs, sn) : __fdiv_rn(sn, cs);
+// Applies sin (kind 0), cos (1) or tan (2) to all RPT rows of a lane with
+// one body for the three: reduction and both polynomials on every row
+// without branching (so the rows' chains interleave), then the quadrant
+// select (sin, cos) or the quotient (tan); rows outside the fast path
+// (|x| >= 65536, inf, NaN) are redone by CUDA's function behind one test
+// for the whole group.
+template <int RPT>
+__device__ __forceinline__ void trig_rows(float (&t)[RPT], int kind) {
+    float sn[RPT], cs[RPT];
+    int q[RPT];
+    bool slow = false;
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const float r = trig_reduce(t[j], q[j]);
+        const float s = __fmul_rn(r, r);
+        sn[j] = sin_poly(r, s);
+        cs[j] = cos_poly(s);
+        slow |= !(fabsf(t[j]) < kTrigFast);
+    }
+    float v[RPT];
+    if (kind == 2) {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j)
+            v[j] = (q[j] & 1) ? -__fdiv_rn(cs[j], sn[j]) : __fdiv_rn(sn[j], cs[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int qq = q[j] + kind;
+            const float a = (qq & 1) ? cs[j] : sn[j];
+            v[j] = (qq & 2) ? -a : a;
+        }
+    }
+    if (slow) {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j)
+            if (!(fabsf(t[j]) < kTrigFast)) v[j] = trig_slow(t[j], kind);
+    }
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) t[j] = v[j];
 }
 
 }  // namespace gpk

@@ -1,7 +1,9 @@
 // gp_probe.cu -- measurement only: sustained lane-operation rates of the
 // FP32 pipe (dependent FADD chains) and the special-function unit (ex2 and
 // rcp approximations) over every SM, timed with CUDA events.  These give
-// the denominators of the ALU roofline of the evaluator.
+// the denominators of the ALU roofline of the evaluator.  The rcp chain
+// carries one FADD per step as well (x <- rcp(x) + d); at 4 FADD lanes per
+// MUFU lane of issue it still measures the MUFU rate.
 #include "gp_internal.cuh"
 
 namespace gpk {
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(kBlock) rcp_probe(float *sink, float d) {
         for (int i = 0; i < kChains; ++i) {
             float y;
             asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[i]));
-            x[i] = y;
+            x[i] = __fadd_rn(y, d);  // keeps rcp(rcp(x)) from cancelling
         }
     }
     float s = 0.0f;

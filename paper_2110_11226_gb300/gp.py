@@ -45,8 +45,9 @@ class EvalOpts(C.Structure):
 
 
 def _load():
-    path = _build.LIB
-    if not os.path.exists(path) or os.environ.get("GP_REBUILD"):
+    # GP_LIBGP selects another build of the same ABI (e.g. an instrumented one)
+    path = os.environ.get("GP_LIBGP") or _build.LIB
+    if path == _build.LIB and (not os.path.exists(path) or os.environ.get("GP_REBUILD")):
         _build.build()
     if not os.path.exists(path):
         raise ImportError(f"libgp.so missing at {path}; run paper_2110_11226_gb300/build.py")
@@ -82,7 +83,7 @@ def _load():
 
 
 _lib = _load()
-LIB_PATH = _build.LIB
+LIB_PATH = os.environ.get("GP_LIBGP") or _build.LIB
 
 
 # ---- marshalling helpers -------------------------------------------------
