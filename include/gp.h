@@ -270,6 +270,29 @@ int gp_probe_pipes(double *out, void *stream);
 int gp_timing_enable(int on);
 int gp_timing_read(double *total_ms, int *n_calls);
 
+/* ---- evaluation without allocation (no counterpart in the paper) --------
+ * For callers that cannot allocate device memory at evaluation time: a
+ * serving process whose device memory is handed out at start-up to another
+ * allocator, code that must not call cudaMalloc/cudaFree because those can
+ * synchronise the device, or a caller with no allocator of its own.
+ * gp_evaluate_static computes exactly what gp_evaluate computes (same
+ * arguments, same results) but uses a fixed scratch array of
+ * GP_STATIC_SCRATCH_BYTES that is part of the library's device image, which
+ * every GPU that loads the library holds until the process exits; it calls
+ * no allocating routine.  A problem whose workspace (gp_workspace_size with
+ * default tunables) exceeds that size gets GP_ERR_WORKSPACE and nothing is
+ * launched; at P = 4096 programs and 16M rows it needs about 12 MiB.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents: calls that overlap on the GPU (different streams, or host
+ * threads without ordering) race; serialise them. */
+#define GP_STATIC_SCRATCH_BYTES (16u << 20)
+int gp_evaluate_static(const gp_node *progs, const int32_t *offsets,
+                       int n_progs, const float *X, int64_t n_rows, int n_feat,
+                       const float *y, const float *w, int metric,
+                       float *out_fitness, void *stream);
+
 /* Frees the library's cached device scratch on every device. */
 void gp_shutdown(void);
 

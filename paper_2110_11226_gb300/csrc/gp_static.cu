@@ -1,0 +1,64 @@
+// gp_static.cu -- gp_evaluate_static: the batched evaluator driven with a
+// scratch area that is part of the library's own device image instead of
+// memory allocated at run time.
+//
+// Some callers cannot allocate device memory when they evaluate: a serving
+// process whose device memory is all handed out at start-up to another
+// allocator, code that must not call cudaMalloc/cudaFree because those can
+// synchronise the whole device, or a caller that owns no allocator at all.
+// They get this entry point: it uses a fixed, file-scope __device__ array as
+// the evaluator's workspace, so it performs no allocation of any kind.
+#include <mutex>
+
+#include "gp_internal.cuh"
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_gp_static_scratch[GP_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxStaticDevices];  // device address of the array, per device
+
+// The array's name is only a host-side handle; its device address is looked
+// up once per device, with that device current.
+int static_scratch(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxStaticDevices) {
+        cudaGetLastError();
+        return GP_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_gp_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return GP_ERR_CUDA;
+        }
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return GP_OK;
+}
+
+}  // namespace
+
+extern "C" int gp_evaluate_static(const gp_node *progs, const int32_t *offsets, int n_progs,
+                                  const float *X, int64_t n_rows, int n_feat, const float *y,
+                                  const float *w, int metric, float *out_fitness, void *stream) {
+    if (n_progs < 1 || n_rows < 1 || n_feat < 1) return GP_ERR_ARG;
+    // the workspace this problem needs with the default tunables
+    const size_t need = gp_workspace_size(n_progs, n_rows, n_feat, nullptr);
+    if (need == 0) return GP_ERR_ARG;
+    if (need > (size_t)GP_STATIC_SCRATCH_BYTES) return GP_ERR_WORKSPACE;
+    void *ws = nullptr;
+    const int rc = static_scratch(&ws);
+    if (rc != GP_OK) return rc;
+    // the evaluator clears the one region that must start at zero (the work
+    // queue counters) on every call and writes every other region before
+    // reading it, so nothing of the previous call leaks into this one
+    return gp_evaluate_ex(progs, offsets, n_progs, X, n_rows, n_feat, y, w, metric, nullptr,
+                          out_fitness, nullptr, nullptr, ws, (size_t)GP_STATIC_SCRATCH_BYTES,
+                          stream);
+}

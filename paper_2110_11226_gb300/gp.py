@@ -71,6 +71,7 @@ def _load():
         "gp_last_device_status": (i32, [P, P]),
         "gp_autotune": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
         "gp_probe_pipes": (i32, [P, P]),
+        "gp_evaluate_static": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
         "gp_timing_enable": (i32, [i32]),
         "gp_timing_read": (i32, [P, P]),
         "gp_shutdown": (None, []),
@@ -147,6 +148,19 @@ def gp_evaluate(progs, offsets, X, y, w=None, metric="mse", out=None, stream=Non
     if out is None:
         out = torch.empty(P, dtype=torch.float32, device=X.device)
     _check("gp_evaluate", _lib.gp_evaluate(
+        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
+        _dptr(y, "y"), _dptr(w, "w"), _metric(metric), _dptr(out, "out"), _stream(stream)))
+    return out
+
+
+def gp_evaluate_static(progs, offsets, X, y, w=None, metric="mse", out=None, stream=None):
+    """gp_evaluate without any device allocation: the library's fixed
+    scratch array serves as workspace (see include/gp.h)."""
+    n_rows, n_feat = _xshape(X)
+    P = _nprogs(offsets)
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=X.device)
+    _check("gp_evaluate_static", _lib.gp_evaluate_static(
         _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
         _dptr(y, "y"), _dptr(w, "w"), _metric(metric), _dptr(out, "out"), _stream(stream)))
     return out
