@@ -41,9 +41,13 @@ if ROOT not in sys.path:
 
 METRIC = "program-row evals/s (GPops/s) and % roofline, batched vs plain eval, same GB300"
 UNIT = "program-row evals/s"
-SFU_OPS = {5, 6, 7, 8, 9, 10, 11, 14}  # div sqrt log exp sin cos tan inv
+# one special-function-unit operation per node of these ops, on this MUFU
+# function (div and inv: reciprocal; sqrt: reciprocal square root; log: lg2;
+# exp: ex2; sin, cos, tan: sin)
+SFU_OF_OP = {5: "rcp", 14: "rcp", 6: "rsqrt", 7: "lg2", 8: "ex2", 9: "sin", 10: "sin", 11: "sin"}
 LOSS_FP32 = {"mae": 3, "mse": 3, "rmse": 3, "logloss": 6}
-LOSS_SFU = {"mae": 0, "mse": 0, "rmse": 0, "logloss": 2}
+LOSS_SFU = {"mae": {}, "mse": {}, "rmse": {}, "logloss": {"ex2": 1, "lg2": 1}}
+KERNEL_SOURCES = ("gp_interp.cuh", "gp_math.cuh", "gp_internal.cuh", "gp_compile.cu")
 
 
 def parse():
@@ -60,6 +64,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the step eagerly instead of replaying its CUDA graph")
     return ap.parse_args()
 
 
@@ -86,13 +92,40 @@ def _depths(name):
             "binary": (2, 8), "const_tune": (4, 10)}[name]
 
 
-def op_counts(nodes, off):
+def op_counts(nodes):
+    """(function nodes, {mufu function: nodes}, all nodes) of a population."""
     op = nodes["op"].astype(np.int64)
-    fn = (op >= 2).astype(np.int64)
-    sfu = np.isin(op, list(SFU_OPS)).astype(np.int64)
-    cfn = np.add.reduceat(fn, off[:-1]) if len(op) else np.zeros(len(off) - 1)
-    csfu = np.add.reduceat(sfu, off[:-1]) if len(op) else np.zeros(len(off) - 1)
-    return int(cfn.sum()), int(csfu.sum()), int(len(op))
+    sfu = {}
+    for code, fn in SFU_OF_OP.items():
+        sfu[fn] = sfu.get(fn, 0) + int((op == code).sum())
+    return int((op >= 2).sum()), sfu, int(len(op))
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2110_11226_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per row of the evaluator from the committed ncu summary, if
+    it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "eval_kernel_pagie1_traffic.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_sources_sha256_16") != kernel_hash() or vals.get("workload") != workload:
+        return None
+    try:
+        return float(vals["dram_bytes_per_row"])
+    except (KeyError, ValueError):
+        return None
 
 
 class ClockSampler:
@@ -227,10 +260,38 @@ def main():
     if args.autotune:
         tuned = gp.gp_autotune(pn, po, dX, dy, dw, metric=wl.metric)
 
-    def step(seed):
-        gp.gp_evaluate(pn, po, dX, dy, dw, metric=wl.metric, out=fit)
+    # the generation step: batched evaluation (pre-pass, persistent
+    # evaluator, FP64 finalize) and tournament selection, captured once as a
+    # CUDA graph on a preallocated workspace and replayed (or launched
+    # eagerly with --no-graph); with several ranks the fitness all-gather
+    # sits between the two and the step runs eagerly
+    opts = tuned if tuned is not None else gp.make_opts()
+    ws_buf = torch.empty(gp.gp_workspace_size(P, N, d.n_feat, opts), dtype=torch.uint8, device=dev)
+    used = gp.gp_resolve_opts(P, N, d.n_feat, opts)
+
+    def step_eager(seed):
+        gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=wl.metric, opts=opts, out=fit, ws=ws_buf)
         gfit = gather_fitness(fit) if ws > 1 else fit
         gp.gp_tournament_ex(gfit, ws * P, wl.tourn_size, seed, out=win)
+
+    use_graph = not args.no_graph and ws == 1
+    graph = None
+    if use_graph:
+        gstream = torch.cuda.Stream()
+        gstream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(gstream):
+            step_eager(42)  # warm the path on the capture stream
+        gstream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gstream):
+            step_eager(42)
+        torch.cuda.synchronize()
+
+    def step(seed):
+        if graph is not None:
+            graph.replay()
+        else:
+            step_eager(seed)
 
     for s in range(args.warmup):
         step(42 + s)
@@ -238,7 +299,6 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
-    gp.gp_timing_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -247,9 +307,13 @@ def main():
             step(1000 + s)
         e1.record(stream)
         torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    # the evaluator kernels alone (events around its launches, on its stream)
+    gp.gp_timing_enable(True)
+    for s in range(min(args.steps, 3)):
+        step_eager(2000 + s)
     eval_ms, n_eval_calls = gp.gp_timing_read()
     gp.gp_timing_enable(False)
-    total_ms = e0.elapsed_time(e1)
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([total_ms], device=dev)
@@ -261,17 +325,23 @@ def main():
     value = ws * rows_evals * args.steps / (total_ms * 1e-3)
     fin = torch.isfinite(fit).float().mean().item()
 
-    # roofline of the evaluator kernel (per launch = one population over N rows)
-    n_fn, n_sfu, n_nodes = op_counts(wl.nodes, wl.offsets)
+    # roofline of the evaluator kernel (per launch = one population over N
+    # rows): node operations over the FP32-pipe and special-function-unit
+    # rates measured in this run, or feature bytes over HBM bandwidth
+    n_fn, sfu_counts, n_nodes = op_counts(wl.nodes)
+    for fn, k in LOSS_SFU[wl.metric].items():
+        sfu_counts[fn] = sfu_counts.get(fn, 0) + k * P
+    n_sfu = sum(sfu_counts.values())
     ops_fp32 = N * (n_fn + LOSS_FP32[wl.metric] * P)
-    ops_sfu = N * (n_sfu + LOSS_SFU[wl.metric] * P)
+    ops_sfu = N * n_sfu
+    t_sfu = sum(N * k / pipes[fn] for fn, k in sfu_counts.items())
     bytes_alg = N * 4 * (d.n_feat + 1 + (d.w is not None))
-    peak_fp32 = pipes["fp32_lane_ops_per_s"]
-    peak_sfu = pipes["mufu_ex2_lane_ops_per_s"]
+    peak_fp32 = pipes["fp32"]
+    peak_sfu = ops_sfu / t_sfu if t_sfu > 0 else pipes["ex2"]  # this op mix's rate
     hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
     t_kernel = eval_ms / max(n_eval_calls, 1) * 1e-3
-    cands = {"fp32": ops_fp32 / peak_fp32, "sfu": ops_sfu / peak_sfu, "hbm": bytes_alg / (hbm * 1e9)}
+    cands = {"fp32": ops_fp32 / peak_fp32, "sfu": t_sfu, "hbm": bytes_alg / (hbm * 1e9)}
     bound = max(cands, key=cands.get)
     if bound == "hbm":
         roof = {"bound": "hbm", "achieved": bytes_alg / t_kernel / 1e9, "peak": hbm, "unit": "GB/s"}
@@ -281,10 +351,15 @@ def main():
         roof = {"bound": "alu", "pipe": bound, "achieved": ops / t_kernel / 1e12,
                 "peak": pk / 1e12, "unit": "Tlane-op/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    tpr = recorded_traffic(wl.name)
+    roof["traffic"] = None if tpr is None else tpr * N
+    roof["algorithmic_bytes"] = bytes_alg
     roof["kernel_ms"] = t_kernel * 1e3
     roof["t_roof_ms"] = {k: v * 1e3 for k, v in cands.items()}
-    roof["peak_source"] = "gp_probe_pipes (FADD / MUFU.EX2 chains on all SMs, this run)"
+    roof["sfu_ops_by_function"] = {k: v * N for k, v in sfu_counts.items()}
+    roof["peak_source"] = ("gp_probe_pipes in this run: FADD and MUFU ex2/rcp/rsqrt/lg2/sin chains on "
+                           "all SMs at the running clock; SFU peak = this op mix's rate")
+    roof["kernel_sources_sha256_16"] = kernel_hash()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -293,11 +368,12 @@ def main():
             "config": {"workload": wl.name, "n_rows": N, "n_feat": d.n_feat, "n_progs": P,
                        "metric": wl.metric, "tourn_size": wl.tourn_size,
                        "mean_nodes": n_nodes / P, "function_nodes": n_fn, "sfu_nodes": n_sfu,
+                       "step": "cuda graph replay" if graph is not None else "eager launches",
                        "l2": "inputs larger than L2" if N * 4 * (d.n_feat + 1) > 129e6 else "L2-resident inputs",
                        "parallelism": f"program shards x{ws} + fitness all-gather" if ws > 1 else "single GPU",
-                       "opts": None if tuned is None else {"rows_per_thread": tuned.rows_per_thread,
-                                                           "chunk_rows": tuned.chunk_rows,
-                                                           "blocks_per_sm": tuned.blocks_per_sm}},
+                       "opts": {"rows_per_thread": used.rows_per_thread, "chunk_rows": used.chunk_rows,
+                                "blocks_per_sm": used.blocks_per_sm or "max resident",
+                                "deep_rows_per_thread": 4, "autotuned": tuned is not None}},
             "node_evals_per_s": value * (n_nodes / P),
             "finite_fitness_frac": fin,
             "clocks": clocks,

@@ -158,6 +158,16 @@ int gp_evaluate_ex(const gp_node *progs, const int32_t *offsets, int n_progs,
 size_t gp_workspace_size(int n_progs, int64_t n_rows, int n_feat,
                          const gp_eval_opts *opts);
 
+/* The tunables gp_evaluate_ex would use for this shape: `opts` (may be NULL)
+ * with every zero field filled from the autotuner's record for the shape, or
+ * else from the built-in defaults (rows_per_thread 8; chunk_rows sized for
+ * about 16 work items per resident warp, 1024..65536 rows; blocks_per_sm 0 =
+ * as many as fit).  Programs deeper than 8 stack slots always run with 4
+ * rows per thread, whatever rows_per_thread says.  Returns GP_ERR_ARG for
+ * invalid opts. */
+int gp_resolve_opts(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts *opts,
+                    gp_eval_opts *out);
+
 /* Plain evaluator: one kernel launch per program, one row per thread in
  * blocks of 256 rows, programs read node by node from global memory and a
  * 20-slot stack held by predicated register selects (the shape of the
@@ -255,10 +265,11 @@ int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs,
                 const float *X, int64_t n_rows, int n_feat, const float *y,
                 const float *w, int metric, gp_eval_opts *best, void *stream);
 
-/* Measurement only: sustained issue rates of the FP32 pipe (FADD) and the
- * special-function unit (ex2, rcp) over all SMs, in lane-operations per
- * second, measured with CUDA events; out[0] = fp32, out[1] = mufu ex2,
- * out[2] = mufu rcp, out[3] = SM count.  Synchronises. */
+/* Measurement only: sustained issue rates of the FP32 pipe (FADD) and of
+ * the special-function unit per function, over all SMs, in lane-operations
+ * per second, measured with CUDA events.  out[8]: out[0] = fp32 FADD,
+ * out[1] = ex2, out[2] = rcp, out[3] = rsqrt, out[4] = lg2, out[5] = sin,
+ * out[6] = SM count, out[7] = 0.  Synchronises. */
 int gp_probe_pipes(double *out, void *stream);
 
 /* Measurement only.  While enabled (on != 0), every batched evaluation

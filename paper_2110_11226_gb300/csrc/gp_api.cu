@@ -298,6 +298,18 @@ size_t gp_workspace_size(int n_progs, int64_t n_rows, int n_feat, const gp_eval_
     return pl.L.total;
 }
 
+int gp_resolve_opts(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts *opts,
+                    gp_eval_opts *out) {
+    if (n_progs < 1 || n_rows < 1 || n_feat < 1 || !out) return GP_ERR_ARG;
+    DevCtx *c = nullptr;
+    int rc = ctx_of_current(&c);
+    if (rc) return rc;
+    Plan pl;
+    if ((rc = make_plan(opts, n_progs, n_rows, n_feat, c, &pl))) return rc;
+    *out = pl.o;
+    return GP_OK;
+}
+
 int gp_evaluate_ex(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
                    int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
                    const gp_eval_opts *opts, float *out_fitness, double *out_fitness64,

@@ -1,9 +1,10 @@
 // gp_probe.cu -- measurement only: sustained lane-operation rates of the
 // FP32 pipe (dependent FADD chains) and the special-function unit (ex2 and
 // rcp approximations) over every SM, timed with CUDA events.  These give
-// the denominators of the ALU roofline of the evaluator.  The rcp chain
-// carries one FADD per step as well (x <- rcp(x) + d); at 4 FADD lanes per
-// MUFU lane of issue it still measures the MUFU rate.
+// the denominators of the ALU roofline of the evaluator: out[0] FADD,
+// out[1] ex2, out[2] rcp, out[3] rsqrt, out[4] lg2, out[5] sin (lane
+// operations per second), out[6] SM count.  The rcp/rsqrt/lg2/sin chains
+// carry one FADD per step, which the FP32 pipe absorbs at its higher rate.
 #include "gp_internal.cuh"
 
 namespace gpk {
@@ -46,7 +47,10 @@ __global__ void __launch_bounds__(kBlock) ex2_probe(float *sink, float d) {
     sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kBlock) rcp_probe(float *sink, float d) {
+// x <- mufu(x) + d: one MUFU and one FADD per step; the FADD keeps an
+// involution (rcp(rcp(x))) from cancelling and the chain bounded
+template <int KIND>
+__global__ void __launch_bounds__(kBlock) mufu_probe(float *sink, float d) {
     float x[kChains];
 #pragma unroll
     for (int i = 0; i < kChains; ++i) x[i] = 1.0f + d * (float)(threadIdx.x + 3 * i + 1);
@@ -54,8 +58,11 @@ __global__ void __launch_bounds__(kBlock) rcp_probe(float *sink, float d) {
 #pragma unroll
         for (int i = 0; i < kChains; ++i) {
             float y;
-            asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[i]));
-            x[i] = __fadd_rn(y, d);  // keeps rcp(rcp(x)) from cancelling
+            if (KIND == 0) asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[i]));
+            if (KIND == 1) asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[i]));
+            if (KIND == 2) asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[i]));
+            if (KIND == 3) asm volatile("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[i]));
+            x[i] = __fadd_rn(y, d + 1.0f);
         }
     }
     float s = 0.0f;
@@ -100,9 +107,16 @@ cudaError_t probe_pipes(double *out, cudaStream_t st) {
     if (e == cudaSuccess) out[0] = lane_ops / (ms * 1e-3);
     if (e == cudaSuccess) e = time_it([&] { ex2_probe<<<grid, kBlock, 0, st>>>(sink, 1e-3f); }, st, &ms);
     if (e == cudaSuccess) out[1] = lane_ops / (ms * 1e-3);
-    if (e == cudaSuccess) e = time_it([&] { rcp_probe<<<grid, kBlock, 0, st>>>(sink, 1e-3f); }, st, &ms);
+    if (e == cudaSuccess) e = time_it([&] { mufu_probe<0><<<grid, kBlock, 0, st>>>(sink, 1e-3f); }, st, &ms);
     if (e == cudaSuccess) out[2] = lane_ops / (ms * 1e-3);
-    out[3] = (double)sms;
+    if (e == cudaSuccess) e = time_it([&] { mufu_probe<1><<<grid, kBlock, 0, st>>>(sink, 1e-3f); }, st, &ms);
+    if (e == cudaSuccess) out[3] = lane_ops / (ms * 1e-3);
+    if (e == cudaSuccess) e = time_it([&] { mufu_probe<2><<<grid, kBlock, 0, st>>>(sink, 1e-3f); }, st, &ms);
+    if (e == cudaSuccess) out[4] = lane_ops / (ms * 1e-3);
+    if (e == cudaSuccess) e = time_it([&] { mufu_probe<3><<<grid, kBlock, 0, st>>>(sink, 1e-3f); }, st, &ms);
+    if (e == cudaSuccess) out[5] = lane_ops / (ms * 1e-3);
+    out[6] = (double)sms;
+    out[7] = 0.0;
     cudaFree(sink);
     return e;
 }

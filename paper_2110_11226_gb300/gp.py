@@ -60,6 +60,7 @@ def _load():
         "gp_evaluate_ex": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P, P, P, P,
                                  C.c_size_t, P]),
         "gp_workspace_size": (C.c_size_t, [i32, i64, i32, P]),
+        "gp_resolve_opts": (i32, [i32, i64, i32, P, P]),
         "gp_evaluate_plain": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
         "gp_predict": (i32, [P, P, i32, P, i64, i32, P, P]),
         "gp_evaluate_host": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
@@ -195,6 +196,14 @@ def gp_workspace_size(n_progs, n_rows, n_feat, opts: Optional[EvalOpts] = None) 
                                       None if opts is None else C.byref(opts)))
 
 
+def gp_resolve_opts(n_progs, n_rows, n_feat, opts: Optional[EvalOpts] = None) -> EvalOpts:
+    out = EvalOpts()
+    _check("gp_resolve_opts", _lib.gp_resolve_opts(int(n_progs), int(n_rows), int(n_feat),
+                                                   None if opts is None else C.byref(opts),
+                                                   C.byref(out)))
+    return out
+
+
 def gp_evaluate_plain(progs, offsets, X, y, w=None, metric="mse", out=None, stream=None):
     n_rows, n_feat = _xshape(X)
     P = _nprogs(offsets)
@@ -308,10 +317,10 @@ def gp_autotune(progs, offsets, X, y, w=None, metric="mse", stream=None) -> Eval
 
 
 def gp_probe_pipes(stream=None) -> dict:
-    out = (C.c_double * 4)()
+    out = (C.c_double * 8)()
     _check("gp_probe_pipes", _lib.gp_probe_pipes(out, _stream(stream)))
-    return {"fp32_lane_ops_per_s": out[0], "mufu_ex2_lane_ops_per_s": out[1],
-            "mufu_rcp_lane_ops_per_s": out[2], "sms": int(out[3])}
+    return {"fp32": out[0], "ex2": out[1], "rcp": out[2], "rsqrt": out[3], "lg2": out[4],
+            "sin": out[5], "sms": int(out[6]), "unit": "lane-operations/s"}
 
 
 def gp_timing_enable(on: bool = True):
