@@ -71,8 +71,14 @@ enum gp_op {
  *   RMSE = sqrt(MSE)                   LOGLOSS = sum w l(p,y) / sum w
  * with l(p,y) = c|p| + log1p(exp(-|p|)), c = 1-y if p >= 0 else y (the
  * logistic loss of sigmoid(p) against a label y in {0,1}; the c|p| term
- * is 0 when c == 0).  All four are smaller-is-better. */
-enum gp_metric { GP_MAE = 0, GP_MSE = 1, GP_RMSE = 2, GP_LOGLOSS = 3 };
+ * is 0 when c == 0).  These four are smaller-is-better.
+ *   PEARSON = |r_w(p, y)|, the absolute weighted Karl Pearson correlation
+ *             cov_w(p,y) / sqrt(var_w(p) var_w(y)) with weighted means;
+ *             0 when either variance is 0, NaN when a sum is not finite.
+ *             Greater is better (pass greater_is_better = 1 to the
+ *             tournament).  Batched evaluator only (gp_evaluate*,
+ *             gp_evaluate_host, gp_evaluate_static, gp_autotune). */
+enum gp_metric { GP_MAE = 0, GP_MSE = 1, GP_RMSE = 2, GP_LOGLOSS = 3, GP_PEARSON = 4 };
 
 enum gp_status {
     GP_OK = 0,
@@ -154,7 +160,9 @@ int gp_evaluate_ex(const gp_node *progs, const int32_t *offsets, int n_progs,
                    double *out_fitness64, int32_t *out_prog_status, void *ws,
                    size_t ws_bytes, void *stream);
 
-/* Bytes of workspace gp_evaluate_ex needs for this shape and these opts. */
+/* Bytes of workspace gp_evaluate_ex needs for this shape and these opts,
+ * whatever the metric (GP_PEARSON needs the most: 24 more bytes per
+ * program and row chunk). */
 size_t gp_workspace_size(int n_progs, int64_t n_rows, int n_feat,
                          const gp_eval_opts *opts);
 
@@ -173,7 +181,8 @@ int gp_resolve_opts(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts 
  * 20-slot stack held by predicated register selects (the shape of the
  * paper's execution kernel, Sec. III-C3 and III-D1), loss fused, per-block
  * partial sums reduced in FP64.  Same arguments and results as
- * gp_evaluate (fitness equal within the FP32 summation order). */
+ * gp_evaluate (fitness equal within the FP32 summation order) for the four
+ * loss metrics; GP_PEARSON returns GP_ERR_ARG. */
 int gp_evaluate_plain(const gp_node *progs, const int32_t *offsets,
                       int n_progs, const float *X, int64_t n_rows, int n_feat,
                       const float *y, const float *w, int metric,
@@ -236,7 +245,8 @@ int gp_tournament(const float *fitness, int n_progs, int tourn_size,
  * operators are 0 on the protected branch; MAE uses sign(p - y) (0 at
  * equality); RMSE = MSE gradient / (2 RMSE) (0 when RMSE == 0).  A program
  * with more than 16 constants gets NaN gradients and sets
- * GP_DEV_TOO_MANY_CONSTS.  Scratch as for gp_evaluate. */
+ * GP_DEV_TOO_MANY_CONSTS.  Loss metrics only (GP_PEARSON returns
+ * GP_ERR_ARG).  Scratch as for gp_evaluate. */
 int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs,
                   const float *X, int64_t n_rows, int n_feat, const float *y,
                   const float *w, int metric, float *out_grad,
@@ -251,6 +261,19 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs,
 int gp_adam_step(gp_node *progs, const int32_t *offsets, int n_progs,
                  const float *grad, float *m, float *v, int step, float lr,
                  float beta1, float beta2, float eps, void *stream);
+
+/* The constants of each program as a dense array, and back: constant k of
+ * program p is its k-th CONST node in prefix order (the numbering of
+ * gp_const_grad), stored at consts[p * 16 + k].  gp_get_consts writes all
+ * 16 slots of every program (slots past its constant count are 0, a
+ * malformed offset range leaves the whole row 0); gp_set_consts writes the
+ * first min(count, 16) slots into the nodes' `c` fields in place and reads
+ * nothing else.  Used to expose the constants as one tensor to automatic
+ * differentiation. */
+int gp_get_consts(const gp_node *progs, const int32_t *offsets, int n_progs,
+                  float *out_consts, void *stream);
+int gp_set_consts(gp_node *progs, const int32_t *offsets, int n_progs,
+                  const float *consts, void *stream);
 
 /* ---- runtime --------------------------------------------------------------
  * Synchronises `stream`, returns the device status bits accumulated since

@@ -39,7 +39,7 @@ OPS = {
     "sqrt": 6, "log": 7, "exp": 8, "sin": 9, "cos": 10, "tan": 11,
     "abs": 12, "neg": 13, "inv": 14,
 }
-METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3}
+METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3, "pearson": 4}
 MAX_STACK = 20
 MAX_LEN = 255
 MAX_CONSTS = 16

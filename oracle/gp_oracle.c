@@ -17,7 +17,9 @@
  *     tree of depth m-1 (Sec. III-C2, hoisted crossover), the stack size is
  *     20.
  *   - Fitness = weighted loss of the predictions against y, reduced per
- *     program (Sec. III-C3): MAE, MSE, RMSE, logistic loss.
+ *     program (Sec. III-C3): MAE, MSE, RMSE, logistic loss; and the
+ *     weighted Karl Pearson correlation coefficient of the predictions
+ *     with y (Sec. III-C3 metric list).
  *   - Tournament selection: k Philox draws per tournament, best adjusted
  *     fitness wins, adjusted = raw + c * len (Sec. III-C1, Eqs. parsimony
  *     and fitness); Philox4x32-10 from Salmon et al. 2011 (Sec. III-B).
@@ -30,7 +32,9 @@
  *   - log-loss on sigmoid(p): c*|p| + log1p(exp(-|p|)), c = 1-y if p>=0
  *     else y, with the c*|p| term dropped when c == 0;
  *   - tournament draws with replacement, index = (u * n) >> 32, ties go to
- *     the earliest draw, NaN counts as the worst fitness.
+ *     the earliest draw, NaN counts as the worst fitness;
+ *   - Pearson fitness = |r_w(p, y)| with weighted means and (co)variances,
+ *     greater is better, and 0 when either variance is 0.
  *
  * Everything is FP64 unless a function says FP32 ("_f32" evaluates every
  * operation rounded to float with the C library's float functions; it is
@@ -60,7 +64,7 @@ enum {
     ORA_NOPS = 15
 };
 
-enum { ORA_MAE = 0, ORA_MSE = 1, ORA_RMSE = 2, ORA_LOGLOSS = 3 };
+enum { ORA_MAE = 0, ORA_MSE = 1, ORA_RMSE = 2, ORA_LOGLOSS = 3, ORA_PEARSON = 4 };
 
 #define ORA_MAX_STACK 20
 #define ORA_MAX_LEN 255
@@ -444,14 +448,22 @@ double ora_loss(int metric, double p, double y) {
  *   MAE/MSE/logloss = sum_i w_i l_i / sum_i w_i, RMSE = sqrt(MSE).
  * w == NULL means all weights 1.  Returns 0, or -1 for a bad metric or a
  * zero total weight.  A malformed program gets NaN and status[p] != 0. */
+static int pearson_fitness(const ora_node *progs, const int32_t *offsets, int n_progs,
+                           const float *X, int64_t ld, const float *y, const float *w,
+                           int64_t row0, int64_t n_eval, double sw, double *out_fit,
+                           int32_t *status, int n_threads);
+
 int ora_fitness(const ora_node *progs, const int32_t *offsets, int n_progs,
                 const float *X, int64_t ld, const float *y, const float *w,
                 int metric, int64_t row0, int64_t n_eval, double *out_fit,
                 int32_t *status, int n_threads) {
-    if (metric < ORA_MAE || metric > ORA_LOGLOSS) return -1;
+    if (metric < ORA_MAE || metric > ORA_PEARSON) return -1;
     double sw = 0.0;
     for (int64_t i = 0; i < n_eval; ++i) sw += w ? (double)w[row0 + i] : 1.0;
     if (!(sw != 0.0)) return -1;
+    if (metric == ORA_PEARSON)
+        return pearson_fitness(progs, offsets, n_progs, X, ld, y, w, row0, n_eval, sw, out_fit,
+                               status, n_threads);
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic)
@@ -473,6 +485,63 @@ int ora_fitness(const ora_node *progs, const int32_t *offsets, int n_progs,
         if (st == ORA_OK) {
             f = se / sw;
             if (metric == ORA_RMSE) f = sqrt(f);
+        }
+        out_fit[p] = f;
+        if (status) status[p] = st;
+    }
+    return 0;
+}
+
+/* Weighted Pearson correlation, by its definition with two passes over
+ * the rows (Sec. III-C3 names the coefficient; the weighting follows the
+ * other metrics):
+ *   pbar = sum w p / sum w,  ybar = sum w y / sum w,
+ *   r = sum w (p-pbar)(y-ybar) / sqrt(sum w (p-pbar)^2 * sum w (y-ybar)^2),
+ * fitness = |r|, and 0 when either sum of squares is 0.  Non-finite
+ * predictions give NaN. */
+static int pearson_fitness(const ora_node *progs, const int32_t *offsets, int n_progs,
+                           const float *X, int64_t ld, const float *y, const float *w,
+                           int64_t row0, int64_t n_eval, double sw, double *out_fit,
+                           int32_t *status, int n_threads) {
+    double swy = 0.0;
+    for (int64_t i = 0; i < n_eval; ++i)
+        swy += (w ? (double)w[row0 + i] : 1.0) * (double)y[row0 + i];
+    const double ybar = swy / sw;
+    double syy = 0.0;
+    for (int64_t i = 0; i < n_eval; ++i) {
+        const double dy = (double)y[row0 + i] - ybar;
+        syy += (w ? (double)w[row0 + i] : 1.0) * dy * dy;
+    }
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int p = 0; p < n_progs; ++p) {
+        const ora_node *prog = progs + offsets[p];
+        int len = offsets[p + 1] - offsets[p];
+        int st = ORA_OK;
+        double swp = 0.0;
+        for (int64_t i = 0; i < n_eval && st == ORA_OK; ++i) {
+            double v;
+            st = eval_row64(prog, len, X, ld, row0 + i, &v);
+            if (st) break;
+            swp += (w ? (double)w[row0 + i] : 1.0) * v;
+        }
+        double f = NAN;
+        if (st == ORA_OK) {
+            const double pbar = swp / sw;
+            double spp = 0.0, spy = 0.0;
+            for (int64_t i = 0; i < n_eval; ++i) {
+                double v;
+                eval_row64(prog, len, X, ld, row0 + i, &v);
+                const double wi = w ? (double)w[row0 + i] : 1.0;
+                const double dp = v - pbar;
+                spp += wi * dp * dp;
+                spy += wi * dp * ((double)y[row0 + i] - ybar);
+            }
+            if (isnan(spp) || isnan(spy) || isinf(spp) || isinf(spy)) f = NAN;
+            else if (spp == 0.0 || syy == 0.0) f = 0.0;
+            else f = fabs(spy / sqrt(spp * syy));
         }
         out_fit[p] = f;
         if (status) status[p] = st;

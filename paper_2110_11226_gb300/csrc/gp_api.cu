@@ -115,7 +115,13 @@ int check_common(const gp_node *progs, const int32_t *offsets, int n_progs, cons
     return GP_OK;
 }
 
+// every metric of the batched evaluator
 int check_metric(int metric) {
+    return (metric >= GP_MAE && metric <= GP_PEARSON) ? GP_OK : GP_ERR_ARG;
+}
+
+// the per-row loss metrics (plain evaluator, constant gradients)
+int check_loss_metric(int metric) {
     return (metric >= GP_MAE && metric <= GP_LOGLOSS) ? GP_OK : GP_ERR_ARG;
 }
 
@@ -161,10 +167,10 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
     return GP_OK;
 }
 
-int eval_info(int rpt, int fmode, int cls, int block, int *regs) {
-    if (rpt == 4) return fmode == 2 ? info_eval_r4_f2(cls, block, regs) : info_eval_r4_f0(cls, block, regs);
-    if (rpt == 8) return fmode == 2 ? info_eval_r8_f2(cls, block, regs) : info_eval_r8_f0(cls, block, regs);
-    return fmode == 2 ? info_eval_r16_f2(cls, block, regs) : info_eval_r16_f0(cls, block, regs);
+int eval_info(int rpt, int fmode, int cls, int block, int *regs, bool mom = false) {
+    if (rpt == 4) return fmode == 2 ? info_eval_r4_f2(cls, block, regs, mom) : info_eval_r4_f0(cls, block, regs, mom);
+    if (rpt == 8) return fmode == 2 ? info_eval_r8_f2(cls, block, regs, mom) : info_eval_r8_f0(cls, block, regs, mom);
+    return fmode == 2 ? info_eval_r16_f2(cls, block, regs, mom) : info_eval_r16_f0(cls, block, regs, mom);
 }
 
 cudaError_t eval_launch(const EvalArgs &a, int rpt, int fmode, int grid, int block, cudaStream_t st) {
@@ -179,12 +185,13 @@ struct Plan {
     Layout L;
 };
 
+// moments: the workspace also holds the correlation extras
 int make_plan(const gp_eval_opts *opts, int n_progs, int64_t n_rows, int n_feat, DevCtx *c,
-              Plan *pl) {
+              Plan *pl, bool moments) {
     int rc = resolve_opts(opts, n_progs, n_rows, n_feat, c, &pl->o);
     if (rc) return rc;
     pl->n_chunks = (int)((n_rows + pl->o.chunk_rows - 1) / pl->o.chunk_rows);
-    pl->L = make_layout(n_progs, pl->n_chunks, false);
+    pl->L = make_layout(n_progs, pl->n_chunks, false, moments);
     return GP_OK;
 }
 
@@ -193,14 +200,22 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
                  int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
                  const Plan &pl, const Workspace &W, DevCtx *c, float *out, double *out64,
                  int32_t *out_status, cudaStream_t st) {
+    const bool mom = metric == GP_PEARSON;
     GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
     CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
                    nullptr, nullptr, nullptr, c->status, nullptr};
+    if (mom) {
+        ca.X = X;
+        ca.ld = n_rows;
+        ca.shift = W.shift;
+    }
     GP_CUDA(launch_compile(ca, st));
     GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
     GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
+    if (mom) GP_CUDA(launch_ystats(y, w, n_rows, W.sumw, W.ystat_part, W.ystat, st));
     const int fmode = (n_feat <= 2) ? 2 : 0;
-    const int rpt = pl.o.rows_per_thread;
+    // the moment epilogue has instances for 4 and 8 rows per thread
+    const int rpt = (mom && pl.o.rows_per_thread == 16) ? 8 : pl.o.rows_per_thread;
     const bool vec = aligned16(X) && aligned16(y) && (!w || aligned16(w)) && (n_rows % 4 == 0);
     std::pair<cudaEvent_t, cudaEvent_t> tev{nullptr, nullptr};
     if (g_timing.on) {
@@ -227,19 +242,35 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
         ea.part = W.part;
         ea.dev_status = c->status;
         ea.vec_ok = vec ? 1 : 0;
+        if (mom) {
+            ea.mom = W.mom;
+            ea.shift = W.shift;
+            ea.ystat = W.ystat;
+        }
         // the deep class keeps 4 rows per thread (its 19-slot stack would
         // otherwise leave room for one block per SM); the same chunk
         // partition serves both
         const int rpt_c = (cls == 0) ? rpt : 4;
         const int block = kEvalBlockThreads;
-        int occ = eval_info(rpt_c, fmode, cls, block, nullptr);
+        int occ = eval_info(rpt_c, fmode, cls, block, nullptr, mom);
         if (occ < 1) occ = 1;
         int bps = pl.o.blocks_per_sm > 0 ? std::min(pl.o.blocks_per_sm, occ) : occ;
         GP_CUDA(eval_launch(ea, rpt_c, fmode, c->sms * bps, block, st));
     }
     if (tev.second) GP_CUDA(cudaEventRecord(tev.second, st));
-    FinalizeArgs fa{W.part, pl.n_chunks, n_progs, W.meta, W.sumw, metric, pl.o.accum,
-                    out, out64, out_status};
+    FinalizeArgs fa{};
+    fa.part = W.part;
+    fa.mom = mom ? W.mom : nullptr;
+    fa.ystat = mom ? W.ystat : nullptr;
+    fa.n_chunks = pl.n_chunks;
+    fa.n_progs = n_progs;
+    fa.meta = W.meta;
+    fa.sumw = W.sumw;
+    fa.metric = metric;
+    fa.accum = pl.o.accum;
+    fa.out = out;
+    fa.out64 = out64;
+    fa.out_prog_status = out_status;
     GP_CUDA(launch_finalize(fa, st));
     return GP_OK;
 }
@@ -271,6 +302,19 @@ int validate_one_host(const gp_node *p, int len, int n_feat, int *hw_out) {
 
 }  // namespace
 
+namespace gpk {
+// workspace bytes of one evaluation with this metric (0 for bad arguments)
+size_t workspace_bytes_for(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts *opts,
+                           int metric) {
+    if (n_progs < 1 || n_rows < 1 || n_feat < 1 || check_metric(metric)) return 0;
+    DevCtx *c = nullptr;
+    if (ctx_of_current(&c)) return 0;
+    Plan pl;
+    if (make_plan(opts, n_progs, n_rows, n_feat, c, &pl, metric == GP_PEARSON)) return 0;
+    return pl.L.total;
+}
+}  // namespace gpk
+
 extern "C" {
 
 const char *gp_version(void) { return "libgp 1.0 (sm_103a)"; }
@@ -294,9 +338,10 @@ size_t gp_workspace_size(int n_progs, int64_t n_rows, int n_feat, const gp_eval_
     DevCtx *c = nullptr;
     if (ctx_of_current(&c)) return 0;
     Plan pl;
-    if (make_plan(opts, n_progs, n_rows, n_feat, c, &pl)) return 0;
+    if (make_plan(opts, n_progs, n_rows, n_feat, c, &pl, true)) return 0;
     return pl.L.total;
 }
+
 
 int gp_resolve_opts(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts *opts,
                     gp_eval_opts *out) {
@@ -305,7 +350,7 @@ int gp_resolve_opts(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts 
     int rc = ctx_of_current(&c);
     if (rc) return rc;
     Plan pl;
-    if ((rc = make_plan(opts, n_progs, n_rows, n_feat, c, &pl))) return rc;
+    if ((rc = make_plan(opts, n_progs, n_rows, n_feat, c, &pl, false))) return rc;
     *out = pl.o;
     return GP_OK;
 }
@@ -321,7 +366,7 @@ int gp_evaluate_ex(const gp_node *progs, const int32_t *offsets, int n_progs, co
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
     Plan pl;
-    if ((rc = make_plan(opts, n_progs, n_rows, n_feat, c, &pl))) return rc;
+    if ((rc = make_plan(opts, n_progs, n_rows, n_feat, c, &pl, metric == GP_PEARSON))) return rc;
     void *base = ws;
     if (ws) {
         if (ws_bytes < pl.L.total || ((uintptr_t)ws & 255u)) return GP_ERR_WORKSPACE;
@@ -348,7 +393,7 @@ int gp_evaluate_plain(const gp_node *progs, const int32_t *offsets, int n_progs,
     int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
     if (rc) return rc;
     if (!y || !out_fitness) return GP_ERR_ARG;
-    if ((rc = check_metric(metric))) return rc;
+    if ((rc = check_loss_metric(metric))) return rc;
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
     const int64_t nb64 = (n_rows + 255) / 256;
@@ -367,8 +412,15 @@ int gp_evaluate_plain(const gp_node *progs, const int32_t *offsets, int n_progs,
     GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
     PlainArgs pa{progs, offsets, W.meta, X, n_rows, n_rows, y, w, metric, n_blocks, W.part};
     for (int p = 0; p < n_progs; ++p) GP_CUDA(launch_plain(pa, p, st));
-    FinalizeArgs fa{W.part, n_blocks, n_progs, W.meta, W.sumw, metric, GP_ACCUM_FP64,
-                    out_fitness, nullptr, nullptr};
+    FinalizeArgs fa{};
+    fa.part = W.part;
+    fa.n_chunks = n_blocks;
+    fa.n_progs = n_progs;
+    fa.meta = W.meta;
+    fa.sumw = W.sumw;
+    fa.metric = metric;
+    fa.accum = GP_ACCUM_FP64;
+    fa.out = out_fitness;
     GP_CUDA(launch_finalize(fa, st));
     return GP_OK;
 }
@@ -507,7 +559,7 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, con
     int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
     if (rc) return rc;
     if (!y || !out_grad) return GP_ERR_ARG;
-    if ((rc = check_metric(metric))) return rc;
+    if ((rc = check_loss_metric(metric))) return rc;
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
     const int64_t chunk = default_chunk(n_progs, n_rows, c->sms);
@@ -541,6 +593,21 @@ int gp_adam_step(gp_node *progs, const int32_t *offsets, int n_progs, const floa
         return GP_ERR_ARG;
     AdamArgs a{progs, offsets, nullptr, nullptr, n_progs, grad, m, v, step, lr, beta1, beta2, eps};
     GP_CUDA(launch_adam(a, S(stream)));
+    return GP_OK;
+}
+
+int gp_get_consts(const gp_node *progs, const int32_t *offsets, int n_progs, float *out_consts,
+                  void *stream) {
+    if (!progs || !offsets || !out_consts || n_progs < 1) return GP_ERR_ARG;
+    GP_CUDA(launch_consts(const_cast<gp_node *>(progs), offsets, n_progs, out_consts, false,
+                          S(stream)));
+    return GP_OK;
+}
+
+int gp_set_consts(gp_node *progs, const int32_t *offsets, int n_progs, const float *consts,
+                  void *stream) {
+    if (!progs || !offsets || !consts || n_progs < 1) return GP_ERR_ARG;
+    GP_CUDA(launch_consts(progs, offsets, n_progs, const_cast<float *>(consts), true, S(stream)));
     return GP_OK;
 }
 

@@ -3,6 +3,7 @@
 // depth classes and by length (length-bucketed work queue); plus the
 // deterministic total-weight sum.
 #include "gp_internal.cuh"
+#include "gp_interp.cuh"
 
 namespace gpk {
 
@@ -15,7 +16,7 @@ static __host__ __device__ inline int op_arity(int op) {
 
 static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int n_progs, int n_chunks, bool grad) {
+Layout make_layout(int n_progs, int n_chunks, bool grad, bool moments) {
     Layout L{};
     size_t o = 0;
     size_t P = (size_t)(n_progs > 0 ? n_progs : 1);
@@ -28,6 +29,12 @@ Layout make_layout(int n_progs, int n_chunks, bool grad) {
     L.order = o;       o = align256(o + P * sizeof(int32_t));
     L.class_count = o; o = align256(o + (kNumClasses + 2) * sizeof(int32_t));
     L.part = o;        o = align256(o + P * C * sizeof(float));
+    if (moments) {
+        L.ystat = o;      o = align256(o + 4 * sizeof(double));
+        L.ystat_part = o; o = align256(o + 2 * kSumwBlocks * sizeof(double));
+        L.shift = o;      o = align256(o + P * sizeof(float));
+        L.mom = o;        o = align256(o + P * C * 3 * sizeof(double));
+    }
     if (grad) {
         L.rchild = o;  o = align256(o + P * kCodeStride);
         L.kslot = o;   o = align256(o + P * kCodeStride);
@@ -49,6 +56,12 @@ Workspace carve(void *base, const Layout &L, bool grad) {
     w.order = reinterpret_cast<int32_t *>(b + L.order);
     w.class_count = reinterpret_cast<int32_t *>(b + L.class_count);
     w.part = reinterpret_cast<float *>(b + L.part);
+    if (L.mom) {
+        w.ystat = reinterpret_cast<double *>(b + L.ystat);
+        w.ystat_part = reinterpret_cast<double *>(b + L.ystat_part);
+        w.shift = reinterpret_cast<float *>(b + L.shift);
+        w.mom = reinterpret_cast<double *>(b + L.mom);
+    }
     if (grad) {
         w.rchild = reinterpret_cast<uint8_t *>(b + L.rchild);
         w.kslot = reinterpret_cast<int8_t *>(b + L.kslot);
@@ -59,10 +72,44 @@ Workspace carve(void *base, const Layout &L, bool grad) {
     return w;
 }
 
-// One thread per program.  Three passes over at most 255 nodes held in
-// per-thread local arrays: (1) reverse scan for validity and subtree sizes,
-// (2) mark terminal children that fold into their binary parent, (3)
-// reverse scan emitting instructions.
+// The value of a function node whose operands are all constants, computed
+// with the evaluator's own FP32 operations, so the folded constant is the
+// very number the evaluator would produce on every row.
+__device__ float fold_unary(int op, float a) {
+    switch (op) {
+        case GP_SQRT: return f_sqrt(a);
+        case GP_LOG: return f_log(a);
+        case GP_EXP: return f_exp(a);
+        case GP_SIN:
+        case GP_COS:
+        case GP_TAN: {
+            float t[1] = {a};
+            trig_rows<1>(t, op - GP_SIN);
+            return t[0];
+        }
+        case GP_ABS: return f_abs(a);
+        case GP_NEG: return f_neg(a);
+        default: return f_inv(a);
+    }
+}
+
+__device__ float fold_binary(int op, float l, float r) {
+    switch (op) {
+        case GP_ADD: return f_add(l, r);
+        case GP_SUB: return f_sub(l, r);
+        case GP_MUL: return f_mul(l, r);
+        default: return f_div(l, r);
+    }
+}
+
+// One thread per program.  Passes over at most 255 nodes held in
+// per-thread local arrays: (1) reverse scan for validity, subtree sizes and
+// the values of constant-only subtrees, (2) mark the inside of every
+// maximal constant-only subtree as dropped (its root becomes one constant)
+// and the terminal children that fold into their binary parent, (3)
+// reverse scan emitting instructions.  Folding constant-only subtrees
+// leaves every row's result bit-identical: the same FP32 operations run on
+// the same inputs, once per program instead of once per row.
 __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n_progs) return;
@@ -72,13 +119,22 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
     const gp_node *prog = a.progs + off;
 
     uint8_t size[GP_MAX_LEN];
-    uint8_t mode[GP_MAX_LEN];  // terminal: 1 = folded; binary: 0/1 R/2 L
+    // terminal: 1 = folded into its parent; binary: 0 / 1 R / 2 L folded;
+    // any node: 3 = inside a constant-only subtree (dropped)
+    uint8_t mode[GP_MAX_LEN];
+    uint8_t kon[GP_MAX_LEN];   // 1: the node's subtree holds no variable
+    float kval[GP_MAX_LEN];    // its value when kon
     int status = GP_PROG_OK;
     int sp = 0, hw = 0, n_consts = 0;
 
     if (len < 1 || len > GP_MAX_LEN) status = GP_PROG_BAD_LENGTH;
     // pass 1: reverse scan with a stack of subtree sizes (kept in size[])
-    uint8_t szst[GP_MAX_LEN];
+    // and of the constant-only flags and values
+    uint8_t szst[GP_MAX_LEN], kst[GP_MAX_LEN];
+    float vst[GP_MAX_LEN];
+    // with a.shift the scan also evaluates the program at row 0 (every
+    // node's value, not only the constant-only ones)
+    const bool row0 = a.shift != nullptr;
     for (int j = len - 1; j >= 0 && status == GP_PROG_OK; --j) {
         const gp_node nd = prog[j];
         const int ar = op_arity(nd.op);
@@ -89,25 +145,46 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
             break;
         }
         int s;
+        uint8_t k;
+        float v = 0.0f;
         if (ar == 0) {
             s = 1;
             n_consts += (nd.op == GP_CONST);
+            k = nd.op == GP_CONST;
+            v = k ? nd.c : (row0 ? a.X[(int64_t)nd.feat * a.ld] : 0.0f);
         } else if (ar == 1) {
             if (sp < 1) { status = GP_PROG_UNDERFLOW; break; }
-            s = 1 + szst[--sp];
+            --sp;
+            s = 1 + szst[sp];
+            k = kst[sp];
+            if (k || row0) v = fold_unary(nd.op, vst[sp]);
         } else {
             if (sp < 2) { status = GP_PROG_UNDERFLOW; break; }
-            const int l = szst[--sp];
-            const int r = szst[--sp];
+            // first pop is the left operand
+            const int l = szst[sp - 1], r = szst[sp - 2];
+            k = kst[sp - 1] & kst[sp - 2];
+            if (k || row0) v = fold_binary(nd.op, vst[sp - 1], vst[sp - 2]);
+            sp -= 2;
             s = 1 + l + r;
         }
         size[j] = (uint8_t)s;
-        szst[sp++] = (uint8_t)s;
+        kon[j] = k;
+        kval[j] = v;
+        szst[sp] = (uint8_t)s;
+        kst[sp] = k;
+        vst[sp] = v;
+        ++sp;
         if (sp > hw) hw = sp;
     }
     if (status == GP_PROG_OK && sp != 1) status = GP_PROG_LEFTOVER;
     if (status == GP_PROG_OK && hw > GP_MAX_STACK) status = GP_PROG_TOO_DEEP;
     if (a.out_prog_status) a.out_prog_status[p] = status;
+    if (row0) {
+        // a non-finite value would poison every shifted row; 0 is as good
+        // as any other finite shift
+        const float k0 = (status == GP_PROG_OK) ? vst[0] : 0.0f;
+        a.shift[p] = isfinite(k0) ? k0 : 0.0f;
+    }
     if (status != GP_PROG_OK) {
         out[0] = make_uint2(make_ins(OP_END, 0, 0), 0u);
         a.meta[p] = ProgMeta{1, status, 0, 0};
@@ -115,15 +192,22 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
         return;
     }
 
-    // pass 2: fold terminal children of binary nodes (prefer the right one)
+    // pass 2: drop the inside of every maximal constant-only subtree (its
+    // root is met first in prefix order), then fold terminal children of
+    // binary nodes (prefer the right one); a constant-only function node
+    // now counts as a terminal
+    for (int j = 0; j < len; ++j) {
+        if (mode[j] == 3 || !kon[j] || op_arity(prog[j].op) == 0) continue;
+        for (int i = j + 1; i < j + size[j]; ++i) mode[i] = 3;
+    }
     for (int j = 0; j < len; ++j) {
         const int op = prog[j].op;
-        if (op_arity(op) != 2) continue;
+        if (op_arity(op) != 2 || kon[j]) continue;  // kon: dropped, or a constant now
         const int lc = j + 1, rc = j + 1 + size[j + 1];
-        if (op_arity(prog[rc].op) == 0) {
+        if (op_arity(prog[rc].op) == 0 || kon[rc]) {
             mode[rc] = 1;
             mode[j] = 1;
-        } else if (op_arity(prog[lc].op) == 0) {
+        } else if (op_arity(prog[lc].op) == 0 || kon[lc]) {
             mode[lc] = 1;
             mode[j] = 2;
         }
@@ -152,7 +236,13 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
     int n = 0, depth = 0;
     sp = 0;
     for (int j = len - 1; j >= 0; --j) {
-        const gp_node nd = prog[j];
+        if (mode[j] == 3) continue;  // inside a folded constant subtree
+        gp_node nd = prog[j];
+        if (kon[j]) {  // a constant, or the root of a constant-only subtree
+            nd.op = GP_CONST;
+            nd.feat = 0;
+            nd.c = kval[j];
+        }
         const int ar = op_arity(nd.op);
         if (ar == 0) {
             if (mode[j]) continue;  // folded into its parent
@@ -172,7 +262,13 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
                 out[n++] = make_uint2(make_ins(ops[b], sp - 2, 0), 0u);
                 --sp;
             } else {
-                const gp_node t = (mode[j] == 1) ? prog[j + 1 + size[j + 1]] : prog[j + 1];
+                const int tj = (mode[j] == 1) ? j + 1 + size[j + 1] : j + 1;
+                gp_node t = prog[tj];
+                if (kon[tj]) {
+                    t.op = GP_CONST;
+                    t.feat = 0;
+                    t.c = kval[tj];
+                }
                 const int x = (t.op == GP_VAR) ? 0 : 1;  // X or C variant
                 // right terminal: t = op(t, u); left terminal: t = op(u, t)
                 const uint32_t fwd[4] = {OP_ADD_X, OP_SUB_X, OP_MUL_X, OP_DIV_X};
@@ -279,6 +375,74 @@ cudaError_t launch_sumw(const float *w, int64_t n_rows, double *part, double *su
                         cudaStream_t st) {
     if (w) sumw_kernel<<<kSumwBlocks, 256, 0, st>>>(w, n_rows, part);
     sumw_final_kernel<<<1, 32, 0, st>>>(part, sumw, w, n_rows);
+    return cudaGetLastError();
+}
+
+// Statistics of y for the correlation fitness, with the partition of
+// sumw_kernel: phase 0 sums w y per block; the first final step sets
+// ybar = sum w y / sum w (FP64) and its float rounding; phase 1 sums
+// w yc and w yc^2 per block with yc = fl(y - fl(ybar)), the very values the
+// evaluator forms; the second final step adds the block sums in order.
+template <int PHASE>
+__global__ void __launch_bounds__(256) ystats_kernel(const float *__restrict__ y,
+                                                     const float *__restrict__ w, int64_t n_rows,
+                                                     const double *ystat, double *part) {
+    __shared__ double red[2][256];
+    const int64_t span = (n_rows + kSumwBlocks - 1) / kSumwBlocks;
+    const int64_t r0 = (int64_t)blockIdx.x * span;
+    const int64_t r1 = min(n_rows, r0 + span);
+    const float ybar = PHASE ? (float)ystat[3] : 0.0f;
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const double wr = w ? (double)w[r] : 1.0;
+        if (PHASE == 0) {
+            s0 += wr * (double)y[r];
+        } else {
+            const double yc = (double)__fsub_rn(y[r], ybar);
+            s0 += wr * yc;
+            s1 += wr * yc * yc;
+        }
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + h];
+            red[1][threadIdx.x] += red[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = red[0][0];
+        part[2 * blockIdx.x + 1] = red[1][0];
+    }
+}
+
+template <int PHASE>
+__global__ void ystats_final_kernel(const double *part, const double *sumw, double *ystat) {
+    if (threadIdx.x != 0) return;
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < kSumwBlocks; ++i) {
+        s0 += part[2 * i];
+        s1 += part[2 * i + 1];
+    }
+    if (PHASE == 0) {
+        const double ybar = s0 / *sumw;
+        ystat[0] = ybar;
+        ystat[3] = (double)(float)ybar;
+    } else {
+        ystat[1] = s0;
+        ystat[2] = s1;
+    }
+}
+
+cudaError_t launch_ystats(const float *y, const float *w, int64_t n_rows, const double *sumw,
+                          double *part, double *ystat, cudaStream_t st) {
+    ystats_kernel<0><<<kSumwBlocks, 256, 0, st>>>(y, w, n_rows, ystat, part);
+    ystats_final_kernel<0><<<1, 32, 0, st>>>(part, sumw, ystat);
+    ystats_kernel<1><<<kSumwBlocks, 256, 0, st>>>(y, w, n_rows, ystat, part);
+    ystats_final_kernel<1><<<1, 32, 0, st>>>(part, sumw, ystat);
     return cudaGetLastError();
 }
 

@@ -5,11 +5,11 @@
 
 namespace gpk {
 cudaError_t launch_eval_r16_f0(const EvalArgs &a, int grid, int block, cudaStream_t st) {
-    if (a.cls != 0) return cudaErrorInvalidValue;
-    return launch_eval_t<16, kSmallDepth - 1, 0, false>(a, grid, block, st);
+    if (a.cls != 0 || a.mom) return cudaErrorInvalidValue;
+    return launch_eval_t<16, kSmallDepth - 1, 0, kEpiLoss>(a, grid, block, st);
 }
-int info_eval_r16_f0(int cls, int block, int *regs) {
-    if (cls != 0) return 0;
-    return info_t<16, kSmallDepth - 1, 0, false>(block, regs);
+int info_eval_r16_f0(int cls, int block, int *regs, bool moments) {
+    if (cls != 0 || moments) return 0;
+    return info_t<16, kSmallDepth - 1, 0, kEpiLoss>(block, regs);
 }
 }  // namespace gpk

@@ -5,11 +5,11 @@
 
 namespace gpk {
 cudaError_t launch_eval_r16_f2(const EvalArgs &a, int grid, int block, cudaStream_t st) {
-    if (a.cls != 0) return cudaErrorInvalidValue;
-    return launch_eval_t<16, kSmallDepth - 1, 2, false>(a, grid, block, st);
+    if (a.cls != 0 || a.mom) return cudaErrorInvalidValue;
+    return launch_eval_t<16, kSmallDepth - 1, 2, kEpiLoss>(a, grid, block, st);
 }
-int info_eval_r16_f2(int cls, int block, int *regs) {
-    if (cls != 0) return 0;
-    return info_t<16, kSmallDepth - 1, 2, false>(block, regs);
+int info_eval_r16_f2(int cls, int block, int *regs, bool moments) {
+    if (cls != 0 || moments) return 0;
+    return info_t<16, kSmallDepth - 1, 2, kEpiLoss>(block, regs);
 }
 }  // namespace gpk

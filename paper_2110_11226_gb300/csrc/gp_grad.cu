@@ -254,4 +254,33 @@ cudaError_t launch_adam(const AdamArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// One thread per program: the k-th CONST node in prefix order is slot k.
+__global__ void __launch_bounds__(128) consts_kernel(gp_node *progs, const int32_t *offsets,
+                                                     int n_progs, float *consts, bool to_nodes) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_progs) return;
+    const int off = offsets[p];
+    const int len = offsets[p + 1] - off;
+    float *row = consts + (size_t)p * GP_MAX_CONSTS;
+    int k = 0;
+    if (len >= 1 && len <= GP_MAX_LEN) {
+        for (int j = 0; j < len && k < GP_MAX_CONSTS; ++j) {
+            gp_node *nd = progs + off + j;
+            if (nd->op != GP_CONST) continue;
+            if (to_nodes) nd->c = row[k];
+            else row[k] = nd->c;
+            ++k;
+        }
+    }
+    if (!to_nodes)
+        for (; k < GP_MAX_CONSTS; ++k) row[k] = 0.0f;
+}
+
+cudaError_t launch_consts(gp_node *progs, const int32_t *offsets, int n_progs, float *consts,
+                          bool to_nodes, cudaStream_t st) {
+    if (n_progs <= 0) return cudaSuccess;
+    consts_kernel<<<(n_progs + 127) / 128, 128, 0, st>>>(progs, offsets, n_progs, consts, to_nodes);
+    return cudaGetLastError();
+}
+
 }  // namespace gpk

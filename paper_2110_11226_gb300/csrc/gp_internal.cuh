@@ -73,6 +73,11 @@ struct Workspace {
     int32_t *order;                // [P] program ids, by class then length
     int32_t *class_count;          // [kNumClasses + 2]
     float *part;                   // [P][n_chunks] per-item partial sums
+    // correlation extras (may be null)
+    double *ystat;                 // [4]: ybar, sum w yc, sum w yc^2, (float) ybar
+    double *ystat_part;            // [kSumwBlocks][2]
+    float *shift;                  // [P] program value at row 0
+    double *mom;                   // [P][n_chunks][3] per-item moment sums
     // constant-gradient extras (may be null)
     uint8_t *rchild;               // [P][256] right child offset per node
     int8_t *kslot;                 // [P][256] constant slot per node or -1
@@ -85,11 +90,18 @@ constexpr int kSumwBlocks = 512;
 
 struct Layout {
     size_t counters, sumw, sumw_part, code, meta, order, class_count, part;
+    size_t ystat, ystat_part, shift, mom;
     size_t rchild, kslot, cnode, gpart, total;
 };
 
-Layout make_layout(int n_progs, int n_chunks, bool grad);
+// moments: reserve the correlation extras (GP_PEARSON)
+Layout make_layout(int n_progs, int n_chunks, bool grad, bool moments = false);
 Workspace carve(void *base, const Layout &L, bool grad);
+
+// workspace bytes of one batched evaluation with this metric (0 for bad
+// arguments); gp_workspace_size reports the largest over all metrics
+size_t workspace_bytes_for(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts *opts,
+                           int metric);
 
 // ---- kernels / launchers (defined in the .cu files) --------------------
 struct CompileArgs {
@@ -104,8 +116,16 @@ struct CompileArgs {
     int16_t *cnode;    // optional
     unsigned int *dev_status;
     int32_t *out_prog_status;  // optional, caller's
+    // optional: each program's value at row 0 of X (column stride ld)
+    const float *X;
+    int64_t ld;
+    float *shift;
 };
 cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st);
+// weighted mean of y and the moments of yc = fl(y - fl(ybar)) (FP64,
+// fixed partition); needs the total weight already in *sumw
+cudaError_t launch_ystats(const float *y, const float *w, int64_t n_rows, const double *sumw,
+                          double *part, double *ystat, cudaStream_t st);
 cudaError_t launch_order(const ProgMeta *meta, int n_progs, int32_t *order,
                          int32_t *class_count, cudaStream_t st);
 cudaError_t launch_sumw(const float *w, int64_t n_rows, double *part,
@@ -131,6 +151,11 @@ struct EvalArgs {
     float *pred;       // predict mode
     unsigned int *dev_status;
     int vec_ok;
+    // moments mode (correlation fitness): per-item sums of w d, w d^2 and
+    // w d yc with d = p - shift[p], yc = y - ybar
+    double *mom;
+    const float *shift;
+    const double *ystat;
 };
 // One launcher per (rows per thread, feature mode) instance; a.cls picks
 // the depth class (register slots).  fmode 2: columns 0 and 1 held in
@@ -139,7 +164,7 @@ struct EvalArgs {
 #define GP_EVAL_INSTANCE(R, F)                                                  \
     cudaError_t launch_eval_r##R##_f##F(const EvalArgs &a, int grid, int block, \
                                         cudaStream_t st);                       \
-    int info_eval_r##R##_f##F(int cls, int block, int *regs);
+    int info_eval_r##R##_f##F(int cls, int block, int *regs, bool moments);
 GP_EVAL_INSTANCE(4, 2)
 GP_EVAL_INSTANCE(4, 0)
 GP_EVAL_INSTANCE(8, 2)
@@ -153,6 +178,8 @@ int info_predict(int block, int *regs);
 
 struct FinalizeArgs {
     const float *part;
+    const double *mom;     // moments mode (GP_PEARSON) instead of part
+    const double *ystat;
     int n_chunks;
     int n_progs;
     const ProgMeta *meta;
@@ -243,6 +270,11 @@ struct AdamArgs {
     float lr, beta1, beta2, eps;
 };
 cudaError_t launch_adam(const AdamArgs &a, cudaStream_t st);
+
+// constants <-> a dense [n_progs][GP_MAX_CONSTS] array (prefix order);
+// to_nodes = false gathers (missing slots 0), true scatters
+cudaError_t launch_consts(gp_node *progs, const int32_t *offsets, int n_progs, float *consts,
+                          bool to_nodes, cudaStream_t st);
 
 cudaError_t probe_pipes(double *out, cudaStream_t st);
 

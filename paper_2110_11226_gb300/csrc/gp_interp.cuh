@@ -213,14 +213,23 @@ constexpr size_t eval_smem_bytes() {
            (size_t)eval_warps<RPT>() * NSLOT * (RPT / 4) * 32 * sizeof(float4);
 }
 
-template <int RPT, int NSLOT, int FMODE, bool PRED>
-__global__ void __launch_bounds__(eval_warps<RPT>() * 32) eval_kernel(const EvalArgs a) {
+// epilogues: the weighted loss sum, the predictions, or the moment sums
+// of the correlation fitness.  The moment epilogue at 8 rows per thread
+// asks for 3 resident blocks (at most 85 registers), the loss epilogue's
+// occupancy; left alone it would take 97 and fit 2.
+constexpr int kEpiLoss = 0, kEpiPred = 1, kEpiMom = 2;
+
+template <int RPT, int NSLOT, int FMODE, int EPI>
+__global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom && RPT == 8 ? 3 : 0) eval_kernel(const EvalArgs a) {
+    constexpr bool PRED = EPI == kEpiPred;
+    constexpr bool MOM = EPI == kEpiMom;
     constexpr int kEvalWarps = eval_warps<RPT>();
     constexpr int kEvalBlock = kEvalWarps * 32;
     extern __shared__ float4 smem_eval[];
     uint2 *cbuf = reinterpret_cast<uint2 *>(smem_eval);
     float4 *stack_all = smem_eval + ((kCodeStride + 1) * sizeof(uint2) + 15) / 16;
     __shared__ float wsum[kEvalWarps];
+    __shared__ double wmom[MOM ? kEvalWarps : 1][3];
     __shared__ unsigned long long s_item;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -230,6 +239,7 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32) eval_kernel(const Eval
     const unsigned long long total = (unsigned long long)n_cls * (unsigned long long)a.n_chunks;
     const bool vec = a.vec_ok != 0;
     const bool two_feat = FMODE == 2 && a.ld > 0;
+    const float ybar = MOM ? (float)a.ystat[3] : 0.0f;
 
     for (unsigned long long it = 0; it <= total; ++it) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1ULL);
@@ -250,6 +260,10 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32) eval_kernel(const Eval
             if (PRED) {
                 for (int64_t r = rb + threadIdx.x; r < re; r += kEvalBlock)
                     a.pred[(size_t)p * a.n_rows + r] = __int_as_float(0x7fc00000);
+            } else if (MOM) {
+                if (threadIdx.x < 3)
+                    a.mom[((size_t)p * a.n_chunks + chunk) * 3 + threadIdx.x] =
+                        __longlong_as_double(0x7ff8000000000000LL);
             } else if (threadIdx.x == 0) {
                 a.part[(size_t)p * a.n_chunks + chunk] = __int_as_float(0x7fc00000);
             }
@@ -263,6 +277,8 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32) eval_kernel(const Eval
         __syncthreads();
 
         float ks = 0.0f, kc = 0.0f;
+        float ms[3] = {0.0f, 0.0f, 0.0f}, mc[3] = {0.0f, 0.0f, 0.0f};
+        const float shift = MOM ? a.shift[p] : 0.0f;
         for (int64_t base = rb + (int64_t)warp * 32 * RPT; base < re;
              base += (int64_t)kEvalWarps * 32 * RPT) {
             const int64_t r0 = base + (int64_t)lane * RPT;
@@ -285,6 +301,26 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32) eval_kernel(const Eval
 #pragma unroll
                 for (int j = 0; j < RPT; ++j)
                     if (r0 + j < re) dst[r0 + j] = t[j];
+            } else if (MOM) {
+                // d = p - shift keeps the sums of squares free of the
+                // cancellation a large mean would cause
+                float yv[RPT], wv[RPT];
+                load_rows<RPT>(yv, a.y, r0, re, vec);
+                if (a.w) load_rows<RPT>(wv, a.w, r0, re, vec);
+                float e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const float d = __fsub_rn(t[j], shift);
+                    const float yc = __fsub_rn(yv[j], ybar);
+                    const float wd = a.w ? __fmul_rn(wv[j], d) : d;
+                    const bool in = r0 + j < re;
+                    e1 = in ? __fadd_rn(e1, wd) : e1;
+                    e2 = in ? __fadd_rn(e2, __fmul_rn(wd, d)) : e2;
+                    e3 = in ? __fadd_rn(e3, __fmul_rn(wd, yc)) : e3;
+                }
+                kahan_add(ms[0], mc[0], e1);
+                kahan_add(ms[1], mc[1], e2);
+                kahan_add(ms[2], mc[2], e3);
             } else {
                 float yv[RPT], wv[RPT];
                 load_rows<RPT>(yv, a.y, r0, re, vec);
@@ -299,14 +335,27 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32) eval_kernel(const Eval
                 kahan_add(ks, kc, e);
             }
         }
-        if (!PRED) {
+        if (MOM) {
+            // the lane's compensated sums in FP64, then a fixed butterfly
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                double v = (double)ms[k] - (double)mc[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) wmom[warp][k] = v;
+            }
+        } else if (!PRED) {
             float v = __fsub_rn(ks, kc);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
             if (lane == 0) wsum[warp] = v;
         }
         __syncthreads();  // wsum complete; everyone is done with cbuf and s_item
-        if (!PRED && threadIdx.x == 0) {
+        if (MOM && threadIdx.x < 3) {
+            double v = 0.0;
+            for (int w = 0; w < kEvalWarps; ++w) v += wmom[w][threadIdx.x];
+            a.mom[((size_t)p * a.n_chunks + chunk) * 3 + threadIdx.x] = v;
+        } else if (!PRED && !MOM && threadIdx.x == 0) {
             float v = 0.0f;
             for (int w = 0; w < kEvalWarps; ++w) v = __fadd_rn(v, wsum[w]);
             a.part[(size_t)p * a.n_chunks + chunk] = v;
@@ -314,22 +363,22 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32) eval_kernel(const Eval
     }
 }
 
-template <int RPT, int NSLOT, int FMODE, bool PRED>
+template <int RPT, int NSLOT, int FMODE, int EPI>
 cudaError_t launch_eval_t(const EvalArgs &a, int grid, int block, cudaStream_t st) {
     (void)block;
     constexpr size_t smem = eval_smem_bytes<RPT, NSLOT>();
-    auto k = eval_kernel<RPT, NSLOT, FMODE, PRED>;
+    auto k = eval_kernel<RPT, NSLOT, FMODE, EPI>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, eval_warps<RPT>() * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int RPT, int NSLOT, int FMODE, bool PRED>
+template <int RPT, int NSLOT, int FMODE, int EPI>
 int info_t(int block, int *regs) {
     (void)block;
     constexpr size_t smem = eval_smem_bytes<RPT, NSLOT>();
-    auto k = eval_kernel<RPT, NSLOT, FMODE, PRED>;
+    auto k = eval_kernel<RPT, NSLOT, FMODE, EPI>;
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 0;
     if (regs) *regs = fa.numRegs;

@@ -4,7 +4,7 @@
 
 namespace gpk {
 cudaError_t launch_predict(const EvalArgs &a, int grid, int block, cudaStream_t st) {
-    return launch_eval_t<4, kDeepSlots, 0, true>(a, grid, block, st);
+    return launch_eval_t<4, kDeepSlots, 0, kEpiPred>(a, grid, block, st);
 }
-int info_predict(int block, int *regs) { return info_t<4, kDeepSlots, 0, true>(block, regs); }
+int info_predict(int block, int *regs) { return info_t<4, kDeepSlots, 0, kEpiPred>(block, regs); }
 }  // namespace gpk

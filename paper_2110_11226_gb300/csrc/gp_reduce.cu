@@ -19,6 +19,23 @@ __device__ __forceinline__ double finish_metric(int metric, double s_e, double s
     return f;
 }
 
+// |r| of the weighted Pearson correlation from shifted moment sums:
+// s1 = sum w d, s2 = sum w d^2, s12 = sum w d yc (d = p - shift), with
+// syc = sum w yc, syy = sum w yc^2 and sw = sum w.  Shifting p or y by a
+// constant leaves r unchanged.  Non-finite sums give NaN; a zero variance
+// gives 0.
+__device__ double pearson_from_moments(double s1, double s2, double s12, double sw, double syc,
+                                       double syy) {
+    const double md = s1 / sw, my = syc / sw;
+    const double vp = s2 / sw - md * md;
+    const double vy = syy / sw - my * my;
+    const double cov = s12 / sw - md * my;
+    if (!isfinite(vp) || !isfinite(cov) || !isfinite(vy))
+        return __longlong_as_double(0x7ff8000000000000LL);
+    if (!(vp > 0.0) || !(vy > 0.0)) return 0.0;
+    return fabs(cov) / sqrt(vp * vy);
+}
+
 // warp w handles program w; lane l adds chunks l, l+32, ... in order, then
 // the 32 lane sums are combined by lane 0 in lane order.
 __global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs a) {
@@ -28,7 +45,18 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs a) {
     const float *part = a.part + (size_t)p * a.n_chunks;
     const ProgMeta m = a.meta[p];
     double f;
-    if (a.accum == GP_ACCUM_KAHAN32) {
+    if (a.mom) {
+        // correlation fitness: the moment sums of d = p - shift and yc,
+        // chunk order per lane then lane order, in FP64
+        const double *mp = a.mom + (size_t)p * a.n_chunks * 3;
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int i = lane; i < a.n_chunks; i += 32)
+            for (int k = 0; k < 3; ++k) s[k] += mp[(size_t)i * 3 + k];
+        double S[3] = {0.0, 0.0, 0.0};
+        for (int l = 0; l < 32; ++l)
+            for (int k = 0; k < 3; ++k) S[k] += __shfl_sync(0xffffffffu, s[k], l);
+        f = pearson_from_moments(S[0], S[1], S[2], *a.sumw, a.ystat[1], a.ystat[2]);
+    } else if (a.accum == GP_ACCUM_KAHAN32) {
         float s = 0.0f, c = 0.0f;
         for (int i = lane; i < a.n_chunks; i += 32) kahan32(s, c, part[i]);
         float mine = __fsub_rn(s, c);

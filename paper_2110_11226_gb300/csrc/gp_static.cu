@@ -49,7 +49,7 @@ extern "C" int gp_evaluate_static(const gp_node *progs, const int32_t *offsets, 
                                   const float *w, int metric, float *out_fitness, void *stream) {
     if (n_progs < 1 || n_rows < 1 || n_feat < 1) return GP_ERR_ARG;
     // the workspace this problem needs with the default tunables
-    const size_t need = gp_workspace_size(n_progs, n_rows, n_feat, nullptr);
+    const size_t need = gpk::workspace_bytes_for(n_progs, n_rows, n_feat, nullptr, metric);
     if (need == 0) return GP_ERR_ARG;
     if (need > (size_t)GP_STATIC_SCRATCH_BYTES) return GP_ERR_WORKSPACE;
     void *ws = nullptr;

@@ -22,7 +22,8 @@ import torch
 
 from . import build as _build
 
-METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3}
+METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3, "pearson": 4}
+GREATER_IS_BETTER = {"pearson"}
 ACCUM = {"fp64": 0, "kahan32": 1}
 MAX_CONSTS = 16
 NODE_DTYPE = np.dtype([("op", "<i2"), ("feat", "<i2"), ("c", "<f4")])
@@ -69,6 +70,8 @@ def _load():
         "gp_tournament": (i32, [P, i32, i32, u64, P]),
         "gp_const_grad": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P, P]),
         "gp_adam_step": (i32, [P, P, i32, P, P, P, i32, f32, f32, f32, f32, P]),
+        "gp_get_consts": (i32, [P, P, i32, P, P]),
+        "gp_set_consts": (i32, [P, P, i32, P, P]),
         "gp_last_device_status": (i32, [P, P]),
         "gp_autotune": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
         "gp_probe_pipes": (i32, [P, P]),
@@ -298,6 +301,49 @@ def gp_adam_step(progs, offsets, grad, m, v, step, lr=1e-2, beta1=0.9, beta2=0.9
         _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(grad, "grad"),
         _dptr(m, "m"), _dptr(v, "v"), int(step), float(lr), float(beta1), float(beta2),
         float(eps), _stream(stream)))
+
+
+def gp_get_consts(progs, offsets, out=None, stream=None):
+    P = _nprogs(offsets)
+    if out is None:
+        out = torch.empty((P, MAX_CONSTS), dtype=torch.float32, device=progs.device)
+    _check("gp_get_consts", _lib.gp_get_consts(_dptr(progs, "progs"), _dptr(offsets, "offsets"),
+                                               P, _dptr(out, "out"), _stream(stream)))
+    return out
+
+
+def gp_set_consts(progs, offsets, consts, stream=None):
+    P = _nprogs(offsets)
+    if consts.shape != (P, MAX_CONSTS) or consts.dtype != torch.float32:
+        raise GPError(f"gp_set_consts: consts must be float32 [{P}, {MAX_CONSTS}]")
+    _check("gp_set_consts", _lib.gp_set_consts(_dptr(progs, "progs"), _dptr(offsets, "offsets"),
+                                               P, _dptr(consts, "consts"), _stream(stream)))
+
+
+class ConstantsFitness(torch.autograd.Function):
+    """fitness[P] as a differentiable function of the constants [P, 16].
+
+    forward writes the constants into the programs' nodes (in place, like
+    gp_adam_step) and runs gp_const_grad, which returns the fitness and its
+    gradient in one pass; backward scales that gradient by the incoming one.
+    Slots past a program's constant count get gradient 0."""
+
+    @staticmethod
+    def forward(ctx, consts, progs, offsets, X, y, w, metric):
+        c = consts.detach().contiguous()
+        gp_set_consts(progs, offsets, c)
+        grad, fit = gp_const_grad(progs, offsets, X, y, w, metric)
+        ctx.save_for_backward(grad)
+        return fit
+
+    @staticmethod
+    def backward(ctx, g_fit):
+        (grad,) = ctx.saved_tensors
+        return grad * g_fit.unsqueeze(1), None, None, None, None, None, None
+
+
+def fitness_of_constants(consts, progs, offsets, X, y, w=None, metric="mse"):
+    return ConstantsFitness.apply(consts, progs, offsets, X, y, w, metric)
 
 
 def gp_last_device_status(stream=None) -> int:

@@ -128,3 +128,46 @@ def check_fitness(gpu_fit, nodes, off, X, y, w, metric, row0=0, n_eval=None, v=N
     assert np.all(np.isnan(gpu_fit[st != 0]))
     mr = float(np.max(rel[strict])) if strict.any() else 0.0
     return FitStats(len(f64), int(strict.sum()), int(cond.sum()), int(flagged.sum()), mr), f64
+
+
+def check_pearson(gpu_fit, nodes, off, X, y, w):
+    """Weighted Pearson fitness |r| against the FP64 oracle.
+
+    A per-row FP32 error e moves the centred prediction vector by at most
+    ||e||_w, and |r| is the cosine of the angle between the centred
+    prediction and target vectors, so |d|r|| <= 2 ||e||_w / sd_w(p); the
+    FP32 accumulation of the shifted moment sums adds a relative error of a
+    few ulp of E_w[(p - p0)^2] / var_w(p) (p0 = the value on row 0, the
+    evaluator's shift).  Programs with flagged rows, or whose squared
+    deviations leave the float range, are counted, not compared."""
+    gpu_fit = np.asarray(gpu_fit, np.float64)
+    f64, st = oracle.fitness(nodes, off, X, y, w, "pearson")
+    v, e, fl = oracle.predict_bound(nodes, off, X, ulps_fn=ULPS)
+    wv = np.ones(v.shape[1]) if w is None else w.astype(np.float64)
+    sw = wv.sum()
+    FMAX = float(np.finfo(np.float32).max)
+    with np.errstate(all="ignore"):
+        mean = (v * wv).sum(axis=1) / sw
+        var = (((v - mean[:, None]) ** 2) * wv).sum(axis=1) / sw
+        dev0 = (((v - v[:, :1]) ** 2) * wv)
+        ew = np.sqrt((e * e * wv).sum(axis=1) / sw)
+        b = 2.0 * ew / np.sqrt(var) + 1e-5 * (dev0.sum(axis=1) / sw) / var
+        rng_flag = (np.nanmax(dev0, axis=1) > 0.5 * FMAX) | (dev0.sum(axis=1) > 0.5 * FMAX) | \
+            ~np.isfinite(v).all(axis=1)
+    flagged = (fl != 0).any(axis=1) | (st != 0) | rng_flag
+    with np.errstate(invalid="ignore"):
+        strict = ~flagged & np.isfinite(f64) & (var > 0) & (b <= 0.25 * REL_FIT * np.abs(f64))
+        err = np.abs(gpu_fit - f64)
+        strict_ok = ~strict | (err <= REL_FIT * np.abs(f64)) | (err <= 1e-12)
+    assert strict_ok.all(), f"pearson mismatch: {np.argwhere(~strict_ok)[:5].ravel()}"
+    cond = ~flagged & ~strict
+    with np.errstate(invalid="ignore"):
+        cond_ok = ~cond | (err <= 1.5 * b + REL_FIT * np.abs(f64)) | (np.isnan(b) & (var == 0))
+        # a program constant in FP64 is constant in FP32 too when the
+        # constant does not depend on the row: both give exactly 0
+        zero_ok = ~(cond & (var == 0)) | (gpu_fit == 0) | (b > 0)
+    assert cond_ok.all(), f"pearson beyond bound: {np.argwhere(~cond_ok)[:5].ravel()}"
+    assert zero_ok.all()
+    assert np.all(np.isnan(gpu_fit[st != 0]))
+    mr = float(np.max(err[strict] / np.abs(f64[strict]))) if strict.any() else 0.0
+    return FitStats(len(f64), int(strict.sum()), int(cond.sum()), int(flagged.sum()), mr), f64

@@ -13,7 +13,7 @@ import torch
 import oracle
 from paper_2110_11226_gb300 import gp, synth
 from helpers import pack, parse_prefix, read_table
-from parity import check_fitness, check_points
+from parity import check_fitness, check_pearson, check_points
 
 pytestmark = pytest.mark.gpu
 
@@ -73,6 +73,35 @@ def test_predict_full_function_set(n_feat, funcs):
     pn, po, dX, _, _ = put(nodes, off, X)
     got = gp.gp_predict(pn, po, dX).cpu().numpy()
     st, _ = check_points(got, nodes, off, X)
+    assert st.ok > 0.5 * st.rows, st
+
+
+def test_constant_subtrees_fold_to_the_per_row_value():
+    """The pre-pass folds every constant-only subtree into one constant,
+    computed with the evaluator's own FP32 operations.  Columns 0-2 of X hold
+    one value each on every row; replacing each read of such a column by a
+    constant of that value makes those subtrees constant-only, and the
+    predictions must not change by a single bit (values below the protection
+    threshold, on the trig slow path, zero and negative included)."""
+    cval = np.array([0.0005, 70000.0, -3.75], np.float32)
+    funcs = synth.FULL_SET + ("tan",)
+    nodes, off = synth.ramped_half_and_half(800, 2, 8, funcs, 6, seed=77)
+    n = 1024 + 45
+    X = np.random.default_rng(5).uniform(-5, 5, size=(6, n)).astype(np.float32)
+    X[:3] = cval[:, None]
+    folded = nodes.copy()
+    is_const_col = (folded["op"] == synth.OP["var"]) & (folded["feat"] < 3)
+    folded["c"][is_const_col] = cval[folded["feat"][is_const_col]]
+    folded["op"][is_const_col] = synth.OP["const"]
+    folded["feat"][is_const_col] = 0
+    assert is_const_col.sum() > 300
+    a = gp.gp_predict(*put(nodes, off, X)[:3]).cpu().numpy()
+    b = gp.gp_predict(*put(folded, off, X)[:3]).cpu().numpy()
+    nan = np.isnan(a)
+    np.testing.assert_array_equal(nan, np.isnan(b))
+    np.testing.assert_array_equal(a[~nan].view(np.uint32), b[~nan].view(np.uint32))
+    # and the folded programs still agree with the oracle
+    st, _ = check_points(b, folded, off, X)
     assert st.ok > 0.5 * st.rows, st
 
 
@@ -140,6 +169,60 @@ def test_fitness_metrics_ragged_many_chunks(metric, weighted):
         fit = gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=metric, opts=opts).cpu().numpy()
         stats, _ = check_fitness(fit, nodes, off, d.X, d.y, w, metric)
         assert stats.strict > 0.5 * stats.programs, stats
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("n_feat", [2, 9])
+def test_pearson_fitness(weighted, n_feat):
+    """Weighted Pearson fitness |r| over several row chunks and a ragged
+    tail: programs from the full set plus exact cases (an affine image of y
+    scores 1, constants score 0), both feature modes, every rows-per-thread
+    instance."""
+    n = 3 * 4096 + 123
+    rng = np.random.default_rng(90 + n_feat)
+    X = rng.uniform(-4, 4, size=(n_feat, n)).astype(np.float32)
+    y = (X[0] * np.float32(0.5) + np.sin(X[1]).astype(np.float32)).astype(np.float32)
+    w = _weights(n, 11) if weighted else None
+    nodes, off = synth.ramped_half_and_half(300, 2, 7, synth.FULL_SET + ("tan",), n_feat,
+                                            seed=91 + n_feat)
+    extra = [
+        [(synth.OP["const"], 0, 2.0)],
+        [(synth.OP["sin"], 0, 0.0), (synth.OP["const"], 0, 0.3)],
+        [(synth.OP["var"], 0, 0.0)],
+        [(synth.OP["add"], 0, 0.0), (synth.OP["mul"], 0, 0.0), (synth.OP["const"], 0, 0.5),
+         (synth.OP["var"], 0, 0.0), (synth.OP["sin"], 0, 0.0), (synth.OP["var"], 1, 0.0)],
+        [(synth.OP["neg"], 0, 0.0), (synth.OP["add"], 0, 0.0), (synth.OP["mul"], 0, 0.0),
+         (synth.OP["const"], 0, 0.5), (synth.OP["var"], 0, 0.0), (synth.OP["sin"], 0, 0.0),
+         (synth.OP["var"], 1, 0.0)],
+    ]
+    nodes, off = pack(synth.unpack(nodes, off) + extra)
+    pn, po, dX, dy, dw = put(nodes, off, X, y, w)
+    for rpt in (4, 8, 16):
+        opts = gp.make_opts(rows_per_thread=rpt, chunk_rows=1024)
+        fit = gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric="pearson", opts=opts).cpu().numpy()
+        st, f64 = check_pearson(fit, nodes, off, X, y, w)
+        assert st.strict > 0.5 * st.programs, st
+        assert fit[-5] == 0.0 and fit[-4] == 0.0
+        assert fit[-2] == pytest.approx(1.0, abs=2e-6) and fit[-1] == pytest.approx(1.0, abs=2e-6)
+    # the default entry point and the host entry point agree with the above
+    fit_d = gp.gp_evaluate(pn, po, dX, dy, dw, metric="pearson").cpu().numpy()
+    check_pearson(fit_d, nodes, off, X, y, w)
+    fit_h = gp.gp_evaluate_host(nodes, off, X, y, w, metric="pearson")
+    np.testing.assert_array_equal(np.isnan(fit_h), np.isnan(fit_d))
+    # selection on |r| (greater is better) is the oracle's, bit for bit
+    win = gp.gp_tournament_ex(torch.from_numpy(fit_d).cuda(), 400, 20, 5,
+                              greater_is_better=True).cpu().numpy()
+    np.testing.assert_array_equal(win, oracle.tournament(fit_d, 400, 20, 5, greater_is_better=True))
+
+
+def test_pearson_rejected_where_unsupported():
+    d = synth.pagie_data(1024, 3)
+    nodes, off = synth.ramped_half_and_half(8, 2, 4, synth.FULL_SET, 2, seed=3)
+    pn, po, dX, dy, _ = put(nodes, off, d.X, d.y)
+    with pytest.raises(gp.GPError):
+        gp.gp_evaluate_plain(pn, po, dX, dy, metric="pearson")
+    with pytest.raises(gp.GPError):
+        gp.gp_const_grad(pn, po, dX, dy, metric="pearson")
 
 
 def test_plain_evaluator_matches_oracle_and_batched():
@@ -400,6 +483,39 @@ def test_adam_steps_match_oracle():
             np.testing.assert_array_equal(after["c"][kidx[~fin]], cur["c"][kidx[~fin]])
         theta = after["c"].astype(np.float64)
     assert np.array_equal(after["op"], nodes["op"])
+
+
+def test_constants_as_a_differentiable_tensor():
+    """gp_get_consts / gp_set_consts move the constants between the nodes and
+    a dense [P, 16] tensor (prefix order, bit for bit), and the autograd
+    wrapper returns gp_const_grad's fitness and gradient for that tensor."""
+    d = synth.pagie_data(4096 + 19, 8)
+    nodes, off = synth.ramped_half_and_half(64, 2, 6, synth.FULL_SET, 2, seed=73, max_consts=16)
+    pn, po, dX, dy, _ = put(nodes, off, d.X, d.y)
+    c = gp.gp_get_consts(pn, po).cpu().numpy()
+    want = np.zeros((64, 16), np.float32)
+    for p in range(64):
+        seg = nodes[off[p]:off[p + 1]]
+        cs = seg["c"][seg["op"] == synth.OP["const"]][:16]
+        want[p, :len(cs)] = cs
+    np.testing.assert_array_equal(c.view(np.uint32), want.view(np.uint32))
+
+    theta = torch.from_numpy(want * np.float32(1.5) - np.float32(0.25)).cuda().requires_grad_(True)
+    fit = gp.fitness_of_constants(theta, pn, po, dX, dy, None, "mse")
+    back = gp.gp_get_consts(pn, po).cpu().numpy()
+    counts = np.array([min(16, int((nodes[off[p]:off[p + 1]]["op"] == synth.OP["const"]).sum()))
+                       for p in range(64)])
+    live = np.arange(16)[None, :] < counts[:, None]
+    np.testing.assert_array_equal(back[live], theta.detach().cpu().numpy()[live])
+    g_ref, f_ref = gp.gp_const_grad(pn, po, dX, dy, metric="mse")
+    assert torch.equal(fit.detach(), f_ref)
+    wts = torch.rand(64, device="cuda")
+    (fit * wts).sum().backward()
+    assert torch.equal(theta.grad, g_ref * wts.unsqueeze(1))
+    assert torch.all(theta.grad.cpu()[torch.from_numpy(~live)] == 0)
+    # the fitness of the rewritten programs agrees with the oracle
+    moved = gp.nodes_from_device(pn)
+    check_fitness(fit.detach().cpu().numpy(), moved, off, d.X, d.y, None, "mse")
 
 
 # --------------------------------------------------------------------------

@@ -43,6 +43,8 @@ MUTANTS = {
     "dcos_sign": ("case ORA_COS:  du = -sin(u); break;", "case ORA_COS:  du = sin(u); break;"),
     "adam_no_bias_correction": ("double mh = m[i] / b1t, vh = v[i] / b2t;",
                                 "double mh = m[i], vh = v[i] / b2t;"),
+    "pearson_p_not_centred": ("spp += wi * dp * dp;", "spp += wi * v * v;"),
+    "pearson_signed": ("else f = fabs(spy / sqrt(spp * syy));", "else f = spy / sqrt(spp * syy);"),
     "bound_drops_mul_term": ("r.e = fabs(a.v) * b.e + fabs(b.v) * a.e + a.e * b.e;",
                              "r.e = fabs(a.v) * b.e + a.e * b.e;"),
 }

@@ -315,6 +315,58 @@ def test_metrics_match_scikit_learn():
         assert ll[i] == pytest.approx(ref, rel=1e-9)
 
 
+def test_pearson_closed_forms_and_numpy():
+    """Weighted Pearson fitness |r|: an affine image of y scores exactly 1
+    whatever its sign, a constant scores 0, unit weights give numpy's
+    corrcoef, integer weights equal duplicated rows, and rescaling the
+    weights or the prediction changes nothing."""
+    rng = np.random.default_rng(21)
+    n = 777
+    X = rng.uniform(-3, 3, size=(2, n)).astype(np.float32)
+    y = X[0].copy()  # y = x0 exactly
+    w = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    progs = [
+        [(synth.OP["add"], 0, 0.0), (synth.OP["mul"], 0, 0.0), (synth.OP["const"], 0, 2.5),
+         (synth.OP["var"], 0, 0.0), (synth.OP["const"], 0, 1.0)],       # 2.5 x0 + 1
+        [(synth.OP["neg"], 0, 0.0), (synth.OP["var"], 0, 0.0)],          # -x0
+        [(synth.OP["const"], 0, 0.375)],                                 # constant
+        [(synth.OP["sin"], 0, 0.0), (synth.OP["var"], 1, 0.0)],          # unrelated
+    ]
+    nodes, off = pack(progs)
+    f = oracle.fitness(nodes, off, X, y, w, "pearson")[0]
+    assert f[0] == pytest.approx(1.0, abs=1e-14) and f[1] == pytest.approx(1.0, abs=1e-14)
+    assert f[2] == 0.0
+    assert f[3] < 0.2
+    # unit weights: numpy's (unweighted) correlation of the oracle's predictions
+    Xr, yr, wr = _rand_data(401, 6)
+    rn, roff = synth.ramped_half_and_half(30, 2, 5, synth.FULL_SET, 2, seed=14)
+    pred = oracle.predict64(rn, roff, Xr)[0]
+    un = oracle.fitness(rn, roff, Xr, yr, None, "pearson")[0]
+    for i in range(len(un)):
+        if not np.all(np.isfinite(pred[i])) or np.ptp(pred[i]) == 0:
+            continue
+        assert un[i] == pytest.approx(abs(np.corrcoef(pred[i], yr.astype(np.float64))[0, 1]),
+                                      rel=1e-10, abs=1e-13)
+    # integer weights == duplicated rows; scaled weights change nothing
+    wi = rng.integers(1, 4, size=len(yr)).astype(np.float32)
+    rep = np.repeat(np.arange(len(yr)), wi.astype(int))
+    fw = oracle.fitness(rn, roff, Xr, yr, wi, "pearson")[0]
+    fd = oracle.fitness(rn, roff, Xr[:, rep], yr[rep], None, "pearson")[0]
+    fs = oracle.fitness(rn, roff, Xr, yr, wi * np.float32(8.0), "pearson")[0]
+    fin = np.isfinite(fw)
+    np.testing.assert_allclose(fw[fin], fd[fin], rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(fw[fin], fs[fin], rtol=1e-12, atol=1e-14)
+    # prediction scaled by -3 (a wrapped program): same |r|
+    scaled = []
+    for prog in synth.unpack(rn, roff):
+        scaled.append([(synth.OP["mul"], 0, 0.0), (synth.OP["const"], 0, -3.0)] + list(prog))
+    sn, soff = pack(scaled)
+    f3 = oracle.fitness(sn, soff, Xr, yr, wr, "pearson")[0]
+    f1 = oracle.fitness(rn, roff, Xr, yr, wr, "pearson")[0]
+    ok = np.isfinite(f1) & np.isfinite(f3) & (f1 > 1e-6)
+    np.testing.assert_allclose(f3[ok], f1[ok], rtol=1e-9)
+
+
 def test_logloss_limits():
     # the c*|p| term vanishes for the matching label, so saturated correct
     # predictions cost 0 and saturated wrong ones cost |p|
