@@ -313,9 +313,13 @@ int gp_timing_read(double *total_ms, int *n_calls);
  * arguments, same results) but uses a fixed scratch array of
  * GP_STATIC_SCRATCH_BYTES that is part of the library's device image, which
  * every GPU that loads the library holds until the process exits; it calls
- * no allocating routine.  A problem whose workspace (gp_workspace_size with
- * default tunables) exceeds that size gets GP_ERR_WORKSPACE and nothing is
- * launched; at P = 4096 programs and 16M rows it needs about 12 MiB.  The
+ * no allocating routine.  When the workspace of the default tunables
+ * exceeds that size, the call uses longer row chunks (65536 rows, then 4x
+ * longer each time) until it fits -- its fitness then equals gp_evaluate_ex
+ * with that chunk_rows, and gp_evaluate's within the FP32 summation order;
+ * at P = 4096 programs and 16M rows that is 65536-row chunks in about
+ * 12 MiB.  A problem that fits with none gets GP_ERR_WORKSPACE and nothing
+ * is launched.  The
  * first call on a device looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream
  * capture.  All calls share the one array and it keeps the last call's

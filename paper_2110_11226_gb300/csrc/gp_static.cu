@@ -48,9 +48,17 @@ extern "C" int gp_evaluate_static(const gp_node *progs, const int32_t *offsets, 
                                   const float *X, int64_t n_rows, int n_feat, const float *y,
                                   const float *w, int metric, float *out_fitness, void *stream) {
     if (n_progs < 1 || n_rows < 1 || n_feat < 1) return GP_ERR_ARG;
-    // the workspace this problem needs with the default tunables
-    const size_t need = gpk::workspace_bytes_for(n_progs, n_rows, n_feat, nullptr, metric);
+    // the default tunables, or, when their workspace does not fit, longer
+    // row chunks (fewer per-chunk partial sums)
+    gp_eval_opts opts{};
+    size_t need = gpk::workspace_bytes_for(n_progs, n_rows, n_feat, nullptr, metric);
     if (need == 0) return GP_ERR_ARG;
+    for (int chunk = 65536; need > (size_t)GP_STATIC_SCRATCH_BYTES && chunk <= (1 << 22);
+         chunk *= 4) {
+        opts.chunk_rows = chunk;
+        need = gpk::workspace_bytes_for(n_progs, n_rows, n_feat, &opts, metric);
+        if (need == 0) return GP_ERR_ARG;
+    }
     if (need > (size_t)GP_STATIC_SCRATCH_BYTES) return GP_ERR_WORKSPACE;
     void *ws = nullptr;
     const int rc = static_scratch(&ws);
@@ -58,7 +66,7 @@ extern "C" int gp_evaluate_static(const gp_node *progs, const int32_t *offsets, 
     // the evaluator clears the one region that must start at zero (the work
     // queue counters) on every call and writes every other region before
     // reading it, so nothing of the previous call leaks into this one
-    return gp_evaluate_ex(progs, offsets, n_progs, X, n_rows, n_feat, y, w, metric, nullptr,
-                          out_fitness, nullptr, nullptr, ws, (size_t)GP_STATIC_SCRATCH_BYTES,
-                          stream);
+    return gp_evaluate_ex(progs, offsets, n_progs, X, n_rows, n_feat, y, w, metric,
+                          opts.chunk_rows ? &opts : nullptr, out_fitness, nullptr, nullptr, ws,
+                          (size_t)GP_STATIC_SCRATCH_BYTES, stream);
 }

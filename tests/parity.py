@@ -138,7 +138,8 @@ def check_pearson(gpu_fit, nodes, off, X, y, w):
     prediction and target vectors, so |d|r|| <= 2 ||e||_w / sd_w(p); the
     FP32 accumulation of the shifted moment sums adds a relative error of a
     few ulp of E_w[(p - p0)^2] / var_w(p) (p0 = the value on row 0, the
-    evaluator's shift).  Programs with flagged rows, or whose squared
+    evaluator's shift; 32 ulp of FP32 covers the 8-row plain sums inside
+    the compensated per-lane sums).  Programs with flagged rows, or whose squared
     deviations leave the float range, are counted, not compared."""
     gpu_fit = np.asarray(gpu_fit, np.float64)
     f64, st = oracle.fitness(nodes, off, X, y, w, "pearson")
@@ -151,7 +152,7 @@ def check_pearson(gpu_fit, nodes, off, X, y, w):
         var = (((v - mean[:, None]) ** 2) * wv).sum(axis=1) / sw
         dev0 = (((v - v[:, :1]) ** 2) * wv)
         ew = np.sqrt((e * e * wv).sum(axis=1) / sw)
-        b = 2.0 * ew / np.sqrt(var) + 1e-5 * (dev0.sum(axis=1) / sw) / var
+        b = 2.0 * ew / np.sqrt(var) + 2e-6 * (dev0.sum(axis=1) / sw) / var
         rng_flag = (np.nanmax(dev0, axis=1) > 0.5 * FMAX) | (dev0.sum(axis=1) > 0.5 * FMAX) | \
             ~np.isfinite(v).all(axis=1)
     flagged = (fl != 0).any(axis=1) | (st != 0) | rng_flag

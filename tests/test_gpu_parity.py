@@ -195,13 +195,30 @@ def test_pearson_fitness(weighted, n_feat):
          (synth.OP["const"], 0, 0.5), (synth.OP["var"], 0, 0.0), (synth.OP["sin"], 0, 0.0),
          (synth.OP["var"], 1, 0.0)],
     ]
-    nodes, off = pack(synth.unpack(nodes, off) + extra)
+    # random programs barely correlate with y (median |r| ~ 0.01), so most
+    # can only be held to their propagated bound; programs close to the
+    # target's form, c1 x0 + c2 sin(x1) + c3 cos(x0), correlate well and
+    # must meet the 1e-4 tolerance
+    crng = np.random.default_rng(7)
+    close = []
+    for _ in range(60):
+        c1, c2, c3 = (float(np.float32(v)) for v in crng.uniform(-2, 2, 3))
+        close.append([(synth.OP["add"], 0, 0.0), (synth.OP["add"], 0, 0.0),
+                      (synth.OP["mul"], 0, 0.0), (synth.OP["const"], 0, c1), (synth.OP["var"], 0, 0.0),
+                      (synth.OP["mul"], 0, 0.0), (synth.OP["const"], 0, c2),
+                      (synth.OP["sin"], 0, 0.0), (synth.OP["var"], 1, 0.0),
+                      (synth.OP["mul"], 0, 0.0), (synth.OP["const"], 0, c3),
+                      (synth.OP["cos"], 0, 0.0), (synth.OP["var"], 0, 0.0)])
+    nodes, off = pack(synth.unpack(nodes, off) + close + extra)
+    n_close = len(close) + len(extra)
     pn, po, dX, dy, dw = put(nodes, off, X, y, w)
     for rpt in (4, 8, 16):
         opts = gp.make_opts(rows_per_thread=rpt, chunk_rows=1024)
         fit = gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric="pearson", opts=opts).cpu().numpy()
         st, f64 = check_pearson(fit, nodes, off, X, y, w)
-        assert st.strict > 0.5 * st.programs, st
+        assert st.flagged < 0.3 * st.programs, st
+        st_close, _ = check_pearson(fit[-n_close:], *pack(close + extra), X, y, w)
+        assert st_close.strict >= 0.8 * len(close), st_close
         assert fit[-5] == 0.0 and fit[-4] == 0.0
         assert fit[-2] == pytest.approx(1.0, abs=2e-6) and fit[-1] == pytest.approx(1.0, abs=2e-6)
     # the default entry point and the host entry point agree with the above
@@ -508,11 +525,15 @@ def test_constants_as_a_differentiable_tensor():
     live = np.arange(16)[None, :] < counts[:, None]
     np.testing.assert_array_equal(back[live], theta.detach().cpu().numpy()[live])
     g_ref, f_ref = gp.gp_const_grad(pn, po, dX, dy, metric="mse")
-    assert torch.equal(fit.detach(), f_ref)
+    # bit for bit, NaN where the program's value leaves the float range
+    torch.testing.assert_close(fit.detach(), f_ref, rtol=0, atol=0, equal_nan=True)
     wts = torch.rand(64, device="cuda")
     (fit * wts).sum().backward()
-    assert torch.equal(theta.grad, g_ref * wts.unsqueeze(1))
-    assert torch.all(theta.grad.cpu()[torch.from_numpy(~live)] == 0)
+    torch.testing.assert_close(theta.grad, g_ref * wts.unsqueeze(1), rtol=0, atol=0,
+                               equal_nan=True)
+    fin = torch.isfinite(f_ref).cpu().numpy()
+    assert fin.sum() > 40
+    assert torch.all(theta.grad.cpu()[torch.from_numpy(~live & fin[:, None])] == 0)
     # the fitness of the rewritten programs agrees with the oracle
     moved = gp.nodes_from_device(pn)
     check_fitness(fit.detach().cpu().numpy(), moved, off, d.X, d.y, None, "mse")
