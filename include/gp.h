@@ -113,7 +113,7 @@ enum gp_accum { GP_ACCUM_FP64 = 0, GP_ACCUM_KAHAN32 = 1 };
  * with the same rows_per_thread and chunk_rows (fixed reduction
  * partition); blocks_per_sm never changes them. */
 typedef struct gp_eval_opts {
-    int rows_per_thread;  /* 4, 8 or 16 (default 8)                       */
+    int rows_per_thread;  /* 4, 8 or 16 (default 4)                       */
     int chunk_rows;       /* rows per work item, multiple of 256          */
     int blocks_per_sm;    /* resident blocks per SM of the persistent grid */
     int accum;            /* gp_accum                                     */
@@ -168,7 +168,7 @@ size_t gp_workspace_size(int n_progs, int64_t n_rows, int n_feat,
 
 /* The tunables gp_evaluate_ex would use for this shape: `opts` (may be NULL)
  * with every zero field filled from the autotuner's record for the shape, or
- * else from the built-in defaults (rows_per_thread 8; chunk_rows sized for
+ * else from the built-in defaults (rows_per_thread 4; chunk_rows sized for
  * about 16 work items per resident warp, 1024..65536 rows; blocks_per_sm 0 =
  * as many as fit).  Programs deeper than 8 stack slots always run with 4
  * rows per thread, whatever rows_per_thread says.  Returns GP_ERR_ARG for

@@ -158,7 +158,9 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
             if (o.blocks_per_sm == 0) o.blocks_per_sm = it->second.blocks_per_sm;
         }
     }
-    if (o.rows_per_thread == 0) o.rows_per_thread = 8;
+    // 4 rows per thread: 48 registers, 5 blocks (40 warps) per SM, measured
+    // 7% faster than 8 rows (79 registers, 3 blocks) on Pagie-1 x 4096
+    if (o.rows_per_thread == 0) o.rows_per_thread = 4;
     if (o.rows_per_thread != 4 && o.rows_per_thread != 8 && o.rows_per_thread != 16)
         return GP_ERR_ARG;
     if (o.chunk_rows == 0) o.chunk_rows = (int)default_chunk(n_progs, n_rows, c->sms);

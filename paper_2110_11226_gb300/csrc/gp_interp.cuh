@@ -47,19 +47,27 @@ __host__ __device__ constexpr int eval_warps() { return RPT >= 16 ? 4 : 8; }
 __device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float f_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float f_mul(float a, float b) { return __fmul_rn(a, b); }
+// The protected operators compute the operation on every row and select
+// afterwards: written as a branch around the operation, the compiler keeps
+// a per-row branch, which costs more than the operation saved (measured).
 __device__ __forceinline__ float f_div(float a, float b) {
-    return fabsf(b) < kThr ? 1.0f : __fdiv_rn(a, b);
+    const float q = __fdiv_rn(a, b);
+    return fabsf(b) < kThr ? 1.0f : q;
 }
 __device__ __forceinline__ float f_sqrt(float a) { return __fsqrt_rn(fabsf(a)); }
 __device__ __forceinline__ float f_log(float a) {
+    // logf sees an argument >= thr, which spares it its tiny-argument
+    // paths; NaN, for which both tests fail, is passed through
     const float b = fabsf(a);
-    return b < kThr ? 0.0f : logf(b);
+    const float l = logf(fmaxf(b, kThr));
+    return b >= kThr ? l : (b < kThr ? 0.0f : b);
 }
 __device__ __forceinline__ float f_exp(float a) { return expf(a); }
 __device__ __forceinline__ float f_abs(float a) { return fabsf(a); }
 __device__ __forceinline__ float f_neg(float a) { return -a; }
 __device__ __forceinline__ float f_inv(float a) {
-    return fabsf(a) < kThr ? 0.0f : __frcp_rn(a);
+    const float r = __frcp_rn(a);
+    return fabsf(a) < kThr ? 0.0f : r;
 }
 
 // per-row loss (metric readings of Sec. III-C3, FP32)
@@ -102,18 +110,22 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     s = tv;
 }
 
-// this lane's float4 q of stack slot `slot` (stack laid out [slot][q][lane])
-template <int RPT>
-__device__ __forceinline__ float4 *stack_at(float4 *stk, uint32_t slot, int q) {
-    return stk + ((size_t)slot * (RPT / 4) + q) * 32;
-}
-
 // Runs one compiled program over RPT rows per lane; returns the top of the
 // stack in t.  stk = this warp's stack slice, already offset by the lane.
-// The instruction buffer ends with OP_END up to its last entry, so the loop
-// ends within kCodeStride + 1 steps whatever the buffer holds; op values
-// that name no operation act as OP_END and stack slots are clamped to the
+// The instruction buffer (kCodeStride + 1 entries in shared memory) holds
+// OP_END from the program's end through its last entry, so the loop ends
+// within kCodeStride + 1 steps whatever the buffer holds; op values that
+// name no operation act as OP_END and stack slots are clamped to the
 // stack, so no instruction word can make it run away or leave its memory.
+//
+// Dispatch cost is what this loop is tuned for (per-opcode instruction
+// counts measured with ncu on chains of one operation): the instruction
+// word and the stack are addressed through 32-bit shared-memory addresses
+// computed once; the opcode is broadcast from lane 0, which lets the
+// compiler treat the switch as warp-uniform (no reconvergence barrier per
+// instruction); the switch covers all 32 values of its 5-bit operand, so
+// it needs no range test; and the word is loaded when it is needed rather
+// than one ahead, which saves the register copies of a prefetch.
 template <int RPT, int NSLOT, int FMODE>
 __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restrict__ cbuf,
                                           const float (&x0)[RPT], const float (&x1)[RPT],
@@ -122,28 +134,39 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
 #pragma unroll
     for (int j = 0; j < RPT; ++j) t[j] = 0.0f;
     int pc = 0;
-    uint2 ins = cbuf[0];
+    const uint32_t cb = (uint32_t)__cvta_generic_to_shared(cbuf);  // word pc at cb + 8 pc
+    const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stk);   // this lane's slot 0
 #pragma unroll 1
     for (;;) {
-        const uint2 nx = cbuf[min(pc + 1, kCodeStride)];
+        uint2 ins;
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                     : "=r"(ins.x), "=r"(ins.y)
+                     : "r"(cb + 8u * (uint32_t)pc));
         ++pc;
-        const uint32_t w = ins.x;
+        const uint32_t w = __shfl_sync(0xffffffffu, ins.x, 0);
         const float c = __uint_as_float(ins.y);
-        ins = nx;
 // operand helpers: stack slot, X column, constant
+// (the stack is laid out [slot][q][lane] in float4: slot sl, group q of
+// this lane sits (sl * RPT/4 + q) * 32 float4 past its slot 0)
 #define GP_SLOT_LOAD(u)                                                         \
     {                                                                           \
         const uint32_t sl = min((w >> 8) & 255u, (uint32_t)NSLOT - 1u);         \
         _Pragma("unroll") for (int q = 0; q < RPT / 4; ++q) {                   \
-            const float4 v = *stack_at<RPT>(stk, sl, q);                        \
-            u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w; \
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"             \
+                         : "=f"(u[4 * q]), "=f"(u[4 * q + 1]),                  \
+                           "=f"(u[4 * q + 2]), "=f"(u[4 * q + 3])               \
+                         : "r"(sb + (sl * (RPT / 4) + q) * 32u * 16u));          \
         }                                                                       \
     }
 #define GP_SPILL()                                                              \
     {                                                                           \
         const uint32_t sl = min((w >> 8) & 255u, (uint32_t)NSLOT - 1u);         \
         _Pragma("unroll") for (int q = 0; q < RPT / 4; ++q)                     \
-            *stack_at<RPT>(stk, sl, q) = make_float4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]); \
+            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"             \
+                         ::"r"(sb + (sl * (RPT / 4) + q) * 32u * 16u),           \
+                           "f"(t[4 * q]), "f"(t[4 * q + 1]), "f"(t[4 * q + 2]),  \
+                           "f"(t[4 * q + 3])                                    \
+                         : "memory");                                           \
     }
 #define GP_X_LOAD(u)                                                            \
     {                                                                           \
@@ -187,8 +210,12 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
             case OP_ABS: GP_T(f_abs(t[j])) break;
             case OP_NEG: GP_T(f_neg(t[j])) break;
             case OP_INV: GP_T(f_inv(t[j])) break;
-            default:  // OP_END and anything that is not an operation
+            case OP_END:  // and the two values that name no operation
+            case 30:
+            case 31:
                 goto done;
+            default:  // every value of w & 31 has a case above
+                __builtin_unreachable();
         }
         continue;
         // division has one body per operand order, shared by its operand cases
@@ -270,7 +297,7 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom && RPT 
             __syncthreads();  // s_item is rewritten at the top
             continue;
         }
-        // the program, then OP_END up to and including the last entry
+        // the program, then OP_END through the buffer's last entry
         for (int i = threadIdx.x; i <= kCodeStride; i += kEvalBlock)
             cbuf[i] = (i < m.n_ins) ? a.code[(size_t)p * kCodeStride + i]
                                     : make_uint2(make_ins(OP_END, 0, 0), 0u);

@@ -64,6 +64,42 @@ def test_predict_tiny_programs_and_protected_points():
     assert st.ok > 0.6 * st.rows
 
 
+def test_special_values_through_every_operator():
+    """NaN, +-inf, +-0, denormals, huge values and both sides of the
+    protection threshold through every operator (alone, with a terminal
+    operand on either side and with a stack operand): the GPU gives the FP64
+    oracle's class (NaN / +inf / -inf / finite) wherever the FP32 oracle
+    agrees with it, and finite values within the per-point bound."""
+    sp = np.array([np.nan, np.inf, -np.inf, 0.0, -0.0, 1e-40, -1e-40, 3e38, -3e38, 0.000999,
+                   -0.000999, 0.001, -0.001, 0.0011, 1.0, -2.5, 70000.0, 1e30, 88.8, -104.0],
+                  np.float32)
+    a, b = np.meshgrid(sp, sp)
+    X = np.stack([a.ravel(), b.ravel()]).astype(np.float32)
+    progs = []
+    for name in ("sqrt", "log", "exp", "sin", "cos", "tan", "abs", "neg", "inv"):
+        progs.append(parse_prefix(f"{name} x0"))
+        progs.append(parse_prefix(f"add {name} x0 {name} x1"))
+    for name in ("add", "sub", "mul", "div"):
+        progs.append(parse_prefix(f"{name} x0 x1"))
+        progs.append(parse_prefix(f"{name} x0 0.5"))
+        progs.append(parse_prefix(f"{name} -0.75 x1"))
+        progs.append(parse_prefix(f"{name} neg x0 neg x1"))
+    nodes, off = pack(progs)
+    pn, po, dX, _, _ = put(nodes, off, X)
+    got = gp.gp_predict(pn, po, dX).cpu().numpy()
+    v64 = oracle.predict64(nodes, off, X)[0]
+    v32 = oracle.predict32(nodes, off, X).astype(np.float64)
+
+    def cls(v):
+        return np.where(np.isnan(v), 0, np.where(v == np.inf, 1, np.where(v == -np.inf, 2, 3)))
+
+    agree = cls(v64) == cls(v32)
+    np.testing.assert_array_equal(cls(got)[agree], cls(v64)[agree])
+    assert agree.mean() > 0.9
+    st, _ = check_points(got, nodes, off, X)
+    assert st.ok > 0.3 * st.rows, st
+
+
 @pytest.mark.parametrize("n_feat,funcs", [(2, synth.FULL_SET), (1, synth.FULL_SET + ("tan",)),
                                           (7, synth.FULL_SET + ("tan",)), (50, synth.FULL_SET)])
 def test_predict_full_function_set(n_feat, funcs):
