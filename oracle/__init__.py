@@ -99,6 +99,8 @@ def _load():
     lib.ora_const_grad32.argtypes = [P, P, i32, P, i64, P, P, i32, i64, i64,
                                      P, P, i32]
     lib.ora_adam.argtypes = [P, P, P, P, i64, i32, f64, f64, f64, f64]
+    lib.ora_mutate.argtypes = [P, P, i32, i32, P, i32, P, i32, C.c_uint32, C.c_uint64,
+                               C.c_uint64, P, P, P]
     lib.ora_max_threads.restype = i32
     _lib = lib
     return lib
@@ -311,3 +313,32 @@ def adam(theta, g, m, v, step, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
     _load().ora_adam(_ptr(theta), _ptr(g), _ptr(m), _ptr(v), theta.size,
                      int(step), float(lr), float(beta1), float(beta2),
                      float(eps))
+
+
+MUT_KINDS = {"reproduction": 0, "crossover": 1, "subtree": 2, "hoist": 3, "point": 4}
+
+
+def mutate(progs, offsets, n_feat, parents, p_crossover=0.7, p_subtree=0.1, p_hoist=0.05,
+           p_point=0.1, p_replace=0.1, subtree_depth=4, functions=None, seed=0, offset=0):
+    """One offspring per pair (parents[2t], parents[2t+1]) (Sec. II-A mutation
+    kinds, Sec. III-C2 hoisted crossover).  functions: op names new function
+    nodes may take (default: every function).  Returns (nodes, offsets, kind)."""
+    lib = _load()
+    progs, offsets = _progs(progs, offsets)
+    parents = np.ascontiguousarray(parents, np.int32)
+    n_out = len(parents) // 2
+    names = functions if functions is not None else [n for n, c in OPS.items() if c >= 2]
+    mask = 0
+    for n in names:
+        mask |= 1 << OPS[n]
+    probs = np.array([p_crossover, p_subtree, p_hoist, p_point, p_replace], np.float64)
+    out = np.zeros(max(1, n_out) * 255, NODE_DTYPE)
+    off = np.zeros(n_out + 1, np.int32)
+    kind = np.zeros(max(1, n_out), np.int32)
+    rc = lib.ora_mutate(_ptr(progs), _ptr(offsets), len(offsets) - 1, int(n_feat), _ptr(parents),
+                        n_out, _ptr(probs), int(subtree_depth), mask, int(seed), int(offset),
+                        _ptr(out), _ptr(off), _ptr(kind))
+    if rc != 0:
+        raise ValueError("oracle mutate: bad arguments")
+    return out[:off[-1]].copy(), off, kind[:n_out].copy()
+

@@ -929,6 +929,228 @@ void ora_adam(double *theta, const double *g, double *m, double *v, int64_t n,
     }
 }
 
+/* ---- mutation (Sec. II-A mutation kinds, Sec. III-C2 hoisted crossover) -- *
+ * One offspring per index t.  Its random words come from one Philox4x32-10
+ * stream: word k = Philox(counter = (k/4, t, offset lo32, offset hi32),
+ * key = (seed lo32, seed hi32))[k%4], taken in order.  A word u picks an
+ * index in [0, n) as (u * n) >> 32 and a kind by comparing u with the
+ * cumulative thresholds floor(p * 2^32).
+ *   kind      : crossover, subtree, hoist, point, else reproduction
+ *   crossover : node i of the parent, node j of the donor (uniform); the
+ *               child is the parent with subtree i replaced by donor
+ *               subtree j; while the child holds more than 255 nodes or
+ *               needs more than 20 stack slots, j moves to a node drawn
+ *               uniformly among its proper descendants (the hoisted
+ *               crossover of Sec. III-C2)
+ *   subtree   : a random "grow" tree of the given depth is the donor
+ *               (drawn first), then as crossover with j = its root
+ *   hoist     : node i of the parent, then k among the proper descendants
+ *               of i (k = i for a terminal); subtree i is replaced by
+ *               subtree k
+ *   point     : each node in prefix order is replaced with probability
+ *               p_replace: a function by one of the allowed functions of
+ *               the same arity, a terminal by a new terminal
+ *   terminal  : one word picks f in [0, n_feat]; f < n_feat gives variable
+ *               f, else a constant c = (w >> 8) * 2^-23 - 1 from the next
+ *               word w (exact in float, uniform on [-1, 1))
+ *   grow tree : a node at depth < limit is a terminal when a word picks
+ *               one of the 2 terminal kinds among 2 + (allowed functions),
+ *               else one of the allowed functions (uniform); nodes at the
+ *               limit are terminals
+ * A parent that is not a valid program is copied unchanged (kind
+ * reproduction) when it has 1 to 255 nodes and replaced by the one-node
+ * program 0 otherwise; an invalid donor turns a crossover into a
+ * reproduction.  Returns 0, or -1 for bad arguments (a parent index out of
+ * range among them). */
+enum { ORA_MUT_REPRO = 0, ORA_MUT_CROSS = 1, ORA_MUT_SUBTREE = 2, ORA_MUT_HOIST = 3,
+       ORA_MUT_POINT = 4 };
+
+typedef struct {
+    uint64_t seed, offset;
+    int64_t t;
+    uint32_t k;
+} ora_stream;
+
+static uint32_t stream_next(ora_stream *s) {
+    uint32_t ctr[4] = {s->k >> 2, (uint32_t)s->t, (uint32_t)s->offset,
+                       (uint32_t)(s->offset >> 32)};
+    uint32_t key[2] = {(uint32_t)s->seed, (uint32_t)(s->seed >> 32)};
+    uint32_t o[4];
+    ora_philox4x32_10(ctr, key, o);
+    uint32_t w = o[s->k & 3];
+    s->k += 1;
+    return w;
+}
+
+static int pick(ora_stream *s, int n) {
+    return (int)(((uint64_t)stream_next(s) * (uint64_t)n) >> 32);
+}
+
+/* number of nodes of the subtree rooted at node i of a prefix list */
+static int subtree_size(const ora_node *p, int len, int i) {
+    int need = 1;
+    for (int m = i; m < len; ++m) {
+        need += ora_op_arity(p[m].op) - 1;
+        if (need == 0) return m - i + 1;
+    }
+    return -1;
+}
+
+static ora_node new_terminal(ora_stream *s, int n_feat) {
+    ora_node nd = {ORA_CONST, 0, 0.0f};
+    int f = pick(s, n_feat + 1);
+    if (f < n_feat) {
+        nd.op = ORA_VAR;
+        nd.feat = (int16_t)f;
+    } else {
+        uint32_t w = stream_next(s);
+        nd.c = (float)(w >> 8) * 0x1p-23f - 1.0f;
+    }
+    return nd;
+}
+
+/* a grow tree of depth <= limit, in prefix order; returns its length */
+static int grow_tree(ora_stream *s, int limit, const int *funcs, int nf, int n_feat,
+                     ora_node *out) {
+    int depth_of_slot[2 * ORA_MAX_LEN];
+    int top = 0, n = 0;
+    depth_of_slot[top++] = 0;
+    while (top > 0) {
+        int d = depth_of_slot[--top];
+        int terminal = d >= limit || pick(s, nf + 2) < 2;
+        if (terminal) {
+            out[n++] = new_terminal(s, n_feat);
+        } else {
+            ora_node nd = {(int16_t)funcs[pick(s, nf)], 0, 0.0f};
+            out[n++] = nd;
+            for (int a = 0; a < ora_op_arity(nd.op); ++a) depth_of_slot[top++] = d + 1;
+        }
+    }
+    return n;
+}
+
+/* parent with subtree [i, i+si) replaced by donor subtree [j, j+sj); the
+ * child's length, or 0 when it exceeds 255 nodes or 20 stack slots */
+static int splice(const ora_node *par, int lp, int i, int si, const ora_node *don, int j, int sj,
+                  ora_node *out) {
+    int len = i + sj + (lp - i - si);
+    if (len > ORA_MAX_LEN) return 0;
+    memcpy(out, par, (size_t)i * sizeof(ora_node));
+    memcpy(out + i, don + j, (size_t)sj * sizeof(ora_node));
+    memcpy(out + i + sj, par + i + si, (size_t)(lp - i - si) * sizeof(ora_node));
+    int hw = 0;
+    ora_validate(out, len, 1 << 15, &hw);
+    return hw <= ORA_MAX_STACK ? len : 0;
+}
+
+/* hoisted crossover of donor subtree j into parent node i */
+static int hoisted_splice(ora_stream *s, const ora_node *par, int lp, int i, const ora_node *don,
+                          int ld, int j, ora_node *out) {
+    int si = subtree_size(par, lp, i);
+    int sj = subtree_size(don, ld, j);
+    for (;;) {
+        int len = splice(par, lp, i, si, don, j, sj, out);
+        if (len > 0) return len;
+        if (sj == 1) return 0; /* a terminal always fits a valid parent */
+        j = j + 1 + pick(s, sj - 1);
+        sj = subtree_size(don, ld, j);
+    }
+}
+
+int ora_mutate(const ora_node *progs, const int32_t *offsets, int n_progs, int n_feat,
+               const int32_t *parents, int n_out, const double probs[5], int subtree_depth,
+               uint32_t funcs_mask, uint64_t seed, uint64_t offset, ora_node *out_nodes,
+               int32_t *out_offsets, int32_t *out_kind) {
+    int funcs[ORA_NOPS], nf = 0, f1[ORA_NOPS], n1 = 0, f2[ORA_NOPS], n2 = 0;
+    for (int op = ORA_ADD; op <= ORA_INV; ++op) {
+        if (!(funcs_mask >> op & 1u)) continue;
+        funcs[nf++] = op;
+        if (ora_op_arity(op) == 1) f1[n1++] = op;
+        else f2[n2++] = op;
+    }
+    if (nf == 0 || n_feat < 1 || subtree_depth < 0 || subtree_depth > 6) return -1;
+    double cum = 0.0;
+    uint64_t thr[4];
+    for (int q = 0; q < 4; ++q) {
+        if (!(probs[q] >= 0.0 && probs[q] <= 1.0)) return -1;
+        cum += probs[q];
+        double v = floor(cum * 4294967296.0);
+        thr[q] = v >= 4294967296.0 ? 4294967296ull : (uint64_t)v;
+    }
+    if (cum > 1.0 + 1e-6 || !(probs[4] >= 0.0 && probs[4] <= 1.0)) return -1;
+    double vr = floor(probs[4] * 4294967296.0);
+    uint64_t thr_replace = vr >= 4294967296.0 ? 4294967296ull : (uint64_t)vr;
+    for (int t = 0; t < 2 * n_out; ++t)
+        if (parents[t] < 0 || parents[t] >= n_progs) return -1;
+
+    ora_node child[ORA_MAX_LEN], tree[ORA_MAX_LEN];
+    int32_t pos = 0;
+    out_offsets[0] = 0;
+    for (int t = 0; t < n_out; ++t) {
+        ora_stream s = {seed, offset, t, 0};
+        uint32_t u = stream_next(&s);
+        int kind = ORA_MUT_REPRO;
+        for (int q = 0; q < 4; ++q)
+            if ((uint64_t)u < thr[q]) { kind = q + 1; break; }
+        const ora_node *par = progs + offsets[parents[2 * t]];
+        int lp = offsets[parents[2 * t] + 1] - offsets[parents[2 * t]];
+        const ora_node *don = progs + offsets[parents[2 * t + 1]];
+        int ld = offsets[parents[2 * t + 1] + 1] - offsets[parents[2 * t + 1]];
+        if (ora_validate(par, lp, n_feat, NULL) != ORA_OK) {
+            kind = ORA_MUT_REPRO;
+            if (lp < 1 || lp > ORA_MAX_LEN) {
+                static const ora_node zero = {ORA_CONST, 0, 0.0f};
+                par = &zero;
+                lp = 1;
+            }
+        }
+        if (kind == ORA_MUT_CROSS && ora_validate(don, ld, n_feat, NULL) != ORA_OK)
+            kind = ORA_MUT_REPRO;
+        int len = 0;
+        if (kind == ORA_MUT_CROSS) {
+            int i = pick(&s, lp);
+            int j = pick(&s, ld);
+            len = hoisted_splice(&s, par, lp, i, don, ld, j, child);
+        } else if (kind == ORA_MUT_SUBTREE) {
+            int lt = grow_tree(&s, subtree_depth, funcs, nf, n_feat, tree);
+            int i = pick(&s, lp);
+            len = hoisted_splice(&s, par, lp, i, tree, lt, 0, child);
+        } else if (kind == ORA_MUT_HOIST) {
+            int i = pick(&s, lp);
+            int si = subtree_size(par, lp, i);
+            int k = si > 1 ? i + 1 + pick(&s, si - 1) : i;
+            len = splice(par, lp, i, si, par, k, subtree_size(par, lp, k), child);
+        } else if (kind == ORA_MUT_POINT) {
+            memcpy(child, par, (size_t)lp * sizeof(ora_node));
+            len = lp;
+            for (int i = 0; i < lp; ++i) {
+                if ((uint64_t)stream_next(&s) >= thr_replace) continue;
+                int a = ora_op_arity(par[i].op);
+                if (a == 0) {
+                    child[i] = new_terminal(&s, n_feat);
+                } else {
+                    const int *same = a == 1 ? f1 : f2;
+                    int ns = a == 1 ? n1 : n2;
+                    if (ns > 0) {
+                        ora_node nd = {(int16_t)same[pick(&s, ns)], 0, 0.0f};
+                        child[i] = nd;
+                    }
+                }
+            }
+        }
+        if (len == 0) { /* reproduction, or a splice that could not fit */
+            memcpy(child, par, (size_t)lp * sizeof(ora_node));
+            len = lp;
+            kind = ORA_MUT_REPRO;
+        }
+        memcpy(out_nodes + pos, child, (size_t)len * sizeof(ora_node));
+        pos += len;
+        out_offsets[t + 1] = pos;
+        if (out_kind) out_kind[t] = kind;
+    }
+    return 0;
+}
+
 int ora_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

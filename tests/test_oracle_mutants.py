@@ -45,6 +45,17 @@ MUTANTS = {
                                 "double mh = m[i], vh = v[i] / b2t;"),
     "pearson_p_not_centred": ("spp += wi * dp * dp;", "spp += wi * v * v;"),
     "pearson_signed": ("else f = fabs(spy / sqrt(spp * syy));", "else f = spy / sqrt(spp * syy);"),
+    "hoist_from_anywhere": ("int k = si > 1 ? i + 1 + pick(&s, si - 1) : i;",
+                            "int k = pick(&s, lp);"),
+    "crossover_not_hoisted": ("        if (sj == 1) return 0; /* a terminal always fits a valid parent */",
+                              "        return 0;"),
+    "point_any_arity": ("                    const int *same = a == 1 ? f1 : f2;",
+                        "                    const int *same = f2;"),
+    "kind_thresholds_not_cumulative": ("        cum += probs[q];", "        cum = probs[q];"),
+    "constant_half_range": ("        nd.c = (float)(w >> 8) * 0x1p-23f - 1.0f;",
+                            "        nd.c = (float)(w >> 8) * 0x1p-24f - 1.0f;"),
+    "grow_ignores_limit": ("        int terminal = d >= limit || pick(s, nf + 2) < 2;",
+                           "        int terminal = d >= limit + 1 || pick(s, nf + 2) < 2;"),
     "bound_drops_mul_term": ("r.e = fabs(a.v) * b.e + fabs(b.v) * a.e + a.e * b.e;",
                              "r.e = fabs(a.v) * b.e + a.e * b.e;"),
 }
@@ -63,7 +74,8 @@ def _run_mutant(name, tmp):
                     "-ffp-contract=off", c, "-o", so, "-lm"], check=True)
     env = dict(os.environ, GP_ORACLE_SO=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_mutation.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
