@@ -103,6 +103,7 @@ enum gp_prog_status {
 #define GP_DEV_BAD_PROGRAM 0x1u      /* a program failed validation     */
 #define GP_DEV_TOO_MANY_CONSTS 0x2u  /* gp_const_grad: > 16 constants  */
 #define GP_DEV_QUEUE_CAP 0x4u        /* persistent work loop hit its cap */
+#define GP_DEV_BAD_PARENT 0x8u       /* gp_mutate: parent index out of range */
 
 /* Cross-block accumulation of the fitness sums. */
 enum gp_accum { GP_ACCUM_FP64 = 0, GP_ACCUM_KAHAN32 = 1 };
@@ -234,6 +235,72 @@ int gp_tournament_ex(const float *fitness, const int32_t *offsets,
  * 0, legacy default stream. */
 int gp_tournament(const float *fitness, int n_progs, int tourn_size,
                   uint64_t seed, int32_t *out_idx);
+
+/* ---- mutation on the device ---------------------------------------------
+ * Builds the next population from tournament winners on the GPU, so a whole
+ * generation (evaluate, select, mutate) runs without a host round trip; the
+ * paper mutates on the CPU (Sec. III-C2, III-D2) and names this as future
+ * work (Sec. V).  Offspring t has parent parents[2t] and donor
+ * parents[2t+1] (e.g. gp_tournament_ex with n_tourn = 2 n_out) and one
+ * Philox4x32-10 stream: word k = Philox(counter = (k/4, t, offset lo32,
+ * offset hi32), key = (seed lo32, seed hi32))[k % 4], taken in order; a word
+ * u picks an index in [0, n) as (u n) >> 32 and a kind by comparing u with
+ * the cumulative thresholds floor(p 2^32) (probabilities summed in double
+ * in the order crossover, subtree, hoist, point).  Use another seed or
+ * offset than the tournament's.
+ *   crossover   node i of the parent and node j of the donor (uniform); the
+ *               child is the parent with subtree i replaced by donor
+ *               subtree j; while the child would exceed 255 nodes or 20
+ *               stack slots, j moves to a node drawn uniformly among its
+ *               proper descendants (the hoisted crossover of Sec. III-C2)
+ *   subtree     a random grow tree of depth <= subtree_depth is the donor
+ *               (drawn first), then as crossover from its root
+ *   hoist       node i, then k among the proper descendants of i (k = i for
+ *               a terminal); subtree i is replaced by subtree k
+ *   point       each node in prefix order is replaced with probability
+ *               p_point_replace: a function by an allowed function of the
+ *               same arity, a terminal by a new terminal
+ *   reproduction  the parent unchanged
+ * A new terminal is variable f when a word picks f < n_feat in [0, n_feat],
+ * else the constant (w >> 8) 2^-23 - 1 of the next word w.  A grow-tree
+ * node above the depth limit is a terminal when a word picks one of 2
+ * terminal kinds among 2 + (number of allowed functions), else an allowed
+ * function (uniform).  A parent that is not a valid program is copied (the
+ * one-node program 0 when its length is outside 1..255); an invalid donor
+ * makes a crossover a reproduction; a parent index out of range gives the
+ * program 0 and sets GP_DEV_BAD_PARENT. */
+enum gp_mut_kind {
+    GP_MUT_REPRODUCTION = 0, GP_MUT_CROSSOVER = 1, GP_MUT_SUBTREE = 2,
+    GP_MUT_HOIST = 3, GP_MUT_POINT = 4
+};
+
+typedef struct gp_mut_params {
+    float p_crossover;      /* probabilities of the kinds; reproduction    */
+    float p_subtree;        /* takes the rest (their sum must be <= 1)     */
+    float p_hoist;
+    float p_point;
+    float p_point_replace;  /* per-node replacement probability (point)    */
+    int subtree_depth;      /* depth limit of subtree mutation's tree, 0..6 */
+    uint32_t functions;     /* bit (1 << op) per function new nodes may use */
+    int reserved[4];        /* must be 0                                   */
+} gp_mut_params;
+
+/* Bytes of scratch gp_mutate needs for n_out offspring. */
+size_t gp_mutate_workspace_size(int n_out);
+
+/* progs/offsets: the current population (n_progs programs, device);
+ * parents [2 n_out] int32 (device); params (host); out_progs: capacity
+ * n_out * 255 nodes (device); out_offsets [n_out + 1] (device, written by
+ * the call: out_offsets[0] = 0); out_kind [n_out] (device, may be NULL):
+ * the gp_mut_kind each offspring got.  ws: scratch of ws_bytes (256-byte
+ * aligned, at least gp_mutate_workspace_size) or NULL for the library
+ * cache.  1 <= n_out <= 2^22, 1 <= n_feat <= 32767.  Asynchronous;
+ * GP_ERR_ARG for bad arguments (nothing launched). */
+int gp_mutate(const gp_node *progs, const int32_t *offsets, int n_progs, int n_feat,
+              const int32_t *parents, int n_out, const gp_mut_params *params,
+              uint64_t seed, uint64_t offset, gp_node *out_progs,
+              int32_t *out_offsets, int32_t *out_kind, void *ws, size_t ws_bytes,
+              void *stream);
 
 /* ---- constant tuning (no counterpart in the paper) ----------------------
  * Gradient of each program's fitness with respect to its ephemeral

@@ -331,7 +331,9 @@ def mutate(progs, offsets, n_feat, parents, p_crossover=0.7, p_subtree=0.1, p_ho
     mask = 0
     for n in names:
         mask |= 1 << OPS[n]
-    probs = np.array([p_crossover, p_subtree, p_hoist, p_point, p_replace], np.float64)
+    # the probabilities are float32 values, as the library takes them
+    probs = np.array([p_crossover, p_subtree, p_hoist, p_point, p_replace],
+                     np.float32).astype(np.float64)
     out = np.zeros(max(1, n_out) * 255, NODE_DTYPE)
     off = np.zeros(n_out + 1, np.int32)
     kind = np.zeros(max(1, n_out), np.int32)

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <cmath>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -597,6 +598,77 @@ int gp_adam_step(gp_node *progs, const int32_t *offsets, int n_progs, const floa
         return GP_ERR_ARG;
     AdamArgs a{progs, offsets, nullptr, nullptr, n_progs, grad, m, v, step, lr, beta1, beta2, eps};
     GP_CUDA(launch_adam(a, S(stream)));
+    return GP_OK;
+}
+
+size_t gp_mutate_workspace_size(int n_out) {
+    if (n_out < 1 || n_out > (1 << 22)) return 0;
+    return round_up((int64_t)n_out * 256 * (int64_t)sizeof(gp_node), 256) +
+           round_up((int64_t)n_out * (int64_t)sizeof(int32_t), 256);
+}
+
+int gp_mutate(const gp_node *progs, const int32_t *offsets, int n_progs, int n_feat,
+              const int32_t *parents, int n_out, const gp_mut_params *params, uint64_t seed,
+              uint64_t offset, gp_node *out_progs, int32_t *out_offsets, int32_t *out_kind,
+              void *ws, size_t ws_bytes, void *stream) {
+    if (!progs || !offsets || !parents || !params || !out_progs || !out_offsets) return GP_ERR_ARG;
+    if (n_progs < 1 || n_feat < 1 || n_feat > 32767 || n_out < 1 || n_out > (1 << 22))
+        return GP_ERR_ARG;
+    const gp_mut_params &q = *params;
+    for (int i = 0; i < 4; ++i)
+        if (q.reserved[i] != 0) return GP_ERR_ARG;
+    const float pk[4] = {q.p_crossover, q.p_subtree, q.p_hoist, q.p_point};
+    MutArgs a{};
+    double cum = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        if (!(pk[i] >= 0.0f && pk[i] <= 1.0f)) return GP_ERR_ARG;
+        cum += (double)pk[i];
+        const double v = std::floor(cum * 4294967296.0);
+        a.thr[i] = v >= 4294967296.0 ? 4294967296ull : (uint64_t)v;
+    }
+    if (cum > 1.0 + 1e-6) return GP_ERR_ARG;
+    if (!(q.p_point_replace >= 0.0f && q.p_point_replace <= 1.0f)) return GP_ERR_ARG;
+    const double vr = std::floor((double)q.p_point_replace * 4294967296.0);
+    a.thr_replace = vr >= 4294967296.0 ? 4294967296ull : (uint64_t)vr;
+    if (q.subtree_depth < 0 || q.subtree_depth > 6) return GP_ERR_ARG;
+    const uint32_t allowed = ((1u << (GP_INV + 1)) - 1u) & ~((1u << GP_ADD) - 1u);
+    if (q.functions == 0 || (q.functions & ~allowed)) return GP_ERR_ARG;
+    for (int op = GP_ADD; op <= GP_INV; ++op) {
+        if (!(q.functions >> op & 1u)) continue;
+        a.funcs[a.n_funcs++] = (int16_t)op;
+        if (op <= GP_DIV) a.binary[a.n_binary++] = (int16_t)op;
+        else a.unary[a.n_unary++] = (int16_t)op;
+    }
+    DevCtx *c = nullptr;
+    int rc = ctx_of_current(&c);
+    if (rc) return rc;
+    const size_t need = gp_mutate_workspace_size(n_out);
+    void *base = ws;
+    if (ws) {
+        if (ws_bytes < need || ((uintptr_t)ws & 255u)) return GP_ERR_WORKSPACE;
+    } else {
+        std::lock_guard<std::mutex> g(g_mu);
+        if ((rc = grow(&c->ws, &c->ws_bytes, need))) return rc;
+        base = c->ws;
+    }
+    char *b = static_cast<char *>(base);
+    a.progs = progs;
+    a.offsets = offsets;
+    a.n_progs = n_progs;
+    a.n_feat = n_feat;
+    a.parents = parents;
+    a.n_out = n_out;
+    a.subtree_depth = q.subtree_depth;
+    a.seed = seed;
+    a.offset = offset;
+    a.scratch = reinterpret_cast<gp_node *>(b);
+    a.lens = reinterpret_cast<int32_t *>(
+        b + round_up((int64_t)n_out * 256 * (int64_t)sizeof(gp_node), 256));
+    a.kind = out_kind;
+    a.out = out_progs;
+    a.out_offsets = out_offsets;
+    a.dev_status = c->status;
+    GP_CUDA(launch_mutate(a, S(stream)));
     return GP_OK;
 }
 

@@ -50,6 +50,23 @@ __host__ __device__ constexpr uint32_t make_ins(uint32_t op, uint32_t slot, uint
     return op | (slot << 8) | (feat << 16);
 }
 
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+//   (c0,c1,c2,c3) <- (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+// with the key advanced by the Weyl constants between rounds.
+static __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += W0;
+        k.y += W1;
+    }
+    return c;
+}
+
 // per-program metadata written by the pre-pass
 struct ProgMeta {
     int32_t n_ins;     // instructions including END
@@ -277,5 +294,28 @@ cudaError_t launch_consts(gp_node *progs, const int32_t *offsets, int n_progs, f
                           bool to_nodes, cudaStream_t st);
 
 cudaError_t probe_pipes(double *out, cudaStream_t st);
+// device-side mutation (gp_mutate)
+struct MutArgs {
+    const gp_node *progs;
+    const int32_t *offsets;
+    int n_progs;
+    int n_feat;
+    const int32_t *parents;  // [2 n_out]
+    int n_out;
+    uint64_t thr[4];         // cumulative kind thresholds, floor(p 2^32)
+    uint64_t thr_replace;    // point mutation, per node
+    int subtree_depth;
+    int n_funcs, n_unary, n_binary;
+    int16_t funcs[16], unary[16], binary[16];  // allowed functions by arity
+    uint64_t seed, offset;
+    gp_node *scratch;        // [n_out][256] children
+    int32_t *lens;           // [n_out]
+    int32_t *kind;           // [n_out] or null
+    gp_node *out;
+    int32_t *out_offsets;    // [n_out + 1]
+    unsigned int *dev_status;
+};
+cudaError_t launch_mutate(const MutArgs &a, cudaStream_t st);
+
 
 }  // namespace gpk

@@ -31,12 +31,37 @@ NODE_DTYPE = np.dtype([("op", "<i2"), ("feat", "<i2"), ("c", "<f4")])
 DEV_BAD_PROGRAM = 0x1
 DEV_TOO_MANY_CONSTS = 0x2
 DEV_QUEUE_CAP = 0x4
+DEV_BAD_PARENT = 0x8
 
 
 class GPError(RuntimeError):
     def __init__(self, fn, code):
         super().__init__(f"{fn} failed: {code} ({_lib.gp_status_string(code).decode()})")
         self.code = code
+
+
+class MutParams(C.Structure):
+    _fields_ = [("p_crossover", C.c_float), ("p_subtree", C.c_float), ("p_hoist", C.c_float),
+                ("p_point", C.c_float), ("p_point_replace", C.c_float),
+                ("subtree_depth", C.c_int), ("functions", C.c_uint32),
+                ("reserved", C.c_int * 4)]
+
+
+MUT_KINDS = {"reproduction": 0, "crossover": 1, "subtree": 2, "hoist": 3, "point": 4}
+OPS = {"const": 0, "var": 1, "add": 2, "sub": 3, "mul": 4, "div": 5, "sqrt": 6, "log": 7,
+       "exp": 8, "sin": 9, "cos": 10, "tan": 11, "abs": 12, "neg": 13, "inv": 14}
+
+
+def make_mut_params(p_crossover=0.7, p_subtree=0.1, p_hoist=0.05, p_point=0.1,
+                    p_replace=0.1, subtree_depth=4, functions=None) -> MutParams:
+    names = functions if functions is not None else [n for n, c in OPS.items() if c >= 2]
+    mask = 0
+    for n in names:
+        mask |= 1 << OPS[n]
+    m = MutParams()
+    m.p_crossover, m.p_subtree, m.p_hoist, m.p_point = p_crossover, p_subtree, p_hoist, p_point
+    m.p_point_replace, m.subtree_depth, m.functions = p_replace, subtree_depth, mask
+    return m
 
 
 class EvalOpts(C.Structure):
@@ -71,6 +96,8 @@ def _load():
         "gp_const_grad": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P, P]),
         "gp_adam_step": (i32, [P, P, i32, P, P, P, i32, f32, f32, f32, f32, P]),
         "gp_get_consts": (i32, [P, P, i32, P, P]),
+        "gp_mutate_workspace_size": (C.c_size_t, [i32]),
+        "gp_mutate": (i32, [P, P, i32, i32, P, i32, P, u64, u64, P, P, P, P, C.c_size_t, P]),
         "gp_set_consts": (i32, [P, P, i32, P, P]),
         "gp_last_device_status": (i32, [P, P]),
         "gp_autotune": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
@@ -344,6 +371,34 @@ class ConstantsFitness(torch.autograd.Function):
 
 def fitness_of_constants(consts, progs, offsets, X, y, w=None, metric="mse"):
     return ConstantsFitness.apply(consts, progs, offsets, X, y, w, metric)
+
+
+def gp_mutate(progs, offsets, n_feat, parents, params: Optional[MutParams] = None, seed=0,
+              offset=0, out=None, out_offsets=None, out_kind=None, ws=None, stream=None):
+    """Next population on the device; returns (nodes, offsets, kind) tensors.
+    `nodes` has capacity n_out * 255; its first offsets[-1] entries are used."""
+    P = _nprogs(offsets)
+    n_out = int(parents.numel()) // 2
+    dev = progs.device
+    if params is None:
+        params = make_mut_params()
+    if out is None:
+        out = torch.empty(n_out * 255, dtype=torch.int64, device=dev)
+    if out_offsets is None:
+        out_offsets = torch.empty(n_out + 1, dtype=torch.int32, device=dev)
+    if out_kind is None:
+        out_kind = torch.empty(n_out, dtype=torch.int32, device=dev)
+    ws_bytes = 0 if ws is None else ws.numel() * ws.element_size()
+    _check("gp_mutate", _lib.gp_mutate(
+        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, int(n_feat), _dptr(parents, "parents"),
+        n_out, C.byref(params), int(seed), int(offset), _dptr(out, "out"),
+        _dptr(out_offsets, "out_offsets"), _dptr(out_kind, "out_kind"), _dptr(ws, "ws"),
+        ws_bytes, _stream(stream)))
+    return out, out_offsets, out_kind
+
+
+def gp_mutate_workspace_size(n_out) -> int:
+    return int(_lib.gp_mutate_workspace_size(int(n_out)))
 
 
 def gp_last_device_status(stream=None) -> int:
