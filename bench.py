@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-generation", action="store_true",
+                    help="skip the whole-generation (evaluate, select, mutate) timing")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-graph", action="store_true",
@@ -107,6 +109,15 @@ def kernel_hash():
     for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2110_11226_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
+
+
+DATA_DESC = {
+    "pagie_small": "synthetic: seeded Pagie-1 rows, ramped half-and-half population",
+    "pagie_large": "synthetic: seeded Pagie-1 rows, ramped half-and-half population",
+    "const_tune": "synthetic: seeded Pagie-1 rows, ramped half-and-half population",
+    "tabular": "synthetic: seeded Higgs-shaped 28-column table, hidden-program target",
+    "binary": "synthetic: seeded 50-column table, hidden-program labels, 5% flipped",
+}
 
 
 def recorded_traffic(workload):
@@ -221,7 +232,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * P * wl.data.n_rows / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl.name, "n_rows": wl.data.n_rows,
+            "data": DATA_DESC.get(wl.name, "synthetic, seeded"),
+            "config": {"workload": wl.name, "n_rows": wl.data.n_rows,
                                             "n_progs": P, "n_feat": wl.data.n_feat, "metric": wl.metric},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": r["sample"]},
@@ -364,7 +376,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded Pagie-1 / program populations)",
+            "data": DATA_DESC.get(wl.name, "synthetic, seeded"),
             "config": {"workload": wl.name, "n_rows": N, "n_feat": d.n_feat, "n_progs": P,
                        "metric": wl.metric, "tourn_size": wl.tourn_size,
                        "mean_nodes": n_nodes / P, "function_nodes": n_fn, "sfu_nodes": n_sfu,
@@ -395,6 +407,57 @@ def main():
         line["plain"] = {"value": rows_evals / (pms * 1e-3), "unit": UNIT, "ms_per_eval": pms,
                          "launches": P + 3}
         line["batched_over_plain"] = value / ws / line["plain"]["value"]
+
+    if rank == 0 and ws == 1 and not args.no_generation:
+        # a whole generation on the device (evaluate, 2 tournaments per
+        # offspring, mutate into a new packed population), one CUDA graph;
+        # reported beside the headline step, which is evaluation + selection
+        win2 = torch.empty(2 * P, dtype=torch.int32, device=dev)
+        mparams = gp.make_mut_params()
+        mws = torch.empty(gp.gp_mutate_workspace_size(P), dtype=torch.uint8, device=dev)
+        mout = torch.empty(P * 255, dtype=torch.int64, device=dev)
+        moff = torch.empty(P + 1, dtype=torch.int32, device=dev)
+        mkind = torch.empty(P, dtype=torch.int32, device=dev)
+
+        def mutate(seed):
+            gp.gp_mutate(pn, po, d.n_feat, win2, mparams, seed=seed, offset=1, out=mout,
+                         out_offsets=moff, out_kind=mkind, ws=mws)
+
+        def gen_eager(seed):
+            gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=wl.metric, opts=opts, out=fit, ws=ws_buf)
+            gp.gp_tournament_ex(fit, 2 * P, wl.tourn_size, seed, out=win2)
+            mutate(seed + 1)
+
+        gs2 = torch.cuda.Stream()
+        gs2.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(gs2):
+            gen_eager(7)
+        gs2.synchronize()
+        ggraph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(ggraph, stream=gs2):
+            gen_eager(7)
+        torch.cuda.synchronize()
+        ggraph.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kg = max(1, min(args.steps, 3))
+        a.record(stream)
+        for _ in range(kg):
+            ggraph.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        gms = a.elapsed_time(b) / kg
+        a.record(stream)
+        for s in range(5):
+            mutate(30 + s)
+        b.record(stream)
+        torch.cuda.synchronize()
+        line["full_generation"] = {
+            "ms": gms, "program_rows_per_s": rows_evals / (gms * 1e-3),
+            "mutate_ms": a.elapsed_time(b) / 5,
+            "new_nodes": int(moff[-1].item()),
+            "kinds": {k: int((mkind == v).sum().item()) for k, v in gp.MUT_KINDS.items()},
+            "step": "cuda graph: evaluate, 2 tournaments per offspring, gp_mutate"}
 
     if rank == 0 and not args.no_e2e:
         hn = wl.nodes
