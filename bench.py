@@ -117,6 +117,7 @@ DATA_DESC = {
     "const_tune": "synthetic: seeded Pagie-1 rows, ramped half-and-half population",
     "tabular": "synthetic: seeded Higgs-shaped 28-column table, hidden-program target",
     "binary": "synthetic: seeded 50-column table, hidden-program labels, 5% flipped",
+    "wide": "synthetic: seeded Epsilon-shaped 2000-column table, hidden-program labels, 5% flipped",
 }
 
 

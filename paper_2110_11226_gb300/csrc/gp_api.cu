@@ -131,16 +131,24 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // ---- tunables -----------------------------------------------------------
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-int64_t default_chunk(int n_progs, int64_t n_rows, int sms) {
+// L2 share for one row chunk of every column (the blocks resident at any
+// moment work on one or two chunks; the L2 holds 129 MB)
+constexpr int64_t kChunkL2Bytes = 48ll << 20;
+
+int64_t default_chunk(int n_progs, int64_t n_rows, int n_feat, int sms) {
     // enough items for dynamic balancing (about 16 per resident warp),
     // chunks of at most 16K rows (measured on Pagie-1 x 4096 programs at
     // 1M and 16M rows: 16K-row chunks beat 64K by 4%, 8K and 32K by 1%),
-    // multiples of 256 rows
+    // and for wide tables few enough rows that one chunk of all columns
+    // stays in L2
     const double items_wanted = 16.0 * sms * 24.0;
     int64_t c = (int64_t)((double)n_rows * (double)n_progs / items_wanted);
-    c = std::max<int64_t>(c, 1024);  // a block's 8 warps x 128 rows
     c = std::min<int64_t>(c, 16384);
-    c = round_up(c, 256);
+    c = std::min<int64_t>(c, kChunkL2Bytes / (4 * ((int64_t)n_feat + 2)));
+    // whole passes of a block (8 warps x 32 lanes x 4 rows): a partial last
+    // pass idles warps (measured on 500K x 2000: 6400-row chunks 5% slower
+    // than 6144)
+    c = std::max<int64_t>(c / 1024 * 1024, 1024);
     return std::min<int64_t>(c, round_up(n_rows, 256));
 }
 
@@ -164,7 +172,7 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
     if (o.rows_per_thread == 0) o.rows_per_thread = 4;
     if (o.rows_per_thread != 4 && o.rows_per_thread != 8 && o.rows_per_thread != 16)
         return GP_ERR_ARG;
-    if (o.chunk_rows == 0) o.chunk_rows = (int)default_chunk(n_progs, n_rows, c->sms);
+    if (o.chunk_rows == 0) o.chunk_rows = (int)default_chunk(n_progs, n_rows, n_feat, c->sms);
     if (o.chunk_rows < 256 || o.chunk_rows % 256 != 0) return GP_ERR_ARG;
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 32) return GP_ERR_ARG;
     if (o.accum != GP_ACCUM_FP64 && o.accum != GP_ACCUM_KAHAN32) return GP_ERR_ARG;
@@ -567,7 +575,7 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, con
     if ((rc = check_loss_metric(metric))) return rc;
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
-    const int64_t chunk = default_chunk(n_progs, n_rows, c->sms);
+    const int64_t chunk = default_chunk(n_progs, n_rows, n_feat, c->sms);
     const int n_chunks = (int)((n_rows + chunk - 1) / chunk);
     Layout L = make_layout(n_progs, n_chunks, true);
     {
@@ -712,7 +720,7 @@ int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs, const
     cudaStream_t st = S(stream);
     float *out = nullptr;
     GP_CUDA(cudaMalloc(&out, (size_t)n_progs * sizeof(float)));
-    const int64_t base_chunk = default_chunk(n_progs, n_rows, c->sms);
+    const int64_t base_chunk = default_chunk(n_progs, n_rows, n_feat, c->sms);
     std::vector<gp_eval_opts> cands;
     const int fmode = (n_feat <= 2) ? 2 : 0;
     for (int rpt : {4, 8, 16}) {

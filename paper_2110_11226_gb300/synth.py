@@ -254,7 +254,10 @@ def classification_data(n_rows: int, seed: int, n_feat: int = 50,
     """Binary labels = [hidden depth-5 program > 0], 5% flipped; weight 1
     for the positive class and 3 for the negative class."""
     rng = np.random.default_rng(seed)
-    X = rng.uniform(-1.0, 1.0, size=(n_feat, n_rows)).astype(np.float32)
+    # drawn in float32 (in place) so that wide tables need no float64 copy
+    X = rng.random((n_feat, n_rows), dtype=np.float32)
+    X *= np.float32(2.0)
+    X -= np.float32(1.0)
     hid = _hidden_program(rng, depth, n_feat)
     h = _compose(hid, X)
     lab = (h > 0).astype(np.float32)
@@ -286,6 +289,7 @@ def workload(name: str, n_rows: Optional[int] = None, n_progs: Optional[int] = N
     tabular     : N=10M x 28, P=2048, depth 2-8, 12-op set, RMSE
     binary      : N=4M x 50, P=1024, weighted log-loss, k=10
     const_tune  : Pagie N=1M, P=2048, depth 4-10, <=16 constants, MSE
+    wide        : Epsilon-shaped N=500K x 2000, P=1024, depth 2-8, log-loss, k=10
     """
     if name == "pagie_small":
         n = n_rows or 4096
@@ -313,4 +317,9 @@ def workload(name: str, n_rows: Optional[int] = None, n_progs: Optional[int] = N
         nodes, off = ramped_half_and_half(n_progs or 2048, 4, 10, FULL_SET, 2, 103,
                                           max_consts=16)
         return Workload(name, d, nodes, off, "mse", 20, FULL_SET)
+    if name == "wide":
+        n = n_rows or 500_000
+        d = classification_data(n, 1239, n_feat=2000, depth=5)
+        nodes, off = ramped_half_and_half(n_progs or 1024, 2, 8, FULL_SET, 2000, 104)
+        return Workload(name, d, nodes, off, "logloss", 10, FULL_SET)
     raise KeyError(name)

@@ -589,7 +589,8 @@ def _subset(nodes, off, idx):
 
 
 @pytest.mark.parametrize("name,n_rows,k", [("pagie_large", 1 << 24, 6), ("pagie_large", 1 << 20, 16),
-                                           ("tabular", 10_000_000, 4), ("binary", 1 << 22, 6)])
+                                           ("tabular", 10_000_000, 4), ("binary", 1 << 22, 6),
+                                           ("wide", 500_000, 6)])
 def test_full_size_fitness_sampled(name, n_rows, k):
     wl = synth.workload(name, n_rows=n_rows)
     d = wl.data
