@@ -39,7 +39,7 @@ OPS = {
     "sqrt": 6, "log": 7, "exp": 8, "sin": 9, "cos": 10, "tan": 11,
     "abs": 12, "neg": 13, "inv": 14,
 }
-METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3, "pearson": 4}
+METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3, "pearson": 4, "spearman": 5}
 MAX_STACK = 20
 MAX_LEN = 255
 MAX_CONSTS = 16
@@ -99,6 +99,9 @@ def _load():
     lib.ora_const_grad32.argtypes = [P, P, i32, P, i64, P, P, i32, i64, i64,
                                      P, P, i32]
     lib.ora_adam.argtypes = [P, P, P, P, i64, i32, f64, f64, f64, f64]
+    lib.ora_average_ranks.argtypes = [P, i64, P]
+    lib.ora_spearman_of.restype = f64
+    lib.ora_spearman_of.argtypes = [P, P, P, i64]
     lib.ora_mutate.argtypes = [P, P, i32, i32, P, i32, P, i32, C.c_uint32, C.c_uint64,
                                C.c_uint64, P, P, P]
     lib.ora_max_threads.restype = i32
@@ -343,4 +346,21 @@ def mutate(progs, offsets, n_feat, parents, p_crossover=0.7, p_subtree=0.1, p_ho
     if rc != 0:
         raise ValueError("oracle mutate: bad arguments")
     return out[:off[-1]].copy(), off, kind[:n_out].copy()
+
+
+def average_ranks(v):
+    """1-based ranks of v, ties sharing the mean of their positions."""
+    v = np.ascontiguousarray(v, np.float64)
+    out = np.empty(len(v), np.float64)
+    if _load().ora_average_ranks(_ptr(v), len(v), _ptr(out)) != 0:
+        raise ValueError("NaN in ranked values")
+    return out
+
+
+def spearman_of(pred, y, w=None) -> float:
+    """Spearman fitness |r_s| of given predictions (Sec. III-C3)."""
+    p = np.ascontiguousarray(pred, np.float64)
+    y = np.ascontiguousarray(y, np.float32)
+    w = None if w is None else np.ascontiguousarray(w, np.float32)
+    return float(_load().ora_spearman_of(_ptr(p), _ptr(y), _ptr(w), len(p)))
 

@@ -64,7 +64,8 @@ enum {
     ORA_NOPS = 15
 };
 
-enum { ORA_MAE = 0, ORA_MSE = 1, ORA_RMSE = 2, ORA_LOGLOSS = 3, ORA_PEARSON = 4 };
+enum { ORA_MAE = 0, ORA_MSE = 1, ORA_RMSE = 2, ORA_LOGLOSS = 3, ORA_PEARSON = 4,
+       ORA_SPEARMAN = 5 };
 
 #define ORA_MAX_STACK 20
 #define ORA_MAX_LEN 255
@@ -452,18 +453,25 @@ static int pearson_fitness(const ora_node *progs, const int32_t *offsets, int n_
                            const float *X, int64_t ld, const float *y, const float *w,
                            int64_t row0, int64_t n_eval, double sw, double *out_fit,
                            int32_t *status, int n_threads);
+static int spearman_fitness(const ora_node *progs, const int32_t *offsets, int n_progs,
+                            const float *X, int64_t ld, const float *y, const float *w,
+                            int64_t row0, int64_t n_eval, double *out_fit, int32_t *status,
+                            int n_threads);
 
 int ora_fitness(const ora_node *progs, const int32_t *offsets, int n_progs,
                 const float *X, int64_t ld, const float *y, const float *w,
                 int metric, int64_t row0, int64_t n_eval, double *out_fit,
                 int32_t *status, int n_threads) {
-    if (metric < ORA_MAE || metric > ORA_PEARSON) return -1;
+    if (metric < ORA_MAE || metric > ORA_SPEARMAN) return -1;
     double sw = 0.0;
     for (int64_t i = 0; i < n_eval; ++i) sw += w ? (double)w[row0 + i] : 1.0;
     if (!(sw != 0.0)) return -1;
     if (metric == ORA_PEARSON)
         return pearson_fitness(progs, offsets, n_progs, X, ld, y, w, row0, n_eval, sw, out_fit,
                                status, n_threads);
+    if (metric == ORA_SPEARMAN)
+        return spearman_fitness(progs, offsets, n_progs, X, ld, y, w, row0, n_eval, out_fit,
+                                status, n_threads);
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic)
@@ -545,6 +553,105 @@ static int pearson_fitness(const ora_node *progs, const int32_t *offsets, int n_
         }
         out_fit[p] = f;
         if (status) status[p] = st;
+    }
+    return 0;
+}
+
+/* Spearman's rank correlation (Sec. III-C3: the ranks of the values, then
+ * Karl Pearson's coefficient of the ranks): rank = 1-based position in
+ * ascending order, tied values sharing the mean of their positions; the
+ * weighted Pearson coefficient of the two rank vectors, as a fitness |r|
+ * (0 when either variance is 0, NaN when a value is NaN). */
+static const double *g_sort_keys;
+static int cmp_by_key(const void *a, const void *b) {
+    double x = g_sort_keys[*(const int64_t *)a], y = g_sort_keys[*(const int64_t *)b];
+    if (x < y) return -1;
+    if (x > y) return 1;
+    int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+    return (i > j) - (i < j);
+}
+
+/* average ranks of v[0..n) into rank[]; returns -1 if a value is NaN */
+int ora_average_ranks(const double *v, int64_t n, double *rank) {
+    for (int64_t i = 0; i < n; ++i)
+        if (isnan(v[i])) return -1;
+    int64_t *idx = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!idx) return -2;
+    for (int64_t i = 0; i < n; ++i) idx[i] = i;
+#ifdef _OPENMP
+#pragma omp critical(ora_sort)
+#endif
+    {
+        g_sort_keys = v;
+        qsort(idx, (size_t)n, sizeof(int64_t), cmp_by_key);
+    }
+    for (int64_t a = 0; a < n;) {
+        int64_t b = a;
+        while (b + 1 < n && v[idx[b + 1]] == v[idx[a]]) ++b;
+        double r = 0.5 * (double)(a + 1 + b + 1);  /* mean of positions a+1..b+1 */
+        for (int64_t m = a; m <= b; ++m) rank[idx[m]] = r;
+        a = b + 1;
+    }
+    free(idx);
+    return 0;
+}
+
+/* |weighted Pearson| of two vectors by its two-pass definition */
+double ora_weighted_abs_pearson(const double *a, const double *b, const float *w, int64_t n) {
+    double sw = 0.0, sa = 0.0, sb = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double wi = w ? (double)w[i] : 1.0;
+        sw += wi;
+        sa += wi * a[i];
+        sb += wi * b[i];
+    }
+    double ma = sa / sw, mb = sb / sw, saa = 0.0, sbb = 0.0, sab = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double wi = w ? (double)w[i] : 1.0;
+        saa += wi * (a[i] - ma) * (a[i] - ma);
+        sbb += wi * (b[i] - mb) * (b[i] - mb);
+        sab += wi * (a[i] - ma) * (b[i] - mb);
+    }
+    if (isnan(saa) || isnan(sab) || isinf(saa) || isinf(sab)) return NAN;
+    if (saa == 0.0 || sbb == 0.0) return 0.0;
+    return fabs(sab / sqrt(saa * sbb));
+}
+
+/* Spearman fitness of given predictions p[0..n) against y (weights w) */
+double ora_spearman_of(const double *p, const float *y, const float *w, int64_t n) {
+    double *rp = (double *)malloc((size_t)n * sizeof(double));
+    double *ry = (double *)malloc((size_t)n * sizeof(double));
+    double *yd = (double *)malloc((size_t)n * sizeof(double));
+    double f = NAN;
+    if (rp && ry && yd) {
+        for (int64_t i = 0; i < n; ++i) yd[i] = (double)y[i];
+        if (ora_average_ranks(p, n, rp) == 0 && ora_average_ranks(yd, n, ry) == 0)
+            f = ora_weighted_abs_pearson(rp, ry, w, n);
+    }
+    free(rp);
+    free(ry);
+    free(yd);
+    return f;
+}
+
+static int spearman_fitness(const ora_node *progs, const int32_t *offsets, int n_progs,
+                            const float *X, int64_t ld, const float *y, const float *w,
+                            int64_t row0, int64_t n_eval, double *out_fit, int32_t *status,
+                            int n_threads) {
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int p = 0; p < n_progs; ++p) {
+        const ora_node *prog = progs + offsets[p];
+        int len = offsets[p + 1] - offsets[p];
+        double *v = (double *)malloc((size_t)n_eval * sizeof(double));
+        int st = v ? ORA_OK : ORA_BAD_LENGTH;
+        for (int64_t i = 0; i < n_eval && st == ORA_OK; ++i)
+            st = eval_row64(prog, len, X, ld, row0 + i, &v[i]);
+        out_fit[p] = st == ORA_OK ? ora_spearman_of(v, y + row0, w ? w + row0 : NULL, n_eval) : NAN;
+        if (status) status[p] = st;
+        free(v);
     }
     return 0;
 }

@@ -45,6 +45,8 @@ MUTANTS = {
                                 "double mh = m[i], vh = v[i] / b2t;"),
     "pearson_p_not_centred": ("spp += wi * dp * dp;", "spp += wi * v * v;"),
     "pearson_signed": ("else f = fabs(spy / sqrt(spp * syy));", "else f = spy / sqrt(spp * syy);"),
+    "ranks_without_tie_average": ("        double r = 0.5 * (double)(a + 1 + b + 1);  /* mean of positions a+1..b+1 */",
+                                  "        double r = (double)(a + 1);"),
     "hoist_from_anywhere": ("int k = si > 1 ? i + 1 + pick(&s, si - 1) : i;",
                             "int k = pick(&s, lp);"),
     "crossover_not_hoisted": ("        if (sj == 1) return 0; /* a terminal always fits a valid parent */",

@@ -367,6 +367,47 @@ def test_pearson_closed_forms_and_numpy():
     np.testing.assert_allclose(f3[ok], f1[ok], rtol=1e-9)
 
 
+def test_spearman_matches_scipy_and_closed_forms():
+    """Spearman fitness |r_s| = |Pearson of the average ranks|: scipy's
+    rankdata and spearmanr (library routines) on the oracle's predictions,
+    with ties; 1 for any strictly monotone image of y, 0 for a constant;
+    weights scaled by a constant change nothing."""
+    st = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(31)
+    v = np.round(rng.normal(size=500), 1)  # many ties
+    np.testing.assert_array_equal(oracle.average_ranks(v), st.rankdata(v))
+    n = 600
+    X = rng.uniform(-2, 2, size=(2, n)).astype(np.float32)
+    X[1, :150] = np.round(X[1, :150])  # ties in a feature
+    y = X[0].copy()
+    progs = [
+        [(synth.OP["exp"], 0, 0.0), (synth.OP["var"], 0, 0.0)],            # monotone up
+        [(synth.OP["neg"], 0, 0.0), (synth.OP["var"], 0, 0.0)],            # monotone down
+        [(synth.OP["const"], 0, 0.5)],                                     # constant
+    ]
+    nodes, off = pack(progs)
+    f = oracle.fitness(nodes, off, X, y, None, "spearman")[0]
+    assert f[0] == pytest.approx(1.0, abs=1e-14) and f[1] == pytest.approx(1.0, abs=1e-14)
+    assert f[2] == 0.0
+    Xr, yr, wr = _rand_data(401, 6)
+    yr[:60] = np.round(yr[:60])  # ties in y
+    rn, roff = synth.ramped_half_and_half(30, 2, 5, synth.FULL_SET, 2, seed=15)
+    pred = oracle.predict64(rn, roff, Xr)[0]
+    un = oracle.fitness(rn, roff, Xr, yr, None, "spearman")[0]
+    checked = 0
+    for i in range(len(un)):
+        if np.isnan(pred[i]).any() or np.ptp(pred[i]) == 0:
+            continue
+        want = abs(st.spearmanr(pred[i], yr.astype(np.float64)).statistic)
+        assert un[i] == pytest.approx(want, rel=1e-10, abs=1e-13)
+        checked += 1
+    assert checked > 15
+    f1 = oracle.fitness(rn, roff, Xr, yr, wr, "spearman")[0]
+    f2 = oracle.fitness(rn, roff, Xr, yr, wr * np.float32(4.0), "spearman")[0]
+    fin = np.isfinite(f1)
+    np.testing.assert_allclose(f1[fin], f2[fin], rtol=1e-12, atol=1e-14)
+
+
 def test_logloss_limits():
     # the c*|p| term vanishes for the matching label, so saturated correct
     # predictions cost 0 and saturated wrong ones cost |p|
