@@ -77,8 +77,16 @@ enum gp_op {
  *             0 when either variance is 0, NaN when a sum is not finite.
  *             Greater is better (pass greater_is_better = 1 to the
  *             tournament).  Batched evaluator only (gp_evaluate*,
- *             gp_evaluate_host, gp_evaluate_static, gp_autotune). */
-enum gp_metric { GP_MAE = 0, GP_MSE = 1, GP_RMSE = 2, GP_LOGLOSS = 3, GP_PEARSON = 4 };
+ *             gp_evaluate_host, gp_evaluate_static, gp_autotune).
+ *   SPEARMAN = |r_w| of the ranks: each row's prediction and target are
+ *             replaced by their 1-based ranks among all rows (ties share
+ *             the mean of their positions), then PEARSON of the ranks with
+ *             the weights w; NaN when a prediction is NaN.  Greater is
+ *             better.  gp_evaluate, gp_evaluate_ex and gp_evaluate_host
+ *             only; it materialises each program's predictions and sorts
+ *             them, so it is far slower than the fused metrics. */
+enum gp_metric { GP_MAE = 0, GP_MSE = 1, GP_RMSE = 2, GP_LOGLOSS = 3, GP_PEARSON = 4,
+                 GP_SPEARMAN = 5 };
 
 enum gp_status {
     GP_OK = 0,

@@ -39,6 +39,8 @@ struct DevCtx {
     size_t ws_bytes = 0;
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    void *rank = nullptr;  // Spearman: predictions, sort buffers, target ranks
+    size_t rank_bytes = 0;
     std::map<ShapeKey, gp_eval_opts> tuned;
 };
 
@@ -118,6 +120,11 @@ int check_common(const gp_node *progs, const int32_t *offsets, int n_progs, cons
 
 // every metric of the batched evaluator
 int check_metric(int metric) {
+    return (metric >= GP_MAE && metric <= GP_SPEARMAN) ? GP_OK : GP_ERR_ARG;
+}
+
+// the metrics fused into the evaluator (no materialised predictions)
+int check_fused_metric(int metric) {
     return (metric >= GP_MAE && metric <= GP_PEARSON) ? GP_OK : GP_ERR_ARG;
 }
 
@@ -313,13 +320,92 @@ int validate_one_host(const gp_node *p, int len, int n_feat, int *hw_out) {
     return GP_PROG_OK;
 }
 
+// every program's value on every row into pred [n_progs][n_rows]
+int run_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                int64_t n_rows, int n_feat, float *out_pred, int32_t *out_status, DevCtx *c,
+                cudaStream_t st) {
+    int rc;
+    const int64_t chunk = std::min<int64_t>(round_up(n_rows, 256), 4096);
+    const int n_chunks = (int)((n_rows + chunk - 1) / chunk);
+    Layout L = make_layout(n_progs, 1, false);
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        if ((rc = grow(&c->ws, &c->ws_bytes, L.total))) return rc;
+    }
+    Workspace W = carve(c->ws, L, false);
+    GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
+    CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
+                   nullptr, nullptr, nullptr, c->status, out_status};
+    GP_CUDA(launch_compile(ca, st));
+    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
+    const bool vec = aligned16(X) && (n_rows % 4 == 0);
+    for (int cls = 0; cls < kNumClasses; ++cls) {
+        EvalArgs ea{};
+        ea.code = W.code;
+        ea.meta = W.meta;
+        ea.order = W.order;
+        ea.class_count = W.class_count;
+        ea.cls = cls;
+        ea.X = X;
+        ea.ld = n_rows;
+        ea.n_rows = n_rows;
+        ea.n_progs = n_progs;
+        ea.metric = GP_MSE;
+        ea.chunk_rows = chunk;
+        ea.n_chunks = n_chunks;
+        ea.counter = W.counters + cls;
+        ea.pred = out_pred;
+        ea.dev_status = c->status;
+        ea.vec_ok = vec ? 1 : 0;
+        int occ = info_predict(kEvalBlockThreads, nullptr);
+        GP_CUDA(launch_predict(ea, c->sms * std::max(occ, 1), kEvalBlockThreads, st));
+    }
+    return GP_OK;
+}
+
+// Spearman: the target's ranks once, then batches of programs predicted
+// into [B][N] (B chosen so the batch and its sort buffers take <= 2 GB),
+// ranked and reduced
+constexpr size_t kRankBudget = 2ull << 30;
+
+int run_spearman(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                 int64_t n_rows, int n_feat, const float *y, const float *w, float *out,
+                 double *out64, int32_t *out_status, DevCtx *c, cudaStream_t st) {
+    if (n_rows >= ((int64_t)1 << 31) - 2) return GP_ERR_ARG;
+    const int64_t per_prog = n_rows * 4 * 6;  // prediction, 4 sort arrays, slack
+    int B = (int)std::max<int64_t>(1, std::min<int64_t>(n_progs, (int64_t)kRankBudget / per_prog));
+    const size_t b_pred = (size_t)round_up((int64_t)B * n_rows * 4, 256);
+    const size_t b_r2y = (size_t)round_up(n_rows * 4, 256);
+    const size_t b_scr = rank_scratch_bytes(B, n_rows);
+    int rc;
+    char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        if ((rc = grow(&c->rank, &c->rank_bytes, b_pred + b_r2y + b_scr))) return rc;
+        base = static_cast<char *>(c->rank);
+    }
+    float *pred = reinterpret_cast<float *>(base);
+    uint32_t *r2y = reinterpret_cast<uint32_t *>(base + b_pred);
+    void *scr = base + b_pred + b_r2y;
+    GP_CUDA(target_ranks(y, n_rows, scr, r2y, st));
+    for (int p0 = 0; p0 < n_progs; p0 += B) {
+        const int b = std::min(B, n_progs - p0);
+        if ((rc = run_predict(progs, offsets + p0, b, X, n_rows, n_feat, pred,
+                              out_status ? out_status + p0 : nullptr, c, st)))
+            return rc;
+        GP_CUDA(spearman_batch(pred, b, n_rows, r2y, w, scr, out + p0, out64 ? out64 + p0 : nullptr,
+                               st));
+    }
+    return GP_OK;
+}
+
 }  // namespace
 
 namespace gpk {
 // workspace bytes of one evaluation with this metric (0 for bad arguments)
 size_t workspace_bytes_for(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts *opts,
                            int metric) {
-    if (n_progs < 1 || n_rows < 1 || n_feat < 1 || check_metric(metric)) return 0;
+    if (n_progs < 1 || n_rows < 1 || n_feat < 1 || check_fused_metric(metric)) return 0;
     DevCtx *c = nullptr;
     if (ctx_of_current(&c)) return 0;
     Plan pl;
@@ -378,6 +464,11 @@ int gp_evaluate_ex(const gp_node *progs, const int32_t *offsets, int n_progs, co
     if ((rc = check_metric(metric))) return rc;
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
+    if (metric == GP_SPEARMAN) {  // library scratch only: its size depends on the batch
+        if (ws) return GP_ERR_ARG;
+        return run_spearman(progs, offsets, n_progs, X, n_rows, n_feat, y, w, out_fitness,
+                            out_fitness64, out_prog_status, c, S(stream));
+    }
     Plan pl;
     if ((rc = make_plan(opts, n_progs, n_rows, n_feat, c, &pl, metric == GP_PEARSON))) return rc;
     void *base = ws;
@@ -445,43 +536,7 @@ int gp_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const 
     if (!out_pred) return GP_ERR_ARG;
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
-    const int64_t chunk = std::min<int64_t>(round_up(n_rows, 256), 4096);
-    const int n_chunks = (int)((n_rows + chunk - 1) / chunk);
-    Layout L = make_layout(n_progs, 1, false);
-    {
-        std::lock_guard<std::mutex> g(g_mu);
-        if ((rc = grow(&c->ws, &c->ws_bytes, L.total))) return rc;
-    }
-    Workspace W = carve(c->ws, L, false);
-    cudaStream_t st = S(stream);
-    GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
-    CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
-                   nullptr, nullptr, nullptr, c->status, nullptr};
-    GP_CUDA(launch_compile(ca, st));
-    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
-    const bool vec = aligned16(X) && (n_rows % 4 == 0);
-    for (int cls = 0; cls < kNumClasses; ++cls) {
-        EvalArgs ea{};
-        ea.code = W.code;
-        ea.meta = W.meta;
-        ea.order = W.order;
-        ea.class_count = W.class_count;
-        ea.cls = cls;
-        ea.X = X;
-        ea.ld = n_rows;
-        ea.n_rows = n_rows;
-        ea.n_progs = n_progs;
-        ea.metric = GP_MSE;
-        ea.chunk_rows = chunk;
-        ea.n_chunks = n_chunks;
-        ea.counter = W.counters + cls;
-        ea.pred = out_pred;
-        ea.dev_status = c->status;
-        ea.vec_ok = vec ? 1 : 0;
-        int occ = info_predict(kEvalBlockThreads, nullptr);
-        GP_CUDA(launch_predict(ea, c->sms * std::max(occ, 1), kEvalBlockThreads, st));
-    }
-    return GP_OK;
+    return run_predict(progs, offsets, n_progs, X, n_rows, n_feat, out_pred, nullptr, c, S(stream));
 }
 
 int gp_validate_host(const gp_node *progs, const int32_t *offsets, int n_progs, int n_feat,
@@ -714,7 +769,7 @@ int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs, const
     int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
     if (rc) return rc;
     if (!y) return GP_ERR_ARG;
-    if ((rc = check_metric(metric))) return rc;
+    if ((rc = check_fused_metric(metric))) return rc;
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
     cudaStream_t st = S(stream);
@@ -830,8 +885,9 @@ void gp_shutdown(void) {
         cudaSetDevice(d);
         if (c.ws) cudaFree(c.ws);
         if (c.stage) cudaFree(c.stage);
-        c.ws = c.stage = nullptr;
-        c.ws_bytes = c.stage_bytes = 0;
+        if (c.rank) cudaFree(c.rank);
+        c.ws = c.stage = c.rank = nullptr;
+        c.ws_bytes = c.stage_bytes = c.rank_bytes = 0;
         c.tuned.clear();
     }
     cudaSetDevice(cur);

@@ -22,8 +22,8 @@ import torch
 
 from . import build as _build
 
-METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3, "pearson": 4}
-GREATER_IS_BETTER = {"pearson"}
+METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3, "pearson": 4, "spearman": 5}
+GREATER_IS_BETTER = {"pearson", "spearman"}
 ACCUM = {"fp64": 0, "kahan32": 1}
 MAX_CONSTS = 16
 NODE_DTYPE = np.dtype([("op", "<i2"), ("feat", "<i2"), ("c", "<f4")])

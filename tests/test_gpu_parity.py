@@ -268,6 +268,91 @@ def test_pearson_fitness(weighted, n_feat):
     np.testing.assert_array_equal(win, oracle.tournament(fit_d, 400, 20, 5, greater_is_better=True))
 
 
+@pytest.mark.parametrize("n,weighted", [(3 * 2048 + 77, False), (40_000, True), (1000, True)])
+def test_spearman_fitness(n, weighted):
+    """Spearman |r_s| through device ranking: equal (1e-9) to the oracle's
+    Spearman of the evaluator's own predictions (the device sort, tie ranks
+    and moment sums against their definition), equal to the oracle's
+    Spearman of the oracle's FP32 predictions for the IEEE operators (whose
+    values are bit-equal), and close to the FP64 oracle otherwise (library
+    functions a few ulp apart can break or make ties, and ranks are
+    discontinuous); ties in predictions and targets, constant and NaN
+    programs, ragged tiles."""
+    rng = np.random.default_rng(n)
+    X = rng.uniform(-3, 3, size=(3, n)).astype(np.float32)
+    X[2] = np.round(X[2])  # a feature with many ties
+    y = (X[0] + np.sin(X[1])).astype(np.float32)
+    y[: n // 10] = np.round(y[: n // 10])  # ties in the target
+    w = _weights(n, 12) if weighted else None
+    ieee = synth.ramped_half_and_half(200, 2, 6, ("add", "sub", "mul", "div", "sqrt", "abs", "neg", "inv"),
+                                      3, seed=41)
+    libm = synth.ramped_half_and_half(200, 2, 6, synth.FULL_SET + ("tan",), 3, seed=42)
+    extra = [[(synth.OP["const"], 0, 1.5)],                                   # constant
+             [(synth.OP["var"], 2, 0.0)],                                     # tied feature
+             [(synth.OP["log"], 0, 0.0), (synth.OP["const"], 0, 0.0)],        # protected: 0
+             [(synth.OP["sqrt"], 0, 0.0), (synth.OP["exp"], 0, 0.0), (synth.OP["exp"], 0, 0.0),
+              (synth.OP["exp"], 0, 0.0), (synth.OP["var"], 0, 0.0)]]          # inf for large x0
+    progs = synth.unpack(*ieee) + synth.unpack(*libm) + extra
+    nodes, off = pack(progs)
+    pn, po, dX, dy, dw = put(nodes, off, X, y, w)
+    fit64 = torch.empty(len(progs), dtype=torch.float64, device="cuda")
+    gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric="spearman", out64=fit64)
+    fit = fit64.cpu().numpy()
+    gpred = gp.gp_predict(pn, po, dX).cpu().numpy().astype(np.float64)
+    p32 = oracle.predict32(nodes, off, X).astype(np.float64)
+    f64, st = oracle.fitness(nodes, off, X, y, w, "spearman")
+    n_ieee = len(ieee[1]) - 1
+    stable = 0
+    for i in range(len(progs)):
+        own = oracle.spearman_of(gpred[i], y, w)
+        if np.isnan(own):
+            assert np.isnan(fit[i]), i
+            continue
+        assert abs(fit[i] - own) <= 1e-9 * max(abs(own), 1e-3), (i, fit[i], own)
+        if i < n_ieee:
+            ref32 = oracle.spearman_of(p32[i], y, w)
+            assert abs(fit[i] - ref32) <= 1e-9 * max(abs(ref32), 1e-3), (i, fit[i], ref32)
+        # against the FP64 oracle where the oracle itself shows the program's
+        # ranks insensitive to FP32 rounding (its FP32 and FP64 values give
+        # the same coefficient); ranks are discontinuous, so elsewhere FP32
+        # may tie or order rows differently and the difference is not bounded
+        # (for the library functions the device values may still sit a few
+        # ulp from the oracle's and swap a few neighbours: one swap of
+        # adjacent ranks moves r_s by at most 12 / n^2; four are allowed)
+        if np.isfinite(f64[i]) and np.all(np.isfinite(p32[i])):
+            if abs(oracle.spearman_of(p32[i], y, w) - f64[i]) <= 1e-9:
+                tol = 1e-6 if i < n_ieee else max(1e-6, 48.0 / n ** 2)
+                assert abs(fit[i] - f64[i]) <= tol, (i, fit[i], f64[i])
+                stable += 1
+    assert stable > 150
+    assert fit[-4] == 0.0
+    assert fit[-2] == 0.0 or np.isnan(fit[-2])
+
+
+def test_spearman_over_several_batches():
+    """2M rows x 300 programs: the ranks of at most 2 GB of predictions are
+    sorted at a time (42 programs per batch here); sampled programs from
+    every batch equal the oracle's Spearman of its FP32 predictions."""
+    wl = synth.workload("pagie_large", n_rows=1 << 21, n_progs=300)
+    d = wl.data
+    pn, po, dX, dy, _ = put(wl.nodes, wl.offsets, d.X, d.y)
+    fit64 = torch.empty(300, dtype=torch.float64, device="cuda")
+    gp.gp_evaluate_ex(pn, po, dX, dy, metric="spearman", out64=fit64)
+    fit = fit64.cpu().numpy()
+    idx = np.arange(3, 300, 19)
+    sn, so = _subset(wl.nodes, wl.offsets, idx)
+    gpred = gp.gp_predict(gp.nodes_to_device(sn), dev(so), dX).cpu().numpy().astype(np.float64)
+    checked = 0
+    for k, i in enumerate(idx):
+        ref = oracle.spearman_of(gpred[k], d.y)
+        if np.isnan(ref):
+            assert np.isnan(fit[i])
+            continue
+        assert abs(fit[i] - ref) <= 1e-9 * max(ref, 1e-3), (i, fit[i], ref)
+        checked += 1
+    assert checked >= 10
+
+
 def test_pearson_rejected_where_unsupported():
     d = synth.pagie_data(1024, 3)
     nodes, off = synth.ramped_half_and_half(8, 2, 4, synth.FULL_SET, 2, seed=3)
@@ -276,6 +361,13 @@ def test_pearson_rejected_where_unsupported():
         gp.gp_evaluate_plain(pn, po, dX, dy, metric="pearson")
     with pytest.raises(gp.GPError):
         gp.gp_const_grad(pn, po, dX, dy, metric="pearson")
+    for m in ("spearman",):
+        with pytest.raises(gp.GPError):
+            gp.gp_evaluate_plain(pn, po, dX, dy, metric=m)
+        with pytest.raises(gp.GPError):
+            gp.gp_evaluate_static(pn, po, dX, dy, metric=m)
+        with pytest.raises(gp.GPError):
+            gp.gp_autotune(pn, po, dX, dy, metric=m)
 
 
 def test_plain_evaluator_matches_oracle_and_batched():
