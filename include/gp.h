@@ -57,13 +57,21 @@ typedef struct gp_node {
  * list [SUB, x0, x1] computes x0 - x1.  Protected operators use the
  * threshold 0.001f with the strict test |v| < 0.001f:
  *   DIV(a,b) = 1 on the protected branch, INV(a) = 0, LOG(a) = 0,
- *   otherwise a/b, 1/a, log|a|; SQRT(a) = sqrt|a|. */
+ *   otherwise a/b, 1/a, log|a|; SQRT(a) = sqrt|a|.
+ * Beyond the paper's benchmark set {+,-,*,/,sin,cos,tan} (whose full list
+ * of 33 functions the paper does not give): SQ(a) = a*a, CUBE(a) = (a*a)*a
+ * (each product rounded), CBRT, TANH, ATAN, SINH, COSH (CUDA's float
+ * functions, unprotected), MAX(a,b) / MIN(a,b) = the larger / smaller
+ * operand, NaN if either is NaN, the right operand when they compare
+ * equal.  Unary ops are 6..21, binary 2..5 and 22..23. */
 enum gp_op {
     GP_CONST = 0, GP_VAR = 1,
     GP_ADD = 2, GP_SUB = 3, GP_MUL = 4, GP_DIV = 5,
     GP_SQRT = 6, GP_LOG = 7, GP_EXP = 8, GP_SIN = 9, GP_COS = 10,
     GP_TAN = 11, GP_ABS = 12, GP_NEG = 13, GP_INV = 14,
-    GP_NUM_OPS = 15
+    GP_SQ = 15, GP_CUBE = 16, GP_CBRT = 17, GP_TANH = 18, GP_ATAN = 19,
+    GP_SINH = 20, GP_COSH = 21, GP_MAX = 22, GP_MIN = 23,
+    GP_NUM_OPS = 24
 };
 
 /* Fitness metrics (Sec. III-C3), weighted means over the rows:

@@ -37,7 +37,8 @@ NODE_DTYPE = np.dtype([("op", "<i2"), ("feat", "<i2"), ("c", "<f4")])
 OPS = {
     "const": 0, "var": 1, "add": 2, "sub": 3, "mul": 4, "div": 5,
     "sqrt": 6, "log": 7, "exp": 8, "sin": 9, "cos": 10, "tan": 11,
-    "abs": 12, "neg": 13, "inv": 14,
+    "abs": 12, "neg": 13, "inv": 14, "sq": 15, "cube": 16, "cbrt": 17,
+    "tanh": 18, "atan": 19, "sinh": 20, "cosh": 21, "max": 22, "min": 23,
 }
 METRICS = {"mae": 0, "mse": 1, "rmse": 2, "logloss": 3, "pearson": 4, "spearman": 5}
 MAX_STACK = 20

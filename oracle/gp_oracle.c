@@ -24,7 +24,7 @@
  *     fitness wins, adjusted = raw + c * len (Sec. III-C1, Eqs. parsimony
  *     and fitness); Philox4x32-10 from Salmon et al. 2011 (Sec. III-B).
  *
- * Readings where the paper is silent (each listed in the design doc):
+ * Readings where the paper is silent:
  *   - first pop of a binary function is its LEFT operand;
  *   - protected operators with threshold 0.001f, compared as |x| < thr:
  *     div -> 1, inv -> 0, log -> 0, sqrt takes |x|; exp/sin/cos/tan plain;
@@ -34,7 +34,11 @@
  *   - tournament draws with replacement, index = (u * n) >> 32, ties go to
  *     the earliest draw, NaN counts as the worst fitness;
  *   - Pearson fitness = |r_w(p, y)| with weighted means and (co)variances,
- *     greater is better, and 0 when either variance is 0.
+ *     greater is better, and 0 when either variance is 0;
+ *   - Spearman fitness = the Pearson fitness of the average ranks;
+ *   - the function set beyond the paper's benchmark set: sq, cube, cbrt,
+ *     tanh, atan, sinh, cosh (unprotected) and max, min (NaN if either
+ *     operand is NaN, the right operand when the two compare equal).
  *
  * Everything is FP64 unless a function says FP32 ("_f32" evaluates every
  * operation rounded to float with the C library's float functions; it is
@@ -61,7 +65,9 @@ enum {
     ORA_ADD = 2, ORA_SUB = 3, ORA_MUL = 4, ORA_DIV = 5,
     ORA_SQRT = 6, ORA_LOG = 7, ORA_EXP = 8, ORA_SIN = 9, ORA_COS = 10,
     ORA_TAN = 11, ORA_ABS = 12, ORA_NEG = 13, ORA_INV = 14,
-    ORA_NOPS = 15
+    ORA_SQ = 15, ORA_CUBE = 16, ORA_CBRT = 17, ORA_TANH = 18, ORA_ATAN = 19,
+    ORA_SINH = 20, ORA_COSH = 21, ORA_MAX = 22, ORA_MIN = 23,
+    ORA_NOPS = 24
 };
 
 enum { ORA_MAE = 0, ORA_MSE = 1, ORA_RMSE = 2, ORA_LOGLOSS = 3, ORA_PEARSON = 4,
@@ -81,7 +87,8 @@ static const float ORA_THR = 0.001f;
 
 static const char *const ora_names[ORA_NOPS] = {
     "const", "var", "add", "sub", "mul", "div", "sqrt", "log", "exp",
-    "sin", "cos", "tan", "abs", "neg", "inv"};
+    "sin", "cos", "tan", "abs", "neg", "inv", "sq", "cube", "cbrt", "tanh",
+    "atan", "sinh", "cosh", "max", "min"};
 
 const char *ora_op_name(int op) {
     return (op >= 0 && op < ORA_NOPS) ? ora_names[op] : "";
@@ -89,8 +96,8 @@ const char *ora_op_name(int op) {
 
 int ora_op_arity(int op) {
     if (op == ORA_CONST || op == ORA_VAR) return 0;
-    if (op >= ORA_ADD && op <= ORA_DIV) return 2;
-    if (op >= ORA_SQRT && op <= ORA_INV) return 1;
+    if ((op >= ORA_ADD && op <= ORA_DIV) || op == ORA_MAX || op == ORA_MIN) return 2;
+    if (op >= ORA_SQRT && op <= ORA_COSH) return 1;
     return -1;
 }
 
@@ -134,6 +141,13 @@ static double fn1_64(int op, double a) {
     case ORA_ABS:  return fabs(a);
     case ORA_NEG:  return -a;
     case ORA_INV:  return fabs(a) < thr ? 0.0 : 1.0 / a;
+    case ORA_SQ:   return a * a;
+    case ORA_CUBE: return a * a * a;
+    case ORA_CBRT: return cbrt(a);
+    case ORA_TANH: return tanh(a);
+    case ORA_ATAN: return atan(a);
+    case ORA_SINH: return sinh(a);
+    case ORA_COSH: return cosh(a);
     }
     return NAN;
 }
@@ -146,6 +160,10 @@ static double fn2_64(int op, double a, double b) {
     case ORA_SUB: return a - b;
     case ORA_MUL: return a * b;
     case ORA_DIV: return fabs(b) < thr ? 1.0 : a / b;
+    /* the larger (smaller) operand; NaN if either is NaN; the right
+     * operand when they compare equal */
+    case ORA_MAX: return (a > b || isnan(a)) ? a : b;
+    case ORA_MIN: return (a < b || isnan(a)) ? a : b;
     }
     return NAN;
 }
@@ -162,6 +180,13 @@ static float fn1_32(int op, float a) {
     case ORA_ABS:  return fabsf(a);
     case ORA_NEG:  return -a;
     case ORA_INV:  return fabsf(a) < ORA_THR ? 0.0f : 1.0f / a;
+    case ORA_SQ:   return a * a;
+    case ORA_CUBE: return (a * a) * a;
+    case ORA_CBRT: return cbrtf(a);
+    case ORA_TANH: return tanhf(a);
+    case ORA_ATAN: return atanf(a);
+    case ORA_SINH: return sinhf(a);
+    case ORA_COSH: return coshf(a);
     }
     return NAN;
 }
@@ -172,6 +197,8 @@ static float fn2_32(int op, float a, float b) {
     case ORA_SUB: return a - b;
     case ORA_MUL: return a * b;
     case ORA_DIV: return fabsf(b) < ORA_THR ? 1.0f : a / b;
+    case ORA_MAX: return (a > b || isnan(a)) ? a : b;
+    case ORA_MIN: return (a < b || isnan(a)) ? a : b;
     }
     return NAN;
 }
@@ -304,6 +331,8 @@ static ora_ve ve_round(ora_ve r, double ulps) {
     return r;
 }
 
+static ora_ve ve_fn2(int op, ora_ve a, ora_ve b);
+
 static ora_ve ve_fn1(int op, ora_ve a, double ulps_fn) {
     const double thr = (double)ORA_THR;
     ora_ve r;
@@ -341,6 +370,28 @@ static ora_ve ve_fn1(int op, ora_ve a, double ulps_fn) {
         r.e = 2.0 * d; /* factor 2 covers the curvature over [a-e, a+e] */
         return ve_round(r, ulps_fn);
     }
+    case ORA_SQ: /* one rounded product */
+        r.e = 2.0 * av * a.e + a.e * a.e;
+        return ve_round(r, 0.5);
+    case ORA_CUBE: { /* two rounded products: (a*a)*a */
+        ora_ve s = ve_fn2(ORA_MUL, a, a);
+        return ve_fn2(ORA_MUL, s, a);
+    }
+    case ORA_CBRT: /* |cbrt(x)-cbrt(y)| <= 2^(2/3) |x-y|^(1/3); slope 1/(3 cbrt^2) */
+        r.e = (fabs(r.v) > 0.0) ? fmin(a.e / (3.0 * r.v * r.v) * 2.0, 1.6 * cbrt(a.e))
+                                : 1.6 * cbrt(a.e);
+        return ve_round(r, ulps_fn);
+    case ORA_TANH: /* slope <= 1 */
+        r.e = fmin(a.e, 2.0);
+        return ve_round(r, ulps_fn);
+    case ORA_ATAN: { /* slope 1/(1+x^2) over [|a|-e, |a|+e] */
+        double lo = fmax(0.0, av - a.e);
+        r.e = a.e / (1.0 + lo * lo);
+        return ve_round(r, ulps_fn);
+    }
+    case ORA_SINH: case ORA_COSH: /* slope <= cosh(|a|+e) */
+        r.e = a.e * cosh(av + a.e);
+        return ve_round(r, ulps_fn);
     }
     r.e = INFINITY;
     r.flags |= 2;
@@ -367,6 +418,10 @@ static ora_ve ve_fn2(int op, ora_ve a, ora_ve b) {
         else { r.e = INFINITY; r.flags |= 2; }
         return ve_round(r, 0.5);
     }
+    case ORA_MAX: case ORA_MIN: /* 1-Lipschitz in each operand, exact */
+        r.e = fmax(a.e, b.e);
+        if (!isfinite(r.v)) r.flags |= 2;
+        return r;
     }
     r.e = INFINITY;
     r.flags |= 2;
@@ -852,6 +907,25 @@ int ora_const_grad(const ora_node *progs, const int32_t *offsets,
                 case ORA_ABS:  du = sgn(u); break;
                 case ORA_NEG:  du = -1.0; break;
                 case ORA_INV:  du = (fabs(u) < thr) ? 0.0 : -1.0 / (u * u); break;
+                case ORA_SQ:   du = 2.0 * u; break;
+                case ORA_CUBE: du = 3.0 * u * u; break;
+                case ORA_CBRT: du = (u == 0.0) ? 0.0 : 1.0 / (3.0 * val[j] * val[j]); break;
+                case ORA_TANH: du = 1.0 - val[j] * val[j]; break;
+                case ORA_ATAN: du = 1.0 / (1.0 + u * u); break;
+                case ORA_SINH: du = cosh(u); break;
+                case ORA_COSH: du = sinh(u); break;
+                case ORA_MAX: {
+                    int takes_left = u > val[right[j]] || isnan(u);
+                    du = takes_left ? 1.0 : 0.0;
+                    dv = 1.0 - du;
+                    break;
+                }
+                case ORA_MIN: {
+                    int takes_left = u < val[right[j]] || isnan(u);
+                    du = takes_left ? 1.0 : 0.0;
+                    dv = 1.0 - du;
+                    break;
+                }
                 }
                 adj[left[j]] = aj * du;
                 if (right[j] >= 0) adj[right[j]] = aj * dv;
@@ -1000,6 +1074,25 @@ int ora_const_grad32(const ora_node *progs, const int32_t *offsets,
                 case ORA_ABS:  du = sgn32(u); break;
                 case ORA_NEG:  du = -1.0f; break;
                 case ORA_INV:  du = (fabsf(u) < ORA_THR) ? 0.0f : -(val[j] * val[j]); break;
+                case ORA_SQ:   du = 2.0f * u; break;
+                case ORA_CUBE: du = 3.0f * (u * u); break;
+                case ORA_CBRT: du = (u == 0.0f) ? 0.0f : 1.0f / (3.0f * (val[j] * val[j])); break;
+                case ORA_TANH: du = 1.0f - val[j] * val[j]; break;
+                case ORA_ATAN: du = 1.0f / (1.0f + u * u); break;
+                case ORA_SINH: du = coshf(u); break;
+                case ORA_COSH: du = sinhf(u); break;
+                case ORA_MAX: {
+                    int takes_left = u > val[right[j]] || isnan(u);
+                    du = takes_left ? 1.0f : 0.0f;
+                    dv = 1.0f - du;
+                    break;
+                }
+                case ORA_MIN: {
+                    int takes_left = u < val[right[j]] || isnan(u);
+                    du = takes_left ? 1.0f : 0.0f;
+                    dv = 1.0f - du;
+                    break;
+                }
                 }
                 adj[left[j]] = aj * du;
                 if (right[j] >= 0) adj[right[j]] = aj * dv;
@@ -1169,7 +1262,7 @@ int ora_mutate(const ora_node *progs, const int32_t *offsets, int n_progs, int n
                uint32_t funcs_mask, uint64_t seed, uint64_t offset, ora_node *out_nodes,
                int32_t *out_offsets, int32_t *out_kind) {
     int funcs[ORA_NOPS], nf = 0, f1[ORA_NOPS], n1 = 0, f2[ORA_NOPS], n2 = 0;
-    for (int op = ORA_ADD; op <= ORA_INV; ++op) {
+    for (int op = ORA_ADD; op < ORA_NOPS; ++op) {
         if (!(funcs_mask >> op & 1u)) continue;
         funcs[nf++] = op;
         if (ora_op_arity(op) == 1) f1[n1++] = op;

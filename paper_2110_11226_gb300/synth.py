@@ -31,16 +31,20 @@ NODE_DTYPE = np.dtype([("op", "<i2"), ("feat", "<i2"), ("c", "<f4")])
 OP = {
     "const": 0, "var": 1, "add": 2, "sub": 3, "mul": 4, "div": 5,
     "sqrt": 6, "log": 7, "exp": 8, "sin": 9, "cos": 10, "tan": 11,
-    "abs": 12, "neg": 13, "inv": 14,
+    "abs": 12, "neg": 13, "inv": 14, "sq": 15, "cube": 16, "cbrt": 17,
+    "tanh": 18, "atan": 19, "sinh": 20, "cosh": 21, "max": 22, "min": 23,
 }
 ARITY = {0: 0, 1: 0, 2: 2, 3: 2, 4: 2, 5: 2, 6: 1, 7: 1, 8: 1, 9: 1,
-         10: 1, 11: 1, 12: 1, 13: 1, 14: 1}
+         10: 1, 11: 1, 12: 1, 13: 1, 14: 1, 15: 1, 16: 1, 17: 1, 18: 1,
+         19: 1, 20: 1, 21: 1, 22: 2, 23: 2}
 OP_NAME = {v: k for k, v in OP.items()}
 
 BASIC_SET = ("add", "sub", "mul", "div")
 FULL_SET = ("add", "sub", "mul", "div", "sqrt", "log", "exp", "sin", "cos",
             "abs", "neg", "inv")
 PAPER_SET = ("add", "sub", "mul", "div", "sin", "cos", "tan")
+EXTENDED_SET = FULL_SET + ("tan", "sq", "cube", "cbrt", "tanh", "atan", "sinh", "cosh",
+                           "max", "min")
 SAFE_SET = ("add", "sub", "mul", "sin", "cos", "abs", "neg")
 
 MAX_LEN = 255

@@ -47,6 +47,11 @@ MUTANTS = {
     "pearson_signed": ("else f = fabs(spy / sqrt(spp * syy));", "else f = spy / sqrt(spp * syy);"),
     "ranks_without_tie_average": ("        double r = 0.5 * (double)(a + 1 + b + 1);  /* mean of positions a+1..b+1 */",
                                   "        double r = (double)(a + 1);"),
+    "cube_as_square": ("    case ORA_CUBE: return a * a * a;", "    case ORA_CUBE: return a * a;"),
+    "max_picks_smaller": ("     * operand when they compare equal */\n    case ORA_MAX: return (a > b || isnan(a)) ? a : b;",
+                          "     * operand when they compare equal */\n    case ORA_MAX: return (a < b || isnan(a)) ? a : b;"),
+    "dtanh_sign": ("                case ORA_TANH: du = 1.0 - val[j] * val[j]; break;",
+                   "                case ORA_TANH: du = 1.0 + val[j] * val[j]; break;"),
     "hoist_from_anywhere": ("int k = si > 1 ? i + 1 + pick(&s, si - 1) : i;",
                             "int k = pick(&s, lp);"),
     "crossover_not_hoisted": ("        if (sj == 1) return 0; /* a terminal always fits a valid parent */",

@@ -43,7 +43,7 @@ def test_tiny_programs_brute_force():
     for i, r in enumerate(rows):
         for j, (a, b) in enumerate(POINTS):
             x0, x1 = float(np.float32(a)), float(np.float32(b))
-            want = eval(r[1], {"math": math, "abs": abs}, {"x0": x0, "x1": x1})
+            want = eval(r[1], {"math": math, "abs": abs, "max": max, "min": min}, {"x0": x0, "x1": x1})
             assert pred[i, j] == want, (r[0], a, b, pred[i, j], want)
             # FP32 mode rounds each step: stays within float accuracy of it
             assert abs(float(p32[i, j]) - want) <= 1e-5 * max(1.0, abs(want)), r[0]
@@ -95,6 +95,19 @@ def _fn(name, a, b=None):
     if name == "abs": return abs(a)
     if name == "neg": return -a
     if name == "inv": return 0.0 if abs(a) < thr else 1.0 / a
+    if name == "sq": return a * a
+    if name == "cube": return (a * a) * a
+    if name == "cbrt": return math.cbrt(a)
+    if name == "tanh": return math.tanh(a)
+    if name == "atan": return math.atan(a)
+    if name in ("sinh", "cosh"):
+        try:
+            return math.sinh(a) if name == "sinh" else math.cosh(a)
+        except OverflowError:
+            return math.copysign(math.inf, a) if name == "sinh" else math.inf
+    if name in ("max", "min"):
+        if math.isnan(a) or math.isnan(b): return math.nan
+        return (a if a > b else b) if name == "max" else (a if a < b else b)
     raise KeyError(name)
 
 
@@ -146,7 +159,7 @@ def _postfix_eval(post, x):
 
 
 def test_reverse_scan_matches_recursive_and_postfix():
-    funcs = synth.FULL_SET + ("tan",)
+    funcs = synth.EXTENDED_SET
     nodes, off = synth.random_programs(300, 7, funcs, 3, seed=7)
     rng = np.random.default_rng(3)
     X = rng.uniform(-3, 3, size=(3, 12)).astype(np.float32)
@@ -444,8 +457,8 @@ def test_fp32_mode_matches_numpy_float32():
         np.testing.assert_array_equal(got[i], np.asarray(want[i], np.float32))
 
 
-def test_error_bound_covers_fp32_evaluation():
-    funcs = synth.FULL_SET + ("tan",)
+@pytest.mark.parametrize("funcs", [synth.FULL_SET + ("tan",), synth.EXTENDED_SET])
+def test_error_bound_covers_fp32_evaluation(funcs):
     nodes, off = synth.ramped_half_and_half(400, 2, 7, funcs, 2, seed=21)
     X = synth.pagie_data(2000, 22).X
     v, e, fl = oracle.predict_bound(nodes, off, X, ulps_fn=4.0)
@@ -566,7 +579,7 @@ def test_const_grad_closed_forms():
 def test_const_grad_matches_central_differences(metric):
     binary = metric == "logloss"
     X, y, w = _rand_data(64, 8, binary=binary)
-    funcs = synth.FULL_SET + ("tan",)
+    funcs = synth.EXTENDED_SET
     nodes, off = synth.ramped_half_and_half(150, 2, 4, funcs, 2, seed=31, max_consts=16,
                                             const_range=(-2.0, 2.0))
     g, fit = oracle.const_grad(nodes, off, X, y, w, metric)
