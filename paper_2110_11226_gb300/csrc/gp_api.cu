@@ -303,8 +303,8 @@ int validate_one_host(const gp_node *p, int len, int n_feat, int *hw_out) {
         const int op = p[j].op;
         int ar;
         if (op == GP_CONST || op == GP_VAR) ar = 0;
-        else if (op >= GP_ADD && op <= GP_DIV) ar = 2;
-        else if (op >= GP_SQRT && op <= GP_INV) ar = 1;
+        else if ((op >= GP_ADD && op <= GP_DIV) || op == GP_MAX || op == GP_MIN) ar = 2;
+        else if (op >= GP_SQRT && op <= GP_COSH) ar = 1;
         else return GP_PROG_BAD_OP;
         if (op == GP_VAR && (p[j].feat < 0 || p[j].feat >= n_feat)) return GP_PROG_BAD_FEATURE;
         if (ar == 0) ++sp;
@@ -694,12 +694,12 @@ int gp_mutate(const gp_node *progs, const int32_t *offsets, int n_progs, int n_f
     const double vr = std::floor((double)q.p_point_replace * 4294967296.0);
     a.thr_replace = vr >= 4294967296.0 ? 4294967296ull : (uint64_t)vr;
     if (q.subtree_depth < 0 || q.subtree_depth > 6) return GP_ERR_ARG;
-    const uint32_t allowed = ((1u << (GP_INV + 1)) - 1u) & ~((1u << GP_ADD) - 1u);
+    const uint32_t allowed = ((1u << (GP_MIN + 1)) - 1u) & ~((1u << GP_ADD) - 1u);
     if (q.functions == 0 || (q.functions & ~allowed)) return GP_ERR_ARG;
-    for (int op = GP_ADD; op <= GP_INV; ++op) {
+    for (int op = GP_ADD; op <= GP_MIN; ++op) {
         if (!(q.functions >> op & 1u)) continue;
         a.funcs[a.n_funcs++] = (int16_t)op;
-        if (op <= GP_DIV) a.binary[a.n_binary++] = (int16_t)op;
+        if (op <= GP_DIV || op >= GP_MAX) a.binary[a.n_binary++] = (int16_t)op;
         else a.unary[a.n_unary++] = (int16_t)op;
     }
     DevCtx *c = nullptr;

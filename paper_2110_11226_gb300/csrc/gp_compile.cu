@@ -9,8 +9,8 @@ namespace gpk {
 
 static __host__ __device__ inline int op_arity(int op) {
     if (op == GP_CONST || op == GP_VAR) return 0;
-    if (op >= GP_ADD && op <= GP_DIV) return 2;
-    if (op >= GP_SQRT && op <= GP_INV) return 1;
+    if ((op >= GP_ADD && op <= GP_DIV) || op == GP_MAX || op == GP_MIN) return 2;
+    if (op >= GP_SQRT && op <= GP_COSH) return 1;
     return -1;
 }
 
@@ -89,7 +89,14 @@ __device__ float fold_unary(int op, float a) {
         }
         case GP_ABS: return f_abs(a);
         case GP_NEG: return f_neg(a);
-        default: return f_inv(a);
+        case GP_INV: return f_inv(a);
+        case GP_SQ: return f_sq(a);
+        case GP_CUBE: return f_cube(a);
+        case GP_CBRT: return f_cbrt(a);
+        case GP_TANH: return f_tanh(a);
+        case GP_ATAN: return f_atan(a);
+        case GP_SINH: return f_sinh(a);
+        default: return f_cosh(a);
     }
 }
 
@@ -98,7 +105,9 @@ __device__ float fold_binary(int op, float l, float r) {
         case GP_ADD: return f_add(l, r);
         case GP_SUB: return f_sub(l, r);
         case GP_MUL: return f_mul(l, r);
-        default: return f_div(l, r);
+        case GP_DIV: return f_div(l, r);
+        case GP_MAX: return f_max(l, r);
+        default: return f_min(l, r);
     }
 }
 
@@ -203,6 +212,7 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
     for (int j = 0; j < len; ++j) {
         const int op = prog[j].op;
         if (op_arity(op) != 2 || kon[j]) continue;  // kon: dropped, or a constant now
+        if (op > GP_DIV) continue;  // max and min take both operands from the stack
         const int lc = j + 1, rc = j + 1 + size[j + 1];
         if (op_arity(prog[rc].op) == 0 || kon[rc]) {
             mode[rc] = 1;
@@ -234,6 +244,7 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
 
     // pass 3: emit in reverse-scan order
     int n = 0, depth = 0;
+    bool ext = false;  // an extended-set instruction was emitted
     sp = 0;
     for (int j = len - 1; j >= 0; --j) {
         if (mode[j] == 3) continue;  // inside a folded constant subtree
@@ -253,12 +264,18 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
                                   __float_as_uint(nd.c));
             ++sp;
         } else if (ar == 1) {
-            out[n++] = make_uint2(make_ins(OP_SQRT + (nd.op - GP_SQRT), 0, 0), 0u);
+            const uint32_t uop = nd.op <= GP_INV ? OP_SQRT + (nd.op - GP_SQRT)
+                                                 : OP_EXT1 | ((uint32_t)(nd.op - GP_SQ) << 5);
+            ext |= nd.op > GP_INV;
+            out[n++] = make_uint2(make_ins(uop, 0, 0), 0u);
         } else {
-            const int b = nd.op - GP_ADD;  // add, sub, mul, div
+            // add, sub, mul, div, max, min
+            const int b = nd.op <= GP_DIV ? nd.op - GP_ADD : 4 + (nd.op - GP_MAX);
             if (mode[j] == 0) {
                 // right operand in slot sp-2, left operand is t
-                const uint32_t ops[4] = {OP_ADD_S, OP_SUB_S, OP_MUL_S, OP_DIV_S};
+                const uint32_t ops[6] = {OP_ADD_S, OP_SUB_S, OP_MUL_S, OP_DIV_S,
+                                         OP_EXT2 | (EXT_MAX << 5), OP_EXT2 | (EXT_MIN << 5)};
+                ext |= b >= 4;
                 out[n++] = make_uint2(make_ins(ops[b], sp - 2, 0), 0u);
                 --sp;
             } else {
@@ -281,6 +298,9 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
         if (sp > depth) depth = sp;
     }
     out[n++] = make_uint2(make_ins(OP_END, 0, 0), 0u);
+    // the extended functions are compiled into the deep-class evaluator
+    // only, so a program that uses them joins that class
+    if (ext) depth = max(depth, kSmallDepth + 1);
     a.meta[p] = ProgMeta{n, GP_PROG_OK, depth, n_consts};
 }
 

@@ -13,6 +13,7 @@
 // adjoint into its slot.  Per-thread sums are Kahan-compensated FP32, warp
 // sums fixed-order, cross-chunk sums FP64 (gp_reduce.cu).
 #include "gp_internal.cuh"
+#include "gp_math.cuh"
 
 namespace gpk {
 
@@ -68,7 +69,14 @@ __device__ __forceinline__ float g_f1(int op, float a) {
     case GP_TAN: return tanf(a);
     case GP_ABS: return fabsf(a);
     case GP_NEG: return -a;
-    default: return fabsf(a) < kThr ? 0.0f : __frcp_rn(a);
+    case GP_INV: return fabsf(a) < kThr ? 0.0f : __frcp_rn(a);
+    case GP_SQ: return f_sq(a);
+    case GP_CUBE: return f_cube(a);
+    case GP_CBRT: return f_cbrt(a);
+    case GP_TANH: return f_tanh(a);
+    case GP_ATAN: return f_atan(a);
+    case GP_SINH: return f_sinh(a);
+    default: return f_cosh(a);
     }
 }
 
@@ -77,9 +85,13 @@ __device__ __forceinline__ float g_f2(int op, float l, float r) {
     case GP_ADD: return __fadd_rn(l, r);
     case GP_SUB: return __fsub_rn(l, r);
     case GP_MUL: return __fmul_rn(l, r);
-    default: return fabsf(r) < kThr ? 1.0f : __fdiv_rn(l, r);
+    case GP_DIV: return fabsf(r) < kThr ? 1.0f : __fdiv_rn(l, r);
+    case GP_MAX: return f_max(l, r);
+    default: return f_min(l, r);
     }
 }
+
+__device__ __forceinline__ bool is_unary(int op) { return op >= GP_SQRT && op <= GP_COSH; }
 
 }  // namespace
 
@@ -140,7 +152,7 @@ __global__ void __launch_bounds__(kGradBlock) grad_kernel(GradArgs a) {
                 float v;
                 if (nd.op == GP_CONST) v = nd.c;
                 else if (nd.op == GP_VAR) v = __ldg(a.X + (int64_t)nd.feat * a.ld + r);
-                else if (nd.op >= GP_SQRT) v = g_f1(nd.op, val[j + 1]);
+                else if (is_unary(nd.op)) v = g_f1(nd.op, val[j + 1]);
                 else v = g_f2(nd.op, val[j + 1], val[j + rc[j]]);
                 val[j] = v;
             }
@@ -162,7 +174,7 @@ __global__ void __launch_bounds__(kGradBlock) grad_kernel(GradArgs a) {
                 }
                 if (nd.op == GP_VAR) continue;
                 const float u = val[j + 1];
-                if (nd.op >= GP_SQRT) {
+                if (is_unary(nd.op)) {
                     float du;
                     switch (nd.op) {
                     case GP_SQRT: du = (u == 0.0f) ? 0.0f : __fdiv_rn(sgnf(u), __fmul_rn(2.0f, val[j])); break;
@@ -173,7 +185,16 @@ __global__ void __launch_bounds__(kGradBlock) grad_kernel(GradArgs a) {
                     case GP_TAN: du = __fadd_rn(1.0f, __fmul_rn(val[j], val[j])); break;
                     case GP_ABS: du = sgnf(u); break;
                     case GP_NEG: du = -1.0f; break;
-                    default: du = fabsf(u) < kThr ? 0.0f : -__fmul_rn(val[j], val[j]); break;
+                    case GP_INV: du = fabsf(u) < kThr ? 0.0f : -__fmul_rn(val[j], val[j]); break;
+                    case GP_SQ: du = __fmul_rn(2.0f, u); break;
+                    case GP_CUBE: du = __fmul_rn(3.0f, __fmul_rn(u, u)); break;
+                    case GP_CBRT:
+                        du = (u == 0.0f) ? 0.0f : __frcp_rn(__fmul_rn(3.0f, __fmul_rn(val[j], val[j])));
+                        break;
+                    case GP_TANH: du = __fsub_rn(1.0f, __fmul_rn(val[j], val[j])); break;
+                    case GP_ATAN: du = __frcp_rn(__fadd_rn(1.0f, __fmul_rn(u, u))); break;
+                    case GP_SINH: du = coshf(u); break;
+                    default: du = sinhf(u); break;  // GP_COSH
                     }
                     adj[j + 1] = __fmul_rn(aj, du);
                 } else {
@@ -183,9 +204,17 @@ __global__ void __launch_bounds__(kGradBlock) grad_kernel(GradArgs a) {
                     case GP_ADD: du = 1.0f; dv = 1.0f; break;
                     case GP_SUB: du = 1.0f; dv = -1.0f; break;
                     case GP_MUL: du = v; dv = u; break;
-                    default:
+                    case GP_DIV:
                         if (fabsf(v) < kThr) { du = 0.0f; dv = 0.0f; }
                         else { du = __frcp_rn(v); dv = -__fdiv_rn(val[j], v); }
+                        break;
+                    case GP_MAX:
+                        du = (u > v || u != u) ? 1.0f : 0.0f;
+                        dv = __fsub_rn(1.0f, du);
+                        break;
+                    default:  // GP_MIN
+                        du = (u < v || u != u) ? 1.0f : 0.0f;
+                        dv = __fsub_rn(1.0f, du);
                         break;
                     }
                     adj[j + 1] = __fmul_rn(aj, du);

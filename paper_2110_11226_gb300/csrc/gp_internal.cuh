@@ -5,8 +5,9 @@
 // the list is evaluated by scanning it from the end).  The top of the stack
 // lives in registers (t); deeper values live in a per-warp shared-memory
 // stack whose slot numbers the pre-pass resolves.  Each instruction is one
-// of 30 operations that name their operand source, so the interpreter's
-// only branch per instruction is one switch:
+// of 30 operations that name their operand source, or one of two entries
+// for the extended functions, so the interpreter's only branch per
+// instruction is one switch:
 //   PUSH_X / PUSH_C        t = X[feat] / c
 //   PUSH_X_SP / PUSH_C_SP  stack[slot] = t first (push onto a non-empty stack)
 //   op_S                   t = op(t, stack[slot])      (right operand popped)
@@ -17,7 +18,8 @@
 // A binary node whose right child is a terminal takes it inline; failing
 // that, one whose left child is a terminal takes it inline with the
 // reversed operation (add and mul commute exactly in IEEE arithmetic);
-// otherwise its right operand sits in a stack slot.  These forms evaluate
+// otherwise its right operand sits in a stack slot, as it always does for
+// max and min.  These forms evaluate
 // the same operations on the same operands as the plain reverse scan, so
 // every result is bit-identical to it.
 #pragma once
@@ -34,8 +36,8 @@ constexpr int kEvalBlockThreads = 256;  // threads per block of the evaluator
 constexpr int kDeepSlots = GP_MAX_STACK - 1;  // s[0..18]
 constexpr float kThr = 0.001f;     // protected-operator threshold
 
-// instruction word x: op in bits 0-4, stack slot in bits 8-15, feature
-// index in bits 16-31; word y: the constant
+// instruction word x: op in bits 0-4, extended function in bits 5-7,
+// stack slot in bits 8-15, feature index in bits 16-31; word y: the constant
 enum : uint32_t {
     OP_PUSH_X = 0, OP_PUSH_C = 1, OP_PUSH_X_SP = 2, OP_PUSH_C_SP = 3,
     OP_ADD_S = 4, OP_SUB_S = 5, OP_MUL_S = 6, OP_DIV_S = 7,
@@ -43,8 +45,14 @@ enum : uint32_t {
     OP_RSUB_X = 12, OP_RSUB_C = 13, OP_MUL_X = 14, OP_MUL_C = 15,
     OP_DIV_X = 16, OP_DIV_C = 17, OP_RDIV_X = 18, OP_RDIV_C = 19,
     OP_SQRT = 20, OP_LOG = 21, OP_EXP = 22, OP_SIN = 23, OP_COS = 24,
-    OP_TAN = 25, OP_ABS = 26, OP_NEG = 27, OP_INV = 28, OP_END = 29
+    OP_TAN = 25, OP_ABS = 26, OP_NEG = 27, OP_INV = 28, OP_END = 29,
+    // the extended function set behind two entries, the function in bits
+    // 5-7: EXT1 unary (sq, cube, cbrt, tanh, atan, sinh, cosh), EXT2 binary
+    // (max, min; the right operand always in a stack slot)
+    OP_EXT1 = 30, OP_EXT2 = 31
 };
+enum : uint32_t { EXT_SQ = 0, EXT_CUBE, EXT_CBRT, EXT_TANH, EXT_ATAN, EXT_SINH, EXT_COSH };
+enum : uint32_t { EXT_MAX = 0, EXT_MIN = 1 };
 
 __host__ __device__ constexpr uint32_t make_ins(uint32_t op, uint32_t slot, uint32_t feat) {
     return op | (slot << 8) | (feat << 16);
@@ -315,7 +323,7 @@ struct MutArgs {
     uint64_t thr_replace;    // point mutation, per node
     int subtree_depth;
     int n_funcs, n_unary, n_binary;
-    int16_t funcs[16], unary[16], binary[16];  // allowed functions by arity
+    int16_t funcs[GP_NUM_OPS], unary[GP_NUM_OPS], binary[GP_NUM_OPS];  // allowed, by arity
     uint64_t seed, offset;
     gp_node *scratch;        // [n_out][256] children
     int32_t *lens;           // [n_out]

@@ -110,6 +110,22 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     s = tv;
 }
 
+// The extended unary functions of four rows, out of line: with a case of
+// their own each in the dispatch switch (a 6-bit switch), their code made
+// the loop 4-5% slower on programs that never use them (measured on
+// Pagie-1 x 4096 programs).
+static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
+    switch (f) {
+        case EXT_SQ: return make_float4(f_sq(v.x), f_sq(v.y), f_sq(v.z), f_sq(v.w));
+        case EXT_CUBE: return make_float4(f_cube(v.x), f_cube(v.y), f_cube(v.z), f_cube(v.w));
+        case EXT_CBRT: return make_float4(f_cbrt(v.x), f_cbrt(v.y), f_cbrt(v.z), f_cbrt(v.w));
+        case EXT_TANH: return make_float4(f_tanh(v.x), f_tanh(v.y), f_tanh(v.z), f_tanh(v.w));
+        case EXT_ATAN: return make_float4(f_atan(v.x), f_atan(v.y), f_atan(v.z), f_atan(v.w));
+        case EXT_SINH: return make_float4(f_sinh(v.x), f_sinh(v.y), f_sinh(v.z), f_sinh(v.w));
+        default: return make_float4(f_cosh(v.x), f_cosh(v.y), f_cosh(v.z), f_cosh(v.w));
+    }
+}
+
 // Runs one compiled program over RPT rows per lane; returns the top of the
 // stack in t.  stk = this warp's stack slice, already offset by the lane.
 // The instruction buffer (kCodeStride + 1 entries in shared memory) holds
@@ -131,6 +147,11 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
                                           const float (&x0)[RPT], const float (&x1)[RPT],
                                           const float *__restrict__ X, int64_t ld, int64_t r0,
                                           int64_t re, bool vec, float4 *stk) {
+    // the extended functions exist only in the deep-class instance, to which
+    // the pre-pass sends every program that uses them: in the shallow
+    // instance, where nearly all programs run, their cases cost 2-3%
+    // (measured on Pagie-1 x 4096 programs, which never use them)
+    constexpr bool kExt = NSLOT == kDeepSlots;
 #pragma unroll
     for (int j = 0; j < RPT; ++j) t[j] = 0.0f;
     int pc = 0;
@@ -210,9 +231,28 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
             case OP_ABS: GP_T(f_abs(t[j])) break;
             case OP_NEG: GP_T(f_neg(t[j])) break;
             case OP_INV: GP_T(f_inv(t[j])) break;
-            case OP_END:  // and the two values that name no operation
-            case 30:
-            case 31:
+            case OP_EXT1:  // out of line, four rows per call
+                if constexpr (kExt) {
+                    _Pragma("unroll") for (int g = 0; g < RPT / 4; ++g) {
+                        const float4 r = ext_rows4(
+                            make_float4(t[4 * g], t[4 * g + 1], t[4 * g + 2], t[4 * g + 3]),
+                            (w >> 5) & 7u);
+                        t[4 * g] = r.x; t[4 * g + 1] = r.y; t[4 * g + 2] = r.z; t[4 * g + 3] = r.w;
+                    }
+                    break;
+                } else {
+                    goto done;
+                }
+            case OP_EXT2:  // max / min, right operand in a stack slot
+                if constexpr (kExt) {
+                    GP_SLOT_LOAD(u)
+                    if (((w >> 5) & 7u) == EXT_MAX) { GP_T(f_max(t[j], u[j])) }
+                    else { GP_T(f_min(t[j], u[j])) }
+                    break;
+                } else {
+                    goto done;
+                }
+            case OP_END:
                 goto done;
             default:  // every value of w & 31 has a case above
                 __builtin_unreachable();

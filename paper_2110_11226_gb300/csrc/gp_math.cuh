@@ -16,6 +16,18 @@ namespace gpk {
 
 constexpr float kTrigFast = 65536.0f;
 
+// the extended function set: two rounded products, CUDA's float functions,
+// and max / min with NaN from either operand and the right operand on ties
+__device__ __forceinline__ float f_sq(float a) { return __fmul_rn(a, a); }
+__device__ __forceinline__ float f_cube(float a) { return __fmul_rn(__fmul_rn(a, a), a); }
+__device__ __forceinline__ float f_cbrt(float a) { return cbrtf(a); }
+__device__ __forceinline__ float f_tanh(float a) { return tanhf(a); }
+__device__ __forceinline__ float f_atan(float a) { return atanf(a); }
+__device__ __forceinline__ float f_sinh(float a) { return sinhf(a); }
+__device__ __forceinline__ float f_cosh(float a) { return coshf(a); }
+__device__ __forceinline__ float f_max(float a, float b) { return (a > b || a != a) ? a : b; }
+__device__ __forceinline__ float f_min(float a, float b) { return (a < b || a != a) ? a : b; }
+
 // pi/2 = HI + MID + LO (float32 parts of the exact value)
 constexpr float kPio2Hi = 1.57079637f;
 constexpr float kPio2Mid = -4.37113883e-08f;

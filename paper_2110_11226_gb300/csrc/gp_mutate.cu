@@ -39,8 +39,8 @@ __device__ __forceinline__ int pick(Stream &s, int n) {
 
 __device__ __forceinline__ int arity_of(int op) {
     if (op == GP_CONST || op == GP_VAR) return 0;
-    if (op >= GP_ADD && op <= GP_DIV) return 2;
-    if (op >= GP_SQRT && op <= GP_INV) return 1;
+    if ((op >= GP_ADD && op <= GP_DIV) || op == GP_MAX || op == GP_MIN) return 2;
+    if (op >= GP_SQRT && op <= GP_COSH) return 1;
     return -1;
 }
 

@@ -7,6 +7,7 @@
 // fused and each block writes one partial sum; the shared finalize pass
 // adds them in FP64.  It is the comparison point for the batched evaluator.
 #include "gp_internal.cuh"
+#include "gp_math.cuh"
 
 namespace gpk {
 
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(256) plain_kernel(PlainArgs a, int p) {
                 st.push(nd.c);
             } else if (op == GP_VAR) {
                 st.push(valid ? __ldg(a.X + (int64_t)nd.feat * a.ld + r) : 0.0f);
-            } else if (op >= GP_SQRT) {
+            } else if (op >= GP_SQRT && op <= GP_COSH) {
                 const float x = st.pop();
                 float z;
                 if (op == GP_SQRT) z = __fsqrt_rn(fabsf(x));
@@ -75,7 +76,14 @@ __global__ void __launch_bounds__(256) plain_kernel(PlainArgs a, int p) {
                 else if (op == GP_TAN) z = tanf(x);
                 else if (op == GP_ABS) z = fabsf(x);
                 else if (op == GP_NEG) z = -x;
-                else z = fabsf(x) < kThr ? 0.0f : __frcp_rn(x);
+                else if (op == GP_INV) z = fabsf(x) < kThr ? 0.0f : __frcp_rn(x);
+                else if (op == GP_SQ) z = f_sq(x);
+                else if (op == GP_CUBE) z = f_cube(x);
+                else if (op == GP_CBRT) z = f_cbrt(x);
+                else if (op == GP_TANH) z = f_tanh(x);
+                else if (op == GP_ATAN) z = f_atan(x);
+                else if (op == GP_SINH) z = f_sinh(x);
+                else z = f_cosh(x);
                 st.push(z);
             } else {
                 const float l = st.pop();
@@ -84,7 +92,9 @@ __global__ void __launch_bounds__(256) plain_kernel(PlainArgs a, int p) {
                 if (op == GP_ADD) z = __fadd_rn(l, rr);
                 else if (op == GP_SUB) z = __fsub_rn(l, rr);
                 else if (op == GP_MUL) z = __fmul_rn(l, rr);
-                else z = fabsf(rr) < kThr ? 1.0f : __fdiv_rn(l, rr);
+                else if (op == GP_DIV) z = fabsf(rr) < kThr ? 1.0f : __fdiv_rn(l, rr);
+                else if (op == GP_MAX) z = f_max(l, rr);
+                else z = f_min(l, rr);
                 st.push(z);
             }
         }

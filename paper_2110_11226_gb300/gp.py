@@ -49,7 +49,9 @@ class MutParams(C.Structure):
 
 MUT_KINDS = {"reproduction": 0, "crossover": 1, "subtree": 2, "hoist": 3, "point": 4}
 OPS = {"const": 0, "var": 1, "add": 2, "sub": 3, "mul": 4, "div": 5, "sqrt": 6, "log": 7,
-       "exp": 8, "sin": 9, "cos": 10, "tan": 11, "abs": 12, "neg": 13, "inv": 14}
+       "exp": 8, "sin": 9, "cos": 10, "tan": 11, "abs": 12, "neg": 13, "inv": 14, "sq": 15,
+       "cube": 16, "cbrt": 17, "tanh": 18, "atan": 19, "sinh": 20, "cosh": 21, "max": 22,
+       "min": 23}
 
 
 def make_mut_params(p_crossover=0.7, p_subtree=0.1, p_hoist=0.05, p_point=0.1,

@@ -58,7 +58,7 @@ def test_default_mix_on_the_large_population_is_bit_exact():
 
 @pytest.mark.parametrize("kind", ["crossover", "subtree", "hoist", "point"])
 def test_each_kind_alone(kind):
-    nodes, off = synth.ramped_half_and_half(700, 2, 9, synth.FULL_SET + ("tan",), 5, seed=8)
+    nodes, off = synth.ramped_half_and_half(700, 2, 9, synth.EXTENDED_SET, 5, seed=8)
     parents = np.random.default_rng(9).integers(0, 700, 2 * 2000)
     probs = dict(p_crossover=0.0, p_subtree=0.0, p_hoist=0.0, p_point=0.0)
     probs["p_" + kind] = 1.0

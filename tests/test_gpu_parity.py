@@ -35,12 +35,13 @@ def _weights(n, seed):
 # per-point values
 # --------------------------------------------------------------------------
 def test_predict_bit_exact_on_ieee_operators():
-    """add/sub/mul/div/inv/sqrt/abs/neg are correctly rounded on both sides
-    and nothing is contracted into FMA: the GPU values equal the oracle's
+    """add/sub/mul/div/inv/sqrt/abs/neg/sq/cube/max/min are correctly rounded
+    (or exact) on both sides and nothing is contracted into FMA: the GPU values equal the oracle's
     FP32 mode bit for bit (pagie_small programs and hand-written ones)."""
     wl = synth.workload("pagie_small")
     extra = synth.unpack(*synth.random_programs(300, 9, ("add", "sub", "mul", "div", "inv",
-                                                         "sqrt", "abs", "neg"), 2, seed=17))
+                                                         "sqrt", "abs", "neg", "sq", "cube",
+                                                         "max", "min"), 2, seed=17))
     progs = synth.unpack(wl.nodes, wl.offsets) + extra
     nodes, off = pack(progs)
     for n in (4096, 4096 + 37, 5):
@@ -76,10 +77,11 @@ def test_special_values_through_every_operator():
     a, b = np.meshgrid(sp, sp)
     X = np.stack([a.ravel(), b.ravel()]).astype(np.float32)
     progs = []
-    for name in ("sqrt", "log", "exp", "sin", "cos", "tan", "abs", "neg", "inv"):
+    for name in ("sqrt", "log", "exp", "sin", "cos", "tan", "abs", "neg", "inv", "sq", "cube",
+                 "cbrt", "tanh", "atan", "sinh", "cosh"):
         progs.append(parse_prefix(f"{name} x0"))
         progs.append(parse_prefix(f"add {name} x0 {name} x1"))
-    for name in ("add", "sub", "mul", "div"):
+    for name in ("add", "sub", "mul", "div", "max", "min"):
         progs.append(parse_prefix(f"{name} x0 x1"))
         progs.append(parse_prefix(f"{name} x0 0.5"))
         progs.append(parse_prefix(f"{name} -0.75 x1"))
@@ -101,7 +103,8 @@ def test_special_values_through_every_operator():
 
 
 @pytest.mark.parametrize("n_feat,funcs", [(2, synth.FULL_SET), (1, synth.FULL_SET + ("tan",)),
-                                          (7, synth.FULL_SET + ("tan",)), (50, synth.FULL_SET)])
+                                          (7, synth.FULL_SET + ("tan",)), (50, synth.FULL_SET),
+                                          (2, synth.EXTENDED_SET), (9, synth.EXTENDED_SET)])
 def test_predict_full_function_set(n_feat, funcs):
     nodes, off = synth.ramped_half_and_half(600, 2, 8, funcs, n_feat, seed=40 + n_feat)
     n = 2048 + 61
@@ -120,7 +123,7 @@ def test_constant_subtrees_fold_to_the_per_row_value():
     predictions must not change by a single bit (values below the protection
     threshold, on the trig slow path, zero and negative included)."""
     cval = np.array([0.0005, 70000.0, -3.75], np.float32)
-    funcs = synth.FULL_SET + ("tan",)
+    funcs = synth.EXTENDED_SET
     nodes, off = synth.ramped_half_and_half(800, 2, 8, funcs, 6, seed=77)
     n = 1024 + 45
     X = np.random.default_rng(5).uniform(-5, 5, size=(6, n)).astype(np.float32)
@@ -517,14 +520,16 @@ def test_tournament_bit_exact():
 # --------------------------------------------------------------------------
 # constant gradients and Adam
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("metric", ["mse", "rmse", "mae", "logloss"])
-def test_const_grad_matches_oracle_reverse_mode(metric):
+@pytest.mark.parametrize("metric,funcs", [("mse", synth.FULL_SET), ("rmse", synth.FULL_SET),
+                                          ("mae", synth.FULL_SET), ("logloss", synth.FULL_SET),
+                                          ("mse", synth.EXTENDED_SET)])
+def test_const_grad_matches_oracle_reverse_mode(metric, funcs):
     n = 2048 + 19
     if metric == "logloss":
         d = synth.classification_data(n, 11, n_feat=4)
     else:
         d = synth.pagie_data(n, 12)
-    nodes, off = synth.ramped_half_and_half(200, 2, 6, synth.FULL_SET, d.n_feat, seed=70,
+    nodes, off = synth.ramped_half_and_half(200, 2, 6, funcs, d.n_feat, seed=70,
                                             max_consts=16)
     pn, po, dX, dy, dw = put(nodes, off, d.X, d.y, d.w)
     g, f = gp.gp_const_grad(pn, po, dX, dy, dw, metric=metric)
@@ -533,8 +538,15 @@ def test_const_grad_matches_oracle_reverse_mode(metric):
     g32, _ = oracle.const_grad32(nodes, off, d.X, d.y, d.w, metric)
     v, e, fl = oracle.predict_bound(nodes, off, d.X, ulps_fn=4.0)
     fbatch = gp.gp_evaluate(pn, po, dX, dy, dw, metric=metric).cpu().numpy()
-    fin = np.isfinite(fbatch)
-    np.testing.assert_allclose(f[fin], fbatch[fin], rtol=5e-6)
+    # the gradient kernel's fitness and the evaluator's use different FP32
+    # function implementations (CUDA's sinf / cosf against the evaluator's
+    # own) and summation orders: they agree where every row value is
+    # certified to 1e-6 by the error bound
+    with np.errstate(invalid="ignore"):
+        cert = ~(fl != 0).any(axis=1) & ((e <= 1e-6 * np.abs(v)) | (e <= 1e-30)).all(axis=1)
+    cert &= np.isfinite(fbatch)
+    assert cert.sum() > 0.2 * len(cert)
+    np.testing.assert_allclose(f[cert], fbatch[cert], rtol=2e-5)
     extra = _mae_flip_tol(nodes, off, d, metric)
     strict, cond = _grad_check(g, g64, g32, gabs, fl, extra, e, v)
     assert strict > 0.4 * len(g64), (strict, cond)
