@@ -386,13 +386,13 @@ def main():
                        "parallelism": f"program shards x{ws} + fitness all-gather" if ws > 1 else "single GPU",
                        "opts": {"rows_per_thread": used.rows_per_thread, "chunk_rows": used.chunk_rows,
                                 "blocks_per_sm": used.blocks_per_sm or "max resident",
-                                "deep_rows_per_thread": 4, "autotuned": tuned is not None}},
+                                "class_1_2_rows_per_thread": 4, "autotuned": tuned is not None}},
             "node_evals_per_s": value * (n_nodes / P),
             "finite_fitness_frac": fin,
             "clocks": clocks,
-            # per step: compile, order, weight sum (+1 with weights), two
-            # evaluator launches (depth classes), finalize, tournament
-            "gpu_launches": (7 + (d.w is not None)) * args.steps,
+            # per step: compile, order, weight sum (+1 with weights), three
+            # evaluator launches (program classes), finalize, tournament
+            "gpu_launches": (8 + (d.w is not None)) * args.steps,
             "roofline": roof,
             "pipes": pipes}
 

@@ -267,10 +267,10 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
             ea.shift = W.shift;
             ea.ystat = W.ystat;
         }
-        // the deep class keeps 4 rows per thread (its 19-slot stack would
-        // otherwise leave room for one block per SM); the same chunk
-        // partition serves both
-        const int rpt_c = (cls == 0) ? rpt : 4;
+        // classes 1 and 2 keep 4 rows per thread (the 19-slot stack would
+        // otherwise leave room for one block per SM; class 2 is rare); the
+        // same chunk partition serves all three
+        const int rpt_c = (cls == kClassShallow) ? rpt : 4;
         const int block = kEvalBlockThreads;
         int occ = eval_info(rpt_c, fmode, cls, block, nullptr, mom);
         if (occ < 1) occ = 1;
@@ -357,7 +357,7 @@ int run_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const
         ea.pred = out_pred;
         ea.dev_status = c->status;
         ea.vec_ok = vec ? 1 : 0;
-        int occ = info_predict(kEvalBlockThreads, nullptr);
+        int occ = info_predict(cls, kEvalBlockThreads, nullptr);
         GP_CUDA(launch_predict(ea, c->sms * std::max(occ, 1), kEvalBlockThreads, st));
     }
     return GP_OK;

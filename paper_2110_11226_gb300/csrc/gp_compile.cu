@@ -1,6 +1,7 @@
 // gp_compile.cu -- device pre-pass: validate each prefix list, compile it
 // to the register-stack form (gp_internal.cuh), and sort the programs into
-// depth classes and by length (length-bucketed work queue); plus the
+// classes (stack depth, extended functions) and by length (length-bucketed
+// work queue); plus the
 // deterministic total-weight sum.
 #include "gp_internal.cuh"
 #include "gp_interp.cuh"
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
     }
     if (status != GP_PROG_OK) {
         out[0] = make_uint2(make_ins(OP_END, 0, 0), 0u);
-        a.meta[p] = ProgMeta{1, status, 0, 0};
+        a.meta[p] = ProgMeta{1, status, 0, 0, 0};
         atomicOr(a.dev_status, GP_DEV_BAD_PROGRAM);
         return;
     }
@@ -298,10 +299,7 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
         if (sp > depth) depth = sp;
     }
     out[n++] = make_uint2(make_ins(OP_END, 0, 0), 0u);
-    // the extended functions are compiled into the deep-class evaluator
-    // only, so a program that uses them joins that class
-    if (ext) depth = max(depth, kSmallDepth + 1);
-    a.meta[p] = ProgMeta{n, GP_PROG_OK, depth, n_consts};
+    a.meta[p] = ProgMeta{n, GP_PROG_OK, (int16_t)depth, (int16_t)(ext ? 1 : 0), n_consts};
 }
 
 cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st) {
@@ -313,9 +311,9 @@ cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st) {
 }
 
 // Counting sort of program ids: key = class * 256 + (256 - n_ins), so the
-// shallow class comes first and, inside a class, longer programs first
-// (longest-processing-time order for the dynamic work queue).  Invalid
-// programs (n_ins = 1) land at the end of the shallow class.  Order inside
+// classes follow one another (0, 1, 2) and, inside a class, longer programs
+// come first (longest-processing-time order for the dynamic work queue).
+// Invalid programs (n_ins = 1) land at the end of class 0.  Order inside
 // one key is arbitrary; results do not depend on it.
 constexpr int kOrderBins = kNumClasses * 256;
 
@@ -327,26 +325,28 @@ __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n
     __syncthreads();
     for (int p = threadIdx.x; p < n_progs; p += blockDim.x) {
         const ProgMeta m = meta[p];
-        const int cls = (m.depth <= kSmallDepth) ? 0 : 1;
+        const int cls = prog_class(m.depth, m.ext);
         const int key = cls * 256 + (256 - m.n_ins);
         atomicAdd(&hist[key], 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int run = 0;
+        int run = 0, prev = 0;
         for (int i = 0; i < kOrderBins; ++i) {
             cursor[i] = run;
             run += hist[i];
-            if (i == 255) class_count[0] = run;
+            if (i % 256 == 255) {
+                class_count[i / 256] = run - prev;
+                prev = run;
+            }
         }
-        class_count[1] = run - class_count[0];
-        class_count[2] = 0;
-        class_count[3] = 0;
+        class_count[kNumClasses] = 0;
+        class_count[kNumClasses + 1] = 0;
     }
     __syncthreads();
     for (int p = threadIdx.x; p < n_progs; p += blockDim.x) {
         const ProgMeta m = meta[p];
-        const int cls = (m.depth <= kSmallDepth) ? 0 : 1;
+        const int cls = prog_class(m.depth, m.ext);
         const int key = cls * 256 + (256 - m.n_ins);
         const int pos = atomicAdd(&cursor[key], 1);
         order[pos] = p;

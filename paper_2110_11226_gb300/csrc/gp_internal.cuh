@@ -79,14 +79,22 @@ static __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 struct ProgMeta {
     int32_t n_ins;     // instructions including END
     int32_t status;    // gp_prog_status
-    int32_t depth;     // largest stack height of the compiled form
+    int16_t depth;     // largest stack height of the compiled form
+    int16_t ext;       // 1: uses an extended function (EXT1/EXT2 words)
     int32_t n_consts;  // CONST nodes
 };
 
-// depth classes: programs whose compiled stack fits kSmallDepth run in a
-// kernel instance with a smaller shared-memory stack (more blocks per SM)
+// Program classes, one evaluator instance each.  Programs whose compiled
+// stack fits kSmallDepth run with a 7-slot shared-memory stack (more blocks
+// per SM): class 0 without the extended functions, class 2 with them (their
+// dispatch entries would slow class 0 down); deeper programs run in class 1
+// (19 slots, every function).
 constexpr int kSmallDepth = 8;     // 7 stack slots + t
-constexpr int kNumClasses = 2;
+constexpr int kNumClasses = 3;
+constexpr int kClassShallow = 0, kClassDeep = 1, kClassShallowExt = 2;
+__host__ __device__ inline int prog_class(int depth, int ext) {
+    return depth > kSmallDepth ? kClassDeep : (ext ? kClassShallowExt : kClassShallow);
+}
 
 // Workspace carved out of one device allocation (all offsets 256-aligned).
 struct Workspace {
@@ -183,7 +191,7 @@ struct EvalArgs {
     const double *ystat;
 };
 // One launcher per (rows per thread, feature mode) instance; a.cls picks
-// the depth class (register slots).  fmode 2: columns 0 and 1 held in
+// the program class (stack slots, extended functions).  fmode 2: columns 0 and 1 held in
 // registers (n_feat <= 2); fmode 0: feature columns loaded per reference.
 // info_*: resident blocks per SM for `block` threads; *regs = registers.
 #define GP_EVAL_INSTANCE(R, F)                                                  \
@@ -199,7 +207,7 @@ GP_EVAL_INSTANCE(16, 0)
 #undef GP_EVAL_INSTANCE
 cudaError_t launch_predict(const EvalArgs &a, int grid, int block,
                            cudaStream_t st);
-int info_predict(int block, int *regs);
+int info_predict(int cls, int block, int *regs);
 
 struct FinalizeArgs {
     const float *part;

@@ -1,6 +1,6 @@
 // gp_interp.cuh -- the batched persistent evaluator (the hot loop).
 //
-// Work: every (program, row-chunk) pair of one depth class is an item of a
+// Work: every (program, row-chunk) pair of one program class is an item of a
 // dynamic queue (one atomic counter); items are ordered chunk-major and,
 // inside a chunk, longest program first, so the blocks that share the GPU
 // at any moment work on the same few row chunks (X stays in L2) and the
@@ -142,16 +142,16 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
 // instruction); the switch covers all 32 values of its 5-bit operand, so
 // it needs no range test; and the word is loaded when it is needed rather
 // than one ahead, which saves the register copies of a prefetch.
-template <int RPT, int NSLOT, int FMODE>
+template <int RPT, int NSLOT, int FMODE, bool EXT>
 __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restrict__ cbuf,
                                           const float (&x0)[RPT], const float (&x1)[RPT],
                                           const float *__restrict__ X, int64_t ld, int64_t r0,
                                           int64_t re, bool vec, float4 *stk) {
-    // the extended functions exist only in the deep-class instance, to which
-    // the pre-pass sends every program that uses them: in the shallow
-    // instance, where nearly all programs run, their cases cost 2-3%
-    // (measured on Pagie-1 x 4096 programs, which never use them)
-    constexpr bool kExt = NSLOT == kDeepSlots;
+    // EXT: the extended functions are compiled in (classes 1 and 2).  In
+    // class 0, where nearly all programs of the usual function set run,
+    // their cases cost 2-3% (measured on Pagie-1 x 4096 programs, which
+    // never use them)
+    constexpr bool kExt = EXT;
 #pragma unroll
     for (int j = 0; j < RPT; ++j) t[j] = 0.0f;
     int pc = 0;
@@ -286,7 +286,7 @@ constexpr size_t eval_smem_bytes() {
 // occupancy; left alone it would take 97 and fit 2.
 constexpr int kEpiLoss = 0, kEpiPred = 1, kEpiMom = 2;
 
-template <int RPT, int NSLOT, int FMODE, int EPI>
+template <int RPT, int NSLOT, int FMODE, int EPI, bool EXT>
 __global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom && RPT == 8 ? 3 : 0) eval_kernel(const EvalArgs a) {
     constexpr bool PRED = EPI == kEpiPred;
     constexpr bool MOM = EPI == kEpiMom;
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom && RPT 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     float4 *stk = stack_all + (size_t)warp * NSLOT * (RPT / 4) * 32 + lane;
-    const int cls_begin = (a.cls == 0) ? 0 : a.class_count[0];
+    const int cls_begin = (a.cls == 0) ? 0 : a.class_count[0] + (a.cls == 2 ? a.class_count[1] : 0);
     const int n_cls = a.class_count[a.cls];
     const unsigned long long total = (unsigned long long)n_cls * (unsigned long long)a.n_chunks;
     const bool vec = a.vec_ok != 0;
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom && RPT 
                 for (int j = 0; j < RPT; ++j) x0[j] = x1[j] = 0.0f;
             }
             float t[RPT];
-            interpret<RPT, NSLOT, FMODE>(t, cbuf, x0, x1, a.X, a.ld, r0, re, vec, stk);
+            interpret<RPT, NSLOT, FMODE, EXT>(t, cbuf, x0, x1, a.X, a.ld, r0, re, vec, stk);
             if (PRED) {
                 float *dst = a.pred + (size_t)p * a.n_rows;
 #pragma unroll
@@ -430,22 +430,22 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom && RPT 
     }
 }
 
-template <int RPT, int NSLOT, int FMODE, int EPI>
+template <int RPT, int NSLOT, int FMODE, int EPI, bool EXT>
 cudaError_t launch_eval_t(const EvalArgs &a, int grid, int block, cudaStream_t st) {
     (void)block;
     constexpr size_t smem = eval_smem_bytes<RPT, NSLOT>();
-    auto k = eval_kernel<RPT, NSLOT, FMODE, EPI>;
+    auto k = eval_kernel<RPT, NSLOT, FMODE, EPI, EXT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, eval_warps<RPT>() * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int RPT, int NSLOT, int FMODE, int EPI>
+template <int RPT, int NSLOT, int FMODE, int EPI, bool EXT>
 int info_t(int block, int *regs) {
     (void)block;
     constexpr size_t smem = eval_smem_bytes<RPT, NSLOT>();
-    auto k = eval_kernel<RPT, NSLOT, FMODE, EPI>;
+    auto k = eval_kernel<RPT, NSLOT, FMODE, EPI, EXT>;
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 0;
     if (regs) *regs = fa.numRegs;

@@ -3,8 +3,9 @@
 //
 // Unlike the fused metrics this one needs every prediction of a program at
 // once: a batch of programs is predicted into [B][N], each segment is sorted
-// by value (a stable LSD radix sort, 4-bit digits, of order-preserving
-// 32-bit keys with the row index as payload), ties get the mean of their
+// by value (a stable LSD radix sort, 8-bit digits in 4 passes, of
+// order-preserving 32-bit keys with the row index as payload; the first
+// pass reads the predictions themselves), ties get the mean of their
 // positions, and the weighted moments of the rank pairs are summed in FP64
 // with a fixed partition.  The target's ranks are computed the same way
 // once per call.  Ranks are kept doubled (first + last position, 1-based),
@@ -14,11 +15,20 @@
 namespace gpk {
 namespace {
 
+// rank pass: 2048 sorted keys per block
 constexpr int kTileItems = 8;                          // per thread
 constexpr int kTileThreads = 256;
-constexpr int kTile = kTileItems * kTileThreads;       // 2048 keys per tile
-constexpr int kRadixBits = 4;
-constexpr int kDigits = 1 << kRadixBits;
+constexpr int kTile = kTileItems * kTileThreads;
+
+// LSD radix sort: 8-bit digits, 4 passes; a sort tile is 4096 keys, 16 per
+// thread, warp w owning keys [512 w, 512 w + 512) of its tile
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadixBits = 8;
+constexpr int kBins = 1 << kRadixBits;
+constexpr int kPasses = 32 / kRadixBits;
 
 // order-preserving key of a float (-0 and +0 become the same key)
 __device__ __forceinline__ uint32_t float_key(float f) {
@@ -27,160 +37,167 @@ __device__ __forceinline__ uint32_t float_key(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__global__ void __launch_bounds__(256) to_keys_kernel(const float *__restrict__ v, int n_seg,
-                                                      int64_t n, uint32_t *keys, uint32_t *vals,
-                                                      uint32_t *nan_flag) {
-    const int64_t total = (int64_t)n_seg * n;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float f = v[i];
-        if (f != f) atomicOr(nan_flag + i / n, 1u);
-        keys[i] = float_key(f);
-        vals[i] = (uint32_t)(i % n);
-    }
+// key of item m of a segment: pass 0 reads the float values (and flags a
+// segment holding NaN), later passes the keys of the previous pass
+template <bool FROM_FLOAT>
+__device__ __forceinline__ uint32_t load_key(const void *src, int64_t m) {
+    if (FROM_FLOAT) return float_key(static_cast<const float *>(src)[m]);
+    return static_cast<const uint32_t *>(src)[m];
 }
 
-// digit counts of one tile: hist[seg][digit][tile]
-__global__ void __launch_bounds__(kTileThreads) hist_kernel(const uint32_t *__restrict__ keys,
-                                                            int64_t n, int n_tiles, int shift,
-                                                            int32_t *hist) {
-    __shared__ int32_t cnt[kDigits];
-    const int seg = blockIdx.y, tile = blockIdx.x;
-    if (threadIdx.x < kDigits) cnt[threadIdx.x] = 0;
+// digit counts of one tile: hist[seg][digit][tile].  Lanes holding the
+// same digit add once (match), so a run of equal digits costs no
+// serialised shared-memory atomics.
+template <bool FROM_FLOAT>
+__global__ void __launch_bounds__(kSortThreads) hist_kernel(const void *__restrict__ src, int64_t n,
+                                                            int n_tiles, int shift, int32_t *hist,
+                                                            uint32_t *nan_flag) {
+    __shared__ int32_t cnt[kBins];
+    const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x, lane = t & 31;
+    cnt[t] = 0;
     __syncthreads();
-    const uint32_t *k = keys + (int64_t)seg * n;
-    const int64_t base = (int64_t)tile * kTile + (int64_t)threadIdx.x * kTileItems;
-#pragma unroll
-    for (int it = 0; it < kTileItems; ++it) {
-        const int64_t m = base + it;
-        if (m < n) atomicAdd(&cnt[(k[m] >> shift) & (kDigits - 1)], 1);
+    const int64_t t0 = (int64_t)tile * kSortTile;
+    const int tl = (int)min((int64_t)kSortTile, n - t0);
+    const int64_t so = (int64_t)seg * n + t0;
+    bool nan = false;
+    for (int i0 = 0; i0 < kSortTile; i0 += kSortThreads) {
+        const int i = i0 + t;
+        const bool in = i < tl;
+        uint32_t d = kBins + lane;  // a group of its own
+        if (in) {
+            if (FROM_FLOAT) {
+                const float f = static_cast<const float *>(src)[so + i];
+                nan |= f != f;
+                d = (float_key(f) >> shift) & (kBins - 1);
+            } else {
+                d = (static_cast<const uint32_t *>(src)[so + i] >> shift) & (kBins - 1);
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (in && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], __popc(peers));
     }
+    if (FROM_FLOAT && __any_sync(0xffffffffu, nan) && lane == 0) atomicOr(nan_flag + seg, 1u);
     __syncthreads();
-    if (threadIdx.x < kDigits)
-        hist[((int64_t)seg * kDigits + threadIdx.x) * n_tiles + tile] = cnt[threadIdx.x];
+    hist[((int64_t)seg * kBins + t) * n_tiles + tile] = cnt[t];
 }
 
-// exclusive scan of hist[seg][*][*] in digit-major order, one block per
-// segment, 1024 entries at a time with a carry
-__global__ void __launch_bounds__(1024) scan_kernel(int32_t *hist, int n_tiles) {
-    __shared__ int32_t warp_sum[32];
-    __shared__ int32_t carry;
-    int32_t *h = hist + (int64_t)blockIdx.x * kDigits * n_tiles;
-    const int64_t len = (int64_t)kDigits * n_tiles;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < len; base += 1024) {
-        const int64_t i = base + threadIdx.x;
-        const int32_t v = i < len ? h[i] : 0;
+// per (segment, digit), one warp: exclusive scan of the tile counts in
+// place, and the digit's total in tot[seg][digit]
+__global__ void __launch_bounds__(256) tile_scan_kernel(int32_t *hist, int32_t *tot, int n_rows_hd,
+                                                        int n_tiles) {
+    const int lane = threadIdx.x & 31;
+    const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (row >= n_rows_hd) return;
+    int32_t *h = hist + (int64_t)row * n_tiles;
+    int32_t carry = 0;
+    for (int base = 0; base < n_tiles; base += 32) {
+        const int i = base + lane;
+        const int32_t v = i < n_tiles ? h[i] : 0;
         int32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) warp_sum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int32_t s = warp_sum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
-            }
-            warp_sum[lane] = s;
-        }
-        __syncthreads();
-        const int32_t before = carry + (warp > 0 ? warp_sum[warp - 1] : 0) + x - v;
-        if (i < len) h[i] = before;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = before + v;
-        __syncthreads();
+        if (i < n_tiles) h[i] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
     }
+    if (lane == 0) tot[row] = carry;
 }
 
-// stable scatter of one tile by one digit: thread t owns items
-// [t*8, t*8+8) of the tile in order; an item's place is the digit's
-// segment offset for this tile, plus the same digit in earlier threads of
-// the tile, plus the same digit in its own earlier items
-__global__ void __launch_bounds__(kTileThreads) scatter_kernel(
-    const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n, int n_tiles,
-    int shift, const int32_t *__restrict__ offs, uint32_t *keys_out, uint32_t *vals_out) {
-    __shared__ int32_t sc[kDigits * kTileThreads];
-    __shared__ int32_t tsum[kTileThreads];
+// exclusive scan of one value per thread over a 256-thread block
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int32_t before = 0;
+    for (int q = 0; q < warp; ++q) before += wsum[q];
+    __syncthreads();
+    return before + x - v;
+}
+
+// Stable scatter of one tile by one digit.  The tile is ranked in shared
+// memory first (warp-level digit groups in key order, then a scan over
+// (digit, warp)), staged in sorted order, and written out run by run so
+// that neighbouring threads store to neighbouring addresses.  Padding
+// beyond a ragged tile's end takes digit 255 and, being last in key order,
+// sorted positions >= the tile length, which are not written.  Pass 0
+// reads float values and produces the row index as the payload.
+template <bool FROM_FLOAT>
+__global__ void __launch_bounds__(kSortThreads) scatter_kernel(
+    const void *__restrict__ src, const uint32_t *__restrict__ vals, int64_t n, int n_tiles,
+    int shift, const int32_t *__restrict__ offs, const int32_t *__restrict__ tot,
+    uint32_t *keys_out, uint32_t *vals_out) {
+    __shared__ uint32_t sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    __shared__ int32_t wcnt[kSortWarps][kBins];
+    __shared__ int32_t dstart[kBins];
+    __shared__ int32_t gbase[kBins];
+    __shared__ int32_t wsum[kSortWarps];
     const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    const int64_t t0 = (int64_t)tile * kSortTile;
+    const int tl = (int)min((int64_t)kSortTile, n - t0);
     const int64_t so = (int64_t)seg * n;
-    const int64_t base = (int64_t)tile * kTile + (int64_t)t * kTileItems;
-    uint32_t kk[kTileItems], vv[kTileItems];
-    int32_t cnt[kDigits];
 #pragma unroll
-    for (int d = 0; d < kDigits; ++d) cnt[d] = 0;
+    for (int w = 0; w < kSortWarps; ++w) wcnt[w][t] = 0;
+    // global position of this tile's first item of digit t: the digit's
+    // start in the segment plus the same digit in earlier tiles
+    const int32_t dbase = block_exclusive_scan(tot[(int64_t)seg * kBins + t], wsum);
+    gbase[t] = dbase + offs[((int64_t)seg * kBins + t) * n_tiles + tile];
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t kk[kSortItems], vv[kSortItems];
+    int32_t off[kSortItems];
 #pragma unroll
-    for (int it = 0; it < kTileItems; ++it) {
-        const int64_t m = base + it;
-        kk[it] = m < n ? keys[so + m] : 0u;
-        vv[it] = m < n ? vals[so + m] : 0u;
-        if (m < n) {
-            const int d = (kk[it] >> shift) & (kDigits - 1);
-#pragma unroll
-            for (int e = 0; e < kDigits; ++e) cnt[e] += (d == e);
-        }
+    for (int r = 0; r < kSortItems; ++r) {
+        const int i = warp * (kSortItems * 32) + r * 32 + lane;
+        const bool in = i < tl;
+        kk[r] = in ? load_key<FROM_FLOAT>(src, so + t0 + i) : 0xffffffffu;
+        vv[r] = FROM_FLOAT ? (uint32_t)(t0 + i) : (in ? vals[so + t0 + i] : 0u);
     }
 #pragma unroll
-    for (int d = 0; d < kDigits; ++d) sc[d * kTileThreads + t] = cnt[d];
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t d = (kk[r] >> shift) & (kBins - 1);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int32_t before = wcnt[warp][d];
+        __syncwarp();
+        if ((peers & lt) == 0) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        off[r] = before + __popc(peers & lt);
+    }
     __syncthreads();
-    // exclusive scan over sc in digit-major order: thread t scans entries
-    // [16t, 16t+16), then the 256 thread totals are scanned
+    // digit t: warps' exclusive prefixes, then the digits' starts in the tile
     int32_t run = 0;
-    int32_t loc[kDigits];
 #pragma unroll
-    for (int e = 0; e < kDigits; ++e) {
-        loc[e] = run;
-        run += sc[t * kDigits + e];
+    for (int w = 0; w < kSortWarps; ++w) {
+        const int32_t c = wcnt[w][t];
+        wcnt[w][t] = run;
+        run += c;
     }
-    tsum[t] = run;
+    dstart[t] = block_exclusive_scan(run, wsum);
     __syncthreads();
-    if (t < 32) {  // warp 0 scans the 256 totals, 8 per lane
-        int32_t part = 0;
-        int32_t v8[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            v8[q] = part;
-            part += tsum[t * 8 + q];
-        }
-        int32_t x = part;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (t >= o) x += y;
-        }
-        const int32_t before = x - part;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) tsum[t * 8 + q] = before + v8[q];
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t d = (kk[r] >> shift) & (kBins - 1);
+        const int pos = dstart[d] + wcnt[warp][d] + off[r];
+        sk[pos] = kk[r];
+        sv[pos] = vv[r];
     }
     __syncthreads();
-    const int32_t pre = tsum[t];
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < kDigits; ++e) sc[t * kDigits + e] = pre + loc[e];
-    __syncthreads();
-    // place of (digit d, thread t) within the tile's digit-d run
-    int32_t start[kDigits];
-#pragma unroll
-    for (int d = 0; d < kDigits; ++d)
-        start[d] = offs[((int64_t)seg * kDigits + d) * n_tiles + tile] +
-                   (sc[d * kTileThreads + t] - sc[d * kTileThreads]);
-#pragma unroll
-    for (int it = 0; it < kTileItems; ++it) {
-        const int64_t m = base + it;
-        if (m >= n) continue;
-        const int d = (kk[it] >> shift) & (kDigits - 1);
-        int32_t pos = 0;
-#pragma unroll
-        for (int e = 0; e < kDigits; ++e)
-            if (d == e) pos = start[e]++;
-        keys_out[so + pos] = kk[it];
-        vals_out[so + pos] = vv[it];
+#pragma unroll 4
+    for (int pos = t; pos < tl; pos += kSortThreads) {
+        const uint32_t k = sk[pos];
+        const uint32_t d = (k >> shift) & (kBins - 1);
+        const int64_t g = so + gbase[d] + (pos - dstart[d]);
+        keys_out[g] = k;
+        vals_out[g] = sv[pos];
     }
 }
 
@@ -312,49 +329,88 @@ __global__ void __launch_bounds__(256) spearman_final_kernel(
     if (out64) out64[seg] = f;
 }
 
-cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys2, uint32_t *vals2,
-                             int n_seg, int64_t n, int32_t *hist, cudaStream_t st) {
-    const int n_tiles = (int)((n + kTile - 1) / kTile);
+// Sorts each of n_seg segments of n float values into keys (order-preserving
+// integers) with the row index as payload; the result is in keys/vals.
+// hist holds n_seg * 256 * n_tiles counts, tot n_seg * 256.
+cudaError_t radix_sort_values(const float *v, uint32_t *keys, uint32_t *vals, uint32_t *keys2,
+                              uint32_t *vals2, int n_seg, int64_t n, int32_t *hist, int32_t *tot,
+                              uint32_t *nan_flag, cudaStream_t st) {
+    const int n_tiles = (int)((n + kSortTile - 1) / kSortTile);
     const dim3 grid(n_tiles, n_seg);
-    for (int pass = 0; pass < 32 / kRadixBits; ++pass) {
+    const int scan_rows = n_seg * kBins;
+    const int scan_blocks = (scan_rows + 7) / 8;
+    for (int pass = 0; pass < kPasses; ++pass) {
         const int shift = pass * kRadixBits;
+        // pass 0: values -> keys2; then keys2 -> keys -> keys2 -> keys
         const uint32_t *ki = (pass & 1) ? keys2 : keys;
         const uint32_t *vi = (pass & 1) ? vals2 : vals;
         uint32_t *ko = (pass & 1) ? keys : keys2;
         uint32_t *vo = (pass & 1) ? vals : vals2;
-        hist_kernel<<<grid, kTileThreads, 0, st>>>(ki, n, n_tiles, shift, hist);
-        scan_kernel<<<n_seg, 1024, 0, st>>>(hist, n_tiles);
-        scatter_kernel<<<grid, kTileThreads, 0, st>>>(ki, vi, n, n_tiles, shift, hist, ko, vo);
+        if (pass == 0) {
+            hist_kernel<true><<<grid, kSortThreads, 0, st>>>(v, n, n_tiles, shift, hist, nan_flag);
+        } else {
+            hist_kernel<false><<<grid, kSortThreads, 0, st>>>(ki, n, n_tiles, shift, hist, nullptr);
+        }
+        tile_scan_kernel<<<scan_blocks, 256, 0, st>>>(hist, tot, scan_rows, n_tiles);
+        if (pass == 0) {
+            scatter_kernel<true><<<grid, kSortThreads, 0, st>>>(v, nullptr, n, n_tiles, shift, hist,
+                                                                tot, ko, vo);
+        } else {
+            scatter_kernel<false><<<grid, kSortThreads, 0, st>>>(ki, vi, n, n_tiles, shift, hist,
+                                                                 tot, ko, vo);
+        }
     }
-    return cudaGetLastError();  // 8 passes: the result is back in keys/vals
+    return cudaGetLastError();  // 4 passes: the result is in keys/vals
 }
 
 }  // namespace
 
-size_t rank_scratch_bytes(int n_seg, int64_t n) {
-    const int64_t n_tiles = (n + kTile - 1) / kTile;
+// scratch of one batch of n_seg segments: keys, vals and their second
+// buffers, the tile digit counts, the digit totals, the rank partials and
+// the NaN flags
+struct RankScratch {
+    uint32_t *keys, *vals, *keys2, *vals2;
+    int32_t *hist, *tot;
+    double *part;
+    uint32_t *nan_flag;
+    size_t bytes;
+};
+
+RankScratch carve_rank(void *scratch, int n_seg, int64_t n) {
+    const int64_t sort_tiles = (n + kSortTile - 1) / kSortTile;
+    const int64_t rank_tiles = (n + kTile - 1) / kTile;
     auto al = [](int64_t x) { return (size_t)((x + 255) / 256 * 256); };
-    return 4 * al((int64_t)n_seg * n * 4) + al((int64_t)n_seg * kDigits * n_tiles * 4) +
-           al((int64_t)n_seg * n_tiles * 6 * 8) + al((int64_t)n_seg * 4);
+    char *b = static_cast<char *>(scratch);
+    RankScratch r{};
+    size_t o = 0;
+    const size_t arr = al((int64_t)n_seg * n * 4);
+    r.keys = reinterpret_cast<uint32_t *>(b + o); o += arr;
+    r.vals = reinterpret_cast<uint32_t *>(b + o); o += arr;
+    r.keys2 = reinterpret_cast<uint32_t *>(b + o); o += arr;
+    r.vals2 = reinterpret_cast<uint32_t *>(b + o); o += arr;
+    r.hist = reinterpret_cast<int32_t *>(b + o); o += al((int64_t)n_seg * kBins * sort_tiles * 4);
+    r.tot = reinterpret_cast<int32_t *>(b + o); o += al((int64_t)n_seg * kBins * 4);
+    r.part = reinterpret_cast<double *>(b + o); o += al((int64_t)n_seg * rank_tiles * 6 * 8);
+    r.nan_flag = reinterpret_cast<uint32_t *>(b + o); o += al((int64_t)n_seg * 4);
+    r.bytes = o;
+    return r;
+}
+
+size_t rank_scratch_bytes(int n_seg, int64_t n) {
+    return carve_rank(nullptr, n_seg, n).bytes;
 }
 
 cudaError_t target_ranks(const float *y, int64_t n, void *scratch, uint32_t *r2y,
                          cudaStream_t st) {
     const int64_t n_tiles = (n + kTile - 1) / kTile;
-    auto al = [](int64_t x) { return (int64_t)((x + 255) / 256 * 256); };
-    char *b = static_cast<char *>(scratch);
-    uint32_t *keys = reinterpret_cast<uint32_t *>(b);
-    uint32_t *vals = reinterpret_cast<uint32_t *>(b + al(n * 4));
-    uint32_t *keys2 = reinterpret_cast<uint32_t *>(b + 2 * al(n * 4));
-    uint32_t *vals2 = reinterpret_cast<uint32_t *>(b + 3 * al(n * 4));
-    int32_t *hist = reinterpret_cast<int32_t *>(b + 4 * al(n * 4));
-    uint32_t *nan_flag = reinterpret_cast<uint32_t *>(b + 4 * al(n * 4) + al(kDigits * n_tiles * 4));
-    cudaMemsetAsync(nan_flag, 0, 4, st);
-    to_keys_kernel<<<1024, 256, 0, st>>>(y, 1, n, keys, vals, nan_flag);
-    cudaError_t e = radix_sort_pairs(keys, vals, keys2, vals2, 1, n, hist, st);
+    const RankScratch r = carve_rank(scratch, 1, n);
+    cudaError_t e = cudaMemsetAsync(r.nan_flag, 0, 4, st);
     if (e != cudaSuccess) return e;
-    rank_kernel<<<dim3((unsigned)n_tiles, 1), kTileThreads, 0, st>>>(keys, vals, n, (int)n_tiles, 0,
-                                                                      r2y, nullptr, nullptr, nullptr);
+    e = radix_sort_values(y, r.keys, r.vals, r.keys2, r.vals2, 1, n, r.hist, r.tot, r.nan_flag, st);
+    if (e != cudaSuccess) return e;
+    rank_kernel<<<dim3((unsigned)n_tiles, 1), kTileThreads, 0, st>>>(r.keys, r.vals, n, (int)n_tiles,
+                                                                      0, r2y, nullptr, nullptr,
+                                                                      nullptr);
     return cudaGetLastError();
 }
 
@@ -362,25 +418,16 @@ cudaError_t spearman_batch(const float *pred, int n_seg, int64_t n, const uint32
                            const float *w, void *scratch, float *out, double *out64,
                            cudaStream_t st) {
     const int64_t n_tiles = (n + kTile - 1) / kTile;
-    auto al = [](int64_t x) { return (int64_t)((x + 255) / 256 * 256); };
-    const int64_t arr = al((int64_t)n_seg * n * 4);
-    char *b = static_cast<char *>(scratch);
-    uint32_t *keys = reinterpret_cast<uint32_t *>(b);
-    uint32_t *vals = reinterpret_cast<uint32_t *>(b + arr);
-    uint32_t *keys2 = reinterpret_cast<uint32_t *>(b + 2 * arr);
-    uint32_t *vals2 = reinterpret_cast<uint32_t *>(b + 3 * arr);
-    int32_t *hist = reinterpret_cast<int32_t *>(b + 4 * arr);
-    double *part = reinterpret_cast<double *>(b + 4 * arr + al((int64_t)n_seg * kDigits * n_tiles * 4));
-    uint32_t *nan_flag = reinterpret_cast<uint32_t *>(
-        reinterpret_cast<char *>(part) + al((int64_t)n_seg * n_tiles * 6 * 8));
-    cudaMemsetAsync(nan_flag, 0, (size_t)n_seg * 4, st);
-    to_keys_kernel<<<2048, 256, 0, st>>>(pred, n_seg, n, keys, vals, nan_flag);
-    cudaError_t e = radix_sort_pairs(keys, vals, keys2, vals2, n_seg, n, hist, st);
+    const RankScratch r = carve_rank(scratch, n_seg, n);
+    cudaError_t e = cudaMemsetAsync(r.nan_flag, 0, (size_t)n_seg * 4, st);
+    if (e != cudaSuccess) return e;
+    e = radix_sort_values(pred, r.keys, r.vals, r.keys2, r.vals2, n_seg, n, r.hist, r.tot,
+                          r.nan_flag, st);
     if (e != cudaSuccess) return e;
     rank_kernel<<<dim3((unsigned)n_tiles, n_seg), kTileThreads, 0, st>>>(
-        keys, vals, n, (int)n_tiles, 1, nullptr, r2y, w, part);
-    spearman_final_kernel<<<(n_seg + 7) / 8, 256, 0, st>>>(part, n_seg, (int)n_tiles, nan_flag, out,
-                                                           out64);
+        r.keys, r.vals, n, (int)n_tiles, 1, nullptr, r2y, w, r.part);
+    spearman_final_kernel<<<(n_seg + 7) / 8, 256, 0, st>>>(r.part, n_seg, (int)n_tiles, r.nan_flag,
+                                                           out, out64);
     return cudaGetLastError();
 }
 

@@ -170,6 +170,67 @@ def test_deep_and_long_programs():
     check_fitness(fit, nodes, off, X, y, None, "mse")
 
 
+def _class_mix(n_feat, seed):
+    """Programs for each evaluator class: the usual set with a compiled stack
+    of at most 8 (class 0), the extended set likewise (class 2) and left
+    spines whose right operands are subtrees, which keep d + 1 values on the
+    stack, over both sets (class 1)."""
+    V, Cn = synth.OP["var"], synth.OP["const"]
+    usual = synth.unpack(*synth.ramped_half_and_half(150, 2, 6, synth.FULL_SET, n_feat, seed=seed))
+    ext = synth.unpack(*synth.ramped_half_and_half(150, 2, 6, synth.EXTENDED_SET, n_feat,
+                                                   seed=seed + 1))
+    deep = []
+    for d in (9, 12, 19):
+        deep.append([(synth.OP["max"], 0, 0.0)] * d + [(V, 1 % n_feat, 0.0)] +
+                    [(synth.OP["tanh"], 0, 0.0), (V, 0, 0.0)] * d)
+        deep.append([(synth.OP["add"], 0, 0.0)] * d + [(V, 1 % n_feat, 0.0)] +
+                    [(synth.OP["mul"], 0, 0.0), (V, 0, 0.0), (Cn, 0, 0.5)] * d)
+        deep.append([(synth.OP["sub"], 0, 0.0)] * d + [(V, 0, 0.0)] +
+                    [(synth.OP["cube"], 0, 0.0), (synth.OP["sin"], 0, 0.0), (V, 1 % n_feat, 0.0)] * d)
+    return [usual, ext, deep]
+
+
+@pytest.mark.parametrize("n_feat", [2, 9])
+@pytest.mark.parametrize("metric", ["rmse", "pearson"])
+def test_fitness_in_every_program_class(n_feat, metric):
+    """One population, interleaved, whose programs fall into all three
+    evaluator classes (7-slot stack without and with the extended functions,
+    19-slot stack): every fitness matches the oracle's, and equals, bit for
+    bit, the fitness of the same programs evaluated one group at a time with
+    the same row chunks (each class reads its own span of the program
+    order)."""
+    groups = _class_mix(n_feat, 300 + n_feat)
+    n = 2 * 4096 + 77
+    rng = np.random.default_rng(n_feat)
+    X = rng.uniform(-3, 3, size=(n_feat, n)).astype(np.float32)
+    y = (X[0] * np.float32(0.75) + np.tanh(X[1 % n_feat])).astype(np.float32)
+    w = _weights(n, 4)
+    progs, where = [], []
+    for g, grp in enumerate(groups):
+        for i, pr in enumerate(grp):
+            progs.append(pr)
+            where.append((g, i))
+    perm = np.random.default_rng(1).permutation(len(progs))
+    progs = [progs[i] for i in perm]
+    where = [where[i] for i in perm]
+    nodes, off = pack(progs)
+    opts = gp.make_opts(chunk_rows=2048)
+    pn, po, dX, dy, dw = put(nodes, off, X, y, w)
+    fit = gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=metric, opts=opts).cpu().numpy()
+    if metric == "pearson":
+        st, _ = check_pearson(fit, nodes, off, X, y, w)
+    else:
+        st, _ = check_fitness(fit, nodes, off, X, y, w, metric)
+    assert st.flagged < 0.3 * st.programs, st
+    for g, grp in enumerate(groups):
+        gn, go = pack(grp)
+        gpn, gpo = gp.nodes_to_device(gn), dev(go.astype(np.int32))
+        alone = gp.gp_evaluate_ex(gpn, gpo, dX, dy, dw, metric=metric, opts=opts).cpu().numpy()
+        mixed = np.array([fit[k] for k in range(len(progs)) if where[k][0] == g])
+        idx = [where[k][1] for k in range(len(progs)) if where[k][0] == g]
+        np.testing.assert_array_equal(mixed.view(np.uint32), alone[idx].view(np.uint32))
+
+
 # --------------------------------------------------------------------------
 # fitness
 # --------------------------------------------------------------------------
