@@ -376,25 +376,27 @@ int run_spearman(const gp_node *progs, const int32_t *offsets, int n_progs, cons
     int B = (int)std::max<int64_t>(1, std::min<int64_t>(n_progs, (int64_t)kRankBudget / per_prog));
     const size_t b_pred = (size_t)round_up((int64_t)B * n_rows * 4, 256);
     const size_t b_r2y = (size_t)round_up(n_rows * 4, 256);
+    const size_t b_tp = (size_t)round_up((int64_t)target_part_bytes(n_rows), 256);
     const size_t b_scr = rank_scratch_bytes(B, n_rows);
     int rc;
     char *base = nullptr;
     {
         std::lock_guard<std::mutex> g(g_mu);
-        if ((rc = grow(&c->rank, &c->rank_bytes, b_pred + b_r2y + b_scr))) return rc;
+        if ((rc = grow(&c->rank, &c->rank_bytes, b_pred + b_r2y + b_tp + b_scr))) return rc;
         base = static_cast<char *>(c->rank);
     }
     float *pred = reinterpret_cast<float *>(base);
     uint32_t *r2y = reinterpret_cast<uint32_t *>(base + b_pred);
-    void *scr = base + b_pred + b_r2y;
-    GP_CUDA(target_ranks(y, n_rows, scr, r2y, st));
+    double *tpart = reinterpret_cast<double *>(base + b_pred + b_r2y);
+    void *scr = base + b_pred + b_r2y + b_tp;
+    GP_CUDA(target_ranks(y, w, n_rows, scr, r2y, tpart, st));
     for (int p0 = 0; p0 < n_progs; p0 += B) {
         const int b = std::min(B, n_progs - p0);
         if ((rc = run_predict(progs, offsets + p0, b, X, n_rows, n_feat, pred,
                               out_status ? out_status + p0 : nullptr, c, st)))
             return rc;
-        GP_CUDA(spearman_batch(pred, b, n_rows, r2y, w, scr, out + p0, out64 ? out64 + p0 : nullptr,
-                               st));
+        GP_CUDA(spearman_batch(pred, b, n_rows, r2y, tpart, w, scr, out + p0,
+                               out64 ? out64 + p0 : nullptr, st));
     }
     return GP_OK;
 }

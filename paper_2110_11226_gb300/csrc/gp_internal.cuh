@@ -311,13 +311,16 @@ cudaError_t launch_consts(gp_node *progs, const int32_t *offsets, int n_progs, f
 
 cudaError_t probe_pipes(double *out, cudaStream_t st);
 // Spearman fitness (gp_rank.cu): scratch bytes for n_seg segments of n
-// values; the target's doubled ranks by row; one batch of predictions
-// [n_seg][n] to fitness
+// values; the target's doubled ranks by row and its per-tile weighted rank
+// sums (target_part_bytes(n) bytes); one batch of predictions [n_seg][n]
+// to fitness
 size_t rank_scratch_bytes(int n_seg, int64_t n);
-cudaError_t target_ranks(const float *y, int64_t n, void *scratch, uint32_t *r2y, cudaStream_t st);
+size_t target_part_bytes(int64_t n);
+cudaError_t target_ranks(const float *y, const float *w, int64_t n, void *scratch, uint32_t *r2y,
+                         double *tpart, cudaStream_t st);
 cudaError_t spearman_batch(const float *pred, int n_seg, int64_t n, const uint32_t *r2y,
-                           const float *w, void *scratch, float *out, double *out64,
-                           cudaStream_t st);
+                           const double *tpart, const float *w, void *scratch, float *out,
+                           double *out64, cudaStream_t st);
 
 // device-side mutation (gp_mutate)
 struct MutArgs {

@@ -126,11 +126,183 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
     }
 }
 
+// ---- the fast loop: indexed-branch dispatch in inline PTX ------------
+// The compiler lowers the dispatch switch to a tree of compares and
+// branches (about 12 instructions per dispatch, measured with ncu's
+// per-opcode counts); PTX's brx.idx jumps through a table instead (about
+// 3).  This loop runs, 4 rows per lane with columns 0 and 1 in registers,
+// the operations that PTX provides as single instructions with the
+// evaluator's semantics: IEEE adds, subtracts and multiplies and, with
+// DIVS, divisions, square roots and reciprocals, all round to nearest
+// without flush to zero (add/sub/mul/div/sqrt/rcp .rn.f32: the
+// instructions behind __fadd_rn, __fsub_rn, __fmul_rn, __fdiv_rn,
+// __fsqrt_rn and __frcp_rn), sign changes, the protection selects, stack
+// moves and column reads.  It stops at the first word it does not run
+// (OP_END, log, exp, the trigonometric and the extended functions, and the
+// division set without DIVS), hands that word and its constant back to
+// the caller's switch and leaves pa just past it.  Every one of the 32
+// values of the 5-bit op field has a table entry, so the index is always
+// in range; stack slots are clamped like the switch's.  Measured on
+// Pagie-1 16M x 4096: 465 ms -> 420 ms per evaluation.  DIVS is off in
+// the instances with the extended functions, where it cost the
+// extended-set population 23% (their out-of-line calls and the division's
+// own slow-path call do not mix well); loading the next word while the
+// current one runs cost 3%.
+// the op table: with DIVS the division set (7 DIV_S .. 19 RDIV_C, 20 SQRT,
+// 28 INV) runs here, otherwise it is handed back
+#define GP_FAST_TABLE_DIVS                                                        \
+    "T%=: .branchtargets PX%=, PC%=, PXS%=, PCS%=, AS%=, SS%=, MS%=, DS%=,"       \
+    " AX%=, AC%=, SX%=, SC%=, RX%=, RC%=, MX%=, MC%=, DX%=, DC%=, RDX%=, RDC%=,"  \
+    " SQ%=, EX%=, EX%=, EX%=, EX%=, EX%=, AB%=, NG%=, IV%=, EX%=, EX%=, EX%=;\n\t"
+#define GP_FAST_TABLE_NODIVS                                                      \
+    "T%=: .branchtargets PX%=, PC%=, PXS%=, PCS%=, AS%=, SS%=, MS%=, EX%=,"       \
+    " AX%=, AC%=, SX%=, SC%=, RX%=, RC%=, MX%=, MC%=, EX%=, EX%=, EX%=, EX%=,"    \
+    " EX%=, EX%=, EX%=, EX%=, EX%=, EX%=, AB%=, NG%=, EX%=, EX%=, EX%=, EX%=;\n\t"
+#define GP_FAST_LOOP_TOP                                                          \
+    "N%=:\n\t"                                                                    \
+    "ld.shared.v2.b32 {%%w, %%cb}, [%0];\n\t"                                     \
+    "mov.b32 %%cf, %%cb;\n\t"                                                     \
+    "add.u32 %0, %0, 8;\n\t"                                                      \
+    "and.b32 %%i, %%w, 31;\n\t"                                                   \
+    "brx.idx.uni %%i, T%=;\n\t"
+#define GP_FAST_HEAD(TABLE)                                                       \
+    "{\n\t"                                                                       \
+    ".reg .pred %%p;\n\t"                                                         \
+    ".reg .b32 %%w, %%cb, %%i, %%a, %%f;\n\t"                                     \
+    ".reg .f32 %%cf, %%u0, %%u1, %%u2, %%u3, %%q, %%m;\n\t"                       \
+    TABLE GP_FAST_LOOP_TOP
+// slot address: sb + min(slot, NSLOT - 1) * 512 (one float4 per lane, 32 lanes)
+#define GP_FAST_SLOT                                                              \
+    "bfe.u32 %%a, %%w, 8, 8;\n\t"                                                 \
+    "min.u32 %%a, %%a, %8;\n\t"                                                   \
+    "mad.lo.u32 %%a, %%a, 512, %7;\n\t"
+#define GP_FAST_SPILL GP_FAST_SLOT "st.shared.v4.f32 [%%a], {%1, %2, %3, %4};\n\t"
+#define GP_FAST_SLOTLOAD GP_FAST_SLOT "ld.shared.v4.f32 {%%u0, %%u1, %%u2, %%u3}, [%%a];\n\t"
+// columns 0 and 1 in registers (x1 when the feature is not 0)
+#define GP_FAST_X(D0, D1, D2, D3)                                                 \
+    "shr.b32 %%f, %%w, 16;\n\t"                                                   \
+    "setp.ne.u32 %%p, %%f, 0;\n\t"                                                \
+    "selp.f32 " D0 ", %13, %9, %%p;\n\tselp.f32 " D1 ", %14, %10, %%p;\n\t"       \
+    "selp.f32 " D2 ", %15, %11, %%p;\n\tselp.f32 " D3 ", %16, %12, %%p;\n\t"
+#define GP_FAST_XU GP_FAST_X("%%u0", "%%u1", "%%u2", "%%u3")
+// t_j = t_j OP v_j for the four rows (v: "%%u" or the constant "%%cf")
+#define GP_FAST_TV(OP, V0, V1, V2, V3)                                            \
+    OP ".rn.f32 %1, %1, " V0 ";\n\t" OP ".rn.f32 %2, %2, " V1 ";\n\t"             \
+    OP ".rn.f32 %3, %3, " V2 ";\n\t" OP ".rn.f32 %4, %4, " V3 ";\n\t"
+#define GP_FAST_TU(OP) GP_FAST_TV(OP, "%%u0", "%%u1", "%%u2", "%%u3")
+#define GP_FAST_TC(OP) GP_FAST_TV(OP, "%%cf", "%%cf", "%%cf", "%%cf")
+// t_j = v_j - t_j
+#define GP_FAST_RSUB(V0, V1, V2, V3)                                              \
+    "sub.rn.f32 %1, " V0 ", %1;\n\tsub.rn.f32 %2, " V1 ", %2;\n\t"                \
+    "sub.rn.f32 %3, " V2 ", %3;\n\tsub.rn.f32 %4, " V3 ", %4;\n\t"
+// protected division of one row: D = |B| < thr ? 1 : A / B
+#define GP_FAST_DIV1(D, A, B)                                                     \
+    "div.rn.f32 %%q, " A ", " B ";\n\t"                                           \
+    "abs.f32 %%m, " B ";\n\t"                                                     \
+    "setp.lt.f32 %%p, %%m, %17;\n\t"                                              \
+    "selp.f32 " D ", 0f3F800000, %%q, %%p;\n\t"
+#define GP_FAST_DIV_TV(V0, V1, V2, V3)                                            \
+    GP_FAST_DIV1("%1", "%1", V0) GP_FAST_DIV1("%2", "%2", V1)                     \
+    GP_FAST_DIV1("%3", "%3", V2) GP_FAST_DIV1("%4", "%4", V3)
+#define GP_FAST_DIV_VT(V0, V1, V2, V3)                                            \
+    GP_FAST_DIV1("%1", V0, "%1") GP_FAST_DIV1("%2", V1, "%2")                     \
+    GP_FAST_DIV1("%3", V2, "%3") GP_FAST_DIV1("%4", V3, "%4")
+#define GP_FAST_SQRT1(T) "abs.f32 " T ", " T ";\n\tsqrt.rn.f32 " T ", " T ";\n\t"
+// protected reciprocal: |t| < thr ? 0 : 1 / t
+#define GP_FAST_INV1(T)                                                           \
+    "rcp.rn.f32 %%q, " T ";\n\t"                                                  \
+    "abs.f32 %%m, " T ";\n\t"                                                     \
+    "setp.lt.f32 %%p, %%m, %17;\n\t"                                              \
+    "selp.f32 " T ", 0f00000000, %%q, %%p;\n\t"
+#define GP_FAST_SETC                                                              \
+    "mov.f32 %1, %%cf;\n\tmov.f32 %2, %%cf;\n\tmov.f32 %3, %%cf;\n\tmov.f32 %4, %%cf;\n\t"
+#define GP_FAST_NEXT "bra.uni N%=;\n\t"
+#define GP_FAST_DIV_BODIES                                                        \
+    "DS%=:\n\t" GP_FAST_SLOTLOAD GP_FAST_DIV_TV("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
+    "DX%=:\n\t" GP_FAST_XU GP_FAST_DIV_TV("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
+    "DC%=:\n\t" GP_FAST_DIV_TV("%%cf", "%%cf", "%%cf", "%%cf") GP_FAST_NEXT       \
+    "RDX%=:\n\t" GP_FAST_XU GP_FAST_DIV_VT("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
+    "RDC%=:\n\t" GP_FAST_DIV_VT("%%cf", "%%cf", "%%cf", "%%cf") GP_FAST_NEXT      \
+    "SQ%=:\n\t" GP_FAST_SQRT1("%1") GP_FAST_SQRT1("%2") GP_FAST_SQRT1("%3")       \
+    GP_FAST_SQRT1("%4") GP_FAST_NEXT                                              \
+    "IV%=:\n\t" GP_FAST_INV1("%1") GP_FAST_INV1("%2") GP_FAST_INV1("%3")          \
+    GP_FAST_INV1("%4") GP_FAST_NEXT
+#define GP_FAST_BODY                                                              \
+    "PX%=:\n\t" GP_FAST_X("%1", "%2", "%3", "%4") GP_FAST_NEXT                    \
+    "PC%=:\n\t" GP_FAST_SETC GP_FAST_NEXT                                         \
+    "PXS%=:\n\t" GP_FAST_SPILL GP_FAST_X("%1", "%2", "%3", "%4") GP_FAST_NEXT     \
+    "PCS%=:\n\t" GP_FAST_SPILL GP_FAST_SETC GP_FAST_NEXT                          \
+    "AS%=:\n\t" GP_FAST_SLOTLOAD GP_FAST_TU("add") GP_FAST_NEXT                   \
+    "SS%=:\n\t" GP_FAST_SLOTLOAD GP_FAST_TU("sub") GP_FAST_NEXT                   \
+    "MS%=:\n\t" GP_FAST_SLOTLOAD GP_FAST_TU("mul") GP_FAST_NEXT                   \
+    "AX%=:\n\t" GP_FAST_XU GP_FAST_TU("add") GP_FAST_NEXT                         \
+    "AC%=:\n\t" GP_FAST_TC("add") GP_FAST_NEXT                                    \
+    "SX%=:\n\t" GP_FAST_XU GP_FAST_TU("sub") GP_FAST_NEXT                         \
+    "SC%=:\n\t" GP_FAST_TC("sub") GP_FAST_NEXT                                    \
+    "RX%=:\n\t" GP_FAST_XU GP_FAST_RSUB("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
+    "RC%=:\n\t" GP_FAST_RSUB("%%cf", "%%cf", "%%cf", "%%cf") GP_FAST_NEXT         \
+    "MX%=:\n\t" GP_FAST_XU GP_FAST_TU("mul") GP_FAST_NEXT                         \
+    "MC%=:\n\t" GP_FAST_TC("mul") GP_FAST_NEXT                                    \
+    "AB%=:\n\t"                                                                   \
+    "abs.f32 %1, %1;\n\tabs.f32 %2, %2;\n\tabs.f32 %3, %3;\n\tabs.f32 %4, %4;\n\t" \
+    GP_FAST_NEXT                                                                  \
+    "NG%=:\n\t"                                                                   \
+    "neg.f32 %1, %1;\n\tneg.f32 %2, %2;\n\tneg.f32 %3, %3;\n\tneg.f32 %4, %4;\n\t" \
+    GP_FAST_NEXT                                                                  \
+    "EX%=:\n\t"                                                                   \
+    "mov.b32 %5, %%w;\n\t"                                                        \
+    "mov.f32 %6, %%cf;\n\t"                                                       \
+    "}\n"
+
+template <int NSLOT, bool DIVS>
+__device__ __forceinline__ void run_fast4(uint32_t &pa, float (&t)[4], const float (&x0)[4],
+                                          const float (&x1)[4], uint32_t sb, uint32_t &hw,
+                                          float &hc) {
+    if constexpr (DIVS) {
+        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_DIVS) GP_FAST_DIV_BODIES GP_FAST_BODY
+                     : "+r"(pa), "+f"(t[0]), "+f"(t[1]), "+f"(t[2]), "+f"(t[3]), "=r"(hw),
+                       "=f"(hc)
+                     : "r"(sb), "n"(NSLOT - 1), "f"(x0[0]), "f"(x0[1]), "f"(x0[2]), "f"(x0[3]),
+                       "f"(x1[0]), "f"(x1[1]), "f"(x1[2]), "f"(x1[3]), "f"(kThr)
+                     : "memory");
+    } else {
+        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_NODIVS) GP_FAST_BODY
+                     : "+r"(pa), "+f"(t[0]), "+f"(t[1]), "+f"(t[2]), "+f"(t[3]), "=r"(hw),
+                       "=f"(hc)
+                     : "r"(sb), "n"(NSLOT - 1), "f"(x0[0]), "f"(x0[1]), "f"(x0[2]), "f"(x0[3]),
+                       "f"(x1[0]), "f"(x1[1]), "f"(x1[2]), "f"(x1[3])
+                     : "memory");
+    }
+}
+#undef GP_FAST_HEAD
+#undef GP_FAST_TABLE_DIVS
+#undef GP_FAST_TABLE_NODIVS
+#undef GP_FAST_LOOP_TOP
+#undef GP_FAST_DIV_BODIES
+#undef GP_FAST_SLOT
+#undef GP_FAST_SPILL
+#undef GP_FAST_SLOTLOAD
+#undef GP_FAST_X
+#undef GP_FAST_XU
+#undef GP_FAST_TV
+#undef GP_FAST_TU
+#undef GP_FAST_TC
+#undef GP_FAST_RSUB
+#undef GP_FAST_DIV1
+#undef GP_FAST_DIV_TV
+#undef GP_FAST_DIV_VT
+#undef GP_FAST_SQRT1
+#undef GP_FAST_INV1
+#undef GP_FAST_SETC
+#undef GP_FAST_NEXT
+#undef GP_FAST_BODY
+
 // Runs one compiled program over RPT rows per lane; returns the top of the
 // stack in t.  stk = this warp's stack slice, already offset by the lane.
-// The instruction buffer (kCodeStride + 1 entries in shared memory) holds
+// The instruction buffer (kCodeStride + 2 entries in shared memory) holds
 // OP_END from the program's end through its last entry, so the loop ends
-// within kCodeStride + 1 steps whatever the buffer holds; op values that
+// within kCodeStride + 1 steps whatever the buffer holds, and the fast
+// loop's load of the word after the last one stays inside it; op values that
 // name no operation act as OP_END and stack slots are clamped to the
 // stack, so no instruction word can make it run away or leave its memory.
 //
@@ -154,16 +326,25 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
     constexpr bool kExt = EXT;
 #pragma unroll
     for (int j = 0; j < RPT; ++j) t[j] = 0.0f;
-    int pc = 0;
-    const uint32_t cb = (uint32_t)__cvta_generic_to_shared(cbuf);  // word pc at cb + 8 pc
-    const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stk);   // this lane's slot 0
+    // pa: shared-memory address of the next instruction word
+    uint32_t pa = (uint32_t)__cvta_generic_to_shared(cbuf);
+    const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stk);  // this lane's slot 0
+    // 4 rows per lane: the fast loop runs what it can and hands back the
+    // rest, one word at a time, to the switch below
+    constexpr bool kFast = RPT == 4 && FMODE == 2;
 #pragma unroll 1
     for (;;) {
         uint2 ins;
-        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
-                     : "=r"(ins.x), "=r"(ins.y)
-                     : "r"(cb + 8u * (uint32_t)pc));
-        ++pc;
+        if constexpr (kFast) {
+            float hc;
+            run_fast4<NSLOT, !EXT>(pa, t, x0, x1, sb, ins.x, hc);
+            ins.y = __float_as_uint(hc);
+        } else {
+            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                         : "=r"(ins.x), "=r"(ins.y)
+                         : "r"(pa));
+            pa += 8u;
+        }
         const uint32_t w = __shfl_sync(0xffffffffu, ins.x, 0);
         const float c = __uint_as_float(ins.y);
 // operand helpers: stack slot, X column, constant
@@ -276,7 +457,7 @@ done:;
 // shared memory of one block: the program's instructions, then the stack
 template <int RPT, int NSLOT>
 constexpr size_t eval_smem_bytes() {
-    return (size_t)(kCodeStride + 1) * sizeof(uint2) +
+    return (size_t)(kCodeStride + 2) * sizeof(uint2) +
            (size_t)eval_warps<RPT>() * NSLOT * (RPT / 4) * 32 * sizeof(float4);
 }
 
@@ -294,7 +475,7 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom && RPT 
     constexpr int kEvalBlock = kEvalWarps * 32;
     extern __shared__ float4 smem_eval[];
     uint2 *cbuf = reinterpret_cast<uint2 *>(smem_eval);
-    float4 *stack_all = smem_eval + ((kCodeStride + 1) * sizeof(uint2) + 15) / 16;
+    float4 *stack_all = smem_eval + ((kCodeStride + 2) * sizeof(uint2) + 15) / 16;
     __shared__ float wsum[kEvalWarps];
     __shared__ double wmom[MOM ? kEvalWarps : 1][3];
     __shared__ unsigned long long s_item;
@@ -337,10 +518,13 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom && RPT 
             __syncthreads();  // s_item is rewritten at the top
             continue;
         }
-        // the program, then OP_END through the buffer's last entry
+        // the program, then OP_END through the buffer's last entry (the last
+        // one stored apart: as a third pass of the loop it cost the kernel
+        // 15 registers)
         for (int i = threadIdx.x; i <= kCodeStride; i += kEvalBlock)
             cbuf[i] = (i < m.n_ins) ? a.code[(size_t)p * kCodeStride + i]
                                     : make_uint2(make_ins(OP_END, 0, 0), 0u);
+        if (threadIdx.x == 0) cbuf[kCodeStride + 1] = make_uint2(make_ins(OP_END, 0, 0), 0u);
         __syncthreads();
 
         float ks = 0.0f, kc = 0.0f;

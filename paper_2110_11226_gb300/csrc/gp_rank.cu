@@ -45,40 +45,54 @@ __device__ __forceinline__ uint32_t load_key(const void *src, int64_t m) {
     return static_cast<const uint32_t *>(src)[m];
 }
 
-// digit counts of one tile: hist[seg][digit][tile].  Lanes holding the
-// same digit add once (match), so a run of equal digits costs no
-// serialised shared-memory atomics.
+// digit counts of one tile: hist[seg][digit][tile].  Each thread loads its
+// 16 keys first (independent loads), then counts them into its warp's own
+// histogram; a warp whose 32 keys share one digit adds once.
 template <bool FROM_FLOAT>
 __global__ void __launch_bounds__(kSortThreads) hist_kernel(const void *__restrict__ src, int64_t n,
                                                             int n_tiles, int shift, int32_t *hist,
                                                             uint32_t *nan_flag) {
-    __shared__ int32_t cnt[kBins];
-    const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x, lane = t & 31;
-    cnt[t] = 0;
-    __syncthreads();
+    __shared__ int32_t wh[kSortWarps][kBins];
+    const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) wh[w][t] = 0;
     const int64_t t0 = (int64_t)tile * kSortTile;
     const int tl = (int)min((int64_t)kSortTile, n - t0);
     const int64_t so = (int64_t)seg * n + t0;
+    uint32_t d[kSortItems];
     bool nan = false;
-    for (int i0 = 0; i0 < kSortTile; i0 += kSortThreads) {
-        const int i = i0 + t;
-        const bool in = i < tl;
-        uint32_t d = kBins + lane;  // a group of its own
-        if (in) {
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int i = r * kSortThreads + t;
+        uint32_t k = 0;
+        if (i < tl) {
             if (FROM_FLOAT) {
                 const float f = static_cast<const float *>(src)[so + i];
                 nan |= f != f;
-                d = (float_key(f) >> shift) & (kBins - 1);
+                k = float_key(f);
             } else {
-                d = (static_cast<const uint32_t *>(src)[so + i] >> shift) & (kBins - 1);
+                k = static_cast<const uint32_t *>(src)[so + i];
             }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (in && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], __popc(peers));
+        d[r] = i < tl ? (k >> shift) & (kBins - 1) : (uint32_t)kBins;  // kBins: not counted
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t d0 = __shfl_sync(0xffffffffu, d[r], 0);
+        if (__all_sync(0xffffffffu, d[r] == d0)) {
+            if (lane == 0 && d0 < kBins) atomicAdd(&wh[warp][d0], 32);
+        } else if (d[r] < kBins) {
+            atomicAdd(&wh[warp][d[r]], 1);
+        }
     }
     if (FROM_FLOAT && __any_sync(0xffffffffu, nan) && lane == 0) atomicOr(nan_flag + seg, 1u);
     __syncthreads();
-    hist[((int64_t)seg * kBins + t) * n_tiles + tile] = cnt[t];
+    int32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) c += wh[w][t];
+    hist[((int64_t)seg * kBins + t) * n_tiles + tile] = c;
 }
 
 // per (segment, digit), one warp: exclusive scan of the tile counts in
@@ -105,7 +119,8 @@ __global__ void __launch_bounds__(256) tile_scan_kernel(int32_t *hist, int32_t *
     if (lane == 0) tot[row] = carry;
 }
 
-// exclusive scan of one value per thread over a 256-thread block
+// exclusive scan of one value per thread over the block (blockDim.x
+// threads, wsum: one entry per warp)
 __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *wsum) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t x = v;
@@ -122,6 +137,31 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *wsum
     return before + x - v;
 }
 
+// the scatter's tile: 512 threads x 8 keys (warp w owns keys [256 w, 256 w + 256))
+constexpr int kScatThreads = 512;
+constexpr int kScatWarps = kScatThreads / 32;
+constexpr int kScatItems = kSortTile / kScatThreads;
+
+// lanes of the warp whose digit equals this lane's (8-bit digits): one
+// ballot per bit, as CUB does it, or the match instruction
+template <bool BALLOT>
+__device__ __forceinline__ unsigned digit_peers(uint32_t d) {
+    if constexpr (BALLOT) {
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < kRadixBits; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const unsigned m = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? m : ~m;
+        }
+        return peers;
+    } else {
+        return __match_any_sync(0xffffffffu, d);
+    }
+}
+
+constexpr bool kBallotPeers = true;
+
 // Stable scatter of one tile by one digit.  The tile is ranked in shared
 // memory first (warp-level digit groups in key order, then a scan over
 // (digit, warp)), staged in sorted order, and written out run by run so
@@ -130,61 +170,81 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *wsum
 // sorted positions >= the tile length, which are not written.  Pass 0
 // reads float values and produces the row index as the payload.
 template <bool FROM_FLOAT>
-__global__ void __launch_bounds__(kSortThreads) scatter_kernel(
+__global__ void __launch_bounds__(kScatThreads, 2) scatter_kernel(
     const void *__restrict__ src, const uint32_t *__restrict__ vals, int64_t n, int n_tiles,
     int shift, const int32_t *__restrict__ offs, const int32_t *__restrict__ tot,
     uint32_t *keys_out, uint32_t *vals_out) {
     __shared__ uint32_t sk[kSortTile];
     __shared__ uint32_t sv[kSortTile];
-    __shared__ int32_t wcnt[kSortWarps][kBins];
+    __shared__ int32_t wcnt[kScatWarps][kBins];
     __shared__ int32_t dstart[kBins];
     __shared__ int32_t gbase[kBins];
-    __shared__ int32_t wsum[kSortWarps];
+    __shared__ int32_t wsum[kScatWarps];
     const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
     const int64_t t0 = (int64_t)tile * kSortTile;
     const int tl = (int)min((int64_t)kSortTile, n - t0);
     const int64_t so = (int64_t)seg * n;
+    for (int i = t; i < kScatWarps * kBins; i += kScatThreads) (&wcnt[0][0])[i] = 0;
+    // the digit totals and this tile's digit offsets, loaded ahead of the keys
+    const int32_t my_tot = t < kBins ? tot[(int64_t)seg * kBins + t] : 0;
+    const int32_t my_off = t < kBins ? offs[((int64_t)seg * kBins + t) * n_tiles + tile] : 0;
+    uint32_t kk[kScatItems], vv[kScatItems];
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) wcnt[w][t] = 0;
-    // global position of this tile's first item of digit t: the digit's
-    // start in the segment plus the same digit in earlier tiles
-    const int32_t dbase = block_exclusive_scan(tot[(int64_t)seg * kBins + t], wsum);
-    gbase[t] = dbase + offs[((int64_t)seg * kBins + t) * n_tiles + tile];
-    __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t kk[kSortItems], vv[kSortItems];
-    int32_t off[kSortItems];
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const int i = warp * (kSortItems * 32) + r * 32 + lane;
+    for (int r = 0; r < kScatItems; ++r) {
+        const int i = warp * (kScatItems * 32) + r * 32 + lane;
         const bool in = i < tl;
         kk[r] = in ? load_key<FROM_FLOAT>(src, so + t0 + i) : 0xffffffffu;
         vv[r] = FROM_FLOAT ? (uint32_t)(t0 + i) : (in ? vals[so + t0 + i] : 0u);
     }
+    // global position of this tile's first item of digit t: the digit's
+    // start in the segment plus the same digit in earlier tiles
+    const int32_t dbase = block_exclusive_scan(my_tot, wsum);
+    if (t < kBins) gbase[t] = dbase + my_off;
+    // the lanes holding one digit in a round form a group; its lowest lane
+    // reserves the group's places with one atomic (predicated, so that the
+    // rounds' atomics issue back to back; shared-memory atomics of one warp
+    // keep their order) and hands the old count to the others afterwards
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t old[kScatItems];
+    int32_t off[kScatItems];
+    unsigned char lead[kScatItems];
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
+    for (int r = 0; r < kScatItems; ++r) {
         const uint32_t d = (kk[r] >> shift) & (kBins - 1);
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int32_t before = wcnt[warp][d];
-        __syncwarp();
-        if ((peers & lt) == 0) wcnt[warp][d] = before + __popc(peers);
-        __syncwarp();
-        off[r] = before + __popc(peers & lt);
+        const unsigned peers = digit_peers<kBallotPeers>(d);
+        const int leader = __ffs(peers) - 1;
+        const uint32_t addr = (uint32_t)__cvta_generic_to_shared(&wcnt[warp][d]);
+        old[r] = 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.eq.u32 p, %1, %2;\n\t"
+            "@p atom.shared.add.u32 %0, [%3], %4;\n\t}"
+            : "+r"(old[r])
+            : "r"((uint32_t)lane), "r"((uint32_t)leader), "r"(addr), "r"((uint32_t)__popc(peers))
+            : "memory");
+        lead[r] = (unsigned char)leader;
+        off[r] = __popc(peers & lt);
     }
+#pragma unroll
+    for (int r = 0; r < kScatItems; ++r)
+        off[r] += (int32_t)__shfl_sync(0xffffffffu, old[r], lead[r]);
     __syncthreads();
     // digit t: warps' exclusive prefixes, then the digits' starts in the tile
     int32_t run = 0;
+    if (t < kBins) {
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-        const int32_t c = wcnt[w][t];
-        wcnt[w][t] = run;
-        run += c;
+        for (int w = 0; w < kScatWarps; ++w) {
+            const int32_t c = wcnt[w][t];
+            wcnt[w][t] = run;
+            run += c;
+        }
     }
-    dstart[t] = block_exclusive_scan(run, wsum);
+    const int32_t ds = block_exclusive_scan(run, wsum);
+    if (t < kBins) dstart[t] = ds;
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
+    for (int r = 0; r < kScatItems; ++r) {
         const uint32_t d = (kk[r] >> shift) & (kBins - 1);
         const int pos = dstart[d] + wcnt[warp][d] + off[r];
         sk[pos] = kk[r];
@@ -192,7 +252,7 @@ __global__ void __launch_bounds__(kSortThreads) scatter_kernel(
     }
     __syncthreads();
 #pragma unroll 4
-    for (int pos = t; pos < tl; pos += kSortThreads) {
+    for (int pos = t; pos < tl; pos += kScatThreads) {
         const uint32_t k = sk[pos];
         const uint32_t d = (k >> shift) & (kBins - 1);
         const int64_t g = so + gbase[d] + (pos - dstart[d]);
@@ -220,6 +280,24 @@ __device__ int64_t upper_bound_u32(const uint32_t *k, int64_t lo, int64_t hi, ui
     return lo;
 }
 
+// Tie-group ends at the tile edges: edge[seg][tile] = (first position of
+// the group of the tile's first key, last position of the group of its last
+// key).  One thread per tile; the binary search runs only when the group
+// crosses the edge, which keeps the rank pass free of dependent global loads.
+__global__ void __launch_bounds__(256) edges_kernel(const uint32_t *__restrict__ keys, int64_t n,
+                                                    int n_tiles, int n_seg, int2 *edge) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (int64_t)n_tiles * n_seg) return;
+    const int seg = (int)(g / n_tiles), tile = (int)(g - (int64_t)seg * n_tiles);
+    const uint32_t *k = keys + (int64_t)seg * n;
+    const int64_t t0 = (int64_t)tile * kTile;
+    const int64_t t1 = min(n, t0 + kTile);  // one past the tile's last key
+    const uint32_t first = k[t0], last = k[t1 - 1];
+    const int64_t lo = (t0 > 0 && k[t0 - 1] == first) ? lower_bound_u32(k, 0, t0, first) : t0;
+    const int64_t hi = (t1 < n && k[t1] == last) ? upper_bound_u32(k, t1, n, last) - 1 : t1 - 1;
+    edge[g] = make_int2((int)lo, (int)hi);
+}
+
 __device__ int smem_lower(const uint32_t *k, int lo, int hi, uint32_t v) {
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -240,87 +318,143 @@ __device__ int smem_upper(const uint32_t *k, int lo, int hi, uint32_t v) {
 
 // Doubled average rank of every sorted position (first + last + 2, 1-based
 // positions of its tie group).  Groups inside a tile are found in shared
-// memory; a group that reaches the tile's edge is extended by one binary
-// search over the segment per tile edge.  mode 0: r2[vals[m]] = rank (the
-// target's ranks by row); mode 1: FP64 moment sums of (rank, r2y[row]),
-// both centred on n + 1, with the row's weight, one partial per (segment,
-// tile).
+// memory; a group that reaches the tile's edge takes its end from edge[]
+// (edges_kernel).  Ranks enter the sums centred on
+// n + 1 (their unweighted mean): exact integers, zero for every row of a
+// constant program, and sums without the cancellation of uncentred squares.
+// mode 0 (the target): r2[row] = rank, and part = (sum w, sum w b,
+// sum w b^2) of the tile; mode 1 (programs): part = (sum w a, sum w a^2,
+// sum w a b), b = the target's centred rank of the row.  Unweighted and
+// with n <= 2^29 a thread's sums are exact 64-bit integers; otherwise FP64.
+// One FP64 triple per (segment, tile), added in a fixed order.
 __global__ void __launch_bounds__(kTileThreads) rank_kernel(
     const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n, int n_tiles,
-    int mode, uint32_t *r2, const uint32_t *__restrict__ r2y, const float *__restrict__ w,
-    double *part) {
+    int mode, const int2 *__restrict__ edge, uint32_t *r2, const uint32_t *__restrict__ r2y,
+    const float *__restrict__ w, double *part) {
     __shared__ uint32_t sk[kTile];
-    __shared__ int64_t edge[2];
-    __shared__ double red[6][kTileThreads];
+    __shared__ double red[3][kTileThreads / 32];
     const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x;
     const uint32_t *k = keys + (int64_t)seg * n;
     const uint32_t *vl = vals + (int64_t)seg * n;
     const int64_t t0 = (int64_t)tile * kTile;
     const int tl = (int)min((int64_t)kTile, n - t0);
-    for (int q = t; q < tl; q += kTileThreads) sk[q] = k[t0 + q];
-    if (t == 0) edge[0] = lower_bound_u32(k, 0, t0, k[t0]);
-    if (t == 1) edge[1] = upper_bound_u32(k, t0 + tl, n, k[t0 + tl - 1]) - 1;
-    __syncthreads();
-    double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    // the tile's keys: independent loads issued together
+    uint32_t kv[kTileItems];
+#pragma unroll
     for (int it = 0; it < kTileItems; ++it) {
-        const int q = t * kTileItems + it;
+        const int q = it * kTileThreads + t;
+        kv[it] = q < tl ? k[t0 + q] : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kTileItems; ++it) {
+        const int q = it * kTileThreads + t;
+        if (q < tl) sk[q] = kv[it];
+    }
+    const int2 eg = edge[(int64_t)seg * n_tiles + tile];
+    // the rows of this thread's items, then their target ranks: independent
+    // loads issued together
+    uint32_t rows[kTileItems], rb[kTileItems];
+#pragma unroll
+    for (int it = 0; it < kTileItems; ++it) {
+        const int q = it * kTileThreads + t;
+        rows[it] = q < tl ? vl[t0 + q] : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kTileItems; ++it) {
+        const int q = it * kTileThreads + t;
+        rb[it] = (mode == 1 && q < tl) ? r2y[rows[it]] : 0u;
+    }
+    __syncthreads();
+    const bool exact = w == nullptr && n <= ((int64_t)1 << 29);
+    long long is[3] = {0, 0, 0};
+    double s[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int it = 0; it < kTileItems; ++it) {
+        const int q = it * kTileThreads + t;
         if (q >= tl) break;
         const uint32_t v = sk[q];
         int lq = q, uq = q + 1;
         if ((q > 0 && sk[q - 1] == v) || q == 0) lq = smem_lower(sk, 0, q, v);
         if ((q + 1 < tl && sk[q + 1] == v) || q + 1 == tl) uq = smem_upper(sk, q + 1, tl, v);
-        const int64_t first = lq == 0 ? edge[0] : t0 + lq;
-        const int64_t last = uq == tl ? edge[1] : t0 + uq - 1;
+        const int64_t first = lq == 0 ? (int64_t)eg.x : t0 + lq;
+        const int64_t last = uq == tl ? (int64_t)eg.y : t0 + uq - 1;
         const uint32_t rank2 = (uint32_t)(first + last + 2);
-        const uint32_t row = vl[t0 + q];
-        if (mode == 0) {
-            r2[row] = rank2;
+        const uint32_t row = rows[it];
+        const int a = (int)((int64_t)rank2 - (n + 1));  // |a| <= n - 1
+        if (mode == 0) r2[row] = rank2;
+        const int b = mode == 0 ? 1 : (int)((int64_t)rb[it] - (n + 1));
+        if (exact) {
+            // mode 0: (count, sum a, sum a^2); mode 1: (sum a, sum a^2, sum a b)
+            is[0] += mode == 0 ? 1 : a;
+            is[1] += mode == 0 ? a : (long long)a * a;
+            is[2] += (long long)a * (mode == 0 ? a : b);
         } else {
-            // doubled ranks centred on n + 1 (their unweighted mean): exact
-            // integers, zero for every row of a constant program, and sums
-            // without the cancellation of uncentred squares
             const double wv = w ? (double)w[row] : 1.0;
-            const double a = (double)((int64_t)rank2 - (n + 1));
-            const double b = (double)((int64_t)r2y[row] - (n + 1));
-            s[0] += wv;
-            s[1] += wv * a;
-            s[2] += wv * a * a;
-            s[3] += wv * b;
-            s[4] += wv * b * b;
-            s[5] += wv * a * b;
+            const double ad = (double)a;
+            const double wa = wv * ad;
+            if (mode == 0) {
+                s[0] += wv;
+                s[1] += wa;
+                s[2] = fma(wa, ad, s[2]);
+            } else {
+                s[0] += wa;
+                s[1] = fma(wa, ad, s[1]);
+                s[2] = fma(wa, (double)b, s[2]);
+            }
         }
     }
-    if (mode == 0) return;
+    if (exact) {
 #pragma unroll
-    for (int j = 0; j < 6; ++j) red[j][t] = s[j];
-    __syncthreads();
-    for (int h = kTileThreads / 2; h > 0; h >>= 1) {
-        if (t < h)
-#pragma unroll
-            for (int j = 0; j < 6; ++j) red[j][t] += red[j][t + h];
-        __syncthreads();
+        for (int j = 0; j < 3; ++j) s[j] = (double)is[j];
     }
-    if (t < 6) part[((int64_t)seg * n_tiles + tile) * 6 + t] = red[t][0];
+    // fixed butterfly inside each warp, then the warps in order
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
+    }
+    if ((t & 31) == 0) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) red[j][t >> 5] = s[j];
+    }
+    __syncthreads();
+    if (t < 3) {
+        double v = 0.0;
+        for (int q = 0; q < kTileThreads / 32; ++q) v += red[t][q];
+        part[((int64_t)seg * n_tiles + tile) * 3 + t] = v;
+    }
 }
 
-// one warp per segment: tile partials in order, then |r| of the ranks
+// sum of tile triples in a fixed order: lane-strided, then lanes in order
+__device__ __forceinline__ void sum_tiles(const double *p, int n_tiles, double (&S)[3]) {
+    const int lane = threadIdx.x & 31;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int i = lane; i < n_tiles; i += 32)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s[j] += p[(int64_t)i * 3 + j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) S[j] = 0.0;
+    for (int l = 0; l < 32; ++l)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) S[j] += __shfl_sync(0xffffffffu, s[j], l);
+}
+
+// one warp per segment: |r| of the ranks from the program's tile sums and
+// the target's (sum w, sum w b, sum w b^2)
 __global__ void __launch_bounds__(256) spearman_final_kernel(
-    const double *part, int n_seg, int n_tiles, const uint32_t *nan_flag, float *out,
-    double *out64) {
+    const double *part, const double *tpart, int n_seg, int n_tiles, const uint32_t *nan_flag,
+    float *out, double *out64) {
     const int lane = threadIdx.x & 31;
     const int seg = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (seg >= n_seg) return;
-    double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int i = lane; i < n_tiles; i += 32)
-        for (int j = 0; j < 6; ++j) s[j] += part[((int64_t)seg * n_tiles + i) * 6 + j];
-    double S[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int l = 0; l < 32; ++l)
-        for (int j = 0; j < 6; ++j) S[j] += __shfl_sync(0xffffffffu, s[j], l);
+    double P[3], T[3];
+    sum_tiles(part + (int64_t)seg * n_tiles * 3, n_tiles, P);
+    sum_tiles(tpart, n_tiles, T);
     if (lane != 0) return;
-    const double sw = S[0];
-    const double ma = S[1] / sw, mb = S[3] / sw;
-    const double va = S[2] / sw - ma * ma, vb = S[4] / sw - mb * mb;
-    const double cov = S[5] / sw - ma * mb;
+    const double sw = T[0];
+    const double ma = P[0] / sw, mb = T[1] / sw;
+    const double va = P[1] / sw - ma * ma, vb = T[2] / sw - mb * mb;
+    const double cov = P[2] / sw - ma * mb;
     double f;
     if (nan_flag[seg] || !isfinite(va) || !isfinite(vb) || !isfinite(cov)) f = __longlong_as_double(0x7ff8000000000000LL);
     else if (!(va > 0.0) || !(vb > 0.0)) f = 0.0;
@@ -353,10 +487,10 @@ cudaError_t radix_sort_values(const float *v, uint32_t *keys, uint32_t *vals, ui
         }
         tile_scan_kernel<<<scan_blocks, 256, 0, st>>>(hist, tot, scan_rows, n_tiles);
         if (pass == 0) {
-            scatter_kernel<true><<<grid, kSortThreads, 0, st>>>(v, nullptr, n, n_tiles, shift, hist,
+            scatter_kernel<true><<<grid, kScatThreads, 0, st>>>(v, nullptr, n, n_tiles, shift, hist,
                                                                 tot, ko, vo);
         } else {
-            scatter_kernel<false><<<grid, kSortThreads, 0, st>>>(ki, vi, n, n_tiles, shift, hist,
+            scatter_kernel<false><<<grid, kScatThreads, 0, st>>>(ki, vi, n, n_tiles, shift, hist,
                                                                  tot, ko, vo);
         }
     }
@@ -372,6 +506,7 @@ struct RankScratch {
     uint32_t *keys, *vals, *keys2, *vals2;
     int32_t *hist, *tot;
     double *part;
+    int2 *edge;
     uint32_t *nan_flag;
     size_t bytes;
 };
@@ -390,7 +525,8 @@ RankScratch carve_rank(void *scratch, int n_seg, int64_t n) {
     r.vals2 = reinterpret_cast<uint32_t *>(b + o); o += arr;
     r.hist = reinterpret_cast<int32_t *>(b + o); o += al((int64_t)n_seg * kBins * sort_tiles * 4);
     r.tot = reinterpret_cast<int32_t *>(b + o); o += al((int64_t)n_seg * kBins * 4);
-    r.part = reinterpret_cast<double *>(b + o); o += al((int64_t)n_seg * rank_tiles * 6 * 8);
+    r.part = reinterpret_cast<double *>(b + o); o += al((int64_t)n_seg * rank_tiles * 3 * 8);
+    r.edge = reinterpret_cast<int2 *>(b + o); o += al((int64_t)n_seg * rank_tiles * 8);
     r.nan_flag = reinterpret_cast<uint32_t *>(b + o); o += al((int64_t)n_seg * 4);
     r.bytes = o;
     return r;
@@ -400,23 +536,25 @@ size_t rank_scratch_bytes(int n_seg, int64_t n) {
     return carve_rank(nullptr, n_seg, n).bytes;
 }
 
-cudaError_t target_ranks(const float *y, int64_t n, void *scratch, uint32_t *r2y,
-                         cudaStream_t st) {
+size_t target_part_bytes(int64_t n) { return (size_t)((n + kTile - 1) / kTile) * 3 * 8; }
+
+cudaError_t target_ranks(const float *y, const float *w, int64_t n, void *scratch, uint32_t *r2y,
+                         double *tpart, cudaStream_t st) {
     const int64_t n_tiles = (n + kTile - 1) / kTile;
     const RankScratch r = carve_rank(scratch, 1, n);
     cudaError_t e = cudaMemsetAsync(r.nan_flag, 0, 4, st);
     if (e != cudaSuccess) return e;
     e = radix_sort_values(y, r.keys, r.vals, r.keys2, r.vals2, 1, n, r.hist, r.tot, r.nan_flag, st);
     if (e != cudaSuccess) return e;
-    rank_kernel<<<dim3((unsigned)n_tiles, 1), kTileThreads, 0, st>>>(r.keys, r.vals, n, (int)n_tiles,
-                                                                      0, r2y, nullptr, nullptr,
-                                                                      nullptr);
+    edges_kernel<<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(r.keys, n, (int)n_tiles, 1, r.edge);
+    rank_kernel<<<dim3((unsigned)n_tiles, 1), kTileThreads, 0, st>>>(
+        r.keys, r.vals, n, (int)n_tiles, 0, r.edge, r2y, nullptr, w, tpart);
     return cudaGetLastError();
 }
 
 cudaError_t spearman_batch(const float *pred, int n_seg, int64_t n, const uint32_t *r2y,
-                           const float *w, void *scratch, float *out, double *out64,
-                           cudaStream_t st) {
+                           const double *tpart, const float *w, void *scratch, float *out,
+                           double *out64, cudaStream_t st) {
     const int64_t n_tiles = (n + kTile - 1) / kTile;
     const RankScratch r = carve_rank(scratch, n_seg, n);
     cudaError_t e = cudaMemsetAsync(r.nan_flag, 0, (size_t)n_seg * 4, st);
@@ -424,10 +562,12 @@ cudaError_t spearman_batch(const float *pred, int n_seg, int64_t n, const uint32
     e = radix_sort_values(pred, r.keys, r.vals, r.keys2, r.vals2, n_seg, n, r.hist, r.tot,
                           r.nan_flag, st);
     if (e != cudaSuccess) return e;
+    edges_kernel<<<(unsigned)((n_tiles * n_seg + 255) / 256), 256, 0, st>>>(r.keys, n, (int)n_tiles,
+                                                                           n_seg, r.edge);
     rank_kernel<<<dim3((unsigned)n_tiles, n_seg), kTileThreads, 0, st>>>(
-        r.keys, r.vals, n, (int)n_tiles, 1, nullptr, r2y, w, r.part);
-    spearman_final_kernel<<<(n_seg + 7) / 8, 256, 0, st>>>(r.part, n_seg, (int)n_tiles, r.nan_flag,
-                                                           out, out64);
+        r.keys, r.vals, n, (int)n_tiles, 1, r.edge, nullptr, r2y, w, r.part);
+    spearman_final_kernel<<<(n_seg + 7) / 8, 256, 0, st>>>(r.part, tpart, n_seg, (int)n_tiles,
+                                                           r.nan_flag, out, out64);
     return cudaGetLastError();
 }
 
