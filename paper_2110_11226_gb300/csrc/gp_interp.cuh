@@ -137,23 +137,25 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
 // without flush to zero (add/sub/mul/div/sqrt/rcp .rn.f32: the
 // instructions behind __fadd_rn, __fsub_rn, __fmul_rn, __fdiv_rn,
 // __fsqrt_rn and __frcp_rn), sign changes, the protection selects, stack
-// moves and column reads.  It stops at the first word it does not run
-// (OP_END, log, exp, the trigonometric and the extended functions, and the
-// division set without DIVS), hands that word and its constant back to
-// the caller's switch and leaves pa just past it.  Every one of the 32
-// values of the 5-bit op field has a table entry, so the index is always
-// in range; stack slots are clamped like the switch's.  Measured on
-// Pagie-1 16M x 4096: 465 ms -> 420 ms per evaluation.  DIVS is off in
-// the instances with the extended functions, where it cost the
-// extended-set population 23% (their out-of-line calls and the division's
-// own slow-path call do not mix well); loading the next word while the
-// current one runs cost 3%.
+// moves and column reads; with DIVS also sin, cos and tan (the steps and
+// constants of trig_rows, transcribed).  It stops at the first word it
+// does not run (OP_END, log, exp, the extended functions, trigonometric
+// arguments outside the fast path, and the division set and trigonometry
+// without DIVS), hands that word and its constant back to the caller's
+// switch and leaves pa just past it.  Every one of the 32 values of the
+// 5-bit op field has a table entry, so the index is always in range; stack
+// slots are clamped like the switch's.  Measured on Pagie-1 16M x 4096:
+// 465 ms -> 420 ms per evaluation, 390 ms with the trigonometry.  DIVS is
+// off in the instances with the extended functions, where the division
+// set cost the extended-set population 23% (their out-of-line calls and
+// the division's own slow-path call do not mix well); loading the next
+// word while the current one runs cost 3%.
 // the op table: with DIVS the division set (7 DIV_S .. 19 RDIV_C, 20 SQRT,
 // 28 INV) runs here, otherwise it is handed back
 #define GP_FAST_TABLE_DIVS                                                        \
     "T%=: .branchtargets PX%=, PC%=, PXS%=, PCS%=, AS%=, SS%=, MS%=, DS%=,"       \
     " AX%=, AC%=, SX%=, SC%=, RX%=, RC%=, MX%=, MC%=, DX%=, DC%=, RDX%=, RDC%=,"  \
-    " SQ%=, EX%=, EX%=, EX%=, EX%=, EX%=, AB%=, NG%=, IV%=, EX%=, EX%=, EX%=;\n\t"
+    " SQ%=, EX%=, EX%=, TSC%=, TSC%=, TTN%=, AB%=, NG%=, IV%=, EX%=, EX%=, EX%=;\n\t"
 #define GP_FAST_TABLE_NODIVS                                                      \
     "T%=: .branchtargets PX%=, PC%=, PXS%=, PCS%=, AS%=, SS%=, MS%=, EX%=,"       \
     " AX%=, AC%=, SX%=, SC%=, RX%=, RC%=, MX%=, MC%=, EX%=, EX%=, EX%=, EX%=,"    \
@@ -217,6 +219,77 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
 #define GP_FAST_SETC                                                              \
     "mov.f32 %1, %%cf;\n\tmov.f32 %2, %%cf;\n\tmov.f32 %3, %%cf;\n\tmov.f32 %4, %%cf;\n\t"
 #define GP_FAST_NEXT "bra.uni N%=;\n\t"
+// sin, cos and tan of the four rows with the steps and constants of
+// trig_rows (gp_math.cuh): Cody-Waite reduction by pi/2 in three FMAs,
+// both polynomials, then the quadrant select or the quotient, so the
+// results are the same bits.  A warp with any row outside the fast path
+// (|x| >= 65536, inf, NaN) hands the word back before touching t, and the
+// caller's switch runs trig_rows with its slow path.
+#define GP_FAST_TRIG_REGS                                                         \
+    ".reg .pred %%ps;\n\t"                                                        \
+    ".reg .b32 %%qq, %%qb, %%kd;\n\t"                                             \
+    ".reg .f32 %%jm, %%jj, %%rr, %%ss, %%sn, %%cn, %%sr;\n\t"
+#define GP_FAST_TRIG_CHECK1(T)                                                    \
+    "abs.f32 %%m, " T ";\n\t"                                                     \
+    "setp.geu.f32 %%p, %%m, 0f47800000;\n\t"                                      \
+    "or.pred %%ps, %%ps, %%p;\n\t"
+#define GP_FAST_TRIG_CHECK                                                        \
+    "setp.ne.u32 %%ps, 0, 0;\n\t"                                                 \
+    GP_FAST_TRIG_CHECK1("%1") GP_FAST_TRIG_CHECK1("%2")                           \
+    GP_FAST_TRIG_CHECK1("%3") GP_FAST_TRIG_CHECK1("%4")                           \
+    "vote.sync.any.pred %%ps, %%ps, 0xffffffff;\n\t"                              \
+    "@%%ps bra EX%=;\n\t"
+// reduction and both polynomials of row T: %%sn = sin r, %%cn = cos r,
+// %%qq = the quadrant word (low bits of j)
+#define GP_FAST_TRIG_POLY(T)                                                      \
+    "fma.rn.f32 %%jm, " T ", 0f3F22F983, 0f4B400000;\n\t"                         \
+    "sub.rn.f32 %%jj, %%jm, 0f4B400000;\n\t"                                      \
+    "neg.f32 %%jj, %%jj;\n\t"                                                     \
+    "fma.rn.f32 %%rr, %%jj, 0f3FC90FDB, " T ";\n\t"                               \
+    "fma.rn.f32 %%rr, %%jj, 0fB33BBD2E, %%rr;\n\t"                                \
+    "fma.rn.f32 %%rr, %%jj, 0fA6F72CED, %%rr;\n\t"                                \
+    "mul.rn.f32 %%ss, %%rr, %%rr;\n\t"                                            \
+    "fma.rn.f32 %%sn, 0f363668F9, %%ss, 0fB95007C0;\n\t"                          \
+    "fma.rn.f32 %%sn, %%sn, %%ss, 0f3C088884;\n\t"                                \
+    "fma.rn.f32 %%sn, %%sn, %%ss, 0fBE2AAAAB;\n\t"                                \
+    "mul.rn.f32 %%sr, %%ss, %%rr;\n\t"                                            \
+    "fma.rn.f32 %%sn, %%sn, %%sr, %%rr;\n\t"                                      \
+    "fma.rn.f32 %%cn, 0fB4920F4E, %%ss, 0f37D0086F;\n\t"                          \
+    "fma.rn.f32 %%cn, %%cn, %%ss, 0fBAB60B5C;\n\t"                                \
+    "fma.rn.f32 %%cn, %%cn, %%ss, 0f3D2AAAAB;\n\t"                                \
+    "fma.rn.f32 %%cn, %%cn, %%ss, 0fBF000000;\n\t"                                \
+    "fma.rn.f32 %%cn, %%cn, %%ss, 0f3F800000;\n\t"                                \
+    "mov.b32 %%qq, %%jm;\n\t"
+// sin (kind 0) or cos (kind 1, in %%kd): a = ((q + kind) & 1) ? cos : sin,
+// negated when (q + kind) & 2
+#define GP_FAST_SINCOS1(T)                                                        \
+    GP_FAST_TRIG_POLY(T)                                                          \
+    "add.u32 %%qq, %%qq, %%kd;\n\t"                                               \
+    "and.b32 %%qb, %%qq, 1;\n\t"                                                  \
+    "setp.ne.u32 %%p, %%qb, 0;\n\t"                                               \
+    "selp.f32 %%sn, %%cn, %%sn, %%p;\n\t"                                         \
+    "and.b32 %%qb, %%qq, 2;\n\t"                                                  \
+    "setp.ne.u32 %%p, %%qb, 0;\n\t"                                               \
+    "neg.f32 %%cn, %%sn;\n\t"                                                     \
+    "selp.f32 " T ", %%cn, %%sn, %%p;\n\t"
+// tan: (q & 1) ? -(cos / sin) : sin / cos
+#define GP_FAST_TAN1(T)                                                           \
+    GP_FAST_TRIG_POLY(T)                                                          \
+    "and.b32 %%qb, %%qq, 1;\n\t"                                                  \
+    "setp.ne.u32 %%p, %%qb, 0;\n\t"                                               \
+    "selp.f32 %%q, %%cn, %%sn, %%p;\n\t"                                          \
+    "selp.f32 %%m, %%sn, %%cn, %%p;\n\t"                                          \
+    "div.rn.f32 %%q, %%q, %%m;\n\t"                                               \
+    "neg.f32 %%m, %%q;\n\t"                                                       \
+    "selp.f32 " T ", %%m, %%q, %%p;\n\t"
+#define GP_FAST_TRIG_BODIES                                                       \
+    "TSC%=:\n\t" GP_FAST_TRIG_CHECK                                               \
+    "sub.u32 %%kd, %%i, 23;\n\t"                                                  \
+    GP_FAST_SINCOS1("%1") GP_FAST_SINCOS1("%2") GP_FAST_SINCOS1("%3")             \
+    GP_FAST_SINCOS1("%4") GP_FAST_NEXT                                            \
+    "TTN%=:\n\t" GP_FAST_TRIG_CHECK                                               \
+    GP_FAST_TAN1("%1") GP_FAST_TAN1("%2") GP_FAST_TAN1("%3") GP_FAST_TAN1("%4")   \
+    GP_FAST_NEXT
 #define GP_FAST_DIV_BODIES                                                        \
     "DS%=:\n\t" GP_FAST_SLOTLOAD GP_FAST_DIV_TV("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
     "DX%=:\n\t" GP_FAST_XU GP_FAST_DIV_TV("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
@@ -259,7 +332,8 @@ __device__ __forceinline__ void run_fast4(uint32_t &pa, float (&t)[4], const flo
                                           const float (&x1)[4], uint32_t sb, uint32_t &hw,
                                           float &hc) {
     if constexpr (DIVS) {
-        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_DIVS) GP_FAST_DIV_BODIES GP_FAST_BODY
+        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_DIVS) GP_FAST_TRIG_REGS GP_FAST_DIV_BODIES
+                     GP_FAST_TRIG_BODIES GP_FAST_BODY
                      : "+r"(pa), "+f"(t[0]), "+f"(t[1]), "+f"(t[2]), "+f"(t[3]), "=r"(hw),
                        "=f"(hc)
                      : "r"(sb), "n"(NSLOT - 1), "f"(x0[0]), "f"(x0[1]), "f"(x0[2]), "f"(x0[3]),
@@ -279,6 +353,13 @@ __device__ __forceinline__ void run_fast4(uint32_t &pa, float (&t)[4], const flo
 #undef GP_FAST_TABLE_NODIVS
 #undef GP_FAST_LOOP_TOP
 #undef GP_FAST_DIV_BODIES
+#undef GP_FAST_TRIG_REGS
+#undef GP_FAST_TRIG_CHECK1
+#undef GP_FAST_TRIG_CHECK
+#undef GP_FAST_TRIG_POLY
+#undef GP_FAST_SINCOS1
+#undef GP_FAST_TAN1
+#undef GP_FAST_TRIG_BODIES
 #undef GP_FAST_SLOT
 #undef GP_FAST_SPILL
 #undef GP_FAST_SLOTLOAD

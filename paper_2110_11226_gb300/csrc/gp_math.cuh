@@ -45,6 +45,23 @@ constexpr float kC0 = 0.0416666679f, kC1 = -0.00138888834f, kC2 = 2.47994594e-05
 // 1.5 * 2^23 rounds to an integer in the FMA pipe, and for |j| < 2^22 the
 // two's-complement low bits of that sum's encoding are j's low bits.
 constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
+
+// The evaluator's fast loop (inline PTX) spells these constants as float
+// bit patterns; the checks keep the two spellings the same numbers.
+static_assert(__builtin_bit_cast(uint32_t, kPio2Hi) == 0x3FC90FDBu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kPio2Mid) == 0xB33BBD2Eu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kPio2Lo) == 0xA6F72CEDu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kTwoOverPi) == 0x3F22F983u, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kS0) == 0xBE2AAAABu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kS1) == 0x3C088884u, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kS2) == 0xB95007C0u, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kS3) == 0x363668F9u, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kC0) == 0x3D2AAAABu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kC1) == 0xBAB60B5Cu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kC2) == 0x37D0086Fu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kC3) == 0xB4920F4Eu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kRoundMagic) == 0x4B400000u, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kTrigFast) == 0x47800000u, "trig constant");
 __device__ __forceinline__ float trig_reduce(float x, int &q) {
     const float jm = __fmaf_rn(x, kTwoOverPi, kRoundMagic);
     const float j = __fsub_rn(jm, kRoundMagic);
