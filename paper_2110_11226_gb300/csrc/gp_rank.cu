@@ -298,28 +298,10 @@ __global__ void __launch_bounds__(256) edges_kernel(const uint32_t *__restrict__
     edge[g] = make_int2((int)lo, (int)hi);
 }
 
-__device__ int smem_lower(const uint32_t *k, int lo, int hi, uint32_t v) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (k[mid] < v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-__device__ int smem_upper(const uint32_t *k, int lo, int hi, uint32_t v) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (k[mid] <= v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // Doubled average rank of every sorted position (first + last + 2, 1-based
-// positions of its tie group).  Groups inside a tile are found in shared
-// memory; a group that reaches the tile's edge takes its end from edge[]
-// (edges_kernel).  Ranks enter the sums centred on
+// positions of its tie group).  Groups inside a tile are found with
+// ballots over the sorted keys in shared memory; a group that reaches the
+// tile's edge takes its end from edge[] (edges_kernel).  Ranks enter the sums centred on
 // n + 1 (their unweighted mean): exact integers, zero for every row of a
 // constant program, and sums without the cancellation of uncentred squares.
 // mode 0 (the target): r2[row] = rank, and part = (sum w, sum w b,
@@ -331,9 +313,13 @@ __global__ void __launch_bounds__(kTileThreads) rank_kernel(
     const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n, int n_tiles,
     int mode, const int2 *__restrict__ edge, uint32_t *r2, const uint32_t *__restrict__ r2y,
     const float *__restrict__ w, double *part) {
+    constexpr int kSegs = kTile / 32;  // 32-position segments of the tile
     __shared__ uint32_t sk[kTile];
+    __shared__ int16_t sfirst[kTile], slast[kTile];
+    __shared__ int seg_first[kSegs], seg_last[kSegs];
     __shared__ double red[3][kTileThreads / 32];
     const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x;
+    const int lane = t & 31;
     const uint32_t *k = keys + (int64_t)seg * n;
     const uint32_t *vl = vals + (int64_t)seg * n;
     const int64_t t0 = (int64_t)tile * kTile;
@@ -365,6 +351,60 @@ __global__ void __launch_bounds__(kTileThreads) rank_kernel(
         rb[it] = (mode == 1 && q < tl) ? r2y[rows[it]] : 0u;
     }
     __syncthreads();
+    // tie groups inside the tile: the warp's 32 positions q = it * 256 + t
+    // are consecutive, so ballots of the group-start and group-end flags
+    // give each position the latest start at or before it and the earliest
+    // end at or after it within its 32-position segment; a segment without
+    // one takes it from the segments before (after) it, scanned by warp 0
+    const unsigned le = (2u << lane) - 1u, ge = ~((1u << lane) - 1u);
+#pragma unroll
+    for (int it = 0; it < kTileItems; ++it) {
+        const int q = it * kTileThreads + t;
+        const int sgi = q >> 5;
+        const bool in = q < tl;
+        const uint32_t v = in ? sk[q] : 0u;
+        const bool start = in && (q == 0 || sk[q - 1] != v);
+        const bool end = in && (q == tl - 1 || sk[q + 1] != v);
+        const unsigned bs = __ballot_sync(0xffffffffu, start);
+        const unsigned be = __ballot_sync(0xffffffffu, end);
+        if (in) {
+            sfirst[q] = (int16_t)((bs & le) ? (sgi << 5) + 31 - __clz(bs & le) : -1);
+            slast[q] = (int16_t)((be & ge) ? (sgi << 5) + __ffs(be & ge) - 1 : -1);
+        }
+        if (lane == 0) {
+            seg_first[sgi] = bs ? (sgi << 5) + 31 - __clz(bs) : -1;
+            seg_last[sgi] = be ? (sgi << 5) + __ffs(be) - 1 : INT_MAX;
+        }
+    }
+    __syncthreads();
+    if (t < 32) {
+        // exclusive prefix max of the segments' latest starts, exclusive
+        // suffix min of their earliest ends (two segments per lane)
+        const int a0 = seg_first[2 * t], a1 = seg_first[2 * t + 1];
+        const int b0 = seg_last[2 * t], b1 = seg_last[2 * t + 1];
+        int x = max(a0, a1);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (t >= o) x = max(x, y);
+        }
+        int before = __shfl_up_sync(0xffffffffu, x, 1);
+        if (t == 0) before = -1;
+        int z = min(b0, b1);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_down_sync(0xffffffffu, z, o);
+            if (t + o < 32) z = min(z, y);
+        }
+        int after = __shfl_down_sync(0xffffffffu, z, 1);
+        if (t == 31) after = INT_MAX;
+        __syncwarp();
+        seg_first[2 * t] = before;
+        seg_first[2 * t + 1] = max(before, a0);
+        seg_last[2 * t + 1] = after;
+        seg_last[2 * t] = min(after, b1);
+    }
+    __syncthreads();
     const bool exact = w == nullptr && n <= ((int64_t)1 << 29);
     long long is[3] = {0, 0, 0};
     double s[3] = {0.0, 0.0, 0.0};
@@ -372,12 +412,11 @@ __global__ void __launch_bounds__(kTileThreads) rank_kernel(
     for (int it = 0; it < kTileItems; ++it) {
         const int q = it * kTileThreads + t;
         if (q >= tl) break;
-        const uint32_t v = sk[q];
-        int lq = q, uq = q + 1;
-        if ((q > 0 && sk[q - 1] == v) || q == 0) lq = smem_lower(sk, 0, q, v);
-        if ((q + 1 < tl && sk[q + 1] == v) || q + 1 == tl) uq = smem_upper(sk, q + 1, tl, v);
+        int lq = sfirst[q], uq = slast[q];
+        if (lq < 0) lq = seg_first[q >> 5];
+        if (uq < 0) uq = seg_last[q >> 5];
         const int64_t first = lq == 0 ? (int64_t)eg.x : t0 + lq;
-        const int64_t last = uq == tl ? (int64_t)eg.y : t0 + uq - 1;
+        const int64_t last = uq == tl - 1 ? (int64_t)eg.y : t0 + uq;
         const uint32_t rank2 = (uint32_t)(first + last + 2);
         const uint32_t row = rows[it];
         const int a = (int)((int64_t)rank2 - (n + 1));  // |a| <= n - 1
