@@ -130,14 +130,15 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
 // The compiler lowers the dispatch switch to a tree of compares and
 // branches (about 12 instructions per dispatch, measured with ncu's
 // per-opcode counts); PTX's brx.idx jumps through a table instead (about
-// 3).  This loop runs, 4 rows per lane with columns 0 and 1 in registers,
-// the operations that PTX provides as single instructions with the
+// 3).  This loop runs, 4 rows per lane, the operations that PTX provides
+// as single instructions with the
 // evaluator's semantics: IEEE adds, subtracts and multiplies and, with
 // DIVS, divisions, square roots and reciprocals, all round to nearest
 // without flush to zero (add/sub/mul/div/sqrt/rcp .rn.f32: the
 // instructions behind __fadd_rn, __fsub_rn, __fmul_rn, __fdiv_rn,
 // __fsqrt_rn and __frcp_rn), sign changes, the protection selects, stack
-// moves and column reads; with DIVS also sin, cos and tan (the steps and
+// moves and, with columns 0 and 1 in registers (XREG), column reads; with
+// DIVS also sin, cos and tan (the steps and
 // constants of trig_rows, transcribed).  It stops at the first word it
 // does not run (OP_END, log, exp, the extended functions, trigonometric
 // arguments outside the fast path, and the division set and trigonometry
@@ -145,7 +146,8 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
 // switch and leaves pa just past it.  Every one of the 32 values of the
 // 5-bit op field has a table entry, so the index is always in range; stack
 // slots are clamped like the switch's.  Measured on Pagie-1 16M x 4096:
-// 465 ms -> 420 ms per evaluation, 390 ms with the trigonometry.  DIVS is
+// 465 ms -> 420 ms per evaluation, 390 ms with the trigonometry; with the
+// columns read by the switch, the 28-column table 119 ms -> 112 ms.  DIVS is
 // off in the instances with the extended functions, where the division
 // set cost the extended-set population 23% (their out-of-line calls and
 // the division's own slow-path call do not mix well); loading the next
@@ -159,6 +161,16 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
 #define GP_FAST_TABLE_NODIVS                                                      \
     "T%=: .branchtargets PX%=, PC%=, PXS%=, PCS%=, AS%=, SS%=, MS%=, EX%=,"       \
     " AX%=, AC%=, SX%=, SC%=, RX%=, RC%=, MX%=, MC%=, EX%=, EX%=, EX%=, EX%=,"    \
+    " EX%=, EX%=, EX%=, EX%=, EX%=, EX%=, AB%=, NG%=, EX%=, EX%=, EX%=, EX%=;\n\t"
+// without columns in registers (more than 2 features) the column reads
+// (PUSH_X, PUSH_X_SP and the _X forms) are handed back too
+#define GP_FAST_TABLE_DIVS_NOX                                                    \
+    "T%=: .branchtargets EX%=, PC%=, EX%=, PCS%=, AS%=, SS%=, MS%=, DS%=,"        \
+    " EX%=, AC%=, EX%=, SC%=, EX%=, RC%=, EX%=, MC%=, EX%=, DC%=, EX%=, RDC%=,"   \
+    " SQ%=, EX%=, EX%=, TSC%=, TSC%=, TTN%=, AB%=, NG%=, IV%=, EX%=, EX%=, EX%=;\n\t"
+#define GP_FAST_TABLE_NODIVS_NOX                                                  \
+    "T%=: .branchtargets EX%=, PC%=, EX%=, PCS%=, AS%=, SS%=, MS%=, EX%=,"        \
+    " EX%=, AC%=, EX%=, SC%=, EX%=, RC%=, EX%=, MC%=, EX%=, EX%=, EX%=, EX%=,"    \
     " EX%=, EX%=, EX%=, EX%=, EX%=, EX%=, AB%=, NG%=, EX%=, EX%=, EX%=, EX%=;\n\t"
 #define GP_FAST_LOOP_TOP                                                          \
     "N%=:\n\t"                                                                    \
@@ -327,11 +339,23 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
     "mov.f32 %6, %%cf;\n\t"                                                       \
     "}\n"
 
-template <int NSLOT, bool DIVS>
+// XREG: columns 0 and 1 held in x0 and x1 (otherwise those are unused and
+// the column reads are handed back)
+#define GP_FAST_OPERANDS                                                          \
+    : "+r"(pa), "+f"(t[0]), "+f"(t[1]), "+f"(t[2]), "+f"(t[3]), "=r"(hw), "=f"(hc) \
+    : "r"(sb), "n"(NSLOT - 1), "f"(x0[0]), "f"(x0[1]), "f"(x0[2]), "f"(x0[3]),    \
+      "f"(x1[0]), "f"(x1[1]), "f"(x1[2]), "f"(x1[3]), "f"(kThr)                   \
+    : "memory"
+template <int NSLOT, bool DIVS, bool XREG>
 __device__ __forceinline__ void run_fast4(uint32_t &pa, float (&t)[4], const float (&x0)[4],
                                           const float (&x1)[4], uint32_t sb, uint32_t &hw,
                                           float &hc) {
-    if constexpr (DIVS) {
+    if constexpr (!XREG && DIVS) {
+        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_DIVS_NOX) GP_FAST_TRIG_REGS GP_FAST_DIV_BODIES
+                     GP_FAST_TRIG_BODIES GP_FAST_BODY GP_FAST_OPERANDS);
+    } else if constexpr (!XREG) {
+        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_NODIVS_NOX) GP_FAST_BODY GP_FAST_OPERANDS);
+    } else if constexpr (DIVS) {
         asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_DIVS) GP_FAST_TRIG_REGS GP_FAST_DIV_BODIES
                      GP_FAST_TRIG_BODIES GP_FAST_BODY
                      : "+r"(pa), "+f"(t[0]), "+f"(t[1]), "+f"(t[2]), "+f"(t[3]), "=r"(hw),
@@ -351,6 +375,9 @@ __device__ __forceinline__ void run_fast4(uint32_t &pa, float (&t)[4], const flo
 #undef GP_FAST_HEAD
 #undef GP_FAST_TABLE_DIVS
 #undef GP_FAST_TABLE_NODIVS
+#undef GP_FAST_TABLE_DIVS_NOX
+#undef GP_FAST_TABLE_NODIVS_NOX
+#undef GP_FAST_OPERANDS
 #undef GP_FAST_LOOP_TOP
 #undef GP_FAST_DIV_BODIES
 #undef GP_FAST_TRIG_REGS
@@ -412,13 +439,13 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stk);  // this lane's slot 0
     // 4 rows per lane: the fast loop runs what it can and hands back the
     // rest, one word at a time, to the switch below
-    constexpr bool kFast = RPT == 4 && FMODE == 2;
+    constexpr bool kFast = RPT == 4;
 #pragma unroll 1
     for (;;) {
         uint2 ins;
         if constexpr (kFast) {
             float hc;
-            run_fast4<NSLOT, !EXT>(pa, t, x0, x1, sb, ins.x, hc);
+            run_fast4<NSLOT, !EXT, FMODE == 2>(pa, t, x0, x1, sb, ins.x, hc);
             ins.y = __float_as_uint(hc);
         } else {
             asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
