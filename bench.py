@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the step eagerly instead of replaying its CUDA graph")
+    ap.add_argument("--spearman", action="store_true",
+                    help="time the Spearman rank fitness on the workload instead (one JSON "
+                         "line of its own, not the headline)")
     return ap.parse_args()
 
 
@@ -242,10 +245,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_spearman(args):
+    """Spearman rank fitness (batched predictions, radix sort, ranks) of the
+    workload's population, timed with CUDA events around gp_evaluate."""
+    import torch
+    from paper_2110_11226_gb300 import gp
+    wl = make_workload(args, 0)
+    d = wl.data
+    P, N = len(wl.offsets) - 1, d.n_rows
+    pn = gp.nodes_to_device(wl.nodes)
+    po = torch.from_numpy(wl.offsets).cuda()
+    dX, dy = torch.from_numpy(d.X).cuda(), torch.from_numpy(d.y).cuda()
+    dw = None if d.w is None else torch.from_numpy(d.w).cuda()
+    out = torch.empty(P, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        gp.gp_evaluate(pn, po, dX, dy, dw, metric="spearman", out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        gp.gp_evaluate(pn, po, dX, dy, dw, metric="spearman", out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"metric": "Spearman fitness program-rows/s", "value": P * N / (ms * 1e-3),
+                      "unit": "program-row evals/s", "ms_per_step": ms, "steps": args.steps,
+                      "warmup": args.warmup, "data": DATA_DESC.get(wl.name, "synthetic"),
+                      "config": {"workload": wl.name, "n_rows": N, "n_progs": P,
+                                 "n_feat": d.n_feat, "metric": "spearman"}}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.spearman:
+        return run_spearman(args)
     import torch
     ws, rank, local = dist_info()
     torch.cuda.set_device(local)

@@ -339,6 +339,7 @@ int run_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const
     GP_CUDA(launch_compile(ca, st));
     GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
     const bool vec = aligned16(X) && (n_rows % 4 == 0);
+    const int fmode = (n_feat <= 2) ? 2 : 0;
     for (int cls = 0; cls < kNumClasses; ++cls) {
         EvalArgs ea{};
         ea.code = W.code;
@@ -347,7 +348,7 @@ int run_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const
         ea.class_count = W.class_count;
         ea.cls = cls;
         ea.X = X;
-        ea.ld = n_rows;
+        ea.ld = (fmode == 2) ? (n_feat == 2 ? n_rows : 0) : n_rows;
         ea.n_rows = n_rows;
         ea.n_progs = n_progs;
         ea.metric = GP_MSE;
@@ -357,8 +358,11 @@ int run_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const
         ea.pred = out_pred;
         ea.dev_status = c->status;
         ea.vec_ok = vec ? 1 : 0;
-        int occ = info_predict(cls, kEvalBlockThreads, nullptr);
-        GP_CUDA(launch_predict(ea, c->sms * std::max(occ, 1), kEvalBlockThreads, st));
+        const int occ = fmode == 2 ? info_predict_f2(cls, kEvalBlockThreads, nullptr)
+                                   : info_predict(cls, kEvalBlockThreads, nullptr);
+        const int grid = c->sms * std::max(occ, 1);
+        GP_CUDA(fmode == 2 ? launch_predict_f2(ea, grid, kEvalBlockThreads, st)
+                           : launch_predict(ea, grid, kEvalBlockThreads, st));
     }
     return GP_OK;
 }

@@ -208,6 +208,9 @@ GP_EVAL_INSTANCE(16, 0)
 cudaError_t launch_predict(const EvalArgs &a, int grid, int block,
                            cudaStream_t st);
 int info_predict(int cls, int block, int *regs);
+// the same for tables of at most two columns (feature mode 2)
+cudaError_t launch_predict_f2(const EvalArgs &a, int grid, int block, cudaStream_t st);
+int info_predict_f2(int cls, int block, int *regs);
 
 struct FinalizeArgs {
     const float *part;

@@ -1,7 +1,7 @@
 // gp_predict.cu -- the evaluator's interpreter with a store epilogue
 // (predictions instead of fitness): gp_predict and the predictions that the
 // rank fitness sorts.  One instance per program class, feature columns
-// loaded per reference.
+// loaded per reference (gp_predict_f2.cu: two columns in registers).
 #include "gp_interp.cuh"
 
 namespace gpk {
