@@ -130,30 +130,32 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
 // The compiler lowers the dispatch switch to a tree of compares and
 // branches (about 12 instructions per dispatch, measured with ncu's
 // per-opcode counts); PTX's brx.idx jumps through a table instead (about
-// 3).  This loop runs, 4 rows per lane, the operations that PTX provides
-// as single instructions with the
-// evaluator's semantics: IEEE adds, subtracts and multiplies and, with
-// DIVS, divisions, square roots and reciprocals, all round to nearest
-// without flush to zero (add/sub/mul/div/sqrt/rcp .rn.f32: the
-// instructions behind __fadd_rn, __fsub_rn, __fmul_rn, __fdiv_rn,
-// __fsqrt_rn and __frcp_rn), sign changes, the protection selects, stack
-// moves and, with columns 0 and 1 in registers (XREG), column reads; with
-// DIVS also sin, cos and tan (the steps and
-// constants of trig_rows, transcribed).  It stops at the first word it
-// does not run (OP_END, log, exp, the extended functions, trigonometric
-// arguments outside the fast path, and the division set and trigonometry
-// without DIVS), hands that word and its constant back to the caller's
-// switch and leaves pa just past it.  Every one of the 32 values of the
-// 5-bit op field has a table entry, so the index is always in range; stack
-// slots are clamped like the switch's.  Measured on Pagie-1 16M x 4096:
-// 465 ms -> 420 ms per evaluation, 390 ms with the trigonometry; with the
-// columns read by the switch, the 28-column table 119 ms -> 112 ms.  DIVS is
-// off in the instances with the extended functions, where the division
-// set cost the extended-set population 23% (their out-of-line calls and
-// the division's own slow-path call do not mix well); loading the next
-// word while the current one runs cost 3%.
-// the op table: with DIVS the division set (7 DIV_S .. 19 RDIV_C, 20 SQRT,
-// 28 INV) runs here, otherwise it is handed back
+// 3).  This loop, 4 rows per lane, runs the operations whose evaluator
+// semantics PTX states directly:
+//   * pushes and stack moves, abs and neg, and IEEE adds, subtracts and
+//     multiplies with every operand form (add/sub/mul.rn.f32, the
+//     instructions behind __fadd_rn, __fsub_rn and __fmul_rn);
+//   * column reads when columns 0 and 1 are held in registers (XREG);
+//   * with DIVS, the protected divisions, square root and reciprocal
+//     (div/sqrt/rcp.rn.f32, as __fdiv_rn, __fsqrt_rn and __frcp_rn, all
+//     without flush to zero, then the protection selects) and sin, cos and
+//     tan (the steps and constants of trig_rows, transcribed).
+// It stops at the first word it does not run (OP_END, log, exp, the
+// extended functions, trigonometric arguments outside the fast path, and
+// whatever XREG or DIVS leave out), hands that word and its constant back
+// to the caller's switch and leaves pa just past it.  Every one of the 32
+// values of the 5-bit op field has a table entry, so the index is always
+// in range; stack slots are clamped like the switch's.
+// Measured on Pagie-1 16M x 4096: 465 ms -> 420 ms per evaluation, 390 ms
+// with the trigonometry; the 28-column table, its column reads handed
+// back, 119 ms -> 112 ms.  DIVS is off in the instances with the extended
+// functions: there it cost the extended-set population 23% (their
+// out-of-line calls and the division's own slow-path call do not mix
+// well).  Loading the next word while the current one runs cost 3%.
+//
+// the op tables: with DIVS the division set (7 DIV_S .. 19 RDIV_C, 20 SQRT,
+// 28 INV) and trigonometry (23 SIN .. 25 TAN) run here, otherwise they are
+// handed back
 #define GP_FAST_TABLE_DIVS                                                        \
     "T%=: .branchtargets PX%=, PC%=, PXS%=, PCS%=, AS%=, SS%=, MS%=, DS%=,"       \
     " AX%=, AC%=, SX%=, SC%=, RX%=, RC%=, MX%=, MC%=, DX%=, DC%=, RDX%=, RDC%=,"  \
