@@ -320,37 +320,27 @@ int validate_one_host(const gp_node *p, int len, int n_feat, int *hw_out) {
     return GP_PROG_OK;
 }
 
-// every program's value on every row into pred [n_progs][n_rows]
-int run_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
-                int64_t n_rows, int n_feat, float *out_pred, int32_t *out_status, DevCtx *c,
-                cudaStream_t st) {
-    int rc;
+// predictions of programs [p0, p0 + b) whose compiled code and metadata
+// are already in W (indexed by program id) into pred [b][n_rows]
+int run_predict_compiled(const Workspace &W, int p0, int b, const float *X, int64_t n_rows,
+                         int n_feat, float *out_pred, DevCtx *c, cudaStream_t st) {
     const int64_t chunk = std::min<int64_t>(round_up(n_rows, 256), 4096);
     const int n_chunks = (int)((n_rows + chunk - 1) / chunk);
-    Layout L = make_layout(n_progs, 1, false);
-    {
-        std::lock_guard<std::mutex> g(g_mu);
-        if ((rc = grow(&c->ws, &c->ws_bytes, L.total))) return rc;
-    }
-    Workspace W = carve(c->ws, L, false);
     GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
-    CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
-                   nullptr, nullptr, nullptr, c->status, out_status};
-    GP_CUDA(launch_compile(ca, st));
-    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
+    GP_CUDA(launch_order(W.meta + p0, b, W.order, W.class_count, st));
     const bool vec = aligned16(X) && (n_rows % 4 == 0);
     const int fmode = (n_feat <= 2) ? 2 : 0;
     for (int cls = 0; cls < kNumClasses; ++cls) {
         EvalArgs ea{};
-        ea.code = W.code;
-        ea.meta = W.meta;
+        ea.code = W.code + (size_t)p0 * kCodeStride;
+        ea.meta = W.meta + p0;
         ea.order = W.order;
         ea.class_count = W.class_count;
         ea.cls = cls;
         ea.X = X;
         ea.ld = (fmode == 2) ? (n_feat == 2 ? n_rows : 0) : n_rows;
         ea.n_rows = n_rows;
-        ea.n_progs = n_progs;
+        ea.n_progs = b;
         ea.metric = GP_MSE;
         ea.chunk_rows = chunk;
         ea.n_chunks = n_chunks;
@@ -365,6 +355,33 @@ int run_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const
                            : launch_predict(ea, grid, kEvalBlockThreads, st));
     }
     return GP_OK;
+}
+
+// the pre-pass of every program into the context's workspace (code, meta,
+// order for up to n_progs programs); *W receives the carved workspace
+int compile_all(const gp_node *progs, const int32_t *offsets, int n_progs, int n_feat,
+                int32_t *out_status, DevCtx *c, Workspace *W, cudaStream_t st) {
+    int rc;
+    Layout L = make_layout(n_progs, 1, false);
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        if ((rc = grow(&c->ws, &c->ws_bytes, L.total))) return rc;
+    }
+    *W = carve(c->ws, L, false);
+    CompileArgs ca{progs, offsets, n_progs, n_feat, W->code, W->meta,
+                   nullptr, nullptr, nullptr, c->status, out_status};
+    GP_CUDA(launch_compile(ca, st));
+    return GP_OK;
+}
+
+// every program's value on every row into pred [n_progs][n_rows]
+int run_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                int64_t n_rows, int n_feat, float *out_pred, int32_t *out_status, DevCtx *c,
+                cudaStream_t st) {
+    Workspace W;
+    int rc = compile_all(progs, offsets, n_progs, n_feat, out_status, c, &W, st);
+    if (rc) return rc;
+    return run_predict_compiled(W, 0, n_progs, X, n_rows, n_feat, out_pred, c, st);
 }
 
 // Spearman: the target's ranks once, then batches of programs predicted
@@ -394,11 +411,13 @@ int run_spearman(const gp_node *progs, const int32_t *offsets, int n_progs, cons
     double *tpart = reinterpret_cast<double *>(base + b_pred + b_r2y);
     void *scr = base + b_pred + b_r2y + b_tp;
     GP_CUDA(target_ranks(y, w, n_rows, scr, r2y, tpart, st));
+    // the pre-pass once for all programs (one thread per program: compiled
+    // batch by batch, its latency came back with every batch)
+    Workspace W;
+    if ((rc = compile_all(progs, offsets, n_progs, n_feat, out_status, c, &W, st))) return rc;
     for (int p0 = 0; p0 < n_progs; p0 += B) {
         const int b = std::min(B, n_progs - p0);
-        if ((rc = run_predict(progs, offsets + p0, b, X, n_rows, n_feat, pred,
-                              out_status ? out_status + p0 : nullptr, c, st)))
-            return rc;
+        if ((rc = run_predict_compiled(W, p0, b, X, n_rows, n_feat, pred, c, st))) return rc;
         GP_CUDA(spearman_batch(pred, b, n_rows, r2y, tpart, w, scr, out + p0,
                                out64 ? out64 + p0 : nullptr, st));
     }
