@@ -572,13 +572,15 @@ constexpr size_t eval_smem_bytes() {
 }
 
 // epilogues: the weighted loss sum, the predictions, or the moment sums
-// of the correlation fitness.  The moment epilogue at 8 rows per thread
-// asks for 3 resident blocks (at most 85 registers), the loss epilogue's
-// occupancy; left alone it would take 97 and fit 2.
+// of the correlation fitness.  The moment epilogue asks for the loss
+// epilogue's occupancy: 5 resident blocks at 4 rows per thread (at most 48
+// registers, with a few spilled words: 4% faster than 4 blocks at 59
+// registers on Pagie-1 16M x 4096) and 3 at 8 rows (at most 85 registers;
+// left alone it would take 97 and fit 2).
 constexpr int kEpiLoss = 0, kEpiPred = 1, kEpiMom = 2;
 
 template <int RPT, int NSLOT, int FMODE, int EPI, bool EXT>
-__global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom && RPT == 8 ? 3 : 0) eval_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom ? (RPT == 8 ? 3 : 5) : 0) eval_kernel(const EvalArgs a) {
     constexpr bool PRED = EPI == kEpiPred;
     constexpr bool MOM = EPI == kEpiMom;
     constexpr int kEvalWarps = eval_warps<RPT>();
