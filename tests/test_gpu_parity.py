@@ -393,17 +393,20 @@ def test_spearman_fitness(n, weighted):
     assert fit[-2] == 0.0 or np.isnan(fit[-2])
 
 
-def test_spearman_over_several_batches():
-    """2M rows x 300 programs: the ranks of at most 2 GB of predictions are
-    sorted at a time (42 programs per batch here); sampled programs from
-    every batch equal the oracle's Spearman of its FP32 predictions."""
-    wl = synth.workload("pagie_large", n_rows=1 << 21, n_progs=300)
+@pytest.mark.parametrize("n_rows,n_progs", [(1 << 21, 300), (1 << 20, 4096)])
+def test_spearman_over_several_batches(n_rows, n_progs):
+    """The ranks of at most 2 GB of predictions are sorted at a time (42
+    programs per batch at 2M rows, 85 at 1M: the second case is the
+    Spearman configuration bench.py times, 49 batches); sampled programs
+    from every batch equal the oracle's Spearman of the device's FP32
+    predictions."""
+    wl = synth.workload("pagie_large", n_rows=n_rows, n_progs=n_progs)
     d = wl.data
     pn, po, dX, dy, _ = put(wl.nodes, wl.offsets, d.X, d.y)
-    fit64 = torch.empty(300, dtype=torch.float64, device="cuda")
+    fit64 = torch.empty(n_progs, dtype=torch.float64, device="cuda")
     gp.gp_evaluate_ex(pn, po, dX, dy, metric="spearman", out64=fit64)
     fit = fit64.cpu().numpy()
-    idx = np.arange(3, 300, 19)
+    idx = np.arange(3, n_progs, max(19, n_progs // 20))
     sn, so = _subset(wl.nodes, wl.offsets, idx)
     gpred = gp.gp_predict(gp.nodes_to_device(sn), dev(so), dX).cpu().numpy().astype(np.float64)
     checked = 0
