@@ -18,7 +18,8 @@
 // register array t[RPT]; deeper values sit in the warp's slice of a
 // shared-memory stack, one float4 per (slot, group of 4 rows, lane), so a
 // push or pop is one or two conflict-free 16-byte accesses per lane.  Each
-// instruction costs one switch (30 cases) and nothing else that branches:
+// instruction costs one indexed branch (the inline-PTX fast loop, 4 rows per
+// lane) or one switch, and nothing else that branches:
 // measured on this GPU, an interpreter's dispatch latency grows with every
 // dependent branch per instruction (about 20-40 cycles each) and with the
 // number of distinct code locations it jumps between, so operand source and
@@ -409,21 +410,23 @@ __device__ __forceinline__ void run_fast4(uint32_t &pa, float (&t)[4], const flo
 
 // Runs one compiled program over RPT rows per lane; returns the top of the
 // stack in t.  stk = this warp's stack slice, already offset by the lane.
-// The instruction buffer (kCodeStride + 2 entries in shared memory) holds
-// OP_END from the program's end through its last entry, so the loop ends
-// within kCodeStride + 1 steps whatever the buffer holds, and the fast
-// loop's load of the word after the last one stays inside it; op values that
-// name no operation act as OP_END and stack slots are clamped to the
-// stack, so no instruction word can make it run away or leave its memory.
+// The instruction buffer (kCodeStride + 2 entries in shared memory, one
+// more than either loop can reach) holds OP_END from the program's end
+// through its last entry, so the loop ends within kCodeStride + 1 steps
+// whatever the buffer holds; op values that name no operation act as
+// OP_END and stack slots are clamped to the stack, so no instruction word
+// can make it run away or leave its memory.
 //
 // Dispatch cost is what this loop is tuned for (per-opcode instruction
-// counts measured with ncu on chains of one operation): the instruction
-// word and the stack are addressed through 32-bit shared-memory addresses
-// computed once; the opcode is broadcast from lane 0, which lets the
-// compiler treat the switch as warp-uniform (no reconvergence barrier per
-// instruction); the switch covers all 32 values of its 5-bit operand, so
-// it needs no range test; and the word is loaded when it is needed rather
-// than one ahead, which saves the register copies of a prefetch.
+// counts measured with ncu on chains of one operation).  At 4 rows per lane
+// the fast loop runs most words and hands the others, one at a time, to
+// the switch below.  The instruction word and the stack are addressed
+// through 32-bit shared-memory addresses computed once; the opcode is
+// broadcast from lane 0, which lets the compiler treat the switch as
+// warp-uniform (no reconvergence barrier per instruction); the switch
+// covers all 32 values of its 5-bit operand, so it needs no range test;
+// and the word is loaded when it is needed rather than one ahead, which
+// saves the register copies of a prefetch.
 template <int RPT, int NSLOT, int FMODE, bool EXT>
 __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restrict__ cbuf,
                                           const float (&x0)[RPT], const float (&x1)[RPT],
