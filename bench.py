@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the step eagerly instead of replaying its CUDA graph")
+    ap.add_argument("--const-tune", action="store_true",
+                    help="time constant tuning (fitness and gradient, then Adam) on the "
+                         "const_tune workload instead (one JSON line of its own)")
     ap.add_argument("--spearman", action="store_true",
                     help="time the Spearman rank fitness on the workload instead (one JSON "
                          "line of its own, not the headline)")
@@ -287,12 +290,69 @@ def run_spearman(args):
                                  "n_feat": d.n_feat, "metric": "spearman"}}))
 
 
+def run_const_tune(args):
+    """Constant tuning on the const_tune workload (Pagie-1 1M rows x 2048
+    programs with up to 16 constants, MSE): a step is 5 x (fitness and
+    gradient of every program's constants in one pass, then one Adam step),
+    timed with CUDA events; the fitness-only evaluation is timed beside it."""
+    import torch
+    from paper_2110_11226_gb300 import gp
+    args.workload = "const_tune"
+    if args.n_rows == 1 << 24:
+        args.n_rows = 0  # the workload's own 1M rows
+    wl = make_workload(args, 0)
+    d = wl.data
+    P, N = len(wl.offsets) - 1, d.n_rows
+    pn = gp.nodes_to_device(wl.nodes)
+    po = torch.from_numpy(wl.offsets).cuda()
+    dX, dy = torch.from_numpy(d.X).cuda(), torch.from_numpy(d.y).cuda()
+    grad = torch.empty((P, gp.MAX_CONSTS), dtype=torch.float32, device="cuda")
+    fit = torch.empty(P, dtype=torch.float32, device="cuda")
+    m = torch.zeros_like(grad)
+    v = torch.zeros_like(grad)
+    inner = 5
+
+    def step(k):
+        for i in range(inner):
+            gp.gp_const_grad(pn, po, dX, dy, metric=wl.metric, out_grad=grad, out_fitness=fit)
+            gp.gp_adam_step(pn, po, grad, m, v, k * inner + i + 1, lr=1e-2)
+
+    def timed(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k in range(reps):
+            fn(k)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    ms = timed(lambda k: step(args.warmup + k), args.steps)
+    grad_ms = timed(lambda k: gp.gp_const_grad(pn, po, dX, dy, metric=wl.metric, out_grad=grad,
+                                               out_fitness=fit), args.steps)
+    adam_ms = timed(lambda k: gp.gp_adam_step(pn, po, grad, m, v, 1000 + k, lr=1e-2), args.steps)
+    eval_ms = timed(lambda k: gp.gp_evaluate(pn, po, dX, dy, metric=wl.metric, out=fit), args.steps)
+    print(json.dumps({"metric": "constant-tuning program-row gradient evals/s",
+                      "value": inner * P * N / (ms * 1e-3), "unit": "program-row evals/s",
+                      "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                      "grad_ms": grad_ms, "adam_ms": adam_ms, "eval_ms": eval_ms,
+                      "grad_over_eval": grad_ms / eval_ms,
+                      "step": f"{inner} x (gp_const_grad + gp_adam_step), eager launches",
+                      "data": DATA_DESC.get(wl.name, "synthetic"),
+                      "config": {"workload": wl.name, "n_rows": N, "n_progs": P,
+                                 "n_feat": d.n_feat, "metric": wl.metric}}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.spearman:
         return run_spearman(args)
+    if args.const_tune:
+        return run_const_tune(args)
     import torch
     ws, rank, local = dist_info()
     torch.cuda.set_device(local)

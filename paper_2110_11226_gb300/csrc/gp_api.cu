@@ -672,7 +672,7 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, con
     GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
     GradArgs ga{progs, offsets, W.meta, W.order, W.rchild, W.kslot, X, n_rows, n_rows, y, w,
                 n_progs, metric, chunk, n_chunks, W.counters, W.part, W.gpart, c->status};
-    GP_CUDA(launch_grad(ga, c->sms * 4, 128, st));
+    GP_CUDA(launch_grad(ga, c->sms * std::max(info_grad(), 1), 128, st));
     GradFinalizeArgs fa{W.part, W.gpart, n_chunks, n_progs, W.meta, W.sumw, metric,
                         out_grad, out_fitness};
     GP_CUDA(launch_grad_finalize(fa, st));

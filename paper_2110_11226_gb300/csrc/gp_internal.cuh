@@ -280,6 +280,8 @@ struct GradArgs {
 };
 cudaError_t launch_grad(const GradArgs &a, int grid, int block,
                         cudaStream_t st);
+// resident blocks of grad_kernel per SM (its launch fills them all)
+int info_grad();
 struct GradFinalizeArgs {
     const float *part;
     const float *gpart;
