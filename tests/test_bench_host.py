@@ -1,0 +1,51 @@
+"""Host logic of bench.py (CPU): the kernel-source hash that keys the
+recorded DRAM traffic ignores comments and blank lines but not code, and the
+recorded figure is read only while that hash matches."""
+from __future__ import annotations
+
+import bench
+
+
+def test_code_only_drops_comments_and_blank_lines():
+    src = """// header comment
+#include "x.h"   // trailing
+
+/* block
+   comment */ int a = 1;
+int b = 2; /* inline */ int c = 3;
+
+"""
+    out = bench._code_only(src)
+    assert out.splitlines() == ['#include "x.h"', " int a = 1;", "int b = 2;  int c = 3;"]
+
+
+def test_hash_follows_code_not_comments(monkeypatch, tmp_path):
+    files = {"gp_interp.cuh": "int f() { return 1; }  // one\n", "gp_math.cuh": "",
+             "gp_internal.cuh": "", "gp_compile.cu": ""}
+    csrc = tmp_path / "paper_2110_11226_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for k, v in files.items():
+        (csrc / k).write_text(v)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_hash()
+    (csrc / "gp_interp.cuh").write_text("// a new comment\n\nint f() { return 1; }  // two\n")
+    assert bench.kernel_hash() == h0
+    (csrc / "gp_interp.cuh").write_text("int f() { return 2; }\n")
+    assert bench.kernel_hash() != h0
+
+
+def test_recorded_traffic_is_keyed_by_the_hash(monkeypatch, tmp_path):
+    csrc = tmp_path / "paper_2110_11226_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for k in ("gp_interp.cuh", "gp_math.cuh", "gp_internal.cuh", "gp_compile.cu"):
+        (csrc / k).write_text("int x;\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.kernel_hash()
+    prof = tmp_path / "profiles" / "eval_kernel_pagie1_traffic.md"
+    prof.write_text(f"- workload: pagie_large\n- kernel_sources_sha256_16: {h}\n"
+                    "- dram_bytes_per_row: 13.5\n")
+    assert bench.recorded_traffic("pagie_large") == 13.5
+    assert bench.recorded_traffic("tabular") is None
+    (csrc / "gp_compile.cu").write_text("int y;\n")
+    assert bench.recorded_traffic("pagie_large") is None
