@@ -49,3 +49,30 @@ def test_recorded_traffic_is_keyed_by_the_hash(monkeypatch, tmp_path):
     assert bench.recorded_traffic("tabular") is None
     (csrc / "gp_compile.cu").write_text("int y;\n")
     assert bench.recorded_traffic("pagie_large") is None
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with the keys the benchmark contract asks of that arm."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--workload", "pagie_small", "--n-rows", "4096", "--steps", "1",
+                        "--warmup", "0", "--cpu-seconds", "1"],
+                       capture_output=True, text=True, cwd=root, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    for k in ("metric", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "dtype", "config"):
+        assert k in d, k
+    assert d["config"]["workload"] == "pagie_small"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
