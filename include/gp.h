@@ -154,12 +154,16 @@ const char *gp_status_string(int status);
  *   w           [n_rows] float32 weights, or NULL for all ones
  *   out_fitness [n_progs] float32; NaN for a malformed program
  * Batched persistent evaluator: one device pre-pass validates and compiles
- * all programs, sorts them by length, and one persistent launch works
- * through (program, row-chunk) items.  Scratch comes from a library-owned
- * per-device cache that grows on demand (cudaMalloc), so the first call at
- * a new size allocates; use gp_evaluate_ex with a caller workspace to
- * avoid that (e.g. under CUDA graph capture).  The same inputs give
- * bit-identical fitness on every call. */
+ * all programs, sorts them by class (stack depth, extended functions) and
+ * length, and one persistent launch per class works through (program,
+ * row-chunk) items.  Scratch comes from a library-owned per-device cache
+ * that grows on demand (cudaMalloc), so the first call at a new size
+ * allocates; use gp_evaluate_ex with a caller workspace to avoid that (e.g.
+ * under CUDA graph capture).  Every call that uses the cache on a device
+ * shares it: calls that could overlap on the GPU (different streams, or
+ * host threads without ordering) must be serialised by the caller, or each
+ * given its own workspace.  The same inputs give bit-identical fitness on
+ * every call. */
 int gp_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs,
                 const float *X, int64_t n_rows, int n_feat, const float *y,
                 const float *w, int metric, float *out_fitness, void *stream);
@@ -186,10 +190,10 @@ size_t gp_workspace_size(int n_progs, int64_t n_rows, int n_feat,
 /* The tunables gp_evaluate_ex would use for this shape: `opts` (may be NULL)
  * with every zero field filled from the autotuner's record for the shape, or
  * else from the built-in defaults (rows_per_thread 4; chunk_rows sized for
- * about 16 work items per resident warp, 1024..65536 rows; blocks_per_sm 0 =
- * as many as fit).  Programs deeper than 8 stack slots always run with 4
- * rows per thread, whatever rows_per_thread says.  Returns GP_ERR_ARG for
- * invalid opts. */
+ * about 16 work items per resident warp, 1024..16384 rows; blocks_per_sm 0 =
+ * as many as fit).  Programs deeper than 8 stack slots, and programs that
+ * use a function from GP_SQ on, always run with 4 rows per thread, whatever
+ * rows_per_thread says.  Returns GP_ERR_ARG for invalid opts. */
 int gp_resolve_opts(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts *opts,
                     gp_eval_opts *out);
 

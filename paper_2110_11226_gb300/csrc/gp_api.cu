@@ -71,6 +71,8 @@ std::pair<cudaEvent_t, cudaEvent_t> timing_pair() {
 int ctx_of_current(DevCtx **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GP_ERR_CUDA;
+    // the first call on a device fills its context; host threads may race here
+    std::lock_guard<std::mutex> g(g_mu);
     DevCtx &c = g_ctx[dev];
     if (!c.init) {
         if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
