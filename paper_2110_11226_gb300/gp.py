@@ -121,14 +121,41 @@ LIB_PATH = os.environ.get("GP_LIBGP") or _build.LIB
 
 
 # ---- marshalling helpers -------------------------------------------------
-def _dptr(t: Optional[torch.Tensor], name: str):
+def _on_device(t: torch.Tensor) -> bool:
+    return t.is_cuda
+
+
+def _dptr(t: Optional[torch.Tensor], name: str, dtype=None, numel: Optional[int] = None):
+    """Device pointer of `t` (None stays None).  The library reads and writes
+    through raw pointers, so the element type and a minimum element count
+    are checked here, before anything reaches the GPU."""
     if t is None:
         return None
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, not {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call needs {numel}")
+    if not _on_device(t):
         raise TypeError(f"{name} must be a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return C.c_void_p(t.data_ptr())
+
+
+_F32, _F64, _I32, _I64 = torch.float32, torch.float64, torch.int32, torch.int64
+
+
+def _progs(progs, offsets):
+    """(progs, offsets) pointers: 8-byte node records held as int64, int32
+    offsets [n_progs + 1]."""
+    return _dptr(progs, "progs", _I64), _dptr(offsets, "offsets", _I32)
+
+
+def _data(X, y, w, n_rows):
+    """(X, y, w) pointers: float32 columns, y and w at least n_rows long."""
+    return (_dptr(X, "X", _F32), _dptr(y, "y", _F32, n_rows), _dptr(w, "w", _F32, n_rows))
 
 
 def _hptr(a: Optional[np.ndarray]):
@@ -180,9 +207,11 @@ def gp_evaluate(progs, offsets, X, y, w=None, metric="mse", out=None, stream=Non
     P = _nprogs(offsets)
     if out is None:
         out = torch.empty(P, dtype=torch.float32, device=X.device)
+    pp, po = _progs(progs, offsets)
+    xp, yp, wp = _data(X, y, w, n_rows)
     _check("gp_evaluate", _lib.gp_evaluate(
-        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
-        _dptr(y, "y"), _dptr(w, "w"), _metric(metric), _dptr(out, "out"), _stream(stream)))
+        pp, po, P, xp, n_rows, n_feat, yp, wp, _metric(metric),
+        _dptr(out, "out", _F32, P), _stream(stream)))
     return out
 
 
@@ -193,9 +222,11 @@ def gp_evaluate_static(progs, offsets, X, y, w=None, metric="mse", out=None, str
     P = _nprogs(offsets)
     if out is None:
         out = torch.empty(P, dtype=torch.float32, device=X.device)
+    pp, po = _progs(progs, offsets)
+    xp, yp, wp = _data(X, y, w, n_rows)
     _check("gp_evaluate_static", _lib.gp_evaluate_static(
-        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
-        _dptr(y, "y"), _dptr(w, "w"), _metric(metric), _dptr(out, "out"), _stream(stream)))
+        pp, po, P, xp, n_rows, n_feat, yp, wp, _metric(metric),
+        _dptr(out, "out", _F32, P), _stream(stream)))
     return out
 
 
@@ -215,11 +246,13 @@ def gp_evaluate_ex(progs, offsets, X, y, w=None, metric="mse", opts: Optional[Ev
     if out is None:
         out = torch.empty(P, dtype=torch.float32, device=X.device)
     ws_ptr, ws_bytes = (None, 0) if ws is None else (_dptr(ws, "ws"), ws.numel() * ws.element_size())
+    pp, po = _progs(progs, offsets)
+    xp, yp, wp = _data(X, y, w, n_rows)
     _check("gp_evaluate_ex", _lib.gp_evaluate_ex(
-        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
-        _dptr(y, "y"), _dptr(w, "w"), _metric(metric),
-        None if opts is None else C.byref(opts), _dptr(out, "out"), _dptr(out64, "out64"),
-        _dptr(out_status, "out_status"), ws_ptr, ws_bytes, _stream(stream)))
+        pp, po, P, xp, n_rows, n_feat, yp, wp, _metric(metric),
+        None if opts is None else C.byref(opts), _dptr(out, "out", _F32, P),
+        _dptr(out64, "out64", _F64, P), _dptr(out_status, "out_status", _I32, P), ws_ptr, ws_bytes,
+        _stream(stream)))
     return out
 
 
@@ -241,9 +274,11 @@ def gp_evaluate_plain(progs, offsets, X, y, w=None, metric="mse", out=None, stre
     P = _nprogs(offsets)
     if out is None:
         out = torch.empty(P, dtype=torch.float32, device=X.device)
+    pp, po = _progs(progs, offsets)
+    xp, yp, wp = _data(X, y, w, n_rows)
     _check("gp_evaluate_plain", _lib.gp_evaluate_plain(
-        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
-        _dptr(y, "y"), _dptr(w, "w"), _metric(metric), _dptr(out, "out"), _stream(stream)))
+        pp, po, P, xp, n_rows, n_feat, yp, wp, _metric(metric),
+        _dptr(out, "out", _F32, P), _stream(stream)))
     return out
 
 
@@ -252,9 +287,10 @@ def gp_predict(progs, offsets, X, out=None, stream=None):
     P = _nprogs(offsets)
     if out is None:
         out = torch.empty((P, n_rows), dtype=torch.float32, device=X.device)
+    pp, po = _progs(progs, offsets)
     _check("gp_predict", _lib.gp_predict(
-        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
-        _dptr(out, "out"), _stream(stream)))
+        pp, po, P, _dptr(X, "X", _F32), n_rows, n_feat, _dptr(out, "out", _F32, P * n_rows),
+        _stream(stream)))
     return out
 
 
@@ -293,9 +329,9 @@ def gp_tournament_ex(fitness, n_tourn, tourn_size, seed, offsets=None, parsimony
     if out is None:
         out = torch.empty(n_tourn, dtype=torch.int32, device=fitness.device)
     _check("gp_tournament_ex", _lib.gp_tournament_ex(
-        _dptr(fitness, "fitness"), _dptr(offsets, "offsets"), P, int(n_tourn), int(tourn_size),
-        float(parsimony), int(bool(greater_is_better)), int(seed), int(offset),
-        _dptr(out, "out"), _stream(stream)))
+        _dptr(fitness, "fitness", _F32), _dptr(offsets, "offsets", _I32, P + 1), P, int(n_tourn),
+        int(tourn_size), float(parsimony), int(bool(greater_is_better)), int(seed), int(offset),
+        _dptr(out, "out", _I32, int(n_tourn)), _stream(stream)))
     return out
 
 
@@ -304,7 +340,7 @@ def gp_tournament(fitness, tourn_size, seed, out=None):
     if out is None:
         out = torch.empty(P, dtype=torch.int32, device=fitness.device)
     _check("gp_tournament", _lib.gp_tournament(
-        _dptr(fitness, "fitness"), P, int(tourn_size), int(seed), _dptr(out, "out")))
+        _dptr(fitness, "fitness", _F32), P, int(tourn_size), int(seed), _dptr(out, "out", _I32, P)))
     return out
 
 
@@ -316,28 +352,32 @@ def gp_const_grad(progs, offsets, X, y, w=None, metric="mse", out_grad=None, out
         out_grad = torch.empty((P, MAX_CONSTS), dtype=torch.float32, device=X.device)
     if out_fitness is None:
         out_fitness = torch.empty(P, dtype=torch.float32, device=X.device)
+    pp, po = _progs(progs, offsets)
+    xp, yp, wp = _data(X, y, w, n_rows)
     _check("gp_const_grad", _lib.gp_const_grad(
-        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(X, "X"), n_rows, n_feat,
-        _dptr(y, "y"), _dptr(w, "w"), _metric(metric), _dptr(out_grad, "out_grad"),
-        _dptr(out_fitness, "out_fitness"), _stream(stream)))
+        pp, po, P, xp, n_rows, n_feat, yp, wp, _metric(metric),
+        _dptr(out_grad, "out_grad", _F32, P * MAX_CONSTS),
+        _dptr(out_fitness, "out_fitness", _F32, P), _stream(stream)))
     return out_grad, out_fitness
 
 
 def gp_adam_step(progs, offsets, grad, m, v, step, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
                  stream=None):
     P = _nprogs(offsets)
+    n = P * MAX_CONSTS
     _check("gp_adam_step", _lib.gp_adam_step(
-        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, _dptr(grad, "grad"),
-        _dptr(m, "m"), _dptr(v, "v"), int(step), float(lr), float(beta1), float(beta2),
-        float(eps), _stream(stream)))
+        *_progs(progs, offsets), P, _dptr(grad, "grad", _F32, n), _dptr(m, "m", _F32, n),
+        _dptr(v, "v", _F32, n), int(step), float(lr), float(beta1), float(beta2), float(eps),
+        _stream(stream)))
 
 
 def gp_get_consts(progs, offsets, out=None, stream=None):
     P = _nprogs(offsets)
     if out is None:
         out = torch.empty((P, MAX_CONSTS), dtype=torch.float32, device=progs.device)
-    _check("gp_get_consts", _lib.gp_get_consts(_dptr(progs, "progs"), _dptr(offsets, "offsets"),
-                                               P, _dptr(out, "out"), _stream(stream)))
+    _check("gp_get_consts", _lib.gp_get_consts(*_progs(progs, offsets), P,
+                                               _dptr(out, "out", _F32, P * MAX_CONSTS),
+                                               _stream(stream)))
     return out
 
 
@@ -345,8 +385,8 @@ def gp_set_consts(progs, offsets, consts, stream=None):
     P = _nprogs(offsets)
     if consts.shape != (P, MAX_CONSTS) or consts.dtype != torch.float32:
         raise GPError(f"gp_set_consts: consts must be float32 [{P}, {MAX_CONSTS}]")
-    _check("gp_set_consts", _lib.gp_set_consts(_dptr(progs, "progs"), _dptr(offsets, "offsets"),
-                                               P, _dptr(consts, "consts"), _stream(stream)))
+    _check("gp_set_consts", _lib.gp_set_consts(*_progs(progs, offsets), P,
+                                               _dptr(consts, "consts"), _stream(stream)))
 
 
 class ConstantsFitness(torch.autograd.Function):
@@ -392,10 +432,10 @@ def gp_mutate(progs, offsets, n_feat, parents, params: Optional[MutParams] = Non
         out_kind = torch.empty(n_out, dtype=torch.int32, device=dev)
     ws_bytes = 0 if ws is None else ws.numel() * ws.element_size()
     _check("gp_mutate", _lib.gp_mutate(
-        _dptr(progs, "progs"), _dptr(offsets, "offsets"), P, int(n_feat), _dptr(parents, "parents"),
-        n_out, C.byref(params), int(seed), int(offset), _dptr(out, "out"),
-        _dptr(out_offsets, "out_offsets"), _dptr(out_kind, "out_kind"), _dptr(ws, "ws"),
-        ws_bytes, _stream(stream)))
+        *_progs(progs, offsets), P, int(n_feat), _dptr(parents, "parents", _I32), n_out,
+        C.byref(params), int(seed), int(offset), _dptr(out, "out", _I64, n_out * 255),
+        _dptr(out_offsets, "out_offsets", _I32, n_out + 1),
+        _dptr(out_kind, "out_kind", _I32, n_out), _dptr(ws, "ws"), ws_bytes, _stream(stream)))
     return out, out_offsets, out_kind
 
 
@@ -412,9 +452,10 @@ def gp_last_device_status(stream=None) -> int:
 def gp_autotune(progs, offsets, X, y, w=None, metric="mse", stream=None) -> EvalOpts:
     n_rows, n_feat = _xshape(X)
     best = EvalOpts()
+    pp, po = _progs(progs, offsets)
+    xp, yp, wp = _data(X, y, w, n_rows)
     _check("gp_autotune", _lib.gp_autotune(
-        _dptr(progs, "progs"), _dptr(offsets, "offsets"), _nprogs(offsets), _dptr(X, "X"),
-        n_rows, n_feat, _dptr(y, "y"), _dptr(w, "w"), _metric(metric), C.byref(best),
+        pp, po, _nprogs(offsets), xp, n_rows, n_feat, yp, wp, _metric(metric), C.byref(best),
         _stream(stream)))
     return best
 
