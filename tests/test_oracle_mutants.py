@@ -65,6 +65,15 @@ MUTANTS = {
                            "        int terminal = d >= limit + 1 || pick(s, nf + 2) < 2;"),
     "bound_drops_mul_term": ("r.e = fabs(a.v) * b.e + fabs(b.v) * a.e + a.e * b.e;",
                              "r.e = fabs(a.v) * b.e + a.e * b.e;"),
+    "parsimony_sign": ("adj = raw + pen;", "adj = raw - pen;"),
+    "nan_counts_as_best": ("if (isnan(adj)) adj = INFINITY;", "if (isnan(adj)) adj = -INFINITY;"),
+    "log_protect_value": ("case ORA_LOG:  return fabs(a) < thr ? 0.0 : log(fabs(a));",
+                          "case ORA_LOG:  return fabs(a) < thr ? 1.0 : log(fabs(a));"),
+    "inv_protect_value": ("case ORA_INV:  return fabs(a) < thr ? 0.0 : 1.0 / a;",
+                          "case ORA_INV:  return fabs(a) < thr ? 1.0 : 1.0 / a;"),
+    "mean_over_rows_not_weights": ("f = se / sw;", "f = se / (double)n_eval;"),
+    "pearson_zero_variance_one": ("else if (spp == 0.0 || syy == 0.0) f = 0.0;",
+                                  "else if (spp == 0.0 || syy == 0.0) f = 1.0;"),
 }
 
 
