@@ -74,6 +74,21 @@ MUTANTS = {
     "mean_over_rows_not_weights": ("f = se / sw;", "f = se / (double)n_eval;"),
     "pearson_zero_variance_one": ("else if (spp == 0.0 || syy == 0.0) f = 0.0;",
                                   "else if (spp == 0.0 || syy == 0.0) f = 1.0;"),
+    "draw_by_modulo": ("return (int64_t)(((uint64_t)o[j & 3] * (uint64_t)n_progs) >> 32);",
+                       "return (int64_t)(o[j & 3] % (uint32_t)n_progs);"),
+    "draw_counter_swapped": ("uint32_t ctr[4] = {(uint32_t)(j >> 2), (uint32_t)t, (uint32_t)offset,",
+                             "uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(j >> 2), (uint32_t)offset,"),
+    "philox_key_schedule": ("k0 += W0; k1 += W1;", "k0 += W0; k1 += W0;"),
+    "drmse_no_half": ("            scale = (f > 0.0) ? scale / (2.0 * f) : 0.0;\n        }\n"
+                      "        for (int k = 0; k < ORA_MAX_CONSTS; ++k) {\n"
+                      "            grad[p * ORA_MAX_CONSTS + k] = (k < nc) ? g[k] * scale : 0.0;\n"
+                      "            /* sum of |per-row",
+                      "            scale = (f > 0.0) ? scale / f : 0.0;\n        }\n"
+                      "        for (int k = 0; k < ORA_MAX_CONSTS; ++k) {\n"
+                      "            grad[p * ORA_MAX_CONSTS + k] = (k < nc) ? g[k] * scale : 0.0;\n"
+                      "            /* sum of |per-row"),
+    "dlogloss_sign": ("                              : exp(p) / (1.0 + exp(p));\n        return s - y;",
+                      "                              : exp(p) / (1.0 + exp(p));\n        return y - s;"),
 }
 
 

@@ -507,6 +507,36 @@ def test_philox_matches_curand_host_generator():
         np.testing.assert_array_equal(mine, out)
 
 
+def test_tournament_draws_are_curand_philox_words():
+    """Draw j of tournament 0 at offset b is word j % 4 of the Philox4x32-10
+    block at counter (j / 4, 0, b, 0), mapped to [0, n) as (u * n) >> 32
+    (Sec. III-B, III-C1).  cuRAND's host generator emits the block of counter
+    (c0, 0, c2, 0) at position 65536 * c0 + c2 of its stream (asserted first),
+    so the draws are pinned to the library's own words."""
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not loadable")
+    PHILOX = 161  # CURAND_RNG_PSEUDO_PHILOX4_32_10
+    seed = 0x0123456789ABCDEF
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), PHILOX) == 0
+    assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_uint64(seed)) == 0
+    out = np.zeros(4 * (65536 + 64), np.uint32)
+    assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(out.size)) == 0
+    lib.curandDestroyGenerator(gen)
+    blocks = out.reshape(-1, 4)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for c0 in (0, 1):
+        for b in (0, 1, 63):
+            np.testing.assert_array_equal(oracle.philox4x32_10([c0, 0, b, 0], key),
+                                          blocks[65536 * c0 + b])
+    for n in (7, 97, 1000, 2 ** 31 - 1):
+        for b in range(64):
+            for j in range(8):
+                u = int(blocks[65536 * (j >> 2) + b][j & 3])
+                assert oracle.tournament_draw(seed, b, 0, j, n) == (u * n) >> 32
+
+
 def test_tournament_draws_uniform():
     n, T = 37, 20000
     draws = np.array([oracle.tournament_draw(42, 0, t, j, n) for t in range(T // 20) for j in range(20)])
