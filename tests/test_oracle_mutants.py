@@ -87,6 +87,33 @@ MUTANTS = {
                       "        for (int k = 0; k < ORA_MAX_CONSTS; ++k) {\n"
                       "            grad[p * ORA_MAX_CONSTS + k] = (k < nc) ? g[k] * scale : 0.0;\n"
                       "            /* sum of |per-row"),
+    "feature_bound_off_by_one": (
+        "        if (p[j].op == ORA_VAR && (p[j].feat < 0 || p[j].feat >= n_feat))",
+        "        if (p[j].op == ORA_VAR && (p[j].feat < 0 || p[j].feat > n_feat))"),
+    "adam_v_not_squared": ("        v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];",
+                           "        v[i] = beta2 * v[i] + (1.0 - beta2) * fabs(g[i]);"),
+    "rank_pearson_mean_unweighted": ("        sb += wi * b[i];", "        sb += b[i];"),
+    "pearson_mean_unweighted": ("            swp += (w ? (double)w[row0 + i] : 1.0) * v;",
+                                "            swp += v;"),
+    "pearson_var_unweighted": ("                spp += wi * dp * dp;", "                spp += dp * dp;"),
+    "dcosh_sign": ("                case ORA_COSH: du = sinh(u); break;",
+                   "                case ORA_COSH: du = -sinh(u); break;"),
+    "datan_no_square": ("                case ORA_ATAN: du = 1.0 / (1.0 + u * u); break;",
+                        "                case ORA_ATAN: du = 1.0 / (1.0 + u); break;"),
+    "sinh_as_cosh": ("    case ORA_SINH: return sinh(a);", "    case ORA_SINH: return cosh(a);"),
+    "crossover_donor_is_parent": (
+        "            int j = pick(&s, ld);\n"
+        "            len = hoisted_splice(&s, par, lp, i, don, ld, j, child);",
+        "            int j = pick(&s, lp);\n"
+        "            len = hoisted_splice(&s, par, lp, i, par, lp, j, child);"),
+    "point_replace_inverted": (
+        "                if ((uint64_t)stream_next(&s) >= thr_replace) continue;",
+        "                if ((uint64_t)stream_next(&s) < thr_replace) continue;"),
+    "hoist_may_keep_root": ("            int k = si > 1 ? i + 1 + pick(&s, si - 1) : i;",
+                            "            int k = si > 1 ? i + pick(&s, si) : i;"),
+    "subtree_depth_plus_one": (
+        "            int lt = grow_tree(&s, subtree_depth, funcs, nf, n_feat, tree);",
+        "            int lt = grow_tree(&s, subtree_depth + 1, funcs, nf, n_feat, tree);"),
     "dlogloss_sign": ("                              : exp(p) / (1.0 + exp(p));\n        return s - y;",
                       "                              : exp(p) / (1.0 + exp(p));\n        return y - s;"),
 }
