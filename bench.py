@@ -124,7 +124,8 @@ def kernel_hash():
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        text = open(os.path.join(ROOT, "paper_2110_11226_gb300", "csrc", f)).read()
+        with open(os.path.join(ROOT, "paper_2110_11226_gb300", "csrc", f)) as fh:
+            text = fh.read()
         h.update(_code_only(text).encode())
     return h.hexdigest()[:16]
 
@@ -146,10 +147,11 @@ def recorded_traffic(workload):
     if not os.path.exists(path):
         return None
     vals = {}
-    for line in open(path):
-        if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_sources_sha256_16") != kernel_hash() or vals.get("workload") != workload:
         return None
     try:
@@ -174,10 +176,11 @@ class ClockSampler:
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            with open(self.path, "w") as out:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                     "--format=csv,noheader,nounits", "-lms", "200"],
+                    stdout=out, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         return self
@@ -193,7 +196,9 @@ class ClockSampler:
     def summary(self):
         rows = []
         if self.path and os.path.exists(self.path):
-            for line in open(self.path):
+            with open(self.path) as fh:
+                lines = fh.readlines()
+            for line in lines:
                 f = [x.strip() for x in line.split(",")]
                 if len(f) < 9:
                     continue
@@ -458,8 +463,10 @@ def main():
     bytes_alg = N * 4 * (d.n_feat + 1 + (d.w is not None))
     peak_fp32 = pipes["fp32"]
     peak_sfu = ops_sfu / t_sfu if t_sfu > 0 else pipes["ex2"]  # this op mix's rate
-    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    hbm = 6800.0
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hbm = json.load(fh)["hbm_gbs"]
     t_kernel = eval_ms / max(n_eval_calls, 1) * 1e-3
     cands = {"fp32": ops_fp32 / peak_fp32, "sfu": t_sfu, "hbm": bytes_alg / (hbm * 1e9)}
     bound = max(cands, key=cands.get)

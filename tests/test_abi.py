@@ -21,13 +21,15 @@ HEADER = os.path.join(ROOT, "include", "gp.h")
 
 
 def _declared():
-    txt = open(HEADER).read()
+    with open(HEADER) as f:
+        txt = f.read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(gp_[a-z0-9_]+)\s*\(", txt)))
 
 
 def _enum(name_prefix):
-    txt = open(HEADER).read()
+    with open(HEADER) as f:
+        txt = f.read()
     return {m.group(1): int(m.group(2)) for m in re.finditer(rf"\b({name_prefix}[A-Z_0-9]+)\s*=\s*(-?\d+)", txt)}
 
 

@@ -121,13 +121,15 @@ MUTANTS = {
 
 def _run_mutant(name, tmp):
     old, new = MUTANTS[name]
-    src = open(SRC).read()
+    with open(SRC) as f:
+        src = f.read()
     assert src.count(old) == 1, name
     d = os.path.join(tmp, name)
     os.makedirs(d, exist_ok=True)
     c = os.path.join(d, "m.c")
     so = os.path.join(d, "m.so")
-    open(c, "w").write(src.replace(old, new))
+    with open(c, "w") as f:
+        f.write(src.replace(old, new))
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
                     "-ffp-contract=off", c, "-o", so, "-lm"], check=True)
     env = dict(os.environ, GP_ORACLE_SO=so)
