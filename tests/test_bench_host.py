@@ -76,3 +76,31 @@ def test_reference_arm_prints_the_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_clock_sampler_reads_clocks_and_throttle_reasons(monkeypatch, tmp_path):
+    """The clocks record of the JSON line: median SM clock under load, the
+    maximum clock, and the throttle reasons seen active, from nvidia-smi's
+    CSV samples (here a stand-in script on PATH); no nvidia-smi at all gives
+    an explicit "unsampled" record."""
+    import os
+    import time
+    fake = tmp_path / "nvidia-smi"
+    rows = ["0, 1900, 2070, 800.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1965, 2070, 900.1, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2010, 2070, 950.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbled line"]
+    fake.write_text("#!/bin/sh\n" + "".join(f"echo '{r}'\n" for r in rows) + "sleep 5\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    with bench.ClockSampler(0) as c:
+        for _ in range(100):
+            time.sleep(0.02)
+            if os.path.getsize(c.path) >= sum(len(r) + 1 for r in rows):
+                break
+    s = c.summary()
+    assert s == {"sm_mhz": 1965.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    monkeypatch.setenv("PATH", str(tmp_path / "empty"))
+    with bench.ClockSampler(0) as c:
+        pass
+    assert c.summary()["reasons"] == ["unsampled"]
