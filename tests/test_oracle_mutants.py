@@ -65,6 +65,13 @@ MUTANTS = {
                            "        int terminal = d >= limit + 1 || pick(s, nf + 2) < 2;"),
     "bound_drops_mul_term": ("r.e = fabs(a.v) * b.e + fabs(b.v) * a.e + a.e * b.e;",
                              "r.e = fabs(a.v) * b.e + a.e * b.e;"),
+    "bound_div_drops_b_term": (
+        "        if (b.e < bv) r.e = (a.e + fabs(r.v) * b.e) / (bv - b.e);",
+        "        if (b.e < bv) r.e = a.e / (bv - b.e);"),
+    "bound_add_max_not_sum": ("        r.e = a.e + b.e;\n        return ve_round(r, 0.5);",
+                              "        r.e = fmax(a.e, b.e);\n        return ve_round(r, 0.5);"),
+    "bound_exp_no_growth": ("        r.e = fabs(r.v) * expm1(a.e);", "        r.e = a.e;"),
+    "bound_sq_drops_linear": ("        r.e = 2.0 * av * a.e + a.e * a.e;", "        r.e = a.e * a.e;"),
     "parsimony_sign": ("adj = raw + pen;", "adj = raw - pen;"),
     "nan_counts_as_best": ("if (isnan(adj)) adj = INFINITY;", "if (isnan(adj)) adj = -INFINITY;"),
     "log_protect_value": ("case ORA_LOG:  return fabs(a) < thr ? 0.0 : log(fabs(a));",
