@@ -93,3 +93,25 @@ def test_host_validation_agrees_with_oracle():
             assert hw[i] == ohw
     rc2, st2, _ = gp.gp_validate_host(*pack(good), n_feat)
     assert rc2 == 0 and np.all(st2 == 0)
+
+
+def test_binding_signatures_match_the_header():
+    """Every prototype in gp.h has a binding entry with the same number of
+    arguments and the same return type, and the binding declares nothing the
+    header lacks."""
+    import ctypes as C
+    from paper_2110_11226_gb300 import gp
+    with open(HEADER) as f:
+        txt = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    protos = re.findall(r"\b(int|size_t|void|const char \*)\s*(gp_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;",
+                        txt, flags=re.S)
+    assert len(protos) >= 20
+    ret = {"int": C.c_int, "size_t": C.c_size_t, "void": None, "const char *": C.c_char_p}
+    for r, name, args in protos:
+        args = " ".join(args.split())
+        n_args = 0 if args in ("", "void") else args.count(",") + 1
+        fn = getattr(gp._lib, name)
+        assert fn.restype is ret[r], name
+        assert len(fn.argtypes) == n_args, (name, len(fn.argtypes), n_args)
+    bound = {n for n in dir(gp) if n.startswith("gp_")}
+    assert bound <= {n for _, n, _ in protos}, bound - {n for _, n, _ in protos}
