@@ -115,3 +115,33 @@ def test_binding_signatures_match_the_header():
         assert len(fn.argtypes) == n_args, (name, len(fn.argtypes), n_args)
     bound = {n for n in dir(gp) if n.startswith("gp_")}
     assert bound <= {n for _, n, _ in protos}, bound - {n for _, n, _ in protos}
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "gp.h"
+int main(void) {
+    gp_node prog[3] = {{GP_ADD, 0, 0.0f}, {GP_VAR, 0, 0.0f}, {GP_CONST, 0, 1.5f}};
+    int32_t off[2] = {0, 3};
+    int32_t st[1] = {-1}, hw[1] = {-1};
+    int rc = gp_validate_host(prog, off, 1, 2, st, hw);
+    printf("%s\n", gp_version());
+    return (rc == GP_OK && st[0] == GP_PROG_OK && hw[0] == 2 && sizeof(gp_node) == 8) ? 0 : 1;
+}
+"""
+
+
+def test_header_is_plain_c_and_a_c_program_links(tmp_path):
+    """gp.h compiles as pedantic C99 with no CUDA or torch headers, and a C
+    program links libgp and calls an entry point that needs no GPU."""
+    import subprocess
+    lib = gpbuild.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(lib)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lgp",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("libgp"), (r.returncode, r.stdout, r.stderr)
