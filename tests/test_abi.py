@@ -145,3 +145,54 @@ def test_header_is_plain_c_and_a_c_program_links(tmp_path):
                     f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.startswith("libgp"), (r.returncode, r.stdout, r.stderr)
+
+
+def test_argument_errors_return_before_any_device_call():
+    """Bad arguments come back as GP_ERR_ARG before the library touches CUDA;
+    arguments that pass every check reach the device lookup, which on a
+    machine without a GPU fails with GP_ERR_CUDA (no CPU fallback).  Runs
+    only where no GPU is visible, so the placeholder pointers can never
+    reach a kernel."""
+    import ctypes as C
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("placeholder pointers are only safe without a GPU")
+    from paper_2110_11226_gb300 import gp
+    lib = gp._lib
+    ARG, CUDA = -1, -4
+    buf = (C.c_uint8 * 4096)()
+    p = C.cast(buf, C.c_void_p)
+    ev = lambda **k: lib.gp_evaluate(k.get("progs", p), k.get("off", p), k.get("P", 4), p,
+                                     k.get("N", 100), k.get("F", 2), k.get("y", p), None,
+                                     k.get("metric", 1), k.get("out", p), None)
+    for bad in (dict(progs=None), dict(off=None), dict(P=0), dict(N=0), dict(F=0), dict(F=32768),
+                dict(N=(1 << 40) + 1), dict(y=None), dict(out=None), dict(metric=6),
+                dict(metric=-1)):
+        assert ev(**bad) == ARG, bad
+    assert ev() == CUDA
+    plain = lambda m: lib.gp_evaluate_plain(p, p, 4, p, 100, 2, p, None, m, p, None)
+    assert plain(4) == ARG and plain(5) == ARG and plain(1) == CUDA
+    assert lib.gp_const_grad(p, p, 4, p, 100, 2, p, None, 4, p, p, None) == ARG
+    assert lib.gp_predict(p, p, 4, p, 100, 2, None, None) == ARG
+    tour = lambda **k: lib.gp_tournament_ex(k.get("fit", p), None, k.get("P", 4), k.get("T", 4),
+                                            k.get("k", 2), 0.0, 0, 1, 0, k.get("out", p), None)
+    for bad in (dict(fit=None), dict(out=None), dict(P=0), dict(T=-1), dict(k=0)):
+        assert tour(**bad) == ARG, bad
+    adam = lambda step=1, b1=0.9, b2=0.999, eps=1e-8: lib.gp_adam_step(
+        p, p, 4, p, p, p, step, 1e-2, b1, b2, eps, None)
+    assert adam(step=0) == ARG and adam(b1=1.0) == ARG and adam(b2=-0.1) == ARG
+    assert adam(eps=0.0) == ARG
+    good = dict(p_crossover=0.7, p_subtree=0.1, p_hoist=0.05, p_point=0.1, p_replace=0.1,
+                subtree_depth=4)
+    mut = lambda params, n_out=4: lib.gp_mutate(p, p, 4, 2, p, n_out, C.byref(params), 1, 0,
+                                                p, p, None, None, 0, None)
+    assert mut(gp.make_mut_params(**good)) == CUDA
+    assert mut(gp.make_mut_params(**good), n_out=0) == ARG
+    for bad in (dict(p_crossover=0.9, p_subtree=0.2), dict(subtree_depth=7), dict(functions=()),
+                dict(p_replace=1.5), dict(p_hoist=-0.1)):
+        assert mut(gp.make_mut_params(**{**good, **bad})) == ARG, bad
+    q = gp.make_mut_params(**good)
+    q.reserved[2] = 1
+    assert mut(q) == ARG
+    assert lib.gp_workspace_size(0, 100, 2, None) == 0
+    assert lib.gp_mutate_workspace_size(0) == 0 and lib.gp_mutate_workspace_size((1 << 22) + 1) == 0
