@@ -196,3 +196,17 @@ def test_argument_errors_return_before_any_device_call():
     assert mut(q) == ARG
     assert lib.gp_workspace_size(0, 100, 2, None) == 0
     assert lib.gp_mutate_workspace_size(0) == 0 and lib.gp_mutate_workspace_size((1 << 22) + 1) == 0
+
+
+def test_build_targets_sm_103a_only_and_covers_every_source():
+    """One -gencode for sm_103a with line info, no host-specific flags, and
+    an object in the library for every .cu file of csrc/."""
+    flags = gpbuild.NVCC_FLAGS
+    gencodes = [flags[i + 1] for i, f in enumerate(flags) if f == "-gencode"]
+    assert gencodes == ["arch=compute_103a,code=sm_103a"]
+    assert "-lineinfo" in flags and not any("march" in f or "arch=sm_" in f for f in flags)
+    gpbuild.build()
+    for s in gpbuild.sources():
+        o = os.path.join(gpbuild.BUILD, os.path.basename(s)[:-3] + ".o")
+        assert os.path.exists(o) and os.path.getmtime(o) <= os.path.getmtime(gpbuild.LIB), s
+    assert len(gpbuild.sources()) >= 15
