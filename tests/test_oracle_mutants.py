@@ -123,6 +123,36 @@ MUTANTS = {
         "            int lt = grow_tree(&s, subtree_depth + 1, funcs, nf, n_feat, tree);"),
     "dlogloss_sign": ("                              : exp(p) / (1.0 + exp(p));\n        return s - y;",
                       "                              : exp(p) / (1.0 + exp(p));\n        return y - s;"),
+    # the FP32 reverse mode (ora_const_grad32)
+    "dcos32_sign": ("                case ORA_COS:  du = -sinf(u); break;",
+                    "                case ORA_COS:  du = sinf(u); break;"),
+    "dsqrt32_no_half": (
+        "                case ORA_SQRT: du = (u == 0.0f) ? 0.0f : sgn32(u) / (2.0f * val[j]); break;",
+        "                case ORA_SQRT: du = (u == 0.0f) ? 0.0f : sgn32(u) / val[j]; break;"),
+    "dinv32_sign": (
+        "                case ORA_INV:  du = (fabsf(u) < ORA_THR) ? 0.0f : -(val[j] * val[j]); break;",
+        "                case ORA_INV:  du = (fabsf(u) < ORA_THR) ? 0.0f : (val[j] * val[j]); break;"),
+    "ddiv32_right_sign": ("                    else { du = 1.0f / v; dv = -(val[j] / v); }",
+                          "                    else { du = 1.0f / v; dv = (val[j] / v); }"),
+    "dlogloss32_sign": (
+        "        float s = (p >= 0.0f) ? 1.0f / (1.0f + expf(-p)) : expf(p) / (1.0f + expf(p));\n"
+        "        return s - y;",
+        "        float s = (p >= 0.0f) ? 1.0f / (1.0f + expf(-p)) : expf(p) / (1.0f + expf(p));\n"
+        "        return y - s;"),
+    "drmse32_no_half": (
+        "            scale = (f > 0.0) ? scale / (2.0 * f) : 0.0;\n        }\n"
+        "        for (int k = 0; k < ORA_MAX_CONSTS; ++k)\n"
+        "            grad[p * ORA_MAX_CONSTS + k] = (k < nc) ? g[k] * scale : 0.0;",
+        "            scale = (f > 0.0) ? scale / f : 0.0;\n        }\n"
+        "        for (int k = 0; k < ORA_MAX_CONSTS; ++k)\n"
+        "            grad[p * ORA_MAX_CONSTS + k] = (k < nc) ? g[k] * scale : 0.0;"),
+    "dmae32_sign": ("    case ORA_MAE: return sgn32(p - y);", "    case ORA_MAE: return sgn32(y - p);"),
+    "dabs32_one": ("                case ORA_ABS:  du = sgn32(u); break;",
+                   "                case ORA_ABS:  du = 1.0f; break;"),
+    "weight32_dropped_from_adjoint": ("            adj[0] = wi * dloss32(metric, pr, yi);",
+                                      "            adj[0] = dloss32(metric, pr, yi);"),
+    "dsin32_as_sin": ("                case ORA_SIN:  du = cosf(u); break;",
+                      "                case ORA_SIN:  du = sinf(u); break;"),
 }
 
 
@@ -139,7 +169,8 @@ def _run_mutant(name, tmp):
         f.write(src.replace(old, new))
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
                     "-ffp-contract=off", c, "-o", so, "-lm"], check=True)
-    env = dict(os.environ, GP_ORACLE_SO=so)
+    # one OpenMP thread per mutant: the mutants already run side by side
+    env = dict(os.environ, GP_ORACLE_SO=so, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_mutation.py")],

@@ -665,3 +665,161 @@ def test_adam_constant_gradient_closed_form():
         before = th.copy()
         oracle.adam(th, g, m, v, t, lr=1e-2)
         np.testing.assert_allclose(th - before, -1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# the FP32 reverse mode (every per-row operation in float, sums in FP64):
+# the yardstick the device adjoint is held to where FP32 rounding moves a
+# gradient far from the FP64 one
+# --------------------------------------------------------------------------
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+def test_const_grad32_closed_forms():
+    X, y, w = _rand_data(700, 12)
+    yd, wd = y.astype(np.float64), w.astype(np.float64)
+    sw = np.sum(wd)
+    c = 0.8125  # exact in float
+    nodes, off = pack([[(synth.OP["const"], 0, c)], parse_prefix(f"mul {c} x0")])
+    x0 = X[0].astype(np.float64)
+    # MSE: 2 (c - ybar_w) for the constant, 2 sum w (c x0 - y) x0 / sum w
+    # for c x0; each row's term is a few float roundings off its exact value
+    g, fit = oracle.const_grad32(nodes, off, X, y, w, "mse")
+    rows = 2 * wd * (c - yd)
+    assert abs(g[0, 0] - rows.sum() / sw) <= 4 * EPS32 * np.abs(rows).sum() / sw
+    rows = 2 * wd * (c * x0 - yd) * x0
+    assert abs(g[1, 0] - rows.sum() / sw) <= 6 * EPS32 * np.abs(rows).sum() / sw
+    assert np.all(g[:, 1:] == 0)
+    # RMSE: the MSE gradient over 2 RMSE
+    g, fit = oracle.const_grad32(nodes[:1], off[:2], X, y, w, "rmse")
+    rmse = math.sqrt(np.sum(wd * (yd - c) ** 2) / sw)
+    assert fit[0] == pytest.approx(rmse, rel=1e-6)
+    assert g[0, 0] == pytest.approx((c - np.sum(wd * yd) / sw) / rmse, rel=1e-5)
+    # MAE: the weighted mean of sign(c - y)
+    g, _ = oracle.const_grad32(nodes[:1], off[:2], X, y, w, "mae")
+    assert g[0, 0] == pytest.approx(np.sum(wd * np.sign(c - yd)) / sw, rel=1e-12, abs=1e-12)
+    # log-loss of sigmoid(c): sigma(c) - ybar_w
+    Xb, yb, wb = _rand_data(500, 13, binary=True)
+    g, fit = oracle.const_grad32(nodes[:1], off[:2], Xb, yb, wb, "logloss")
+    ybw = np.sum(wb.astype(np.float64) * yb) / np.sum(wb.astype(np.float64))
+    assert g[0, 0] == pytest.approx(1.0 / (1.0 + math.exp(-c)) - ybw, rel=1e-5)
+
+
+def _fitness_of_fp32_predictions(nodes, off, X, y, w, metric):
+    """Fitness of the oracle's FP32 predictions, the loss and sums in FP64."""
+    p32 = oracle.predict32(nodes, off, X)
+    p = p32.astype(np.float64)
+    yd, wd = y.astype(np.float64), w.astype(np.float64)
+    with np.errstate(all="ignore"):
+        # a squared error beyond the float range makes the FP32 fitness
+        # infinite: there is no slope to compare
+        if metric in ("mse", "rmse") and not np.all(np.isfinite((p32 - y) * (p32 - y))):
+            return np.full(p.shape[0], np.inf)
+        if metric in ("mse", "rmse"):
+            l = (p - yd) ** 2
+        elif metric == "mae":
+            l = np.abs(p - yd)
+        else:
+            l = np.logaddexp(0.0, p) - yd * p
+        f = (l * wd).sum(axis=1) / wd.sum()
+    return np.sqrt(f) if metric == "rmse" else f
+
+
+@pytest.mark.parametrize("metric", ["mse", "rmse", "mae", "logloss"])
+def test_const_grad32_matches_central_differences_of_fp32_fitness(metric):
+    # the FP32 adjoint against difference quotients of a fitness built from
+    # the FP32 forward evaluation (predict32), not from the adjoint's own
+    # forward pass
+    X, y, w = _rand_data(2000, 14, binary=metric == "logloss")
+    nodes, off = synth.ramped_half_and_half(200, 2, 4, synth.FULL_SET + ("tan",), 2, seed=33,
+                                            max_consts=16, const_range=(-2.0, 2.0))
+    g, _ = oracle.const_grad32(nodes, off, X, y, w, metric)
+    g64, _ = oracle.const_grad(nodes, off, X, y, w, metric)
+    # MAE's slope jumps wherever a row's prediction crosses its target, so
+    # its quotients take a narrower step
+    h = 2e-4 if metric == "mae" else 2e-3
+    checked = skipped = 0
+    for p in range(len(off) - 1):
+        seg = np.arange(off[p], off[p + 1])
+        sub = nodes[seg].copy()
+        soff = np.array([0, len(seg)], np.int32)
+        kidx = np.flatnonzero(sub["op"] == synth.OP["const"])
+        for k, node in enumerate(kidx):
+            def f_at(h):
+                nn = sub.copy()
+                nn["c"][node] = np.float32(sub["c"][node] + h)
+                return _fitness_of_fp32_predictions(nn, soff, X, y, w, metric)[0], float(nn["c"][node])
+            fp, cp = f_at(2 * h)
+            fm, cm = f_at(-2 * h)
+            fp2, cp2 = f_at(h)
+            fm2, cm2 = f_at(-h)
+            if not all(np.isfinite([fp, fm, fp2, fm2])):
+                skipped += 1
+                continue
+            d1 = (fp - fm) / (cp - cm)
+            d2 = (fp2 - fm2) / (cp2 - cm2)
+            scale = max(abs(d1), abs(d2), 1e-4)
+            if abs(d1 - d2) > 1e-3 * scale:  # not smooth over [c-h, c+h]
+                skipped += 1
+                continue
+            # the same quotient of the FP64 fitness: where the two disagree,
+            # FP32 rounding (a constant absorbed by a much larger operand)
+            # hides the slope from the FP32 quotient
+            nn = sub.copy()
+            nn["c"][node] = np.float32(cp2)
+            q64p = oracle.fitness(nn, soff, X, y, w, metric)[0][0]
+            nn["c"][node] = np.float32(cm2)
+            q64m = oracle.fitness(nn, soff, X, y, w, metric)[0][0]
+            d64 = (q64p - q64m) / (cp2 - cm2)
+            if not np.isfinite(d64) or abs(d64 - d2) > 1e-3 * max(scale, abs(d64)):
+                skipped += 1
+                continue
+            # and where even the FP64 quotient misses the FP64 reverse mode
+            # (pinned above to FP64 differences and closed forms), a value
+            # swamps the constant's effect at this step: no slope to see
+            if abs(d64 - g64[p, k]) > 1e-3 * max(abs(d64), abs(g64[p, k]), 1e-4):
+                skipped += 1
+                continue
+            assert abs(g[p, k] - d2) <= 2e-3 * scale + 4 * abs(d1 - d2), (p, k, g[p, k], d2, d1)
+            checked += 1
+    assert checked >= 80 and checked >= 2 * skipped, (checked, skipped)
+
+
+@pytest.mark.parametrize("metric", ["mse", "rmse", "mae", "logloss"])
+def test_const_grad32_agrees_with_fp64_reverse_mode_on_certified_programs(metric):
+    # Where the FP32 error bound certifies every row of a program to 1e-5
+    # (no protected-operator decision can flip), FP32 rounding moves each
+    # per-row contribution by a few ulps; the sum then differs from the FP64
+    # gradient by far less than 1e-5 of the sum of |contributions| (measured
+    # about 7e-7 at most).  A wrong derivative rule moves it by a fraction of
+    # that sum itself.
+    rng = np.random.default_rng(15)
+    n = 1500
+    X = rng.uniform(-5, 5, size=(2, n)).astype(np.float32)
+    if metric == "logloss":
+        y = (rng.random(n) < 0.4).astype(np.float32)
+    else:
+        y = rng.normal(1.0, 2.0, n).astype(np.float32)
+    w = rng.uniform(0.5, 3.0, n).astype(np.float32)
+    nodes, off = synth.ramped_half_and_half(300, 2, 5, synth.FULL_SET, 2, seed=41, max_consts=16,
+                                            const_range=(-2.0, 2.0))
+    g64, _, gabs = oracle.const_grad(nodes, off, X, y, w, metric, with_abs=True)
+    g32, f32 = oracle.const_grad32(nodes, off, X, y, w, metric)
+    v, e, fl = oracle.predict_bound(nodes, off, X)
+    with np.errstate(invalid="ignore"):
+        cert = np.all((fl == 0) & np.isfinite(v) & (e <= 1e-5 * np.maximum(np.abs(v), 1e-30)),
+                      axis=1)
+    cert &= np.all(np.isfinite(g64), axis=1)
+    assert cert.sum() >= 120
+    # the certified programs cover every function of the set under a constant
+    names = set()
+    for p in np.flatnonzero(cert):
+        seg = nodes["op"][off[p]:off[p + 1]]
+        if (seg == synth.OP["const"]).any():
+            names |= {synth.OP_NAME[int(o)] for o in seg}
+    assert set(synth.FULL_SET) <= names, set(synth.FULL_SET) - names
+    with np.errstate(invalid="ignore"):  # inf - inf outside the certified programs
+        bad = cert[:, None] & (np.abs(g32 - g64) > 1e-5 * gabs + 1e-300)
+    assert not bad.any(), (np.argwhere(bad)[:5], g32[bad][:5], g64[bad][:5])
+    f64 = oracle.fitness(nodes, off, X, y, w, metric)[0]
+    np.testing.assert_allclose(f32[cert], f64[cert], rtol=1e-5)
