@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--no-generation", action="store_true",
                     help="skip the whole-generation (evaluate, select, mutate) timing")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--rows-per-thread", type=int, default=0,
+                    help="evaluator rows per thread (4, 8 or 16; 0: the library's default)")
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="resident evaluator blocks per SM (0: as many as fit)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the step eagerly instead of replaying its CUDA graph")
@@ -390,7 +394,8 @@ def main():
     # CUDA graph on a preallocated workspace and replayed (or launched
     # eagerly with --no-graph); with several ranks the fitness all-gather
     # sits between the two and the step runs eagerly
-    opts = tuned if tuned is not None else gp.make_opts()
+    opts = tuned if tuned is not None else gp.make_opts(rows_per_thread=args.rows_per_thread,
+                                                        blocks_per_sm=args.blocks_per_sm)
     ws_buf = torch.empty(gp.gp_workspace_size(P, N, d.n_feat, opts), dtype=torch.uint8, device=dev)
     used = gp.gp_resolve_opts(P, N, d.n_feat, opts)
 

@@ -216,6 +216,17 @@ int gp_predict(const gp_node *progs, const int32_t *offsets, int n_progs,
                const float *X, int64_t n_rows, int n_feat, float *out_pred,
                void *stream);
 
+/* Predictions as gp_predict, with the evaluator's rows per thread taken
+ * from opts (NULL: the defaults; only rows_per_thread is read, 4 or 8, and
+ * it applies to the programs of the common class -- stack of at most 8
+ * values, no extended function -- the others always run 4 rows per
+ * thread).  Every prediction is the same bits whatever rows_per_thread
+ * says: the per-row operations do not depend on how rows are grouped.
+ * Returns GP_ERR_ARG for bad arguments or opts. */
+int gp_predict_ex(const gp_node *progs, const int32_t *offsets, int n_progs,
+                  const float *X, int64_t n_rows, int n_feat, const gp_eval_opts *opts,
+                  float *out_pred, void *stream);
+
 /* End-to-end variant of gp_evaluate for HOST buffers: progs, offsets, X,
  * y, w (may be NULL) and out_fitness are host pointers (pinned memory is
  * fastest).  Validates the programs on the host first (GP_ERR_PROGRAM,

@@ -1,0 +1,474 @@
+"""Write gp_fast.cuh: the evaluator's indexed-branch fast loop in inline PTX.
+
+The loop runs the compiled instruction words of one program (the format of
+gp_internal.cuh) over RPT rows per lane, RPT = 4 or 8.  A lane's rows are
+held as RPT/2 pairs of 32-bit floats in 64-bit registers, and every
+operation that rounds each row on its own -- add, sub, mul and fma -- runs
+as one packed instruction per pair (add/sub/mul/fma.rn.f32x2: round to
+nearest per element, no flush to zero, so the bits are those of the scalar
+instructions).  Divisions, square roots, reciprocals and the selects of
+the protected operators run per row.  One word is dispatched by one
+indexed branch (brx.idx through a 64-entry table on the low six bits of
+the word).
+
+sin, cos, log and exp transcribe the steps and constants of gp_math.cuh
+(trig_rows, log_pos, exp_fast), so the loop and the C++ fallback give the
+same bits; the constants are written here as the bit patterns that
+gp_math.cuh's static_asserts pin.  Code size matters as much as
+instruction count (at 8 rows per lane an unrolled body per operation
+overflowed the instruction cache: ncu's no_instruction stall rose to 4 per
+issue), so the division forms share two bodies (operands staged in U),
+sin and cos share one, and tan goes to the C++ switch.
+
+Variants: RPT in {4, 8} x DIVS (the division set, square root, reciprocal,
+sin, cos, log and exp run here; without DIVS they are handed back) x
+XREG (columns 0 and 1 held in registers; without it every column read is
+handed back).  A word the loop does not run -- END, the extended
+functions, the trigonometric and exponential arguments outside their fast
+paths, and whatever DIVS or XREG leave out -- is handed back to the
+caller's switch with its constant, the address just past it, and the rows
+untouched.
+
+Run: python paper_2110_11226_gb300/csrc/gen_fast.py  (rewrites gp_fast.cuh)
+"""
+from __future__ import annotations
+
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# op codes (gp_internal.cuh); bit 5 of a column-read word picks column 1
+OPS = dict(PUSH_X=0, PUSH_C=1, PUSH_X_SP=2, PUSH_C_SP=3, ADD_S=4, SUB_S=5, MUL_S=6, DIV_S=7,
+           ADD_X=8, ADD_C=9, SUB_X=10, SUB_C=11, RSUB_X=12, RSUB_C=13, MUL_X=14, MUL_C=15,
+           DIV_X=16, DIV_C=17, RDIV_X=18, RDIV_C=19, SQRT=20, LOG=21, EXP=22, SIN=23, COS=24,
+           TAN=25, ABS=26, NEG=27, INV=28, END=29, EXT1=30, EXT2=31)
+COL1 = 32
+
+# float bit patterns (pinned by static_asserts in gp_math.cuh)
+K = dict(two_over_pi=0x3F22F983, magic=0x4B400000, pio2_hi=0x3FC90FDB, pio2_mid=0xB33BBD2E,
+         pio2_lo=0xA6F72CED, s0=0xBE2AAAAB, s1=0x3C088884, s2=0xB95007C0, s3=0x363668F9,
+         c0=0x3D2AAAAB, c1=0xBAB60B5C, c2=0x37D0086F, c3=0xB4920F4E, trig_fast=0x47800000,
+         lp0=0xBEFFFFFD, lp1=0x3EAAAB7A, lp2=0xBE80024D, lp3=0x3E4C6960, lp4=0xBE29AE98,
+         lp5=0x3E18C293, lp6=0xBE12824F, lp7=0x3DB2E3B9, ln2_hi=0x3F317200, ln2_lo=0x35BFBE8E,
+         e1=0x3F800000, e2=0x3EFFFFFE, e3=0x3E2AAA06, e4=0x3D2AAC20, e5=0x3C09371C,
+         e6=0x3AB57078, log2e=0x3FB8AA3B, exp_fast=0x42AE0000, one=0x3F800000,
+         mhalf=0xBF000000, flt_max=0x7F7FFFFF)
+NEG = 0x80000000
+
+
+def kf(name, neg=False):
+    """a float immediate: 0fXXXXXXXX"""
+    return f"0f{(K[name] ^ (NEG if neg else 0)):08X}"
+
+
+def kp(name, neg=False):
+    """a 64-bit immediate holding the constant in both halves"""
+    b = K[name] ^ (NEG if neg else 0)
+    return f"0x{b:08X}{b:08X}"
+
+
+class Gen:
+    def __init__(self, rpt, divs, xreg):
+        self.rpt, self.divs, self.xreg = rpt, divs, xreg
+        self.np = rpt // 2               # pairs per lane
+        p = self.np
+        self.T = [f"%{1 + i}" for i in range(p)]
+        self.HW, self.HC, self.SB, self.NSM1 = f"%{p + 1}", f"%{p + 2}", f"%{p + 3}", f"%{p + 4}"
+        self.X = [[f"%{p + 5 + i}" for i in range(p)], [f"%{2 * p + 5 + i}" for i in range(p)]]
+        self.THR = f"%{3 * p + 5}"
+        self.slot_bytes = (rpt // 4) * 512
+        self.lines = []
+
+    # -- emission helpers -------------------------------------------------
+    def e(self, s):
+        self.lines.append(s)
+
+    def label(self, name):
+        self.lines.append(f"{name}%=:")
+
+    def nxt(self):
+        self.e("bra.uni N%=;")
+
+    def unpack(self, i, a, b, src=None):
+        self.e(f"mov.b64 {{{a}, {b}}}, {src or self.T[i]};")
+
+    def pack(self, i, a, b, dst=None):
+        self.e(f"mov.b64 {dst or self.T[i]}, {{{a}, {b}}};")
+
+    def slot_addr(self):
+        self.e("bfe.u32 %%a, %%w, 8, 8;")
+        self.e(f"min.u32 %%a, %%a, {self.NSM1};")
+        self.e(f"mad.lo.u32 %%a, %%a, {self.slot_bytes}, {self.SB};")
+
+    def slot_load(self):
+        self.slot_addr()
+        for q in range(self.rpt // 4):
+            off = f"+{512 * q}" if q else ""
+            self.e(f"ld.shared.v2.b64 {{%%U{2 * q}, %%U{2 * q + 1}}}, [%%a{off}];")
+
+    def spill(self):
+        self.slot_addr()
+        for q in range(self.rpt // 4):
+            off = f"+{512 * q}" if q else ""
+            self.e(f"st.shared.v2.b64 [%%a{off}], {{{self.T[2 * q]}, {self.T[2 * q + 1]}}};")
+
+    def cpair(self):
+        self.e("mov.b64 %%C, {%%cf, %%cf};")
+
+    def pairwise(self, op, srcs):
+        """T_i = op(T_i, src_i) or with a callable giving the operands"""
+        for i in range(self.np):
+            a, b = srcs(i)
+            self.e(f"{op}.rn.f32x2 {self.T[i]}, {a}, {b};")
+
+    # protected division of one row: d = |b| < thr ? 1 : a / b
+    def div1(self, d, a, b):
+        self.e(f"div.rn.f32 %%q, {a}, {b};")
+        self.e(f"abs.f32 %%m, {b};")
+        self.e(f"setp.lt.f32 %%p, %%m, {self.THR};")
+        self.e(f"selp.f32 {d}, 0f3F800000, %%q, %%p;")
+
+    def div_body(self, reverse):
+        """the rows divided by (or, reversed, dividing) the operand pairs in U"""
+        for i in range(self.np):
+            self.unpack(i, "%%v0", "%%v1")
+            self.e(f"mov.b64 {{%%u0, %%u1}}, %%U{i};")
+            for v, o in (("%%v0", "%%u0"), ("%%v1", "%%u1")):
+                if reverse:
+                    self.div1(v, o, v)
+                else:
+                    self.div1(v, v, o)
+            self.pack(i, "%%v0", "%%v1")
+
+    # a warp-wide test of every row before any row changes: bra EX if any
+    # row has |t| >= bound or is NaN
+    def range_check(self, bound):
+        self.e("setp.ne.u32 %%ps, 0, 0;")
+        for i in range(self.np):
+            self.unpack(i, "%%v0", "%%v1")
+            for v in ("%%v0", "%%v1"):
+                self.e(f"abs.f32 %%m, {v};")
+                self.e(f"setp.geu.f32 %%p, %%m, {kf(bound)};")
+                self.e("or.pred %%ps, %%ps, %%p;")
+        self.e("vote.sync.any.pred %%ps, %%ps, 0xffffffff;")
+        self.e("@%%ps bra EX%=;")
+
+    # sin or cos of every row (the steps of trig_rows): one body for both,
+    # the kind (0 sin, 1 cos) from the dispatch index
+    def trig(self):
+        self.range_check("trig_fast")
+        self.e(f"sub.u32 %%kd, %%i, {OPS['SIN']};")
+        for i in range(self.np):
+            t = self.T[i]
+            self.e(f"mov.b64 %%K0, {kp('two_over_pi')};")
+            self.e(f"mov.b64 %%K1, {kp('magic')};")
+            self.e(f"fma.rn.f32x2 %%JM, {t}, %%K0, %%K1;")
+            self.e("sub.rn.f32x2 %%JJ, %%JM, %%K1;")
+            # r = x - j (HI + MID + LO): fma(j, -HI, x) is fma(-j, HI, x) bit for bit
+            self.e(f"mov.b64 %%K0, {kp('pio2_hi', True)};")
+            self.e(f"fma.rn.f32x2 %%R, %%JJ, %%K0, {t};")
+            self.e(f"mov.b64 %%K0, {kp('pio2_mid', True)};")
+            self.e("fma.rn.f32x2 %%R, %%JJ, %%K0, %%R;")
+            self.e(f"mov.b64 %%K0, {kp('pio2_lo', True)};")
+            self.e("fma.rn.f32x2 %%R, %%JJ, %%K0, %%R;")
+            self.e("mul.rn.f32x2 %%S, %%R, %%R;")
+            # sin r = r + (s r)(S0 + s (S1 + s (S2 + s S3)))
+            self.e(f"mov.b64 %%K0, {kp('s3')};")
+            self.e(f"mov.b64 %%K1, {kp('s2')};")
+            self.e("fma.rn.f32x2 %%P, %%K0, %%S, %%K1;")
+            for c in ("s1", "s0"):
+                self.e(f"mov.b64 %%K0, {kp(c)};")
+                self.e("fma.rn.f32x2 %%P, %%P, %%S, %%K0;")
+            self.e("mul.rn.f32x2 %%Q, %%S, %%R;")
+            self.e("fma.rn.f32x2 %%P, %%P, %%Q, %%R;")
+            # cos r = 1 + s (-1/2 + s (C0 + s (C1 + s (C2 + s C3))))
+            self.e(f"mov.b64 %%K0, {kp('c3')};")
+            self.e(f"mov.b64 %%K1, {kp('c2')};")
+            self.e("fma.rn.f32x2 %%Q, %%K0, %%S, %%K1;")
+            for c in ("c1", "c0", "mhalf", "one"):
+                self.e(f"mov.b64 %%K0, {kp(c)};")
+                self.e("fma.rn.f32x2 %%Q, %%Q, %%S, %%K0;")
+            self.unpack(i, "%%n0", "%%n1", "%%JM")   # quadrant words
+            self.unpack(i, "%%s0", "%%s1", "%%P")    # sin r
+            self.unpack(i, "%%c0", "%%c1", "%%Q")    # cos r
+            for r in (0, 1):
+                # a = ((q + kind) & 1) ? cos : sin; negated (sign bit flipped)
+                # when (q + kind) & 2
+                n, sn, cn, v = f"%%n{r}", f"%%s{r}", f"%%c{r}", f"%%v{r}"
+                self.e(f"add.u32 {n}, {n}, %%kd;")
+                self.e(f"and.b32 %%a, {n}, 1;")
+                self.e("setp.ne.u32 %%p, %%a, 0;")
+                self.e(f"selp.f32 %%q, {cn}, {sn}, %%p;")
+                self.e(f"shl.b32 {n}, {n}, 30;")
+                self.e(f"and.b32 {n}, {n}, 0x80000000;")
+                self.e(f"mov.b32 %%a, %%q;")
+                self.e(f"xor.b32 %%a, %%a, {n};")
+                self.e(f"mov.b32 {v}, %%a;")
+            self.pack(i, "%%v0", "%%v1")
+
+    # log of every row (f_log: the logarithm of max(|t|, thr), 0 below the
+    # threshold, inf and NaN passed through)
+    def log(self):
+        for i in range(self.np):
+            self.unpack(i, "%%v0", "%%v1")
+            for r in (0, 1):
+                v, b, n, m, k = f"%%v{r}", f"%%u{r}", f"%%n{r}", f"%%m{r}", f"%%k{r}"
+                self.e(f"abs.f32 {b}, {v};")
+                self.e(f"max.f32 %%q, {b}, {self.THR};")
+                self.e(f"mov.b32 {n}, %%q;")
+                self.e(f"sub.u32 {k}, {n}, 0x3F3504F3;")
+                self.e(f"shr.s32 {k}, {k}, 23;")
+                self.e(f"mad.lo.u32 {m}, {k}, 0xFF800000, {n};")   # bits of m = i - (k << 23)
+                self.e(f"add.u32 {k}, {k}, 0x4B400000;")           # bits of 1.5 * 2^23 + k
+            self.e("mov.b64 %%F, {%%m0, %%m1};")
+            self.e("mov.b64 %%JM, {%%k0, %%k1};")
+            self.e(f"mov.b64 %%K0, {kp('one')};")
+            self.e("sub.rn.f32x2 %%F, %%F, %%K0;")                # f = m - 1
+            self.e(f"mov.b64 %%K1, {kp('magic')};")
+            self.e("sub.rn.f32x2 %%JJ, %%JM, %%K1;")              # k as a float
+            self.e(f"mov.b64 %%K0, {kp('lp7')};")
+            self.e(f"mov.b64 %%K1, {kp('lp6')};")
+            self.e("fma.rn.f32x2 %%P, %%K0, %%F, %%K1;")
+            for c in ("lp5", "lp4", "lp3", "lp2", "lp1", "lp0"):
+                self.e(f"mov.b64 %%K0, {kp(c)};")
+                self.e("fma.rn.f32x2 %%P, %%P, %%F, %%K0;")
+            self.e("mul.rn.f32x2 %%S, %%F, %%F;")
+            self.e("fma.rn.f32x2 %%R, %%S, %%P, %%F;")
+            self.e(f"mov.b64 %%K0, {kp('ln2_lo')};")
+            self.e("fma.rn.f32x2 %%R, %%JJ, %%K0, %%R;")
+            self.e(f"mov.b64 %%K0, {kp('ln2_hi')};")
+            self.e("fma.rn.f32x2 %%R, %%JJ, %%K0, %%R;")
+            self.unpack(i, "%%s0", "%%s1", "%%R")
+            for r in (0, 1):
+                v, b, s = f"%%v{r}", f"%%u{r}", f"%%s{r}"
+                # b < thr ? 0 : (b <= FLT_MAX ? log : b)
+                self.e(f"setp.le.f32 %%p, {b}, {kf('flt_max')};")
+                self.e(f"selp.f32 {v}, {s}, {b}, %%p;")
+                self.e(f"setp.lt.f32 %%p, {b}, {self.THR};")
+                self.e(f"selp.f32 {v}, 0f00000000, {v}, %%p;")
+            self.pack(i, "%%v0", "%%v1")
+
+    # exp of every row when all |t| < 87 (exp_fast), else handed back
+    def exp(self):
+        self.range_check("exp_fast")
+        for i in range(self.np):
+            t = self.T[i]
+            self.e(f"mov.b64 %%K0, {kp('log2e')};")
+            self.e(f"mov.b64 %%K1, {kp('magic')};")
+            self.e(f"fma.rn.f32x2 %%JM, {t}, %%K0, %%K1;")
+            self.e("sub.rn.f32x2 %%JJ, %%JM, %%K1;")
+            self.e(f"mov.b64 %%K0, {kp('ln2_hi', True)};")
+            self.e(f"fma.rn.f32x2 %%R, %%JJ, %%K0, {t};")
+            self.e(f"mov.b64 %%K0, {kp('ln2_lo', True)};")
+            self.e("fma.rn.f32x2 %%R, %%JJ, %%K0, %%R;")
+            self.e(f"mov.b64 %%K0, {kp('e6')};")
+            self.e(f"mov.b64 %%K1, {kp('e5')};")
+            self.e("fma.rn.f32x2 %%P, %%K0, %%R, %%K1;")
+            for c in ("e4", "e3", "e2", "e1", "one"):
+                self.e(f"mov.b64 %%K0, {kp(c)};")
+                self.e("fma.rn.f32x2 %%P, %%P, %%R, %%K0;")
+            self.unpack(i, "%%n0", "%%n1", "%%JM")
+            for r in (0, 1):
+                # 2^j: the low bits of the rounded sum are j, shifted into the exponent
+                self.e(f"mad.lo.u32 %%n{r}, %%n{r}, 8388608, 0x3F800000;")
+            self.e("mov.b64 %%S, {%%n0, %%n1};")
+            self.e(f"mul.rn.f32x2 {t}, %%P, %%S;")
+
+    # -- the loop -----------------------------------------------------------
+    def table(self):
+        """64 branch targets; a label names one body (ops sharing a body say so
+        by sharing its label, and no two different bodies share a label)"""
+        ent = ["EX"] * 64
+        base = dict(PUSH_C="PC", PUSH_C_SP="PCS", ADD_S="AS", SUB_S="SS", MUL_S="MS",
+                    ADD_C="AC", SUB_C="SC", RSUB_C="RC", MUL_C="MC", ABS="AB", NEG="NG")
+        for k, v in base.items():
+            ent[OPS[k]] = v
+        if self.divs:
+            for k, v in dict(DIV_S="DS", DIV_C="DC", RDIV_C="RDC", SQRT="SQ", INV="IV",
+                             SIN="TRG", COS="TRG", LOG="LG", EXP="XP").items():
+                ent[OPS[k]] = v
+        if self.xreg:
+            xops = dict(PUSH_X="PX", PUSH_X_SP="PXS", ADD_X="AX", SUB_X="SX", RSUB_X="RX",
+                        MUL_X="MX")
+            if self.divs:
+                xops.update(DIV_X="DX", RDIV_X="RDX")
+            for k, v in xops.items():
+                ent[OPS[k]] = v + "0"
+                ent[OPS[k] | COL1] = v + "1"
+        owner = {}
+        for op, lab in enumerate(ent):
+            base = op & (COL1 - 1)
+            if lab == "EX":
+                continue
+            kind = {OPS["SIN"]: "trig", OPS["COS"]: "trig"}.get(base, base)
+            assert owner.setdefault(lab, kind) == kind, f"label {lab} names two bodies"
+        return ent
+
+    def generate(self):
+        p = self.np
+        ent = self.table()
+        used = sorted(set(ent) - {"EX"})
+        e = self.e
+        e("{")
+        e(".reg .pred %%p, %%ps;")
+        e(".reg .b32 %%w, %%cb, %%i, %%a, %%kd, %%n<2>, %%m<2>, %%k<2>;")
+        e(".reg .f32 %%cf, %%q, %%m, %%v<2>, %%u<2>, %%s<2>, %%c<2>;")
+        e(f".reg .b64 %%C, %%U<{p}>, %%K<2>, %%JM, %%JJ, %%R, %%S, %%P, %%Q, %%F;")
+        e("T%=: .branchtargets " + ", ".join(f"{x}%=" for x in ent) + ";")
+        self.label("N")
+        e("ld.shared.v2.b32 {%%w, %%cb}, [%0];")
+        e("mov.b32 %%cf, %%cb;")
+        e("add.u32 %0, %0, 8;")
+        e("and.b32 %%i, %%w, 63;")
+        e("brx.idx.uni %%i, T%=;")
+        X = self.X
+        for name in used:
+            self.label(name)
+            col = int(name[-1]) if name[-1] in "01" and name not in ("PC",) else None
+            stem = name[:-1] if col is not None else name
+            if stem == "PX" or stem == "PXS":
+                if stem == "PXS":
+                    self.spill()
+                for i in range(p):
+                    e(f"mov.b64 {self.T[i]}, {X[col][i]};")
+            elif stem in ("PC", "PCS"):
+                if stem == "PCS":
+                    self.spill()
+                self.cpair()
+                for i in range(p):
+                    e(f"mov.b64 {self.T[i]}, %%C;")
+            elif stem in ("AS", "SS", "MS"):
+                self.slot_load()
+                op = dict(AS="add", SS="sub", MS="mul")[stem]
+                self.pairwise(op, lambda i: (self.T[i], f"%%U{i}"))
+            elif stem in ("AX", "SX", "MX"):
+                op = dict(AX="add", SX="sub", MX="mul")[stem]
+                self.pairwise(op, lambda i, c=col: (self.T[i], X[c][i]))
+            elif stem == "RX":
+                self.pairwise("sub", lambda i, c=col: (X[c][i], self.T[i]))
+            elif stem in ("AC", "SC", "MC"):
+                self.cpair()
+                op = dict(AC="add", SC="sub", MC="mul")[stem]
+                self.pairwise(op, lambda i: (self.T[i], "%%C"))
+            elif stem == "RC":
+                self.cpair()
+                self.pairwise("sub", lambda i: ("%%C", self.T[i]))
+            elif stem == "AB" or stem == "NG":
+                op = "abs" if stem == "AB" else "neg"
+                for i in range(p):
+                    self.unpack(i, "%%v0", "%%v1")
+                    e(f"{op}.f32 %%v0, %%v0;")
+                    e(f"{op}.f32 %%v1, %%v1;")
+                    self.pack(i, "%%v0", "%%v1")
+            elif stem == "DS":
+                # the divisor pairs into U, then the shared body
+                self.slot_load()
+                e("bra.uni DTU%=;")
+                continue
+            elif stem in ("DC", "RDC"):
+                self.cpair()
+                for i in range(p):
+                    e(f"mov.b64 %%U{i}, %%C;")
+                e("bra.uni DTU%=;" if stem == "DC" else "bra.uni DUT%=;")
+                continue
+            elif stem in ("DX", "RDX"):
+                for i in range(p):
+                    e(f"mov.b64 %%U{i}, {X[col][i]};")
+                e("bra.uni DTU%=;" if stem == "DX" else "bra.uni DUT%=;")
+                continue
+            elif stem == "SQ":
+                for i in range(p):
+                    self.unpack(i, "%%v0", "%%v1")
+                    for v in ("%%v0", "%%v1"):
+                        e(f"abs.f32 {v}, {v};")
+                        e(f"sqrt.rn.f32 {v}, {v};")
+                    self.pack(i, "%%v0", "%%v1")
+            elif stem == "IV":
+                # |t| < thr ? 0 : 1 / t
+                for i in range(p):
+                    self.unpack(i, "%%v0", "%%v1")
+                    for v in ("%%v0", "%%v1"):
+                        e(f"rcp.rn.f32 %%q, {v};")
+                        e(f"abs.f32 %%m, {v};")
+                        e(f"setp.lt.f32 %%p, %%m, {self.THR};")
+                        e(f"selp.f32 {v}, 0f00000000, %%q, %%p;")
+                    self.pack(i, "%%v0", "%%v1")
+            elif stem == "TRG":
+                self.trig()
+            elif stem == "LG":
+                self.log()
+            elif stem == "XP":
+                self.exp()
+            else:
+                raise ValueError(name)
+            self.nxt()
+        if self.divs:
+            # t = t / u and t = u / t with the protection, the operands in U
+            self.label("DTU")
+            self.div_body(False)
+            self.nxt()
+            self.label("DUT")
+            self.div_body(True)
+            self.nxt()
+        self.label("EX")
+        e(f"mov.b32 {self.HW}, %%w;")
+        e(f"mov.f32 {self.HC}, %%cf;")
+        e("}")
+        return self.lines
+
+
+
+def function(rpt, divs, xreg):
+    g = Gen(rpt, divs, xreg)
+    lines = g.generate()
+    p = rpt // 2
+    name = f"fast_r{rpt}_{'divs' if divs else 'nodivs'}_{'x' if xreg else 'nox'}"
+    body = "\n".join(f'        "{ln}\\n\\t"' for ln in lines)
+    outs = ", ".join(['"+r"(pa)'] + [f'"+l"(t[{i}])' for i in range(p)] + ['"=r"(hw)', '"=f"(hc)'])
+    ins = ", ".join(['"r"(sb)', '"n"(NSLOT - 1)'] + [f'"l"(x0[{i}])' for i in range(p)]
+                    + [f'"l"(x1[{i}])' for i in range(p)] + ['"f"(kThr)'])
+    return (f"template <int NSLOT>\n"
+            f"__device__ __forceinline__ void {name}(uint32_t &pa, uint64_t (&t)[{p}],\n"
+            f"        const uint64_t (&x0)[{p}], const uint64_t (&x1)[{p}], uint32_t sb,\n"
+            f"        uint32_t &hw, float &hc) {{\n"
+            f"    asm volatile(\n{body}\n"
+            f"        : {outs}\n"
+            f"        : {ins}\n"
+            f"        : \"memory\");\n}}\n")
+
+
+HEADER = '''// gp_fast.cuh -- the evaluator's indexed-branch fast loop in inline PTX.
+// GENERATED by gen_fast.py (same directory); edit that script, not this file.
+//
+// fast_r<RPT>_<divs|nodivs>_<x|nox><NSLOT>(pa, t, x0, x1, sb, hw, hc) runs
+// compiled instruction words from the shared-memory address pa over RPT
+// rows per lane, held as RPT/2 pairs {row 2i, row 2i+1} in t.  It stops at
+// the first word it does not run, returns that word and its constant in
+// hw and hc, leaves pa just past it and the rows untouched by it.  sb is
+// the lane's slot-0 address in the shared-memory stack ([slot][q][lane]
+// float4); slots are clamped to NSLOT - 1; x0 and x1 hold columns 0 and 1
+// of the lane's rows (read only by the _x variants).  Every one of the 64
+// values of the six-bit dispatch index has a table entry.
+#pragma once
+
+#include <cstdint>
+
+namespace gpk {
+
+'''
+
+
+def main():
+    parts = [HEADER]
+    for rpt in (4, 8):
+        for divs in (True, False):
+            for xreg in (True, False):
+                parts.append(function(rpt, divs, xreg))
+                parts.append("\n")
+    parts.append("}  // namespace gpk\n")
+    with open(os.path.join(HERE, "gp_fast.cuh"), "w") as f:
+        f.write("".join(parts))
+
+
+if __name__ == "__main__":
+    main()

@@ -189,9 +189,12 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
     return GP_OK;
 }
 
-int eval_info(int rpt, int fmode, int cls, int block, int *regs, bool mom = false) {
+int eval_info(int rpt, int fmode, int cls, int block, int *regs, bool mom = false,
+              bool pred = false) {
     if (rpt == 4) return fmode == 2 ? info_eval_r4_f2(cls, block, regs, mom) : info_eval_r4_f0(cls, block, regs, mom);
-    if (rpt == 8) return fmode == 2 ? info_eval_r8_f2(cls, block, regs, mom) : info_eval_r8_f0(cls, block, regs, mom);
+    if (rpt == 8)
+        return fmode == 2 ? info_eval_r8_f2(cls, block, regs, mom, pred)
+                          : info_eval_r8_f0(cls, block, regs, mom, pred);
     return fmode == 2 ? info_eval_r16_f2(cls, block, regs, mom) : info_eval_r16_f0(cls, block, regs, mom);
 }
 
@@ -325,7 +328,7 @@ int validate_one_host(const gp_node *p, int len, int n_feat, int *hw_out) {
 // predictions of programs [p0, p0 + b) whose compiled code and metadata
 // are already in W (indexed by program id) into pred [b][n_rows]
 int run_predict_compiled(const Workspace &W, int p0, int b, const float *X, int64_t n_rows,
-                         int n_feat, float *out_pred, DevCtx *c, cudaStream_t st) {
+                         int n_feat, float *out_pred, DevCtx *c, cudaStream_t st, int rpt = 4) {
     const int64_t chunk = std::min<int64_t>(round_up(n_rows, 256), 4096);
     const int n_chunks = (int)((n_rows + chunk - 1) / chunk);
     GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
@@ -350,6 +353,12 @@ int run_predict_compiled(const Workspace &W, int p0, int b, const float *X, int6
         ea.pred = out_pred;
         ea.dev_status = c->status;
         ea.vec_ok = vec ? 1 : 0;
+        if (cls == kClassShallow && rpt == 8) {
+            // the class-0 instance at 8 rows per thread (its store epilogue)
+            const int occ = eval_info(8, fmode, cls, kEvalBlockThreads, nullptr, false, true);
+            GP_CUDA(eval_launch(ea, 8, fmode, c->sms * std::max(occ, 1), kEvalBlockThreads, st));
+            continue;
+        }
         const int occ = fmode == 2 ? info_predict_f2(cls, kEvalBlockThreads, nullptr)
                                    : info_predict(cls, kEvalBlockThreads, nullptr);
         const int grid = c->sms * std::max(occ, 1);
@@ -379,11 +388,11 @@ int compile_all(const gp_node *progs, const int32_t *offsets, int n_progs, int n
 // every program's value on every row into pred [n_progs][n_rows]
 int run_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
                 int64_t n_rows, int n_feat, float *out_pred, int32_t *out_status, DevCtx *c,
-                cudaStream_t st) {
+                cudaStream_t st, int rpt = 4) {
     Workspace W;
     int rc = compile_all(progs, offsets, n_progs, n_feat, out_status, c, &W, st);
     if (rc) return rc;
-    return run_predict_compiled(W, 0, n_progs, X, n_rows, n_feat, out_pred, c, st);
+    return run_predict_compiled(W, 0, n_progs, X, n_rows, n_feat, out_pred, c, st, rpt);
 }
 
 // Spearman: the target's ranks once, then batches of programs predicted
@@ -564,6 +573,20 @@ int gp_predict(const gp_node *progs, const int32_t *offsets, int n_progs, const 
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
     return run_predict(progs, offsets, n_progs, X, n_rows, n_feat, out_pred, nullptr, c, S(stream));
+}
+
+int gp_predict_ex(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
+                  int64_t n_rows, int n_feat, const gp_eval_opts *opts, float *out_pred,
+                  void *stream) {
+    int rc = check_common(progs, offsets, n_progs, X, n_rows, n_feat);
+    if (rc) return rc;
+    if (!out_pred) return GP_ERR_ARG;
+    const int rpt = opts && opts->rows_per_thread ? opts->rows_per_thread : 4;
+    if (rpt != 4 && rpt != 8) return GP_ERR_ARG;
+    DevCtx *c = nullptr;
+    if ((rc = ctx_of_current(&c))) return rc;
+    return run_predict(progs, offsets, n_progs, X, n_rows, n_feat, out_pred, nullptr, c,
+                       S(stream), rpt);
 }
 
 int gp_validate_host(const gp_node *progs, const int32_t *offsets, int n_progs, int n_feat,

@@ -260,24 +260,25 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
             if (mode[j]) continue;  // folded into its parent
             const bool x = nd.op == GP_VAR;
             const bool spill = sp > 0;  // the old top goes to slot sp-1
-            const uint32_t op = spill ? (x ? OP_PUSH_X_SP : OP_PUSH_C_SP) : (x ? OP_PUSH_X : OP_PUSH_C);
+            const uint32_t op = (spill ? (x ? OP_PUSH_X_SP : OP_PUSH_C_SP) : (x ? OP_PUSH_X : OP_PUSH_C)) |
+                                ((x && nd.feat == 1) ? kOpCol1 : 0u);
             out[n++] = make_uint2(make_ins(op, spill ? sp - 1 : 0, (uint32_t)(uint16_t)nd.feat),
                                   __float_as_uint(nd.c));
             ++sp;
         } else if (ar == 1) {
-            const uint32_t uop = nd.op <= GP_INV ? OP_SQRT + (nd.op - GP_SQRT)
-                                                 : OP_EXT1 | ((uint32_t)(nd.op - GP_SQ) << 5);
-            ext |= nd.op > GP_INV;
-            out[n++] = make_uint2(make_ins(uop, 0, 0), 0u);
+            const bool e = nd.op > GP_INV;  // extended function: its number in the feature field
+            ext |= e;
+            out[n++] = make_uint2(e ? make_ins(OP_EXT1, 0, (uint32_t)(nd.op - GP_SQ))
+                                    : make_ins(OP_SQRT + (nd.op - GP_SQRT), 0, 0),
+                                  0u);
         } else {
             // add, sub, mul, div, max, min
             const int b = nd.op <= GP_DIV ? nd.op - GP_ADD : 4 + (nd.op - GP_MAX);
             if (mode[j] == 0) {
                 // right operand in slot sp-2, left operand is t
-                const uint32_t ops[6] = {OP_ADD_S, OP_SUB_S, OP_MUL_S, OP_DIV_S,
-                                         OP_EXT2 | (EXT_MAX << 5), OP_EXT2 | (EXT_MIN << 5)};
+                const uint32_t ops[6] = {OP_ADD_S, OP_SUB_S, OP_MUL_S, OP_DIV_S, OP_EXT2, OP_EXT2};
                 ext |= b >= 4;
-                out[n++] = make_uint2(make_ins(ops[b], sp - 2, 0), 0u);
+                out[n++] = make_uint2(make_ins(ops[b], sp - 2, b >= 4 ? (uint32_t)(b - 4) : 0u), 0u);
                 --sp;
             } else {
                 const int tj = (mode[j] == 1) ? j + 1 + size[j + 1] : j + 1;
@@ -291,7 +292,8 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
                 // right terminal: t = op(t, u); left terminal: t = op(u, t)
                 const uint32_t fwd[4] = {OP_ADD_X, OP_SUB_X, OP_MUL_X, OP_DIV_X};
                 const uint32_t rev[4] = {OP_ADD_X, OP_RSUB_X, OP_MUL_X, OP_RDIV_X};
-                const uint32_t op = ((mode[j] == 1) ? fwd[b] : rev[b]) + x;
+                const uint32_t op = (((mode[j] == 1) ? fwd[b] : rev[b]) + x) |
+                                    ((x == 0 && t.feat == 1) ? kOpCol1 : 0u);
                 out[n++] = make_uint2(make_ins(op, 0, (uint32_t)(uint16_t)t.feat),
                                       __float_as_uint(t.c));
             }

@@ -36,8 +36,11 @@ constexpr int kEvalBlockThreads = 256;  // threads per block of the evaluator
 constexpr int kDeepSlots = GP_MAX_STACK - 1;  // s[0..18]
 constexpr float kThr = 0.001f;     // protected-operator threshold
 
-// instruction word x: op in bits 0-4, extended function in bits 5-7,
-// stack slot in bits 8-15, feature index in bits 16-31; word y: the constant
+// instruction word x: op in bits 0-4; bit 5 set on a column read of
+// column 1 (the fast loop's dispatch index is bits 0-5, so with the two
+// columns held in registers each column has its own table entry); stack
+// slot in bits 8-15; feature index (column reads) or extended function
+// number (EXT1, EXT2) in bits 16-31.  Word y: the constant.
 enum : uint32_t {
     OP_PUSH_X = 0, OP_PUSH_C = 1, OP_PUSH_X_SP = 2, OP_PUSH_C_SP = 3,
     OP_ADD_S = 4, OP_SUB_S = 5, OP_MUL_S = 6, OP_DIV_S = 7,
@@ -47,10 +50,11 @@ enum : uint32_t {
     OP_SQRT = 20, OP_LOG = 21, OP_EXP = 22, OP_SIN = 23, OP_COS = 24,
     OP_TAN = 25, OP_ABS = 26, OP_NEG = 27, OP_INV = 28, OP_END = 29,
     // the extended function set behind two entries, the function in bits
-    // 5-7: EXT1 unary (sq, cube, cbrt, tanh, atan, sinh, cosh), EXT2 binary
-    // (max, min; the right operand always in a stack slot)
+    // 16-18: EXT1 unary (sq, cube, cbrt, tanh, atan, sinh, cosh), EXT2
+    // binary (max, min; the right operand always in a stack slot)
     OP_EXT1 = 30, OP_EXT2 = 31
 };
+constexpr uint32_t kOpCol1 = 32;  // bit 5: a column read of column 1
 enum : uint32_t { EXT_SQ = 0, EXT_CUBE, EXT_CBRT, EXT_TANH, EXT_ATAN, EXT_SINH, EXT_COSH };
 enum : uint32_t { EXT_MAX = 0, EXT_MIN = 1 };
 
@@ -200,11 +204,14 @@ struct EvalArgs {
     int info_eval_r##R##_f##F(int cls, int block, int *regs, bool moments);
 GP_EVAL_INSTANCE(4, 2)
 GP_EVAL_INSTANCE(4, 0)
-GP_EVAL_INSTANCE(8, 2)
-GP_EVAL_INSTANCE(8, 0)
 GP_EVAL_INSTANCE(16, 2)
 GP_EVAL_INSTANCE(16, 0)
 #undef GP_EVAL_INSTANCE
+// 8 rows per thread: class 0 only, with the store epilogue too (pred)
+cudaError_t launch_eval_r8_f2(const EvalArgs &a, int grid, int block, cudaStream_t st);
+int info_eval_r8_f2(int cls, int block, int *regs, bool moments, bool pred = false);
+cudaError_t launch_eval_r8_f0(const EvalArgs &a, int grid, int block, cudaStream_t st);
+int info_eval_r8_f0(int cls, int block, int *regs, bool moments, bool pred = false);
 cudaError_t launch_predict(const EvalArgs &a, int grid, int block,
                            cudaStream_t st);
 int info_predict(int cls, int block, int *regs);

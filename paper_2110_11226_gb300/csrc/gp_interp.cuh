@@ -36,6 +36,7 @@
 
 #include "gp_internal.cuh"
 #include "gp_math.cuh"
+#include "gp_fast.cuh"
 
 namespace gpk {
 
@@ -57,13 +58,15 @@ __device__ __forceinline__ float f_div(float a, float b) {
 }
 __device__ __forceinline__ float f_sqrt(float a) { return __fsqrt_rn(fabsf(a)); }
 __device__ __forceinline__ float f_log(float a) {
-    // logf sees an argument >= thr, which spares it its tiny-argument
-    // paths; NaN, for which both tests fail, is passed through
+    // the logarithm sees max(|a|, thr); inf and NaN, for which both tests
+    // fail, are passed through
     const float b = fabsf(a);
-    const float l = logf(fmaxf(b, kThr));
-    return b >= kThr ? l : (b < kThr ? 0.0f : b);
+    const float l = log_pos(fmaxf(b, kThr));
+    return b < kThr ? 0.0f : (b <= 3.40282347e38f ? l : b);
 }
-__device__ __forceinline__ float f_exp(float a) { return expf(a); }
+__device__ __forceinline__ float f_exp(float a) {
+    return fabsf(a) < kExpFast ? exp_fast(a) : expf(a);
+}
 __device__ __forceinline__ float f_abs(float a) { return fabsf(a); }
 __device__ __forceinline__ float f_neg(float a) { return -a; }
 __device__ __forceinline__ float f_inv(float a) {
@@ -131,282 +134,47 @@ static __device__ __noinline__ float4 ext_rows4(float4 v, uint32_t f) {
 // The compiler lowers the dispatch switch to a tree of compares and
 // branches (about 12 instructions per dispatch, measured with ncu's
 // per-opcode counts); PTX's brx.idx jumps through a table instead (about
-// 3).  This loop, 4 rows per lane, runs the operations whose evaluator
-// semantics PTX states directly:
-//   * pushes and stack moves, abs and neg, and IEEE adds, subtracts and
-//     multiplies with every operand form (add/sub/mul.rn.f32, the
-//     instructions behind __fadd_rn, __fsub_rn and __fmul_rn);
-//   * column reads when columns 0 and 1 are held in registers (XREG);
-//   * with DIVS, the protected divisions, square root and reciprocal
-//     (div/sqrt/rcp.rn.f32, as __fdiv_rn, __fsqrt_rn and __frcp_rn, all
-//     without flush to zero, then the protection selects) and sin, cos and
-//     tan (the steps and constants of trig_rows, transcribed).
-// It stops at the first word it does not run (OP_END, log, exp, the
-// extended functions, trigonometric arguments outside the fast path, and
-// whatever XREG or DIVS leave out), hands that word and its constant back
-// to the caller's switch and leaves pa just past it.  Every one of the 32
-// values of the 5-bit op field has a table entry, so the index is always
-// in range; stack slots are clamped like the switch's.
-// Measured on Pagie-1 16M x 4096: 465 ms -> 420 ms per evaluation, 390 ms
-// with the trigonometry; the 28-column table, its column reads handed
-// back, 119 ms -> 112 ms.  DIVS is off in the instances with the extended
-// functions: there it cost the extended-set population 23% (their
-// out-of-line calls and the division's own slow-path call do not mix
-// well).  Loading the next word while the current one runs cost 3%.
-//
-// the op tables: with DIVS the division set (7 DIV_S .. 19 RDIV_C, 20 SQRT,
-// 28 INV) and trigonometry (23 SIN .. 25 TAN) run here, otherwise they are
-// handed back
-#define GP_FAST_TABLE_DIVS                                                        \
-    "T%=: .branchtargets PX%=, PC%=, PXS%=, PCS%=, AS%=, SS%=, MS%=, DS%=,"       \
-    " AX%=, AC%=, SX%=, SC%=, RX%=, RC%=, MX%=, MC%=, DX%=, DC%=, RDX%=, RDC%=,"  \
-    " SQ%=, EX%=, EX%=, TSC%=, TSC%=, TTN%=, AB%=, NG%=, IV%=, EX%=, EX%=, EX%=;\n\t"
-#define GP_FAST_TABLE_NODIVS                                                      \
-    "T%=: .branchtargets PX%=, PC%=, PXS%=, PCS%=, AS%=, SS%=, MS%=, EX%=,"       \
-    " AX%=, AC%=, SX%=, SC%=, RX%=, RC%=, MX%=, MC%=, EX%=, EX%=, EX%=, EX%=,"    \
-    " EX%=, EX%=, EX%=, EX%=, EX%=, EX%=, AB%=, NG%=, EX%=, EX%=, EX%=, EX%=;\n\t"
-// without columns in registers (more than 2 features) the column reads
-// (PUSH_X, PUSH_X_SP and the _X forms) are handed back too
-#define GP_FAST_TABLE_DIVS_NOX                                                    \
-    "T%=: .branchtargets EX%=, PC%=, EX%=, PCS%=, AS%=, SS%=, MS%=, DS%=,"        \
-    " EX%=, AC%=, EX%=, SC%=, EX%=, RC%=, EX%=, MC%=, EX%=, DC%=, EX%=, RDC%=,"   \
-    " SQ%=, EX%=, EX%=, TSC%=, TSC%=, TTN%=, AB%=, NG%=, IV%=, EX%=, EX%=, EX%=;\n\t"
-#define GP_FAST_TABLE_NODIVS_NOX                                                  \
-    "T%=: .branchtargets EX%=, PC%=, EX%=, PCS%=, AS%=, SS%=, MS%=, EX%=,"        \
-    " EX%=, AC%=, EX%=, SC%=, EX%=, RC%=, EX%=, MC%=, EX%=, EX%=, EX%=, EX%=,"    \
-    " EX%=, EX%=, EX%=, EX%=, EX%=, EX%=, AB%=, NG%=, EX%=, EX%=, EX%=, EX%=;\n\t"
-#define GP_FAST_LOOP_TOP                                                          \
-    "N%=:\n\t"                                                                    \
-    "ld.shared.v2.b32 {%%w, %%cb}, [%0];\n\t"                                     \
-    "mov.b32 %%cf, %%cb;\n\t"                                                     \
-    "add.u32 %0, %0, 8;\n\t"                                                      \
-    "and.b32 %%i, %%w, 31;\n\t"                                                   \
-    "brx.idx.uni %%i, T%=;\n\t"
-#define GP_FAST_HEAD(TABLE)                                                       \
-    "{\n\t"                                                                       \
-    ".reg .pred %%p;\n\t"                                                         \
-    ".reg .b32 %%w, %%cb, %%i, %%a, %%f;\n\t"                                     \
-    ".reg .f32 %%cf, %%u0, %%u1, %%u2, %%u3, %%q, %%m;\n\t"                       \
-    TABLE GP_FAST_LOOP_TOP
-// slot address: sb + min(slot, NSLOT - 1) * 512 (one float4 per lane, 32 lanes)
-#define GP_FAST_SLOT                                                              \
-    "bfe.u32 %%a, %%w, 8, 8;\n\t"                                                 \
-    "min.u32 %%a, %%a, %8;\n\t"                                                   \
-    "mad.lo.u32 %%a, %%a, 512, %7;\n\t"
-#define GP_FAST_SPILL GP_FAST_SLOT "st.shared.v4.f32 [%%a], {%1, %2, %3, %4};\n\t"
-#define GP_FAST_SLOTLOAD GP_FAST_SLOT "ld.shared.v4.f32 {%%u0, %%u1, %%u2, %%u3}, [%%a];\n\t"
-// columns 0 and 1 in registers (x1 when the feature is not 0)
-#define GP_FAST_X(D0, D1, D2, D3)                                                 \
-    "shr.b32 %%f, %%w, 16;\n\t"                                                   \
-    "setp.ne.u32 %%p, %%f, 0;\n\t"                                                \
-    "selp.f32 " D0 ", %13, %9, %%p;\n\tselp.f32 " D1 ", %14, %10, %%p;\n\t"       \
-    "selp.f32 " D2 ", %15, %11, %%p;\n\tselp.f32 " D3 ", %16, %12, %%p;\n\t"
-#define GP_FAST_XU GP_FAST_X("%%u0", "%%u1", "%%u2", "%%u3")
-// t_j = t_j OP v_j for the four rows (v: "%%u" or the constant "%%cf")
-#define GP_FAST_TV(OP, V0, V1, V2, V3)                                            \
-    OP ".rn.f32 %1, %1, " V0 ";\n\t" OP ".rn.f32 %2, %2, " V1 ";\n\t"             \
-    OP ".rn.f32 %3, %3, " V2 ";\n\t" OP ".rn.f32 %4, %4, " V3 ";\n\t"
-#define GP_FAST_TU(OP) GP_FAST_TV(OP, "%%u0", "%%u1", "%%u2", "%%u3")
-#define GP_FAST_TC(OP) GP_FAST_TV(OP, "%%cf", "%%cf", "%%cf", "%%cf")
-// t_j = v_j - t_j
-#define GP_FAST_RSUB(V0, V1, V2, V3)                                              \
-    "sub.rn.f32 %1, " V0 ", %1;\n\tsub.rn.f32 %2, " V1 ", %2;\n\t"                \
-    "sub.rn.f32 %3, " V2 ", %3;\n\tsub.rn.f32 %4, " V3 ", %4;\n\t"
-// protected division of one row: D = |B| < thr ? 1 : A / B
-#define GP_FAST_DIV1(D, A, B)                                                     \
-    "div.rn.f32 %%q, " A ", " B ";\n\t"                                           \
-    "abs.f32 %%m, " B ";\n\t"                                                     \
-    "setp.lt.f32 %%p, %%m, %17;\n\t"                                              \
-    "selp.f32 " D ", 0f3F800000, %%q, %%p;\n\t"
-#define GP_FAST_DIV_TV(V0, V1, V2, V3)                                            \
-    GP_FAST_DIV1("%1", "%1", V0) GP_FAST_DIV1("%2", "%2", V1)                     \
-    GP_FAST_DIV1("%3", "%3", V2) GP_FAST_DIV1("%4", "%4", V3)
-#define GP_FAST_DIV_VT(V0, V1, V2, V3)                                            \
-    GP_FAST_DIV1("%1", V0, "%1") GP_FAST_DIV1("%2", V1, "%2")                     \
-    GP_FAST_DIV1("%3", V2, "%3") GP_FAST_DIV1("%4", V3, "%4")
-#define GP_FAST_SQRT1(T) "abs.f32 " T ", " T ";\n\tsqrt.rn.f32 " T ", " T ";\n\t"
-// protected reciprocal: |t| < thr ? 0 : 1 / t
-#define GP_FAST_INV1(T)                                                           \
-    "rcp.rn.f32 %%q, " T ";\n\t"                                                  \
-    "abs.f32 %%m, " T ";\n\t"                                                     \
-    "setp.lt.f32 %%p, %%m, %17;\n\t"                                              \
-    "selp.f32 " T ", 0f00000000, %%q, %%p;\n\t"
-#define GP_FAST_SETC                                                              \
-    "mov.f32 %1, %%cf;\n\tmov.f32 %2, %%cf;\n\tmov.f32 %3, %%cf;\n\tmov.f32 %4, %%cf;\n\t"
-#define GP_FAST_NEXT "bra.uni N%=;\n\t"
-// sin, cos and tan of the four rows with the steps and constants of
-// trig_rows (gp_math.cuh): Cody-Waite reduction by pi/2 in three FMAs,
-// both polynomials, then the quadrant select or the quotient, so the
-// results are the same bits.  A warp with any row outside the fast path
-// (|x| >= 65536, inf, NaN) hands the word back before touching t, and the
-// caller's switch runs trig_rows with its slow path.
-#define GP_FAST_TRIG_REGS                                                         \
-    ".reg .pred %%ps;\n\t"                                                        \
-    ".reg .b32 %%qq, %%qb, %%kd;\n\t"                                             \
-    ".reg .f32 %%jm, %%jj, %%rr, %%ss, %%sn, %%cn, %%sr;\n\t"
-#define GP_FAST_TRIG_CHECK1(T)                                                    \
-    "abs.f32 %%m, " T ";\n\t"                                                     \
-    "setp.geu.f32 %%p, %%m, 0f47800000;\n\t"                                      \
-    "or.pred %%ps, %%ps, %%p;\n\t"
-#define GP_FAST_TRIG_CHECK                                                        \
-    "setp.ne.u32 %%ps, 0, 0;\n\t"                                                 \
-    GP_FAST_TRIG_CHECK1("%1") GP_FAST_TRIG_CHECK1("%2")                           \
-    GP_FAST_TRIG_CHECK1("%3") GP_FAST_TRIG_CHECK1("%4")                           \
-    "vote.sync.any.pred %%ps, %%ps, 0xffffffff;\n\t"                              \
-    "@%%ps bra EX%=;\n\t"
-// reduction and both polynomials of row T: %%sn = sin r, %%cn = cos r,
-// %%qq = the quadrant word (low bits of j)
-#define GP_FAST_TRIG_POLY(T)                                                      \
-    "fma.rn.f32 %%jm, " T ", 0f3F22F983, 0f4B400000;\n\t"                         \
-    "sub.rn.f32 %%jj, %%jm, 0f4B400000;\n\t"                                      \
-    "neg.f32 %%jj, %%jj;\n\t"                                                     \
-    "fma.rn.f32 %%rr, %%jj, 0f3FC90FDB, " T ";\n\t"                               \
-    "fma.rn.f32 %%rr, %%jj, 0fB33BBD2E, %%rr;\n\t"                                \
-    "fma.rn.f32 %%rr, %%jj, 0fA6F72CED, %%rr;\n\t"                                \
-    "mul.rn.f32 %%ss, %%rr, %%rr;\n\t"                                            \
-    "fma.rn.f32 %%sn, 0f363668F9, %%ss, 0fB95007C0;\n\t"                          \
-    "fma.rn.f32 %%sn, %%sn, %%ss, 0f3C088884;\n\t"                                \
-    "fma.rn.f32 %%sn, %%sn, %%ss, 0fBE2AAAAB;\n\t"                                \
-    "mul.rn.f32 %%sr, %%ss, %%rr;\n\t"                                            \
-    "fma.rn.f32 %%sn, %%sn, %%sr, %%rr;\n\t"                                      \
-    "fma.rn.f32 %%cn, 0fB4920F4E, %%ss, 0f37D0086F;\n\t"                          \
-    "fma.rn.f32 %%cn, %%cn, %%ss, 0fBAB60B5C;\n\t"                                \
-    "fma.rn.f32 %%cn, %%cn, %%ss, 0f3D2AAAAB;\n\t"                                \
-    "fma.rn.f32 %%cn, %%cn, %%ss, 0fBF000000;\n\t"                                \
-    "fma.rn.f32 %%cn, %%cn, %%ss, 0f3F800000;\n\t"                                \
-    "mov.b32 %%qq, %%jm;\n\t"
-// sin (kind 0) or cos (kind 1, in %%kd): a = ((q + kind) & 1) ? cos : sin,
-// negated when (q + kind) & 2
-#define GP_FAST_SINCOS1(T)                                                        \
-    GP_FAST_TRIG_POLY(T)                                                          \
-    "add.u32 %%qq, %%qq, %%kd;\n\t"                                               \
-    "and.b32 %%qb, %%qq, 1;\n\t"                                                  \
-    "setp.ne.u32 %%p, %%qb, 0;\n\t"                                               \
-    "selp.f32 %%sn, %%cn, %%sn, %%p;\n\t"                                         \
-    "and.b32 %%qb, %%qq, 2;\n\t"                                                  \
-    "setp.ne.u32 %%p, %%qb, 0;\n\t"                                               \
-    "neg.f32 %%cn, %%sn;\n\t"                                                     \
-    "selp.f32 " T ", %%cn, %%sn, %%p;\n\t"
-// tan: (q & 1) ? -(cos / sin) : sin / cos
-#define GP_FAST_TAN1(T)                                                           \
-    GP_FAST_TRIG_POLY(T)                                                          \
-    "and.b32 %%qb, %%qq, 1;\n\t"                                                  \
-    "setp.ne.u32 %%p, %%qb, 0;\n\t"                                               \
-    "selp.f32 %%q, %%cn, %%sn, %%p;\n\t"                                          \
-    "selp.f32 %%m, %%sn, %%cn, %%p;\n\t"                                          \
-    "div.rn.f32 %%q, %%q, %%m;\n\t"                                               \
-    "neg.f32 %%m, %%q;\n\t"                                                       \
-    "selp.f32 " T ", %%m, %%q, %%p;\n\t"
-#define GP_FAST_TRIG_BODIES                                                       \
-    "TSC%=:\n\t" GP_FAST_TRIG_CHECK                                               \
-    "sub.u32 %%kd, %%i, 23;\n\t"                                                  \
-    GP_FAST_SINCOS1("%1") GP_FAST_SINCOS1("%2") GP_FAST_SINCOS1("%3")             \
-    GP_FAST_SINCOS1("%4") GP_FAST_NEXT                                            \
-    "TTN%=:\n\t" GP_FAST_TRIG_CHECK                                               \
-    GP_FAST_TAN1("%1") GP_FAST_TAN1("%2") GP_FAST_TAN1("%3") GP_FAST_TAN1("%4")   \
-    GP_FAST_NEXT
-#define GP_FAST_DIV_BODIES                                                        \
-    "DS%=:\n\t" GP_FAST_SLOTLOAD GP_FAST_DIV_TV("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
-    "DX%=:\n\t" GP_FAST_XU GP_FAST_DIV_TV("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
-    "DC%=:\n\t" GP_FAST_DIV_TV("%%cf", "%%cf", "%%cf", "%%cf") GP_FAST_NEXT       \
-    "RDX%=:\n\t" GP_FAST_XU GP_FAST_DIV_VT("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
-    "RDC%=:\n\t" GP_FAST_DIV_VT("%%cf", "%%cf", "%%cf", "%%cf") GP_FAST_NEXT      \
-    "SQ%=:\n\t" GP_FAST_SQRT1("%1") GP_FAST_SQRT1("%2") GP_FAST_SQRT1("%3")       \
-    GP_FAST_SQRT1("%4") GP_FAST_NEXT                                              \
-    "IV%=:\n\t" GP_FAST_INV1("%1") GP_FAST_INV1("%2") GP_FAST_INV1("%3")          \
-    GP_FAST_INV1("%4") GP_FAST_NEXT
-#define GP_FAST_BODY                                                              \
-    "PX%=:\n\t" GP_FAST_X("%1", "%2", "%3", "%4") GP_FAST_NEXT                    \
-    "PC%=:\n\t" GP_FAST_SETC GP_FAST_NEXT                                         \
-    "PXS%=:\n\t" GP_FAST_SPILL GP_FAST_X("%1", "%2", "%3", "%4") GP_FAST_NEXT     \
-    "PCS%=:\n\t" GP_FAST_SPILL GP_FAST_SETC GP_FAST_NEXT                          \
-    "AS%=:\n\t" GP_FAST_SLOTLOAD GP_FAST_TU("add") GP_FAST_NEXT                   \
-    "SS%=:\n\t" GP_FAST_SLOTLOAD GP_FAST_TU("sub") GP_FAST_NEXT                   \
-    "MS%=:\n\t" GP_FAST_SLOTLOAD GP_FAST_TU("mul") GP_FAST_NEXT                   \
-    "AX%=:\n\t" GP_FAST_XU GP_FAST_TU("add") GP_FAST_NEXT                         \
-    "AC%=:\n\t" GP_FAST_TC("add") GP_FAST_NEXT                                    \
-    "SX%=:\n\t" GP_FAST_XU GP_FAST_TU("sub") GP_FAST_NEXT                         \
-    "SC%=:\n\t" GP_FAST_TC("sub") GP_FAST_NEXT                                    \
-    "RX%=:\n\t" GP_FAST_XU GP_FAST_RSUB("%%u0", "%%u1", "%%u2", "%%u3") GP_FAST_NEXT \
-    "RC%=:\n\t" GP_FAST_RSUB("%%cf", "%%cf", "%%cf", "%%cf") GP_FAST_NEXT         \
-    "MX%=:\n\t" GP_FAST_XU GP_FAST_TU("mul") GP_FAST_NEXT                         \
-    "MC%=:\n\t" GP_FAST_TC("mul") GP_FAST_NEXT                                    \
-    "AB%=:\n\t"                                                                   \
-    "abs.f32 %1, %1;\n\tabs.f32 %2, %2;\n\tabs.f32 %3, %3;\n\tabs.f32 %4, %4;\n\t" \
-    GP_FAST_NEXT                                                                  \
-    "NG%=:\n\t"                                                                   \
-    "neg.f32 %1, %1;\n\tneg.f32 %2, %2;\n\tneg.f32 %3, %3;\n\tneg.f32 %4, %4;\n\t" \
-    GP_FAST_NEXT                                                                  \
-    "EX%=:\n\t"                                                                   \
-    "mov.b32 %5, %%w;\n\t"                                                        \
-    "mov.f32 %6, %%cf;\n\t"                                                       \
-    "}\n"
+// 3).  gp_fast.cuh (written by gen_fast.py) holds the loop for 4 and 8 rows
+// per lane: a lane's rows sit in RPT/2 64-bit pairs and add, sub, mul and
+// fma run as one packed f32x2 instruction per pair (per-element round to
+// nearest, no flush to zero: the bits of the scalar operations).  It runs
+// pushes and stack moves, add/sub/mul with every operand form, abs, neg,
+// column reads from registers (XREG) and, with DIVS, the protected
+// divisions, square root, reciprocal, sin, cos, tan, log and exp (the steps
+// and constants of gp_math.cuh, so results are the same bits).  It stops
+// at the first word it does not run (END, the extended functions, a
+// trigonometric or exponential argument outside the fast path in any row
+// of the warp, and whatever XREG or DIVS leave out), hands that word and
+// its constant back to the switch below and leaves pa just past it.  DIVS
+// is off in the instances with the extended functions: there the division
+// set in the loop cost the extended-set population 23% (their out-of-line
+// calls and the division's own slow-path call do not mix well).
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
 
-// XREG: columns 0 and 1 held in x0 and x1 (otherwise those are unused and
-// the column reads are handed back)
-#define GP_FAST_OPERANDS                                                          \
-    : "+r"(pa), "+f"(t[0]), "+f"(t[1]), "+f"(t[2]), "+f"(t[3]), "=r"(hw), "=f"(hc) \
-    : "r"(sb), "n"(NSLOT - 1), "f"(x0[0]), "f"(x0[1]), "f"(x0[2]), "f"(x0[3]),    \
-      "f"(x1[0]), "f"(x1[1]), "f"(x1[2]), "f"(x1[3]), "f"(kThr)                   \
-    : "memory"
-template <int NSLOT, bool DIVS, bool XREG>
-__device__ __forceinline__ void run_fast4(uint32_t &pa, float (&t)[4], const float (&x0)[4],
-                                          const float (&x1)[4], uint32_t sb, uint32_t &hw,
-                                          float &hc) {
-    if constexpr (!XREG && DIVS) {
-        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_DIVS_NOX) GP_FAST_TRIG_REGS GP_FAST_DIV_BODIES
-                     GP_FAST_TRIG_BODIES GP_FAST_BODY GP_FAST_OPERANDS);
-    } else if constexpr (!XREG) {
-        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_NODIVS_NOX) GP_FAST_BODY GP_FAST_OPERANDS);
-    } else if constexpr (DIVS) {
-        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_DIVS) GP_FAST_TRIG_REGS GP_FAST_DIV_BODIES
-                     GP_FAST_TRIG_BODIES GP_FAST_BODY
-                     : "+r"(pa), "+f"(t[0]), "+f"(t[1]), "+f"(t[2]), "+f"(t[3]), "=r"(hw),
-                       "=f"(hc)
-                     : "r"(sb), "n"(NSLOT - 1), "f"(x0[0]), "f"(x0[1]), "f"(x0[2]), "f"(x0[3]),
-                       "f"(x1[0]), "f"(x1[1]), "f"(x1[2]), "f"(x1[3]), "f"(kThr)
-                     : "memory");
+template <int RPT, int NSLOT, bool DIVS, bool XREG>
+__device__ __forceinline__ void run_fast(uint32_t &pa, uint64_t (&t)[RPT / 2],
+                                         const uint64_t (&x0)[RPT / 2],
+                                         const uint64_t (&x1)[RPT / 2], uint32_t sb,
+                                         uint32_t &hw, float &hc) {
+    if constexpr (RPT == 4) {
+        if constexpr (DIVS && XREG) fast_r4_divs_x<NSLOT>(pa, t, x0, x1, sb, hw, hc);
+        else if constexpr (DIVS) fast_r4_divs_nox<NSLOT>(pa, t, x0, x1, sb, hw, hc);
+        else if constexpr (XREG) fast_r4_nodivs_x<NSLOT>(pa, t, x0, x1, sb, hw, hc);
+        else fast_r4_nodivs_nox<NSLOT>(pa, t, x0, x1, sb, hw, hc);
     } else {
-        asm volatile(GP_FAST_HEAD(GP_FAST_TABLE_NODIVS) GP_FAST_BODY
-                     : "+r"(pa), "+f"(t[0]), "+f"(t[1]), "+f"(t[2]), "+f"(t[3]), "=r"(hw),
-                       "=f"(hc)
-                     : "r"(sb), "n"(NSLOT - 1), "f"(x0[0]), "f"(x0[1]), "f"(x0[2]), "f"(x0[3]),
-                       "f"(x1[0]), "f"(x1[1]), "f"(x1[2]), "f"(x1[3])
-                     : "memory");
+        if constexpr (DIVS && XREG) fast_r8_divs_x<NSLOT>(pa, t, x0, x1, sb, hw, hc);
+        else if constexpr (DIVS) fast_r8_divs_nox<NSLOT>(pa, t, x0, x1, sb, hw, hc);
+        else if constexpr (XREG) fast_r8_nodivs_x<NSLOT>(pa, t, x0, x1, sb, hw, hc);
+        else fast_r8_nodivs_nox<NSLOT>(pa, t, x0, x1, sb, hw, hc);
     }
 }
-#undef GP_FAST_HEAD
-#undef GP_FAST_TABLE_DIVS
-#undef GP_FAST_TABLE_NODIVS
-#undef GP_FAST_TABLE_DIVS_NOX
-#undef GP_FAST_TABLE_NODIVS_NOX
-#undef GP_FAST_OPERANDS
-#undef GP_FAST_LOOP_TOP
-#undef GP_FAST_DIV_BODIES
-#undef GP_FAST_TRIG_REGS
-#undef GP_FAST_TRIG_CHECK1
-#undef GP_FAST_TRIG_CHECK
-#undef GP_FAST_TRIG_POLY
-#undef GP_FAST_SINCOS1
-#undef GP_FAST_TAN1
-#undef GP_FAST_TRIG_BODIES
-#undef GP_FAST_SLOT
-#undef GP_FAST_SPILL
-#undef GP_FAST_SLOTLOAD
-#undef GP_FAST_X
-#undef GP_FAST_XU
-#undef GP_FAST_TV
-#undef GP_FAST_TU
-#undef GP_FAST_TC
-#undef GP_FAST_RSUB
-#undef GP_FAST_DIV1
-#undef GP_FAST_DIV_TV
-#undef GP_FAST_DIV_VT
-#undef GP_FAST_SQRT1
-#undef GP_FAST_INV1
-#undef GP_FAST_SETC
-#undef GP_FAST_NEXT
-#undef GP_FAST_BODY
 
 // Runs one compiled program over RPT rows per lane; returns the top of the
 // stack in t.  stk = this warp's stack slice, already offset by the lane.
@@ -418,9 +186,9 @@ __device__ __forceinline__ void run_fast4(uint32_t &pa, float (&t)[4], const flo
 // can make it run away or leave its memory.
 //
 // Dispatch cost is what this loop is tuned for (per-opcode instruction
-// counts measured with ncu on chains of one operation).  At 4 rows per lane
-// the fast loop runs most words and hands the others, one at a time, to
-// the switch below.  The instruction word and the stack are addressed
+// counts measured with ncu on chains of one operation).  At 4 and 8 rows
+// per lane the fast loop runs most words and hands the others, one at a
+// time, to the switch below.  The instruction word and the stack are addressed
 // through 32-bit shared-memory addresses computed once; the opcode is
 // broadcast from lane 0, which lets the compiler treat the switch as
 // warp-uniform (no reconvergence barrier per instruction); the switch
@@ -442,15 +210,30 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
     // pa: shared-memory address of the next instruction word
     uint32_t pa = (uint32_t)__cvta_generic_to_shared(cbuf);
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stk);  // this lane's slot 0
-    // 4 rows per lane: the fast loop runs what it can and hands back the
-    // rest, one word at a time, to the switch below
-    constexpr bool kFast = RPT == 4;
+    // 4 or 8 rows per lane: the fast loop runs what it can and hands back
+    // the rest, one word at a time, to the switch below; the rows cross
+    // between the two as pairs {row 2i, row 2i+1} (register moves)
+    constexpr bool kFast = RPT == 4 || RPT == 8;
+    constexpr int kPairs = kFast ? RPT / 2 : 1;
+    uint64_t x0p[kPairs], x1p[kPairs];
+    if constexpr (kFast) {
+#pragma unroll
+        for (int i = 0; i < kPairs; ++i) {
+            x0p[i] = pack2(x0[2 * i], x0[2 * i + 1]);
+            x1p[i] = pack2(x1[2 * i], x1[2 * i + 1]);
+        }
+    }
 #pragma unroll 1
     for (;;) {
         uint2 ins;
         if constexpr (kFast) {
             float hc;
-            run_fast4<NSLOT, !EXT, FMODE == 2>(pa, t, x0, x1, sb, ins.x, hc);
+            uint64_t tp[kPairs];
+#pragma unroll
+            for (int i = 0; i < kPairs; ++i) tp[i] = pack2(t[2 * i], t[2 * i + 1]);
+            run_fast<RPT, NSLOT, !EXT, FMODE == 2>(pa, tp, x0p, x1p, sb, ins.x, hc);
+#pragma unroll
+            for (int i = 0; i < kPairs; ++i) unpack2(tp[i], t[2 * i], t[2 * i + 1]);
             ins.y = __float_as_uint(hc);
         } else {
             asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
@@ -530,7 +313,7 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
                     _Pragma("unroll") for (int g = 0; g < RPT / 4; ++g) {
                         const float4 r = ext_rows4(
                             make_float4(t[4 * g], t[4 * g + 1], t[4 * g + 2], t[4 * g + 3]),
-                            (w >> 5) & 7u);
+                            (w >> 16) & 7u);
                         t[4 * g] = r.x; t[4 * g + 1] = r.y; t[4 * g + 2] = r.z; t[4 * g + 3] = r.w;
                     }
                     break;
@@ -540,7 +323,7 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
             case OP_EXT2:  // max / min, right operand in a stack slot
                 if constexpr (kExt) {
                     GP_SLOT_LOAD(u)
-                    if (((w >> 5) & 7u) == EXT_MAX) { GP_T(f_max(t[j], u[j])) }
+                    if (((w >> 16) & 7u) == EXT_MAX) { GP_T(f_max(t[j], u[j])) }
                     else { GP_T(f_min(t[j], u[j])) }
                     break;
                 } else {

@@ -1,6 +1,6 @@
-// gp_math.cuh -- sin, cos and tan for the evaluator's hot loop.
+// gp_math.cuh -- sin, cos, tan, log and exp for the evaluator's hot loop.
 //
-// Small inline fast path, out-of-line fallback: the fast path covers finite
+// Small inline fast path, out-of-line fallback: the trigonometric fast path covers finite
 // |x| < 65536 with a Cody-Waite reduction by pi/2 (W. J. Cody and W. Waite,
 // "Software Manual for the Elementary Functions", 1980) carried out with
 // three fused multiply-adds against a three-part split of pi/2, then
@@ -8,6 +8,16 @@
 // minimax fit by Lawson's iteration, < 1 ulp in float32 on the interval).
 // Everything else -- huge arguments, inf, NaN -- goes to CUDA's sinf/cosf
 // through a non-inlined call, so the interpreter's inline code stays small.
+//
+// log: x = 2^k m with m in [sqrt(1/2), sqrt(2)), log x = k ln2 + log(1 + f)
+// with f = m - 1 and a degree-9 polynomial for log(1 + f) (coefficients
+// from fit_log.py: 1.14 ulp over [0.001, 3.4e38]); it runs on
+// max(|a|, 0.001), so no zero, negative or subnormal argument reaches it.
+// exp: for |x| < 87, 2^j e^r with j the integer nearest x log2(e), the
+// Cody-Waite reduction r = x - j ln2 in two FMAs and a degree-6 polynomial
+// (coefficients from fit_exp.py: 1.04 ulp); other arguments go to CUDA's
+// expf.  The inline-PTX loop of the evaluator transcribes the same steps
+// and constants, so both give the same bits.
 #pragma once
 
 #include <cstdint>
@@ -62,6 +72,75 @@ static_assert(__builtin_bit_cast(uint32_t, kC2) == 0x37D0086Fu, "trig constant")
 static_assert(__builtin_bit_cast(uint32_t, kC3) == 0xB4920F4Eu, "trig constant");
 static_assert(__builtin_bit_cast(uint32_t, kRoundMagic) == 0x4B400000u, "trig constant");
 static_assert(__builtin_bit_cast(uint32_t, kTrigFast) == 0x47800000u, "trig constant");
+// log: the bit pattern of sqrt(1/2) splits x into 2^k m; log(1 + f) ~
+// f + f^2 (P0 + f (P1 + ... + f P7)); ln2 = LN2_HI (16 significant bits,
+// so k * LN2_HI is exact) + LN2_LO
+constexpr uint32_t kSqrtHalfBits = 0x3F3504F3u;
+constexpr float kLogP0 = -0.49999991059303284f, kLogP1 = 0.33333951234817505f,
+                kLogP2 = -0.25001755356788635f, kLogP3 = 0.19962072372436523f,
+                kLogP4 = -0.16570508480072021f, kLogP5 = 0.14917974174022675f,
+                kLogP6 = -0.14307521283626556f, kLogP7 = 0.08734840899705887f;
+constexpr float kLn2Hi = 0.693145751953125f, kLn2Lo = 1.428606765330187e-06f;
+// exp: e^r ~ 1 + r (E1 + r (E2 + ... + r E6)) on |r| <= 0.35
+constexpr float kExpE1 = 1.0f, kExpE2 = 0.4999999403953552f, kExpE3 = 0.1666642129421234f,
+                kExpE4 = 0.041668057441711426f, kExpE5 = 0.008374955505132675f,
+                kExpE6 = 0.001384272240102291f;
+constexpr float kLog2e = 1.4426950216293335f;
+constexpr float kExpFast = 87.0f;
+static_assert(__builtin_bit_cast(uint32_t, kLogP0) == 0xBEFFFFFDu, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kLogP1) == 0x3EAAAB7Au, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kLogP2) == 0xBE80024Du, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kLogP3) == 0x3E4C6960u, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kLogP4) == 0xBE29AE98u, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kLogP5) == 0x3E18C293u, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kLogP6) == 0xBE12824Fu, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kLogP7) == 0x3DB2E3B9u, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kLn2Hi) == 0x3F317200u, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kLn2Lo) == 0x35BFBE8Eu, "log constant");
+static_assert(__builtin_bit_cast(uint32_t, kExpE1) == 0x3F800000u, "exp constant");
+static_assert(__builtin_bit_cast(uint32_t, kExpE2) == 0x3EFFFFFEu, "exp constant");
+static_assert(__builtin_bit_cast(uint32_t, kExpE3) == 0x3E2AAA06u, "exp constant");
+static_assert(__builtin_bit_cast(uint32_t, kExpE4) == 0x3D2AAC20u, "exp constant");
+static_assert(__builtin_bit_cast(uint32_t, kExpE5) == 0x3C09371Cu, "exp constant");
+static_assert(__builtin_bit_cast(uint32_t, kExpE6) == 0x3AB57078u, "exp constant");
+static_assert(__builtin_bit_cast(uint32_t, kLog2e) == 0x3FB8AA3Bu, "exp constant");
+static_assert(__builtin_bit_cast(uint32_t, kExpFast) == 0x42AE0000u, "exp constant");
+
+// log x for x >= 0.001 (finite; the caller selects inf and NaN itself)
+__device__ __forceinline__ float log_pos(float x) {
+    const int32_t i = __float_as_int(x);
+    const int32_t k = (int32_t)((uint32_t)i - kSqrtHalfBits) >> 23;
+    const float m = __int_as_float(i - (int32_t)((uint32_t)k << 23));
+    const float f = __fsub_rn(m, 1.0f);
+    const float kf = __fsub_rn(__int_as_float(k + 0x4B400000), kRoundMagic);  // exactly k
+    float p = __fmaf_rn(kLogP7, f, kLogP6);
+    p = __fmaf_rn(p, f, kLogP5);
+    p = __fmaf_rn(p, f, kLogP4);
+    p = __fmaf_rn(p, f, kLogP3);
+    p = __fmaf_rn(p, f, kLogP2);
+    p = __fmaf_rn(p, f, kLogP1);
+    p = __fmaf_rn(p, f, kLogP0);
+    float r = __fmaf_rn(__fmul_rn(f, f), p, f);
+    r = __fmaf_rn(kf, kLn2Lo, r);
+    return __fmaf_rn(kf, kLn2Hi, r);
+}
+
+// e^x for |x| < 87: the product of the polynomial and 2^j is one rounding
+__device__ __forceinline__ float exp_fast(float x) {
+    const float jm = __fmaf_rn(x, kLog2e, kRoundMagic);
+    const float jf = __fsub_rn(jm, kRoundMagic);
+    float r = __fmaf_rn(jf, -kLn2Hi, x);
+    r = __fmaf_rn(jf, -kLn2Lo, r);
+    float p = __fmaf_rn(kExpE6, r, kExpE5);
+    p = __fmaf_rn(p, r, kExpE4);
+    p = __fmaf_rn(p, r, kExpE3);
+    p = __fmaf_rn(p, r, kExpE2);
+    p = __fmaf_rn(p, r, kExpE1);
+    p = __fmaf_rn(p, r, 1.0f);
+    const float s = __int_as_float((int32_t)(((uint32_t)__float_as_int(jm) << 23) + 0x3F800000u));
+    return __fmul_rn(p, s);
+}
+
 __device__ __forceinline__ float trig_reduce(float x, int &q) {
     const float jm = __fmaf_rn(x, kTwoOverPi, kRoundMagic);
     const float j = __fsub_rn(jm, kRoundMagic);

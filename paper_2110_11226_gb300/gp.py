@@ -91,6 +91,7 @@ def _load():
         "gp_resolve_opts": (i32, [i32, i64, i32, P, P]),
         "gp_evaluate_plain": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
         "gp_predict": (i32, [P, P, i32, P, i64, i32, P, P]),
+        "gp_predict_ex": (i32, [P, P, i32, P, i64, i32, P, P, P]),
         "gp_evaluate_host": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
         "gp_validate_host": (i32, [P, P, i32, i32, P, P]),
         "gp_tournament_ex": (i32, [P, P, i32, i32, i32, f32, i32, u64, u64, P, P]),
@@ -291,6 +292,18 @@ def gp_predict(progs, offsets, X, out=None, stream=None):
     _check("gp_predict", _lib.gp_predict(
         pp, po, P, _dptr(X, "X", _F32), n_rows, n_feat, _dptr(out, "out", _F32, P * n_rows),
         _stream(stream)))
+    return out
+
+
+def gp_predict_ex(progs, offsets, X, opts: Optional[EvalOpts] = None, out=None, stream=None):
+    n_rows, n_feat = _xshape(X)
+    P = _nprogs(offsets)
+    if out is None:
+        out = torch.empty((P, n_rows), dtype=torch.float32, device=X.device)
+    pp, po = _progs(progs, offsets)
+    _check("gp_predict_ex", _lib.gp_predict_ex(
+        pp, po, P, _dptr(X, "X", _F32), n_rows, n_feat, None if opts is None else C.byref(opts),
+        _dptr(out, "out", _F32, P * n_rows), _stream(stream)))
     return out
 
 

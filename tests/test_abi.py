@@ -174,6 +174,10 @@ def test_argument_errors_return_before_any_device_call():
     assert plain(4) == ARG and plain(5) == ARG and plain(1) == CUDA
     assert lib.gp_const_grad(p, p, 4, p, 100, 2, p, None, 4, p, p, None) == ARG
     assert lib.gp_predict(p, p, 4, p, 100, 2, None, None) == ARG
+    assert lib.gp_predict_ex(p, p, 4, p, 100, 2, None, None, None) == ARG
+    opt = gp.make_opts(rows_per_thread=16)
+    assert lib.gp_predict_ex(p, p, 4, p, 100, 2, C.byref(opt), p, None) == ARG
+    assert lib.gp_predict_ex(p, p, 4, p, 100, 2, None, p, None) == CUDA
     tour = lambda **k: lib.gp_tournament_ex(k.get("fit", p), None, k.get("P", 4), k.get("T", 4),
                                             k.get("k", 2), 0.0, 0, 1, 0, k.get("out", p), None)
     for bad in (dict(fit=None), dict(out=None), dict(P=0), dict(T=-1), dict(k=0)):

@@ -64,6 +64,8 @@ def test_well_formed_arguments_reach_the_library(lib):
             pn, po, X, y, w, out=torch.empty(P), out64=torch.empty(P, dtype=torch.float64),
             out_status=torch.empty(P, **i32), ws=torch.empty(1024, dtype=torch.uint8)),
         "gp_predict": lambda: gp.gp_predict(pn, po, X, out=torch.empty(P, X.shape[1])),
+        "gp_predict_ex": lambda: gp.gp_predict_ex(pn, po, X, gp.make_opts(rows_per_thread=8),
+                                                  out=torch.empty(P, X.shape[1])),
         "gp_const_grad": lambda: gp.gp_const_grad(pn, po, X, y, w,
                                                   out_grad=torch.empty(P, gp.MAX_CONSTS),
                                                   out_fitness=torch.empty(P)),

@@ -139,8 +139,50 @@ def test_constant_subtrees_fold_to_the_per_row_value():
     nan = np.isnan(a)
     np.testing.assert_array_equal(nan, np.isnan(b))
     np.testing.assert_array_equal(a[~nan].view(np.uint32), b[~nan].view(np.uint32))
+    # the same through the loop at 8 rows per lane
+    a8 = gp.gp_predict_ex(*put(nodes, off, X)[:3], gp.make_opts(rows_per_thread=8)).cpu().numpy()
+    np.testing.assert_array_equal(nan, np.isnan(a8))
+    np.testing.assert_array_equal(a[~nan].view(np.uint32), a8[~nan].view(np.uint32))
     # and the folded programs still agree with the oracle
     st, _ = check_points(b, folded, off, X)
+    assert st.ok > 0.5 * st.rows, st
+
+
+def _special_rows(X, seed):
+    """Overwrite a scattering of rows with values that reach the protected
+    branches and the slow paths: zero, both sides of the threshold,
+    arguments of exp beyond 87 and of sin/cos beyond 65536, huge, inf, NaN."""
+    vals = np.array([0.0, -0.0, 0.0005, -0.0009999, 0.001, 0.0011, 88.5, -100.0, 70000.0,
+                     1e30, -1e30, np.inf, -np.inf, np.nan, 1e-40], np.float32)
+    rng = np.random.default_rng(seed)
+    for f in range(X.shape[0]):
+        idx = rng.choice(X.shape[1], size=3 * len(vals), replace=False)
+        X[f, idx] = np.tile(vals, 3)
+    return X
+
+
+@pytest.mark.parametrize("n_feat,funcs", [(2, synth.FULL_SET + ("tan",)), (1, synth.FULL_SET),
+                                          (9, synth.FULL_SET + ("tan",)),
+                                          (2, synth.EXTENDED_SET)])
+def test_predictions_do_not_depend_on_rows_per_thread(n_feat, funcs):
+    """The fast loop at 8 rows per lane (four packed pairs) gives every row
+    the bits of the loop at 4 rows per lane: each row's operations are the
+    same whichever way rows are grouped, and a warp that hands a word back
+    (trig or exp argument off the fast path) has it done by the same C++
+    functions."""
+    nodes, off = synth.ramped_half_and_half(900, 2, 8, funcs, n_feat, seed=60 + n_feat)
+    n = 4096 + 37
+    X = np.random.default_rng(n_feat).uniform(-6, 6, size=(n_feat, n)).astype(np.float32)
+    X = _special_rows(X, n_feat)
+    pn, po, dX, _, _ = put(nodes, off, X)
+    a = gp.gp_predict_ex(pn, po, dX, gp.make_opts(rows_per_thread=4)).cpu().numpy()
+    b = gp.gp_predict_ex(pn, po, dX, gp.make_opts(rows_per_thread=8)).cpu().numpy()
+    c = gp.gp_predict(pn, po, dX).cpu().numpy()
+    for other in (b, c):
+        nan = np.isnan(a)
+        np.testing.assert_array_equal(nan, np.isnan(other))
+        np.testing.assert_array_equal(a[~nan].view(np.uint32), other[~nan].view(np.uint32))
+    st, _ = check_points(b, nodes, off, X)
     assert st.ok > 0.5 * st.rows, st
 
 
