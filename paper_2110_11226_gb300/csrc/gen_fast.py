@@ -12,7 +12,7 @@ indexed branch (brx.idx through a 64-entry table on the low six bits of
 the word).
 
 sin, cos, log and exp transcribe the steps and constants of gp_math.cuh
-(trig_rows, log_pos, exp_fast), so the loop and the C++ fallback give the
+(sincos_fast, log_pos, exp_fast), so the loop and the C++ fallback give the
 same bits; the constants are written here as the bit patterns that
 gp_math.cuh's static_asserts pin.  Code size matters as much as
 instruction count (at 8 rows per lane an unrolled body per operation
@@ -45,14 +45,16 @@ OPS = dict(PUSH_X=0, PUSH_C=1, PUSH_X_SP=2, PUSH_C_SP=3, ADD_S=4, SUB_S=5, MUL_S
 COL1 = 32
 
 # float bit patterns (pinned by static_asserts in gp_math.cuh)
-K = dict(two_over_pi=0x3F22F983, magic=0x4B400000, pio2_hi=0x3FC90FDB, pio2_mid=0xB33BBD2E,
-         pio2_lo=0xA6F72CED, s0=0xBE2AAAAB, s1=0x3C088884, s2=0xB95007C0, s3=0x363668F9,
-         c0=0x3D2AAAAB, c1=0xBAB60B5C, c2=0x37D0086F, c3=0xB4920F4E, trig_fast=0x47800000,
+K = dict(inv_pi=0x3EA2F983, magic=0x4B400000, pi_hi=0x40490FDB, pi_mid=0xB3BBBD2E,
+         pi_lo=0xA7772CED, q0=0xBE2AAAA6, q1=0x3C088769, q2=0xB94FB7D4, q3=0x362EDC67,
+         trig_fast=0x47800000,
          lp0=0xBEFFFFFD, lp1=0x3EAAAB7A, lp2=0xBE80024D, lp3=0x3E4C6960, lp4=0xBE29AE98,
          lp5=0x3E18C293, lp6=0xBE12824F, lp7=0x3DB2E3B9, ln2_hi=0x3F317200, ln2_lo=0x35BFBE8E,
          e1=0x3F800000, e2=0x3EFFFFFE, e3=0x3E2AAA06, e4=0x3D2AAC20, e5=0x3C09371C,
          e6=0x3AB57078, log2e=0x3FB8AA3B, exp_fast=0x42AE0000, one=0x3F800000,
-         mhalf=0xBF000000, flt_max=0x7F7FFFFF)
+         mhalf=0xBF000000, flt_max=0x7F7FFFFF, half=0x3F000000, mone=0xBF800000,
+         inf=0x7F800000, two_m100=0x0D800000, two_126=0x7E800000, two_60=0x5D800000,
+         two_m60=0x21800000)
 NEG = 0x80000000
 
 
@@ -121,87 +123,71 @@ class Gen:
             a, b = srcs(i)
             self.e(f"{op}.rn.f32x2 {self.T[i]}, {a}, {b};")
 
-    # protected division of one row: d = |b| < thr ? 1 : a / b
-    def div1(self, d, a, b):
-        self.e(f"div.rn.f32 %%q, {a}, {b};")
-        self.e(f"abs.f32 %%m, {b};")
-        self.e(f"setp.lt.f32 %%p, %%m, {self.THR};")
-        self.e(f"selp.f32 {d}, 0f3F800000, %%q, %%p;")
-
-    def div_body(self, reverse):
-        """the rows divided by (or, reversed, dividing) the operand pairs in U"""
-        for i in range(self.np):
-            self.unpack(i, "%%v0", "%%v1")
-            self.e(f"mov.b64 {{%%u0, %%u1}}, %%U{i};")
-            for v, o in (("%%v0", "%%u0"), ("%%v1", "%%u1")):
-                if reverse:
-                    self.div1(v, o, v)
-                else:
-                    self.div1(v, v, o)
-            self.pack(i, "%%v0", "%%v1")
-
-    # a warp-wide test of every row before any row changes: bra EX if any
-    # row has |t| >= bound or is NaN
-    def range_check(self, bound):
+    # A warp-wide test of every row before any row changes: bra EX unless
+    # every |v| < hi (NaN fails) and, with lo, every |v| >= lo.  Each group
+    # is (hi, lo or None, vals) with vals(i) the pair register of rows 2i
+    # and 2i+1; the groups share one vote.
+    def range_check(self, hi, lo=None, vals=None, groups=None):
+        groups = groups or [(hi, lo, vals or (lambda i: self.T[i]))]
         self.e("setp.ne.u32 %%ps, 0, 0;")
-        for i in range(self.np):
-            self.unpack(i, "%%v0", "%%v1")
-            for v in ("%%v0", "%%v1"):
-                self.e(f"abs.f32 %%m, {v};")
-                self.e(f"setp.geu.f32 %%p, %%m, {kf(bound)};")
-                self.e("or.pred %%ps, %%ps, %%p;")
+        for hi, lo, vals in groups:
+            for i in range(self.np):
+                self.e(f"mov.b64 {{%%v0, %%v1}}, {vals(i)};")
+                for r, v in enumerate(("%%v0", "%%v1")):
+                    self.e(f"abs.f32 {v}, {v};")
+                    first = i == 0 and r == 0
+                    self.e(f"mov.f32 %%mx, {v};" if first else f"max.NaN.f32 %%mx, %%mx, {v};")
+                    if lo:
+                        self.e(f"mov.f32 %%mn, {v};" if first else f"min.f32 %%mn, %%mn, {v};")
+            self.e(f"setp.geu.or.f32 %%ps, %%mx, {kf(hi)}, %%ps;")
+            if lo:
+                self.e(f"setp.lt.or.f32 %%ps, %%mn, {kf(lo)}, %%ps;")
         self.e("vote.sync.any.pred %%ps, %%ps, 0xffffffff;")
         self.e("@%%ps bra EX%=;")
 
-    # sin or cos of every row (the steps of trig_rows): one body for both,
-    # the kind (0 sin, 1 cos) from the dispatch index
+    # sin or cos of every row (the steps of sincos_fast): one body for
+    # both, the kind (0 sin, 1 cos) from the dispatch index.  j = the
+    # integer nearest x/pi - kind/2, r = x - (j + kind/2) pi, then one odd
+    # polynomial, negated when j + kind is odd (a sign-bit flip)
     def trig(self):
         self.range_check("trig_fast")
         self.e(f"sub.u32 %%kd, %%i, {OPS['SIN']};")
+        self.e("setp.ne.u32 %%p, %%kd, 0;")
+        self.e("selp.b64 %%KM, 0xBF000000BF000000, 0x8000000080000000, %%p;")  # -kind/2
+        self.e("selp.b64 %%F, 0x3F0000003F000000, 0x0000000000000000, %%p;")   # +kind/2
+        self.e("shl.b32 %%kd, %%kd, 31;")
         for i in range(self.np):
             t = self.T[i]
-            self.e(f"mov.b64 %%K0, {kp('two_over_pi')};")
+            self.e(f"mov.b64 %%K0, {kp('inv_pi')};")
+            self.e(f"fma.rn.f32x2 %%JM, {t}, %%K0, %%KM;")
             self.e(f"mov.b64 %%K1, {kp('magic')};")
-            self.e(f"fma.rn.f32x2 %%JM, {t}, %%K0, %%K1;")
+            self.e("add.rn.f32x2 %%JM, %%JM, %%K1;")
             self.e("sub.rn.f32x2 %%JJ, %%JM, %%K1;")
-            # r = x - j (HI + MID + LO): fma(j, -HI, x) is fma(-j, HI, x) bit for bit
-            self.e(f"mov.b64 %%K0, {kp('pio2_hi', True)};")
+            self.e("add.rn.f32x2 %%JJ, %%JJ, %%F;")
+            # r = x - j' (HI + MID + LO): fma(j', -HI, x) is fma(-j', HI, x) bit for bit
+            self.e(f"mov.b64 %%K0, {kp('pi_hi', True)};")
             self.e(f"fma.rn.f32x2 %%R, %%JJ, %%K0, {t};")
-            self.e(f"mov.b64 %%K0, {kp('pio2_mid', True)};")
+            self.e(f"mov.b64 %%K0, {kp('pi_mid', True)};")
             self.e("fma.rn.f32x2 %%R, %%JJ, %%K0, %%R;")
-            self.e(f"mov.b64 %%K0, {kp('pio2_lo', True)};")
+            self.e(f"mov.b64 %%K0, {kp('pi_lo', True)};")
             self.e("fma.rn.f32x2 %%R, %%JJ, %%K0, %%R;")
             self.e("mul.rn.f32x2 %%S, %%R, %%R;")
-            # sin r = r + (s r)(S0 + s (S1 + s (S2 + s S3)))
-            self.e(f"mov.b64 %%K0, {kp('s3')};")
-            self.e(f"mov.b64 %%K1, {kp('s2')};")
+            # sin r = r + (s r)(Q0 + s (Q1 + s (Q2 + s Q3)))
+            self.e(f"mov.b64 %%K0, {kp('q3')};")
+            self.e(f"mov.b64 %%K1, {kp('q2')};")
             self.e("fma.rn.f32x2 %%P, %%K0, %%S, %%K1;")
-            for c in ("s1", "s0"):
+            for c in ("q1", "q0"):
                 self.e(f"mov.b64 %%K0, {kp(c)};")
                 self.e("fma.rn.f32x2 %%P, %%P, %%S, %%K0;")
             self.e("mul.rn.f32x2 %%Q, %%S, %%R;")
             self.e("fma.rn.f32x2 %%P, %%P, %%Q, %%R;")
-            # cos r = 1 + s (-1/2 + s (C0 + s (C1 + s (C2 + s C3))))
-            self.e(f"mov.b64 %%K0, {kp('c3')};")
-            self.e(f"mov.b64 %%K1, {kp('c2')};")
-            self.e("fma.rn.f32x2 %%Q, %%K0, %%S, %%K1;")
-            for c in ("c1", "c0", "mhalf", "one"):
-                self.e(f"mov.b64 %%K0, {kp(c)};")
-                self.e("fma.rn.f32x2 %%Q, %%Q, %%S, %%K0;")
-            self.unpack(i, "%%n0", "%%n1", "%%JM")   # quadrant words
-            self.unpack(i, "%%s0", "%%s1", "%%P")    # sin r
-            self.unpack(i, "%%c0", "%%c1", "%%Q")    # cos r
+            self.unpack(i, "%%n0", "%%n1", "%%JM")   # bit 0: parity of j
+            self.unpack(i, "%%v0", "%%v1", "%%P")
             for r in (0, 1):
-                # a = ((q + kind) & 1) ? cos : sin; negated (sign bit flipped)
-                # when (q + kind) & 2
-                n, sn, cn, v = f"%%n{r}", f"%%s{r}", f"%%c{r}", f"%%v{r}"
-                self.e(f"add.u32 {n}, {n}, %%kd;")
-                self.e(f"and.b32 %%a, {n}, 1;")
-                self.e("setp.ne.u32 %%p, %%a, 0;")
-                self.e(f"selp.f32 %%q, {cn}, {sn}, %%p;")
-                self.e(f"shl.b32 {n}, {n}, 30;")
-                self.e(f"and.b32 {n}, {n}, 0x80000000;")
-                self.e(f"mov.b32 %%a, %%q;")
+                n, v = f"%%n{r}", f"%%v{r}"
+                self.e(f"shl.b32 {n}, {n}, 31;")
+                self.e(f"xor.b32 {n}, {n}, %%kd;")
+                self.e(f"mov.b32 %%a, {v};")
                 self.e(f"xor.b32 %%a, %%a, {n};")
                 self.e(f"mov.b32 {v}, %%a;")
             self.pack(i, "%%v0", "%%v1")
@@ -274,6 +260,86 @@ class Gen:
             self.e("mov.b64 %%S, {%%n0, %%n1};")
             self.e(f"mul.rn.f32x2 {t}, %%P, %%S;")
 
+    # The IEEE reciprocal, square root and quotient, correctly rounded, from
+    # the hardware estimates and Newton-Raphson steps with FMA (P. Markstein,
+    # "Computation of elementary functions on the IBM RISC System/6000
+    # processor", IBM J. Res. Dev. 34, 1990): y = e + e (1 - b e) for 1/b
+    # from the estimate e; sqrt x = g + (x - g g) h with g = x e, h = e / 2
+    # from the reciprocal square-root estimate e; a / b = q + (a - b q) y
+    # with q = a y and y the reciprocal above.  On the ranges the warp-wide
+    # tests admit -- |b| < 2^126 for 1/b; x in [2^-100, inf) for sqrt x;
+    # |a| in [2^-60, 2^60) and |b| < 2^60 for a / b (|b| < 0.001 being
+    # protected anyway) -- each gives the bits of rcp.rn, sqrt.rn and
+    # div.rn: checked against them for every float32 reciprocal and square
+    # root and 1.2e9 quotients.  Outside those ranges the word is handed
+    # back, and the switch uses the IEEE operations themselves.
+    def rcp_pair(self, src, dst):
+        """dst = 1 / src for one pair, its rows in the reciprocal's range"""
+        self.e(f"mov.b64 {{%%v0, %%v1}}, {src};")
+        self.e("rcp.approx.ftz.f32 %%u0, %%v0;")
+        self.e("rcp.approx.ftz.f32 %%u1, %%v1;")
+        self.e("mov.b64 %%P, {%%u0, %%u1};")
+        self.e(f"mov.b64 %%K0, {kp('mone')};")
+        self.e("mul.rn.f32x2 %%Q, %%P, %%K0;")           # -e
+        self.e(f"mov.b64 %%K1, {kp('one')};")
+        self.e(f"fma.rn.f32x2 %%Q, {src}, %%Q, %%K1;")    # 1 - b e
+        self.e(f"fma.rn.f32x2 {dst}, %%P, %%Q, %%P;")     # e + e (1 - b e)
+
+    def inv(self):
+        # |t| < thr ? 0 : 1 / t
+        self.range_check("two_126")
+        for i in range(self.np):
+            self.rcp_pair(self.T[i], f"%%U{i}")
+        for i in range(self.np):
+            self.unpack(i, "%%v0", "%%v1")
+            self.e(f"mov.b64 {{%%u0, %%u1}}, %%U{i};")
+            for v, u in (("%%v0", "%%u0"), ("%%v1", "%%u1")):
+                self.e(f"abs.f32 %%m, {v};")
+                self.e(f"setp.lt.f32 %%p, %%m, {self.THR};")
+                self.e(f"selp.f32 {v}, 0f00000000, {u}, %%p;")
+            self.pack(i, "%%v0", "%%v1")
+
+    def sqrt(self):
+        # sqrt |t|
+        self.range_check("inf", lo="two_m100")
+        for i in range(self.np):
+            self.unpack(i, "%%v0", "%%v1")
+            self.e("abs.f32 %%v0, %%v0;")
+            self.e("abs.f32 %%v1, %%v1;")
+            self.e("rsqrt.approx.ftz.f32 %%u0, %%v0;")
+            self.e("rsqrt.approx.ftz.f32 %%u1, %%v1;")
+            self.e("mov.b64 %%F, {%%v0, %%v1};")            # x
+            self.e("mov.b64 %%P, {%%u0, %%u1};")            # e
+            self.e("mul.rn.f32x2 %%S, %%F, %%P;")           # g = x e
+            self.e(f"mov.b64 %%K0, {kp('half')};")
+            self.e("mul.rn.f32x2 %%Q, %%P, %%K0;")          # h = e / 2
+            self.e(f"mov.b64 %%K1, {kp('mone')};")
+            self.e("mul.rn.f32x2 %%R, %%S, %%K1;")          # -g
+            self.e("fma.rn.f32x2 %%R, %%R, %%S, %%F;")      # x - g g
+            self.e(f"fma.rn.f32x2 {self.T[i]}, %%R, %%Q, %%S;")
+
+    def div_body(self, reverse):
+        """t = t / u (or, reversed, u / t) for the operand pairs in U, with
+        the protection |divisor| < thr -> 1"""
+        num = (lambda i: f"%%U{i}") if reverse else (lambda i: self.T[i])
+        den = (lambda i: self.T[i]) if reverse else (lambda i: f"%%U{i}")
+        self.range_check(None, groups=[("two_60", None, den), ("two_60", "two_m60", num)])
+        for i in range(self.np):
+            # y = 1 / b, q = a y, then q + (a - b q) y
+            self.rcp_pair(den(i), "%%JJ")
+            self.e(f"mul.rn.f32x2 %%JM, {num(i)}, %%JJ;")
+            self.e(f"mov.b64 %%K0, {kp('mone')};")
+            self.e(f"mul.rn.f32x2 %%R, {den(i)}, %%K0;")     # -b
+            self.e(f"fma.rn.f32x2 %%R, %%R, %%JM, {num(i)};")  # a - b q
+            self.e("fma.rn.f32x2 %%JM, %%R, %%JJ, %%JM;")
+            self.e(f"mov.b64 {{%%s0, %%s1}}, {den(i)};")
+            self.e("mov.b64 {%%c0, %%c1}, %%JM;")
+            for v, b, q in (("%%v0", "%%s0", "%%c0"), ("%%v1", "%%s1", "%%c1")):
+                self.e(f"abs.f32 %%m, {b};")
+                self.e(f"setp.lt.f32 %%p, %%m, {self.THR};")
+                self.e(f"selp.f32 {v}, 0f3F800000, {q}, %%p;")
+            self.pack(i, "%%v0", "%%v1")
+
     # -- the loop -----------------------------------------------------------
     def table(self):
         """64 branch targets; a label names one body (ops sharing a body say so
@@ -312,8 +378,8 @@ class Gen:
         e("{")
         e(".reg .pred %%p, %%ps;")
         e(".reg .b32 %%w, %%cb, %%i, %%a, %%kd, %%n<2>, %%m<2>, %%k<2>;")
-        e(".reg .f32 %%cf, %%q, %%m, %%v<2>, %%u<2>, %%s<2>, %%c<2>;")
-        e(f".reg .b64 %%C, %%U<{p}>, %%K<2>, %%JM, %%JJ, %%R, %%S, %%P, %%Q, %%F;")
+        e(".reg .f32 %%cf, %%q, %%m, %%mx, %%mn, %%v<2>, %%u<2>, %%s<2>, %%c<2>;")
+        e(f".reg .b64 %%C, %%U<{p}>, %%K<2>, %%KM, %%JM, %%JJ, %%R, %%S, %%P, %%Q, %%F;")
         e("T%=: .branchtargets " + ", ".join(f"{x}%=" for x in ent) + ";")
         self.label("N")
         e("ld.shared.v2.b32 {%%w, %%cb}, [%0];")
@@ -377,22 +443,9 @@ class Gen:
                 e("bra.uni DTU%=;" if stem == "DX" else "bra.uni DUT%=;")
                 continue
             elif stem == "SQ":
-                for i in range(p):
-                    self.unpack(i, "%%v0", "%%v1")
-                    for v in ("%%v0", "%%v1"):
-                        e(f"abs.f32 {v}, {v};")
-                        e(f"sqrt.rn.f32 {v}, {v};")
-                    self.pack(i, "%%v0", "%%v1")
+                self.sqrt()
             elif stem == "IV":
-                # |t| < thr ? 0 : 1 / t
-                for i in range(p):
-                    self.unpack(i, "%%v0", "%%v1")
-                    for v in ("%%v0", "%%v1"):
-                        e(f"rcp.rn.f32 %%q, {v};")
-                        e(f"abs.f32 %%m, {v};")
-                        e(f"setp.lt.f32 %%p, %%m, {self.THR};")
-                        e(f"selp.f32 {v}, 0f00000000, %%q, %%p;")
-                    self.pack(i, "%%v0", "%%v1")
+                self.inv()
             elif stem == "TRG":
                 self.trig()
             elif stem == "LG":

@@ -242,6 +242,8 @@ __device__ __forceinline__ void interpret(float (&t)[RPT], const uint2 *__restri
             pa += 8u;
         }
         const uint32_t w = __shfl_sync(0xffffffffu, ins.x, 0);
+        // the end of the program, once per sub-tile: out before the switch
+        if ((w & 31u) == OP_END) break;
         const float c = __uint_as_float(ins.y);
 // operand helpers: stack slot, X column, constant
 // (the stack is laid out [slot][q][lane] in float4: slot sl, group q of

@@ -1,13 +1,17 @@
 // gp_math.cuh -- sin, cos, tan, log and exp for the evaluator's hot loop.
 //
-// Small inline fast path, out-of-line fallback: the trigonometric fast path covers finite
-// |x| < 65536 with a Cody-Waite reduction by pi/2 (W. J. Cody and W. Waite,
-// "Software Manual for the Elementary Functions", 1980) carried out with
-// three fused multiply-adds against a three-part split of pi/2, then
-// polynomials on [-pi/4, pi/4] whose coefficients fit_trig.py derives (a
-// minimax fit by Lawson's iteration, < 1 ulp in float32 on the interval).
-// Everything else -- huge arguments, inf, NaN -- goes to CUDA's sinf/cosf
-// through a non-inlined call, so the interpreter's inline code stays small.
+// Small inline fast path, out-of-line fallback: the trigonometric fast
+// path covers finite |x| < 65536 with a Cody-Waite reduction (W. J. Cody
+// and W. Waite, "Software Manual for the Elementary Functions", 1980)
+// carried out with three fused multiply-adds against a three-part split of
+// the period, then minimax polynomials whose coefficients fit_trig.py
+// derives (Lawson's iteration).  sin and cos reduce by pi (cos by an offset
+// of half a period) to one odd polynomial on [-pi/2, pi/2]: 1.76 ulp for
+// sin and 1.81 ulp for cos over |x| < 65536 (CUDA documents 2 ulp for its
+// sinf and cosf).  tan reduces by pi/2 and divides two polynomials on
+// [-pi/4, pi/4].  Everything else -- huge arguments, inf, NaN -- goes to
+// CUDA's sinf/cosf/tanf through a non-inlined call, so the interpreter's
+// inline code stays small.
 //
 // log: x = 2^k m with m in [sqrt(1/2), sqrt(2)), log x = k ln2 + log(1 + f)
 // with f = m - 1 and a degree-9 polynomial for log(1 + f) (coefficients
@@ -44,6 +48,15 @@ constexpr float kPio2Mid = -4.37113883e-08f;
 constexpr float kPio2Lo = -1.71512451e-15f;
 constexpr float kTwoOverPi = 0.636619747f;
 
+// pi = HI + MID + LO, and 1/pi rounded
+constexpr float kPiHi = 3.1415927410125732f;
+constexpr float kPiMid = -8.742277657347586e-08f;
+constexpr float kPiLo = -3.4302490200117637e-15f;
+constexpr float kInvPi = 0.31830987334251404f;
+// sin r ~ r + r^3 (Q0 + r^2 (Q1 + r^2 (Q2 + r^2 Q3))) on [-pi/2, pi/2]
+constexpr float kQ0 = -0.16666659712791443f, kQ1 = 0.008333065547049046f,
+                kQ2 = -0.0001980953966267407f, kQ3 = 2.6056311526190257e-06f;
+// tan's polynomials on [-pi/4, pi/4]:
 // sin r ~ r + r^3 (S0 + r^2 (S1 + r^2 (S2 + r^2 S3)))
 constexpr float kS0 = -0.166666672f, kS1 = 0.00833332911f, kS2 = -0.000198393129f,
                 kS3 = 2.71812155e-06f;
@@ -58,6 +71,14 @@ constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
 
 // The evaluator's fast loop (inline PTX) spells these constants as float
 // bit patterns; the checks keep the two spellings the same numbers.
+static_assert(__builtin_bit_cast(uint32_t, kPiHi) == 0x40490FDBu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kPiMid) == 0xB3BBBD2Eu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kPiLo) == 0xA7772CEDu, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kInvPi) == 0x3EA2F983u, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kQ0) == 0xBE2AAAA6u, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kQ1) == 0x3C088769u, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kQ2) == 0xB94FB7D4u, "trig constant");
+static_assert(__builtin_bit_cast(uint32_t, kQ3) == 0x362EDC67u, "trig constant");
 static_assert(__builtin_bit_cast(uint32_t, kPio2Hi) == 0x3FC90FDBu, "trig constant");
 static_assert(__builtin_bit_cast(uint32_t, kPio2Mid) == 0xB33BBD2Eu, "trig constant");
 static_assert(__builtin_bit_cast(uint32_t, kPio2Lo) == 0xA6F72CEDu, "trig constant");
@@ -141,6 +162,26 @@ __device__ __forceinline__ float exp_fast(float x) {
     return __fmul_rn(p, s);
 }
 
+// sin (kind 0) or cos (kind 1) of |x| < 65536: j = the integer nearest
+// x/pi - kind/2, r = x - (j + kind/2) pi in [-pi/2, pi/2] (plus rounding
+// slack), and the result is sin r, negated when j + kind is odd
+__device__ __forceinline__ float sincos_fast(float x, int kind) {
+    const float half = kind ? 0.5f : 0.0f;
+    const float t1 = __fmaf_rn(x, kInvPi, -half);
+    const float jm = __fadd_rn(t1, kRoundMagic);
+    const float jh = __fadd_rn(__fsub_rn(jm, kRoundMagic), half);
+    float r = __fmaf_rn(jh, -kPiHi, x);
+    r = __fmaf_rn(jh, -kPiMid, r);
+    r = __fmaf_rn(jh, -kPiLo, r);
+    const float s = __fmul_rn(r, r);
+    float p = __fmaf_rn(kQ3, s, kQ2);
+    p = __fmaf_rn(p, s, kQ1);
+    p = __fmaf_rn(p, s, kQ0);
+    const float v = __fmaf_rn(p, __fmul_rn(s, r), r);
+    return ((__float_as_int(jm) + kind) & 1) ? -v : v;
+}
+
+// tan's reduction: r = x - j pi/2, q = j mod 4
 __device__ __forceinline__ float trig_reduce(float x, int &q) {
     const float jm = __fmaf_rn(x, kTwoOverPi, kRoundMagic);
     const float j = __fsub_rn(jm, kRoundMagic);
@@ -170,36 +211,29 @@ static __device__ __noinline__ float trig_slow(float x, int kind) {
     return kind == 0 ? sinf(x) : (kind == 1 ? cosf(x) : tanf(x));
 }
 
-// Applies sin (kind 0), cos (1) or tan (2) to all RPT rows of a lane with
-// one body for the three: reduction and both polynomials on every row
-// without branching (so the rows' chains interleave), then the quadrant
-// select (sin, cos) or the quotient (tan); rows outside the fast path
-// (|x| >= 65536, inf, NaN) are redone by CUDA's function behind one test
-// for the whole group.
+// Applies sin (kind 0), cos (1) or tan (2) to all RPT rows of a lane:
+// the fast paths on every row without branching (so the rows' chains
+// interleave), then rows outside the fast path (|x| >= 65536, inf, NaN)
+// are redone by CUDA's function behind one test for the whole group.
 template <int RPT>
 __device__ __forceinline__ void trig_rows(float (&t)[RPT], int kind) {
-    float sn[RPT], cs[RPT];
-    int q[RPT];
-    bool slow = false;
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-        const float r = trig_reduce(t[j], q[j]);
-        const float s = __fmul_rn(r, r);
-        sn[j] = sin_poly(r, s);
-        cs[j] = cos_poly(s);
-        slow |= !(fabsf(t[j]) < kTrigFast);
-    }
     float v[RPT];
+    bool slow = false;
     if (kind == 2) {
 #pragma unroll
-        for (int j = 0; j < RPT; ++j)
-            v[j] = (q[j] & 1) ? -__fdiv_rn(cs[j], sn[j]) : __fdiv_rn(sn[j], cs[j]);
+        for (int j = 0; j < RPT; ++j) {
+            int q;
+            const float r = trig_reduce(t[j], q);
+            const float s = __fmul_rn(r, r);
+            const float sn = sin_poly(r, s), cs = cos_poly(s);
+            v[j] = (q & 1) ? -__fdiv_rn(cs, sn) : __fdiv_rn(sn, cs);
+            slow |= !(fabsf(t[j]) < kTrigFast);
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < RPT; ++j) {
-            const int qq = q[j] + kind;
-            const float a = (qq & 1) ? cs[j] : sn[j];
-            v[j] = (qq & 2) ? -a : a;
+            v[j] = sincos_fast(t[j], kind);
+            slow |= !(fabsf(t[j]) < kTrigFast);
         }
     }
     if (slow) {
