@@ -17,8 +17,9 @@ same bits; the constants are written here as the bit patterns that
 gp_math.cuh's static_asserts pin.  Code size matters as much as
 instruction count (at 8 rows per lane an unrolled body per operation
 overflowed the instruction cache: ncu's no_instruction stall rose to 4 per
-issue), so the division forms share two bodies (operands staged in U),
-sin and cos share one, and tan goes to the C++ switch.
+issue), so the division forms share one body (the divisor staged in U;
+the reversed forms swap the rows into U first), sin and cos share one,
+and tan goes to the C++ switch.
 
 Variants: RPT in {4, 8} x DIVS (the division set, square root, reciprocal,
 sin, cos, log and exp run here; without DIVS they are handed back) x
@@ -318,12 +319,16 @@ class Gen:
             self.e("fma.rn.f32x2 %%R, %%R, %%S, %%F;")      # x - g g
             self.e(f"fma.rn.f32x2 {self.T[i]}, %%R, %%Q, %%S;")
 
-    def div_body(self, reverse):
-        """t = t / u (or, reversed, u / t) for the operand pairs in U, with
-        the protection |divisor| < thr -> 1"""
-        num = (lambda i: f"%%U{i}") if reverse else (lambda i: self.T[i])
-        den = (lambda i: self.T[i]) if reverse else (lambda i: f"%%U{i}")
+    def div_check(self, num, den):
         self.range_check(None, groups=[("two_60", None, den), ("two_60", "two_m60", num)])
+
+    def div_body(self):
+        """t = t / u for the divisor pairs in U, with the protection
+        |divisor| < thr -> 1; DTUX: the same after the range test"""
+        num = lambda i: self.T[i]
+        den = lambda i: f"%%U{i}"
+        self.div_check(num, den)
+        self.label("DTUX")
         for i in range(self.np):
             # y = 1 / b, q = a y, then q + (a - b q) y
             self.rcp_pair(den(i), "%%JJ")
@@ -431,16 +436,28 @@ class Gen:
                 self.slot_load()
                 e("bra.uni DTU%=;")
                 continue
-            elif stem in ("DC", "RDC"):
-                self.cpair()
+            elif stem in ("DC", "DX"):
+                src = "%%C" if stem == "DC" else None
+                if stem == "DC":
+                    self.cpair()
                 for i in range(p):
-                    e(f"mov.b64 %%U{i}, %%C;")
-                e("bra.uni DTU%=;" if stem == "DC" else "bra.uni DUT%=;")
+                    e(f"mov.b64 %%U{i}, {src or X[col][i]};")
+                e("bra.uni DTU%=;")
                 continue
-            elif stem in ("DX", "RDX"):
+            elif stem in ("RDC", "RDX"):
+                # u / t: the range test on these operands first (a word
+                # handed back must leave the rows untouched), then the rows
+                # become the divisor and the operand the dividend, and the
+                # shared body divides (rare: 0.13 words per program of the
+                # Pagie-1 population)
+                if stem == "RDC":
+                    self.cpair()
+                opnd = (lambda i: "%%C") if stem == "RDC" else (lambda i, c=col: X[c][i])
+                self.div_check(num=opnd, den=lambda i: self.T[i])
                 for i in range(p):
-                    e(f"mov.b64 %%U{i}, {X[col][i]};")
-                e("bra.uni DTU%=;" if stem == "DX" else "bra.uni DUT%=;")
+                    e(f"mov.b64 %%U{i}, {self.T[i]};")
+                    e(f"mov.b64 {self.T[i]}, {opnd(i)};")
+                e("bra.uni DTUX%=;")
                 continue
             elif stem == "SQ":
                 self.sqrt()
@@ -456,12 +473,9 @@ class Gen:
                 raise ValueError(name)
             self.nxt()
         if self.divs:
-            # t = t / u and t = u / t with the protection, the operands in U
+            # t = t / u with the protection, the divisor pairs in U
             self.label("DTU")
-            self.div_body(False)
-            self.nxt()
-            self.label("DUT")
-            self.div_body(True)
+            self.div_body()
             self.nxt()
         self.label("EX")
         e(f"mov.b32 {self.HW}, %%w;")
@@ -486,8 +500,7 @@ def function(rpt, divs, xreg):
             f"        uint32_t &hw, float &hc) {{\n"
             f"    asm volatile(\n{body}\n"
             f"        : {outs}\n"
-            f"        : {ins}\n"
-            f"        : \"memory\");\n}}\n")
+            f"        : {ins});\n}}\n")
 
 
 HEADER = '''// gp_fast.cuh -- the evaluator's indexed-branch fast loop in inline PTX.
@@ -501,7 +514,12 @@ HEADER = '''// gp_fast.cuh -- the evaluator's indexed-branch fast loop in inline
 // the lane's slot-0 address in the shared-memory stack ([slot][q][lane]
 // float4); slots are clamped to NSLOT - 1; x0 and x1 hold columns 0 and 1
 // of the lane's rows (read only by the _x variants).  Every one of the 64
-// values of the six-bit dispatch index has a table entry.
+// values of the six-bit dispatch index has a table entry.  The statement
+// declares no memory clobber: the shared memory it reads and writes (the
+// code buffer, written before a barrier, and the stack, touched elsewhere
+// only by other volatile asm statements, which keep their order) needs none,
+// and a clobber made the compiler reload the kernel arguments after every
+// call.
 #pragma once
 
 #include <cstdint>

@@ -106,6 +106,58 @@ __device__ __forceinline__ void load_rows(float (&v)[RPT], const float *__restri
     }
 }
 
+// RPT consecutive rows of one column from p; with vec all of them as
+// 16-byte loads, otherwise the first nv rows one by one and 0 after them
+template <int RPT>
+__device__ __forceinline__ void load_chunk_rows(float (&v)[RPT], const float *__restrict__ p,
+                                                bool vec, int nv) {
+    if (vec) {
+#pragma unroll
+        for (int q = 0; q < RPT / 4; ++q) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(p) + q);
+            v[4 * q + 0] = f.x;
+            v[4 * q + 1] = f.y;
+            v[4 * q + 2] = f.z;
+            v[4 * q + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) v[j] = (j < nv) ? __ldg(p + j) : 0.0f;
+    }
+}
+
+// the weighted losses of a lane's rows added in row order (the first nv
+// rows count); the metric and the weights are tested once, not per row
+template <int RPT>
+__device__ __forceinline__ float loss_sum(int metric, const float (&t)[RPT],
+                                          const float (&yv)[RPT], const float (&wv)[RPT],
+                                          bool has_w, bool full, int nv) {
+    float l[RPT];
+    if (metric == GP_MAE) {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) l[j] = row_loss(GP_MAE, t[j], yv[j]);
+    } else if (metric == GP_LOGLOSS) {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) l[j] = row_loss(GP_LOGLOSS, t[j], yv[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) l[j] = row_loss(GP_MSE, t[j], yv[j]);
+    }
+    if (has_w) {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) l[j] = __fmul_rn(wv[j], l[j]);
+    }
+    float e = 0.0f;
+    if (full) {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) e = __fadd_rn(e, l[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) e = (j < nv) ? __fadd_rn(e, l[j]) : e;
+    }
+    return e;
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     const float yv = __fsub_rn(x, c);
     const float tv = __fadd_rn(s, yv);
@@ -360,15 +412,18 @@ constexpr size_t eval_smem_bytes() {
 }
 
 // epilogues: the weighted loss sum, the predictions, or the moment sums
-// of the correlation fitness.  The moment epilogue asks for the loss
-// epilogue's occupancy: 5 resident blocks at 4 rows per thread (at most 48
-// registers, with a few spilled words: 4% faster than 4 blocks at 59
-// registers on Pagie-1 16M x 4096) and 3 at 8 rows (at most 85 registers;
-// left alone it would take 97 and fit 2).
+// of the correlation fitness.  At 8 rows per thread every epilogue asks for
+// 3 resident blocks (at most 80 registers; left alone the loss epilogue
+// took 81 and fit 2).  At 4 rows the moment epilogue asks for 5 (at most 48
+// registers, a few spilled words: 4% faster than 4 blocks at 59 registers
+// on Pagie-1 16M x 4096); the others are left alone (46 registers: 5 fit),
+// because asking for 5 blocks there changed their schedule and cost 7%.
 constexpr int kEpiLoss = 0, kEpiPred = 1, kEpiMom = 2;
 
 template <int RPT, int NSLOT, int FMODE, int EPI, bool EXT>
-__global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom ? (RPT == 8 ? 3 : 5) : 0) eval_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(eval_warps<RPT>() * 32,
+                                  RPT == 8 ? 3 : (EPI == kEpiMom && RPT == 4 ? 5 : 0))
+    eval_kernel(const EvalArgs a) {
     constexpr bool PRED = EPI == kEpiPred;
     constexpr bool MOM = EPI == kEpiMom;
     constexpr int kEvalWarps = eval_warps<RPT>();
@@ -430,13 +485,25 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom ? (RPT 
         float ks = 0.0f, kc = 0.0f;
         float ms[3] = {0.0f, 0.0f, 0.0f}, mc[3] = {0.0f, 0.0f, 0.0f};
         const float shift = MOM ? a.shift[p] : 0.0f;
-        for (int64_t base = rb + (int64_t)warp * 32 * RPT; base < re;
-             base += (int64_t)kEvalWarps * 32 * RPT) {
-            const int64_t r0 = base + (int64_t)lane * RPT;
+        // rows of the chunk in 32-bit offsets from its first row (a chunk
+        // holds at most 2^30 rows); pointers to the chunk's columns once
+        const int n_in = (int)(re - rb);
+        // the column pointers are formed per use from the kernel arguments
+        // (held in constant memory): four live 64-bit pointers would cost
+        // the loop 8 registers and a resident block
+        const int64_t x1off = two_feat ? a.ld : 0;
+        for (int base = warp * 32 * RPT; base < n_in; base += kEvalWarps * 32 * RPT) {
+            const int o = base + lane * RPT;  // this lane's first row in the chunk
+            // every row of the warp is in the chunk except in its last
+            // sub-tile; decided once for the warp (a vote), so the loads and
+            // the loss take no divergent branch (each per-lane test had cost
+            // a reconvergence barrier pair per sub-tile)
+            const bool full = __all_sync(0xffffffffu, o + RPT <= n_in);
+            const int nv = full ? RPT : n_in - o;  // rows of the lane to count
             float x0[RPT], x1[RPT];
             if (FMODE == 2) {
-                load_rows<RPT>(x0, a.X, r0, re, vec);
-                if (two_feat) load_rows<RPT>(x1, a.X + a.ld, r0, re, vec);
+                load_chunk_rows<RPT>(x0, a.X + (rb + o), full && vec, nv);
+                if (two_feat) load_chunk_rows<RPT>(x1, a.X + (x1off + rb + o), full && vec, nv);
                 else {
 #pragma unroll
                     for (int j = 0; j < RPT; ++j) x1[j] = x0[j];
@@ -446,44 +513,37 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32, EPI == kEpiMom ? (RPT 
                 for (int j = 0; j < RPT; ++j) x0[j] = x1[j] = 0.0f;
             }
             float t[RPT];
-            interpret<RPT, NSLOT, FMODE, EXT>(t, cbuf, x0, x1, a.X, a.ld, r0, re, vec, stk);
+            interpret<RPT, NSLOT, FMODE, EXT>(t, cbuf, x0, x1, a.X, a.ld, rb + o, re, vec, stk);
             if (PRED) {
-                float *dst = a.pred + (size_t)p * a.n_rows;
+                float *dst = a.pred + (size_t)p * a.n_rows + rb + o;
 #pragma unroll
                 for (int j = 0; j < RPT; ++j)
-                    if (r0 + j < re) dst[r0 + j] = t[j];
+                    if (j < nv) dst[j] = t[j];
             } else if (MOM) {
                 // d = p - shift keeps the sums of squares free of the
                 // cancellation a large mean would cause
                 float yv[RPT], wv[RPT];
-                load_rows<RPT>(yv, a.y, r0, re, vec);
-                if (a.w) load_rows<RPT>(wv, a.w, r0, re, vec);
+                load_chunk_rows<RPT>(yv, a.y + (rb + o), full && vec, nv);
+                if (a.w) load_chunk_rows<RPT>(wv, a.w + (rb + o), full && vec, nv);
                 float e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) {
                     const float d = __fsub_rn(t[j], shift);
-                    const float yc = __fsub_rn(yv[j], ybar);
+                    const float yc_ = __fsub_rn(yv[j], ybar);
                     const float wd = a.w ? __fmul_rn(wv[j], d) : d;
-                    const bool in = r0 + j < re;
+                    const bool in = j < nv;
                     e1 = in ? __fadd_rn(e1, wd) : e1;
                     e2 = in ? __fadd_rn(e2, __fmul_rn(wd, d)) : e2;
-                    e3 = in ? __fadd_rn(e3, __fmul_rn(wd, yc)) : e3;
+                    e3 = in ? __fadd_rn(e3, __fmul_rn(wd, yc_)) : e3;
                 }
                 kahan_add(ms[0], mc[0], e1);
                 kahan_add(ms[1], mc[1], e2);
                 kahan_add(ms[2], mc[2], e3);
             } else {
                 float yv[RPT], wv[RPT];
-                load_rows<RPT>(yv, a.y, r0, re, vec);
-                if (a.w) load_rows<RPT>(wv, a.w, r0, re, vec);
-                float e = 0.0f;
-#pragma unroll
-                for (int j = 0; j < RPT; ++j) {
-                    float l = row_loss(a.metric, t[j], yv[j]);
-                    if (a.w) l = __fmul_rn(wv[j], l);
-                    e = (r0 + j < re) ? __fadd_rn(e, l) : e;
-                }
-                kahan_add(ks, kc, e);
+                load_chunk_rows<RPT>(yv, a.y + (rb + o), full && vec, nv);
+                if (a.w) load_chunk_rows<RPT>(wv, a.w + (rb + o), full && vec, nv);
+                kahan_add(ks, kc, loss_sum<RPT>(a.metric, t, yv, wv, a.w != nullptr, full, nv));
             }
         }
         if (MOM) {
