@@ -692,12 +692,33 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, con
     GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
     CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
                    W.rchild, W.kslot, W.cnode, c->status, nullptr};
+    ca.grad = 1;  // the gradient form: no constant folding, slots and spill sources
     GP_CUDA(launch_compile(ca, st));
-    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
+    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st, 1));
     GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
-    GradArgs ga{progs, offsets, W.meta, W.order, W.rchild, W.kslot, X, n_rows, n_rows, y, w,
-                n_progs, metric, chunk, n_chunks, W.counters, W.part, W.gpart, c->status};
-    GP_CUDA(launch_grad(ga, c->sms * std::max(info_grad(), 1), 128, st));
+    // one launch per length bucket of the compiled programs
+    for (int bucket = 0; bucket < kGradBuckets; ++bucket) {
+        GradArgs ga{};
+        ga.code = W.code;
+        ga.meta = W.meta;
+        ga.order = W.order;
+        ga.class_count = W.class_count;
+        ga.bucket = bucket;
+        ga.X = X;
+        ga.ld = n_rows;
+        ga.n_rows = n_rows;
+        ga.n_feat = n_feat;
+        ga.y = y;
+        ga.w = w;
+        ga.metric = metric;
+        ga.chunk_rows = chunk;
+        ga.n_chunks = n_chunks;
+        ga.counter = W.counters;
+        ga.part = W.part;
+        ga.gpart = W.gpart;
+        ga.dev_status = c->status;
+        GP_CUDA(launch_grad(ga, c->sms, st));
+    }
     GradFinalizeArgs fa{W.part, W.gpart, n_chunks, n_progs, W.meta, W.sumw, metric,
                         out_grad, out_fitness};
     GP_CUDA(launch_grad_finalize(fa, st));

@@ -28,7 +28,7 @@ Layout make_layout(int n_progs, int n_chunks, bool grad, bool moments) {
     L.code = o;        o = align256(o + P * kCodeStride * sizeof(uint2));
     L.meta = o;        o = align256(o + P * sizeof(ProgMeta));
     L.order = o;       o = align256(o + P * sizeof(int32_t));
-    L.class_count = o; o = align256(o + (kNumClasses + 2) * sizeof(int32_t));
+    L.class_count = o; o = align256(o + (kOrderClasses + 2) * sizeof(int32_t));
     L.part = o;        o = align256(o + P * C * sizeof(float));
     if (moments) {
         L.ystat = o;      o = align256(o + 4 * sizeof(double));
@@ -160,19 +160,19 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
         if (ar == 0) {
             s = 1;
             n_consts += (nd.op == GP_CONST);
-            k = nd.op == GP_CONST;
+            k = nd.op == GP_CONST;  // (the gradient form clears k of functions below)
             v = k ? nd.c : (row0 ? a.X[(int64_t)nd.feat * a.ld] : 0.0f);
         } else if (ar == 1) {
             if (sp < 1) { status = GP_PROG_UNDERFLOW; break; }
             --sp;
             s = 1 + szst[sp];
-            k = kst[sp];
+            k = a.grad ? 0 : kst[sp];
             if (k || row0) v = fold_unary(nd.op, vst[sp]);
         } else {
             if (sp < 2) { status = GP_PROG_UNDERFLOW; break; }
             // first pop is the left operand
             const int l = szst[sp - 1], r = szst[sp - 2];
-            k = kst[sp - 1] & kst[sp - 2];
+            k = a.grad ? 0 : (kst[sp - 1] & kst[sp - 2]);
             if (k || row0) v = fold_binary(nd.op, vst[sp - 1], vst[sp - 2]);
             sp -= 2;
             s = 1 + l + r;
@@ -243,6 +243,19 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
         for (; k < GP_MAX_CONSTS; ++k) cn[k] = -1;
     }
 
+    // gradient form: the slot of each constant (k-th CONST in prefix order)
+    // and, per stack slot, the word whose result was spilled into it
+    uint8_t cslot[GP_MAX_LEN];
+    uint8_t spill_src[GP_MAX_STACK];
+    if (a.grad) {
+        int k = 0;
+        for (int j = 0; j < len; ++j) {
+            cslot[j] = (uint8_t)(k < GP_MAX_CONSTS ? k : GP_MAX_CONSTS);
+            k += prog[j].op == GP_CONST;
+        }
+    }
+    auto aux = [&](uint32_t v) { return a.grad ? (v << 24) : 0u; };
+
     // pass 3: emit in reverse-scan order
     int n = 0, depth = 0;
     bool ext = false;  // an extended-set instruction was emitted
@@ -262,8 +275,10 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
             const bool spill = sp > 0;  // the old top goes to slot sp-1
             const uint32_t op = (spill ? (x ? OP_PUSH_X_SP : OP_PUSH_C_SP) : (x ? OP_PUSH_X : OP_PUSH_C)) |
                                 ((x && nd.feat == 1) ? kOpCol1 : 0u);
-            out[n++] = make_uint2(make_ins(op, spill ? sp - 1 : 0, (uint32_t)(uint16_t)nd.feat),
-                                  __float_as_uint(nd.c));
+            if (spill && a.grad) spill_src[sp - 1] = (uint8_t)(n - 1);
+            const uint32_t w = x ? make_ins(op, spill ? sp - 1 : 0, (uint32_t)(uint16_t)nd.feat)
+                                 : (make_ins(op, spill ? sp - 1 : 0, 0) | aux(a.grad ? cslot[j] : 0u));
+            out[n++] = make_uint2(w, __float_as_uint(nd.c));
             ++sp;
         } else if (ar == 1) {
             const bool e = nd.op > GP_INV;  // extended function: its number in the feature field
@@ -278,7 +293,9 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
                 // right operand in slot sp-2, left operand is t
                 const uint32_t ops[6] = {OP_ADD_S, OP_SUB_S, OP_MUL_S, OP_DIV_S, OP_EXT2, OP_EXT2};
                 ext |= b >= 4;
-                out[n++] = make_uint2(make_ins(ops[b], sp - 2, b >= 4 ? (uint32_t)(b - 4) : 0u), 0u);
+                out[n++] = make_uint2(make_ins(ops[b], sp - 2, b >= 4 ? (uint32_t)(b - 4) : 0u) |
+                                          aux(a.grad ? spill_src[sp - 2] : 0u),
+                                      0u);
                 --sp;
             } else {
                 const int tj = (mode[j] == 1) ? j + 1 + size[j + 1] : j + 1;
@@ -294,8 +311,9 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
                 const uint32_t rev[4] = {OP_ADD_X, OP_RSUB_X, OP_MUL_X, OP_RDIV_X};
                 const uint32_t op = (((mode[j] == 1) ? fwd[b] : rev[b]) + x) |
                                     ((x == 0 && t.feat == 1) ? kOpCol1 : 0u);
-                out[n++] = make_uint2(make_ins(op, 0, (uint32_t)(uint16_t)t.feat),
-                                      __float_as_uint(t.c));
+                const uint32_t w = x == 0 ? make_ins(op, 0, (uint32_t)(uint16_t)t.feat)
+                                          : (make_ins(op, 0, 0) | aux(a.grad ? cslot[tj] : 0u));
+                out[n++] = make_uint2(w, __float_as_uint(t.c));
             }
         }
         if (sp > depth) depth = sp;
@@ -315,19 +333,26 @@ cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st) {
 // Counting sort of program ids: key = class * 256 + (256 - n_ins), so the
 // classes follow one another (0, 1, 2) and, inside a class, longer programs
 // come first (longest-processing-time order for the dynamic work queue).
+// mode 0: the evaluator's classes (stack depth, extended functions); mode
+// 1: the gradient's length buckets.
 // Invalid programs (n_ins = 1) land at the end of class 0.  Order inside
 // one key is arbitrary; results do not depend on it.
-constexpr int kOrderBins = kNumClasses * 256;
+constexpr int kOrderBins = kOrderClasses * 256;
+
+__device__ __forceinline__ int order_class(const ProgMeta &m, int mode) {
+    return mode == 0 ? prog_class(m.depth, m.ext) : grad_bucket(m.n_ins, m.depth);
+}
 
 __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n_progs,
-                                                     int32_t *order, int32_t *class_count) {
+                                                     int32_t *order, int32_t *class_count,
+                                                     int mode) {
     __shared__ int hist[kOrderBins];
     __shared__ int cursor[kOrderBins];
     for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (int p = threadIdx.x; p < n_progs; p += blockDim.x) {
         const ProgMeta m = meta[p];
-        const int cls = prog_class(m.depth, m.ext);
+        const int cls = order_class(m, mode);
         const int key = cls * 256 + (256 - m.n_ins);
         atomicAdd(&hist[key], 1);
     }
@@ -342,13 +367,13 @@ __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n
                 prev = run;
             }
         }
-        class_count[kNumClasses] = 0;
-        class_count[kNumClasses + 1] = 0;
+        class_count[kOrderClasses] = 0;
+        class_count[kOrderClasses + 1] = 0;
     }
     __syncthreads();
     for (int p = threadIdx.x; p < n_progs; p += blockDim.x) {
         const ProgMeta m = meta[p];
-        const int cls = prog_class(m.depth, m.ext);
+        const int cls = order_class(m, mode);
         const int key = cls * 256 + (256 - m.n_ins);
         const int pos = atomicAdd(&cursor[key], 1);
         order[pos] = p;
@@ -356,8 +381,8 @@ __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n
 }
 
 cudaError_t launch_order(const ProgMeta *meta, int n_progs, int32_t *order,
-                         int32_t *class_count, cudaStream_t st) {
-    order_kernel<<<1, 1024, 0, st>>>(meta, n_progs, order, class_count);
+                         int32_t *class_count, cudaStream_t st, int mode) {
+    order_kernel<<<1, 1024, 0, st>>>(meta, n_progs, order, class_count, mode);
     return cudaGetLastError();
 }
 

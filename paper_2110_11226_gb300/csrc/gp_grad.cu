@@ -3,47 +3,38 @@
 // has a counterpart in the paper; they serve constant tuning between
 // generations.
 //
-// Per row, the forward values of all nodes are recomputed (children have
-// larger prefix positions, so a reverse sweep over the list computes each
-// node from already computed children with the same FP32 operations as the
-// stack evaluator) and kept in per-thread local memory; nothing of size
-// programs x rows x nodes is ever stored.  The adjoint sweep then runs in
-// prefix order, parents before children: the root gets w * dl/dp and every
-// function hands its children their share; a constant adds its node's
-// adjoint into its slot.  Per-thread sums are Kahan-compensated FP32, warp
-// sums fixed-order, cross-chunk sums FP64 (gp_reduce.cu).
+// The adjoint runs on the compiled stack form of the evaluator
+// (gp_internal.cuh), in its gradient variant: no constant-only subtree is
+// folded, every word that reads a constant names the constant's slot, and
+// every word that pops a stack slot names the word whose result was spilled
+// into it.  A block takes one (program, row chunk) item; its warps run the
+// program over their own sub-tiles of 32 * RPT rows:
+//   forward   the words in order, as the evaluator runs them (the same FP32
+//             operations, so the fitness equals gp_evaluate's), each word's
+//             result written to the warp's tape in shared memory -- one float
+//             per word and row, nothing of size programs x rows x nodes;
+//   adjoint   the words in reverse: the adjoint of the top of the stack in
+//             registers, the adjoints of spilled values in the warp's stack
+//             slots (the forward values there are dead by then); a word's
+//             input is the previous word's result on the tape, a popped
+//             slot's value the spilled word's result; a word that reads a
+//             constant adds its share to that constant's per-lane sum.
+// Programs are bucketed by compiled length (kGradCap0, 1, 2, 256 words) and
+// depth, one launch per bucket with a tape sized for its longest program.
+// Per-lane sums are FP32 (the loss Kahan-compensated), warp sums
+// fixed-order, chunk sums FP64 in order (gp_reduce.cu).
 #include "gp_internal.cuh"
-#include "gp_math.cuh"
+#include "gp_interp.cuh"
 
 namespace gpk {
 
 namespace {
 
-constexpr int kGradBlock = 128;
-
-__device__ __forceinline__ void kahan(float &s, float &c, float x) {
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = isfinite(t) ? __fsub_rn(__fsub_rn(t, s), y) : 0.0f;
-    s = t;
-}
-
 __device__ __forceinline__ float sgnf(float x) {
     return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f);
 }
 
-__device__ __forceinline__ float g_loss(int metric, float p, float y) {
-    if (metric == GP_MAE) return fabsf(__fsub_rn(p, y));
-    if (metric == GP_LOGLOSS) {
-        const float ap = fabsf(p);
-        const float c = (p >= 0.0f) ? __fsub_rn(1.0f, y) : y;
-        const float lin = (c == 0.0f) ? 0.0f : __fmul_rn(c, ap);
-        return __fadd_rn(lin, log1pf(expf(-ap)));
-    }
-    const float d = __fsub_rn(p, y);
-    return __fmul_rn(d, d);
-}
-
+// d loss / d p of one row (the metric readings of Sec. III-C3)
 __device__ __forceinline__ float g_dloss(int metric, float p, float y) {
     if (metric == GP_MAE) return sgnf(__fsub_rn(p, y));
     if (metric == GP_LOGLOSS) {
@@ -59,203 +50,356 @@ __device__ __forceinline__ float g_dloss(int metric, float p, float y) {
     return __fmul_rn(2.0f, __fsub_rn(p, y));
 }
 
-__device__ __forceinline__ float g_f1(int op, float a) {
+// derivative of a unary word at input u with output v (the protected
+// operators have derivative 0 on their protected branch)
+__device__ __forceinline__ float d_unary(uint32_t op, uint32_t ext, float u, float v) {
     switch (op) {
-    case GP_SQRT: return __fsqrt_rn(fabsf(a));
-    case GP_LOG: return fabsf(a) < kThr ? 0.0f : logf(fabsf(a));
-    case GP_EXP: return expf(a);
-    case GP_SIN: return sinf(a);
-    case GP_COS: return cosf(a);
-    case GP_TAN: return tanf(a);
-    case GP_ABS: return fabsf(a);
-    case GP_NEG: return -a;
-    case GP_INV: return fabsf(a) < kThr ? 0.0f : __frcp_rn(a);
-    case GP_SQ: return f_sq(a);
-    case GP_CUBE: return f_cube(a);
-    case GP_CBRT: return f_cbrt(a);
-    case GP_TANH: return f_tanh(a);
-    case GP_ATAN: return f_atan(a);
-    case GP_SINH: return f_sinh(a);
-    default: return f_cosh(a);
+    case OP_SQRT: return (u == 0.0f) ? 0.0f : __fdiv_rn(sgnf(u), __fmul_rn(2.0f, v));
+    case OP_LOG: return fabsf(u) < kThr ? 0.0f : __frcp_rn(u);
+    case OP_EXP: return v;
+    case OP_SIN: return cosf(u);
+    case OP_COS: return -sinf(u);
+    case OP_TAN: return __fadd_rn(1.0f, __fmul_rn(v, v));
+    case OP_ABS: return sgnf(u);
+    case OP_NEG: return -1.0f;
+    case OP_INV: return fabsf(u) < kThr ? 0.0f : -__fmul_rn(v, v);
+    default:  // OP_EXT1
+        switch (ext) {
+        case EXT_SQ: return __fmul_rn(2.0f, u);
+        case EXT_CUBE: return __fmul_rn(3.0f, __fmul_rn(u, u));
+        case EXT_CBRT: return (u == 0.0f) ? 0.0f : __frcp_rn(__fmul_rn(3.0f, __fmul_rn(v, v)));
+        case EXT_TANH: return __fsub_rn(1.0f, __fmul_rn(v, v));
+        case EXT_ATAN: return __frcp_rn(__fadd_rn(1.0f, __fmul_rn(u, u)));
+        case EXT_SINH: return coshf(u);
+        default: return sinhf(u);  // EXT_COSH
+        }
     }
 }
 
-__device__ __forceinline__ float g_f2(int op, float l, float r) {
-    switch (op) {
-    case GP_ADD: return __fadd_rn(l, r);
-    case GP_SUB: return __fsub_rn(l, r);
-    case GP_MUL: return __fmul_rn(l, r);
-    case GP_DIV: return fabsf(r) < kThr ? 1.0f : __fdiv_rn(l, r);
-    case GP_MAX: return f_max(l, r);
-    default: return f_min(l, r);
+// v into constant k's per-lane sum (k uniform over the warp).  Plain FP32:
+// a lane adds at most 512 terms per 16K-row chunk (then FP64 across
+// chunks); compensated sums had cost 16 registers and a resident block.
+__device__ __forceinline__ void gadd(float (&gs)[GP_MAX_CONSTS], uint32_t k, float v) {
+#define GP_GADD_CASE(q) \
+    case q: gs[q] = __fadd_rn(gs[q], v); break;
+    switch (k) {
+        GP_GADD_CASE(0) GP_GADD_CASE(1) GP_GADD_CASE(2) GP_GADD_CASE(3)
+        GP_GADD_CASE(4) GP_GADD_CASE(5) GP_GADD_CASE(6) GP_GADD_CASE(7)
+        GP_GADD_CASE(8) GP_GADD_CASE(9) GP_GADD_CASE(10) GP_GADD_CASE(11)
+        GP_GADD_CASE(12) GP_GADD_CASE(13) GP_GADD_CASE(14) GP_GADD_CASE(15)
+        default: break;
     }
+#undef GP_GADD_CASE
 }
 
-__device__ __forceinline__ bool is_unary(int op) { return op >= GP_SQRT && op <= GP_COSH; }
+// the extended unary functions of one row (the evaluator's, so the forward
+// values are its values)
+__device__ __forceinline__ float f_ext1(uint32_t fn, float x) {
+    switch (fn) {
+    case EXT_SQ: return f_sq(x);
+    case EXT_CUBE: return f_cube(x);
+    case EXT_CBRT: return f_cbrt(x);
+    case EXT_TANH: return f_tanh(x);
+    case EXT_ATAN: return f_atan(x);
+    case EXT_SINH: return f_sinh(x);
+    default: return f_cosh(x);
+    }
+}
 
 }  // namespace
 
-__global__ void __launch_bounds__(kGradBlock) grad_kernel(GradArgs a) {
-    __shared__ gp_node s_nodes[kGradBlock / 32][kCodeStride];
-    __shared__ uint8_t s_rc[kGradBlock / 32][kCodeStride];
-    __shared__ int8_t s_ks[kGradBlock / 32][kCodeStride];
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    gp_node *nodes = s_nodes[wi];
-    uint8_t *rc = s_rc[wi];
-    int8_t *ks = s_ks[wi];
-    const unsigned long long total =
-        (unsigned long long)a.n_progs * (unsigned long long)a.n_chunks;
-    float val[GP_MAX_LEN], adj[GP_MAX_LEN];
+// shared memory of one block: the program's words, then per warp the tape
+// [CAP words][RPT rows][32 lanes] and the adjoint slots [NSLOT][RPT][32]
+template <int RPT, int WARPS, int CAP, int NSLOT>
+constexpr size_t grad_smem_bytes() {
+    return ((size_t)(CAP + 2) * sizeof(uint2) + 15) / 16 * 16 +
+           (size_t)WARPS * (CAP + NSLOT) * RPT * 32 * sizeof(float);
+}
+
+template <int RPT, int WARPS, int CAP, int NSLOT, int MINB, bool XREG>
+__global__ void __launch_bounds__(WARPS * 32, MINB) grad_kernel(const GradArgs a) {
+    extern __shared__ float4 smem_grad[];
+    uint2 *cbuf = reinterpret_cast<uint2 *>(smem_grad);
+    float *tape_all = reinterpret_cast<float *>(smem_grad + ((CAP + 2) * sizeof(uint2) + 15) / 16);
+    float *slot_all = tape_all + (size_t)WARPS * CAP * RPT * 32;
+    __shared__ float wsum[WARPS];
+    __shared__ float wgrad[WARPS][GP_MAX_CONSTS];
+    __shared__ unsigned long long s_item;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    // element (word i, row j) of this lane: tape[(i * RPT + j) * 32]
+    float *tape = tape_all + (size_t)warp * CAP * RPT * 32 + lane;
+    float *adjs = slot_all + (size_t)warp * NSLOT * RPT * 32 + lane;
+    int cls_begin = 0;
+    for (int b = 0; b < a.bucket; ++b) cls_begin += a.class_count[b];
+    const int n_cls = a.class_count[a.bucket];
+    const unsigned long long total = (unsigned long long)n_cls * (unsigned long long)a.n_chunks;
+    const bool two_feat = XREG && a.n_feat == 2;
 
     for (unsigned long long it = 0; it <= total; ++it) {
-        if (it == total) {
-            if (lane == 0) atomicOr(a.dev_status, GP_DEV_QUEUE_CAP);
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter + a.bucket, 1ULL);
+        __syncthreads();
+        const unsigned long long item = s_item;
+        if (item >= total || it == total) {  // the cap cannot trigger: one item per pass
+            if (it == total && threadIdx.x == 0) atomicOr(a.dev_status, GP_DEV_QUEUE_CAP);
             break;
         }
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(a.counter, 1ULL);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= total) break;
-        const int chunk = (int)(item / (unsigned long long)a.n_progs);
-        const int rank = (int)(item - (unsigned long long)chunk * a.n_progs);
-        const int p = a.order[rank];
+        const int chunk = (int)(item / (unsigned long long)n_cls);
+        const int rank = (int)(item - (unsigned long long)chunk * n_cls);
+        const int p = a.order[cls_begin + rank];
         const ProgMeta m = a.meta[p];
         float *gp = a.gpart + ((size_t)p * a.n_chunks + chunk) * GP_MAX_CONSTS;
-        if (m.status != GP_PROG_OK || m.n_consts > GP_MAX_CONSTS) {
-            if (lane == 0) {
+        if (m.status != GP_PROG_OK || m.n_consts > GP_MAX_CONSTS || m.n_ins > CAP) {
+            if (threadIdx.x == 0) {
                 a.part[(size_t)p * a.n_chunks + chunk] = __int_as_float(0x7fc00000);
-                for (int k = 0; k < GP_MAX_CONSTS; ++k) gp[k] = __int_as_float(0x7fc00000);
                 if (m.n_consts > GP_MAX_CONSTS) atomicOr(a.dev_status, GP_DEV_TOO_MANY_CONSTS);
             }
+            if (threadIdx.x < GP_MAX_CONSTS) gp[threadIdx.x] = __int_as_float(0x7fc00000);
+            __syncthreads();  // s_item is rewritten at the top
             continue;
         }
-        const int off = a.offsets[p];
-        const int len = a.offsets[p + 1] - off;
-        __syncwarp();
-        for (int i = lane; i < len; i += 32) {
-            nodes[i] = a.progs[off + i];
-            rc[i] = a.rchild[(size_t)p * kCodeStride + i];
-            ks[i] = a.kslot[(size_t)p * kCodeStride + i];
-        }
-        __syncwarp();
+        const int n_ins = m.n_ins;
+        for (int i = threadIdx.x; i < n_ins; i += WARPS * 32) cbuf[i] = a.code[(size_t)p * kCodeStride + i];
+        __syncthreads();
 
         const int64_t rb = (int64_t)chunk * a.chunk_rows;
         const int64_t re = min(a.n_rows, rb + a.chunk_rows);
-        float gs[GP_MAX_CONSTS], gc[GP_MAX_CONSTS];
+        const int n_in = (int)(re - rb);
+        float gs[GP_MAX_CONSTS];
 #pragma unroll
-        for (int k = 0; k < GP_MAX_CONSTS; ++k) gs[k] = gc[k] = 0.0f;
+        for (int k = 0; k < GP_MAX_CONSTS; ++k) gs[k] = 0.0f;
         float ls = 0.0f, lc = 0.0f;
-        for (int64_t r = rb + lane; r < re; r += 32) {
-            // forward: children before parents
-            for (int j = len - 1; j >= 0; --j) {
-                const gp_node nd = nodes[j];
-                float v;
-                if (nd.op == GP_CONST) v = nd.c;
-                else if (nd.op == GP_VAR) v = __ldg(a.X + (int64_t)nd.feat * a.ld + r);
-                else if (is_unary(nd.op)) v = g_f1(nd.op, val[j + 1]);
-                else v = g_f2(nd.op, val[j + 1], val[j + rc[j]]);
-                val[j] = v;
-            }
-            const float pr = val[0];
-            const float yv = __ldg(a.y + r);
-            const float wv = a.w ? __ldg(a.w + r) : 1.0f;
-            kahan(ls, lc, __fmul_rn(wv, g_loss(a.metric, pr, yv)));
-            // adjoint: parents before children
-            adj[0] = __fmul_rn(wv, g_dloss(a.metric, pr, yv));
-            for (int j = 0; j < len; ++j) {
-                const gp_node nd = nodes[j];
-                const float aj = adj[j];
-                if (nd.op == GP_CONST) {
-                    const int k = ks[j];
+        for (int base = warp * 32 * RPT; base < n_in; base += WARPS * 32 * RPT) {
+            const int o = base + lane * RPT;
+            const bool full = __all_sync(0xffffffffu, o + RPT <= n_in);
+            const int nv = full ? RPT : n_in - o;
+            const int64_t r0 = rb + o;
+            float x0[RPT], x1[RPT];
+            if (XREG) {
 #pragma unroll
-                    for (int q = 0; q < GP_MAX_CONSTS; ++q)
-                        if (q == k) kahan(gs[q], gc[q], aj);
-                    continue;
-                }
-                if (nd.op == GP_VAR) continue;
-                const float u = val[j + 1];
-                if (is_unary(nd.op)) {
-                    float du;
-                    switch (nd.op) {
-                    case GP_SQRT: du = (u == 0.0f) ? 0.0f : __fdiv_rn(sgnf(u), __fmul_rn(2.0f, val[j])); break;
-                    case GP_LOG: du = fabsf(u) < kThr ? 0.0f : __frcp_rn(u); break;
-                    case GP_EXP: du = val[j]; break;
-                    case GP_SIN: du = cosf(u); break;
-                    case GP_COS: du = -sinf(u); break;
-                    case GP_TAN: du = __fadd_rn(1.0f, __fmul_rn(val[j], val[j])); break;
-                    case GP_ABS: du = sgnf(u); break;
-                    case GP_NEG: du = -1.0f; break;
-                    case GP_INV: du = fabsf(u) < kThr ? 0.0f : -__fmul_rn(val[j], val[j]); break;
-                    case GP_SQ: du = __fmul_rn(2.0f, u); break;
-                    case GP_CUBE: du = __fmul_rn(3.0f, __fmul_rn(u, u)); break;
-                    case GP_CBRT:
-                        du = (u == 0.0f) ? 0.0f : __frcp_rn(__fmul_rn(3.0f, __fmul_rn(val[j], val[j])));
-                        break;
-                    case GP_TANH: du = __fsub_rn(1.0f, __fmul_rn(val[j], val[j])); break;
-                    case GP_ATAN: du = __frcp_rn(__fadd_rn(1.0f, __fmul_rn(u, u))); break;
-                    case GP_SINH: du = coshf(u); break;
-                    default: du = sinhf(u); break;  // GP_COSH
-                    }
-                    adj[j + 1] = __fmul_rn(aj, du);
-                } else {
-                    const float v = val[j + rc[j]];
-                    float du, dv;
-                    switch (nd.op) {
-                    case GP_ADD: du = 1.0f; dv = 1.0f; break;
-                    case GP_SUB: du = 1.0f; dv = -1.0f; break;
-                    case GP_MUL: du = v; dv = u; break;
-                    case GP_DIV:
-                        if (fabsf(v) < kThr) { du = 0.0f; dv = 0.0f; }
-                        else { du = __frcp_rn(v); dv = -__fdiv_rn(val[j], v); }
-                        break;
-                    case GP_MAX:
-                        du = (u > v || u != u) ? 1.0f : 0.0f;
-                        dv = __fsub_rn(1.0f, du);
-                        break;
-                    default:  // GP_MIN
-                        du = (u < v || u != u) ? 1.0f : 0.0f;
-                        dv = __fsub_rn(1.0f, du);
-                        break;
-                    }
-                    adj[j + 1] = __fmul_rn(aj, du);
-                    adj[j + rc[j]] = __fmul_rn(aj, dv);
+                for (int j = 0; j < RPT; ++j) {
+                    x0[j] = (j < nv) ? __ldg(a.X + r0 + j) : 0.0f;
+                    x1[j] = two_feat ? ((j < nv) ? __ldg(a.X + a.ld + r0 + j) : 0.0f) : x0[j];
                 }
             }
+            // the value of column feat on the lane's rows
+            auto column = [&](uint32_t feat, float (&u)[RPT]) {
+                if (XREG) {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) u[j] = feat ? x1[j] : x0[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j)
+                        u[j] = (j < nv) ? __ldg(a.X + (int64_t)feat * a.ld + r0 + j) : 0.0f;
+                }
+            };
+            // ---- forward: every word's result onto the tape (one switch
+            // per word over its operation, each case with its operands)
+            float t[RPT];
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) t[j] = 0.0f;
+            for (int i = 0; i < n_ins - 1; ++i) {
+                const uint2 ins = cbuf[i];
+                const uint32_t w = __shfl_sync(0xffffffffu, ins.x, 0);
+                const float c = __uint_as_float(ins.y);
+                float u[RPT];
+#define GP_TAPE(q) tape[((q) * RPT + j) * 32]
+#define GP_ROWS(stmt) _Pragma("unroll") for (int j = 0; j < RPT; ++j) { stmt; }
+                switch (w & 31u) {
+                case OP_PUSH_X: case OP_PUSH_X_SP: column(w >> 16, u); GP_ROWS(t[j] = u[j]) break;
+                case OP_PUSH_C: case OP_PUSH_C_SP: GP_ROWS(t[j] = c) break;
+                case OP_ADD_S: GP_ROWS(t[j] = f_add(t[j], GP_TAPE(w >> 24))) break;
+                case OP_SUB_S: GP_ROWS(t[j] = f_sub(t[j], GP_TAPE(w >> 24))) break;
+                case OP_MUL_S: GP_ROWS(t[j] = f_mul(t[j], GP_TAPE(w >> 24))) break;
+                case OP_DIV_S: GP_ROWS(t[j] = f_div(t[j], GP_TAPE(w >> 24))) break;
+                case OP_ADD_X: column(w >> 16, u); GP_ROWS(t[j] = f_add(t[j], u[j])) break;
+                case OP_ADD_C: GP_ROWS(t[j] = f_add(t[j], c)) break;
+                case OP_SUB_X: column(w >> 16, u); GP_ROWS(t[j] = f_sub(t[j], u[j])) break;
+                case OP_SUB_C: GP_ROWS(t[j] = f_sub(t[j], c)) break;
+                case OP_RSUB_X: column(w >> 16, u); GP_ROWS(t[j] = f_sub(u[j], t[j])) break;
+                case OP_RSUB_C: GP_ROWS(t[j] = f_sub(c, t[j])) break;
+                case OP_MUL_X: column(w >> 16, u); GP_ROWS(t[j] = f_mul(t[j], u[j])) break;
+                case OP_MUL_C: GP_ROWS(t[j] = f_mul(t[j], c)) break;
+                case OP_DIV_X: column(w >> 16, u); GP_ROWS(t[j] = f_div(t[j], u[j])) break;
+                case OP_DIV_C: GP_ROWS(t[j] = f_div(t[j], c)) break;
+                case OP_RDIV_X: column(w >> 16, u); GP_ROWS(t[j] = f_div(u[j], t[j])) break;
+                case OP_RDIV_C: GP_ROWS(t[j] = f_div(c, t[j])) break;
+                case OP_SQRT: GP_ROWS(t[j] = f_sqrt(t[j])) break;
+                case OP_LOG: GP_ROWS(t[j] = f_log(t[j])) break;
+                case OP_EXP: GP_ROWS(t[j] = f_exp(t[j])) break;
+                case OP_SIN: case OP_COS: case OP_TAN: trig_rows<RPT>(t, (int)((w & 31u) - OP_SIN)); break;
+                case OP_ABS: GP_ROWS(t[j] = f_abs(t[j])) break;
+                case OP_NEG: GP_ROWS(t[j] = f_neg(t[j])) break;
+                case OP_INV: GP_ROWS(t[j] = f_inv(t[j])) break;
+                case OP_EXT1: GP_ROWS(t[j] = f_ext1((w >> 16) & 7u, t[j])) break;
+                case OP_EXT2:
+                    if (((w >> 16) & 7u) == EXT_MAX) { GP_ROWS(t[j] = f_max(t[j], GP_TAPE(w >> 24))) }
+                    else { GP_ROWS(t[j] = f_min(t[j], GP_TAPE(w >> 24))) }
+                    break;
+                default: break;  // OP_END is never reached here
+                }
+                GP_ROWS(GP_TAPE(i) = t[j])
+            }
+            // ---- the loss and its derivative per row
+            float at[RPT];
+            {
+                float e = 0.0f;
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const bool in = j < nv;
+                    const float yv = in ? __ldg(a.y + r0 + j) : 0.0f;
+                    const float wv = (a.w && in) ? __ldg(a.w + r0 + j) : 1.0f;
+                    float l = row_loss(a.metric, t[j], yv);
+                    if (a.w) l = __fmul_rn(wv, l);
+                    e = in ? __fadd_rn(e, l) : e;
+                    at[j] = in ? __fmul_rn(wv, g_dloss(a.metric, t[j], yv)) : 0.0f;
+                }
+                kahan_add(ls, lc, e);
+            }
+            // the lane's share of constant k: its rows' adjoints times d
+#define GP_SHARE(k, d)                                                     \
+    {                                                                      \
+        float s_ = 0.0f;                                                   \
+        _Pragma("unroll") for (int j = 0; j < RPT; ++j)                    \
+            s_ = (j < nv) ? __fadd_rn(s_, __fmul_rn(at[j], (d))) : s_;     \
+        gadd(gs, (k), s_);                                                 \
+    }
+            // ---- adjoint: the words in reverse, one switch per word; the
+            // word's input is the previous word's result (tin), its output
+            // its own (v); a popped slot's value is the spilled word's result
+            for (int i = n_ins - 2; i >= 0; --i) {
+                const uint2 ins = cbuf[i];
+                const uint32_t w = __shfl_sync(0xffffffffu, ins.x, 0);
+                const float c = __uint_as_float(ins.y);
+                const uint32_t slot = min((w >> 8) & 255u, (uint32_t)NSLOT - 1u);
+                const uint32_t aux = w >> 24;
+#define GP_ADJ(j) adjs[(slot * RPT + (j)) * 32]
+#define GP_TIN GP_TAPE(i - 1)
+#define GP_V GP_TAPE(i)
+                float u[RPT];
+                switch (w & 31u) {
+                case OP_PUSH_X: break;
+                case OP_PUSH_X_SP: GP_ROWS(at[j] = GP_ADJ(j)) break;
+                case OP_PUSH_C: GP_SHARE(aux, 1.0f) break;
+                case OP_PUSH_C_SP: GP_SHARE(aux, 1.0f) GP_ROWS(at[j] = GP_ADJ(j)) break;
+                case OP_ADD_S: GP_ROWS(GP_ADJ(j) = at[j]) break;
+                case OP_SUB_S: GP_ROWS(GP_ADJ(j) = -at[j]) break;
+                case OP_MUL_S:
+                    GP_ROWS(GP_ADJ(j) = __fmul_rn(at[j], GP_TIN); at[j] = __fmul_rn(at[j], GP_TAPE(aux)))
+                    break;
+                case OP_DIV_S:
+                    GP_ROWS(const float r = GP_TAPE(aux); const bool p0 = fabsf(r) < kThr;
+                            GP_ADJ(j) = p0 ? 0.0f : __fmul_rn(at[j], -__fdiv_rn(GP_V, r));
+                            at[j] = p0 ? 0.0f : __fmul_rn(at[j], __frcp_rn(r)))
+                    break;
+                case OP_ADD_X: case OP_SUB_X: break;
+                case OP_ADD_C: GP_SHARE(aux, 1.0f) break;
+                case OP_SUB_C: GP_SHARE(aux, -1.0f) break;
+                case OP_RSUB_X: GP_ROWS(at[j] = -at[j]) break;
+                case OP_RSUB_C: GP_SHARE(aux, 1.0f) GP_ROWS(at[j] = -at[j]) break;
+                case OP_MUL_X: column(w >> 16, u); GP_ROWS(at[j] = __fmul_rn(at[j], u[j])) break;
+                case OP_MUL_C: GP_SHARE(aux, GP_TIN) GP_ROWS(at[j] = __fmul_rn(at[j], c)) break;
+                case OP_DIV_X:
+                    column(w >> 16, u);
+                    GP_ROWS(at[j] = fabsf(u[j]) < kThr ? 0.0f : __fmul_rn(at[j], __frcp_rn(u[j])))
+                    break;
+                case OP_DIV_C:
+                    if (fabsf(c) < kThr) { GP_ROWS(at[j] = 0.0f) }
+                    else {
+                        GP_SHARE(aux, -__fdiv_rn(GP_V, c))
+                        GP_ROWS(at[j] = __fmul_rn(at[j], __frcp_rn(c)))
+                    }
+                    break;
+                case OP_RDIV_X:
+                    GP_ROWS(const float r = GP_TIN;
+                            at[j] = fabsf(r) < kThr ? 0.0f : __fmul_rn(at[j], -__fdiv_rn(GP_V, r)))
+                    break;
+                case OP_RDIV_C:
+                    GP_SHARE(aux, fabsf(GP_TIN) < kThr ? 0.0f : __frcp_rn(GP_TIN))
+                    GP_ROWS(const float r = GP_TIN;
+                            at[j] = fabsf(r) < kThr ? 0.0f : __fmul_rn(at[j], -__fdiv_rn(GP_V, r)))
+                    break;
+                case OP_EXT2:
+                    GP_ROWS(const float l = GP_TIN; const float r = GP_TAPE(aux);
+                            const bool left = (((w >> 16) & 7u) == EXT_MAX) ? (l > r || l != l)
+                                                                             : (l < r || l != l);
+                            GP_ADJ(j) = left ? 0.0f : at[j]; at[j] = left ? at[j] : 0.0f)
+                    break;
+                default:  // the unary functions
+                    GP_ROWS(at[j] = __fmul_rn(at[j], d_unary(w & 31u, (w >> 16) & 7u, GP_TIN, GP_V)))
+                    break;
+                }
+#undef GP_ADJ
+#undef GP_TIN
+#undef GP_V
+            }
+#undef GP_SHARE
+#undef GP_ROWS
+#undef GP_TAPE
         }
+        // fixed butterfly per warp, then the warps in order
         float lv = __fsub_rn(ls, lc);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lv = __fadd_rn(lv, __shfl_xor_sync(0xffffffffu, lv, o));
-        float gv[GP_MAX_CONSTS];
+        for (int off = 16; off > 0; off >>= 1) lv = __fadd_rn(lv, __shfl_xor_sync(0xffffffffu, lv, off));
+        if (lane == 0) wsum[warp] = lv;
 #pragma unroll
         for (int k = 0; k < GP_MAX_CONSTS; ++k) {
-            gv[k] = __fsub_rn(gs[k], gc[k]);
+            float v = gs[k];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) gv[k] = __fadd_rn(gv[k], __shfl_xor_sync(0xffffffffu, gv[k], o));
+            for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
+            if (lane == 0) wgrad[warp][k] = v;
         }
-        if (lane == 0) {
-            a.part[(size_t)p * a.n_chunks + chunk] = lv;
-#pragma unroll
-            for (int k = 0; k < GP_MAX_CONSTS; ++k) gp[k] = gv[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float v = 0.0f;
+            for (int q = 0; q < WARPS; ++q) v = __fadd_rn(v, wsum[q]);
+            a.part[(size_t)p * a.n_chunks + chunk] = v;
+        } else if (threadIdx.x >= 32 && threadIdx.x < 32 + GP_MAX_CONSTS) {
+            const int k = threadIdx.x - 32;
+            float v = 0.0f;
+            for (int q = 0; q < WARPS; ++q) v = __fadd_rn(v, wgrad[q][k]);
+            gp[k] = v;
         }
+        __syncthreads();  // wsum, wgrad, cbuf and s_item are reused
     }
 }
 
-// Latency-bound (per node a dependent chain through the per-thread value
-// and adjoint arrays in local memory), so the launch fills every SM: at 16
-// warps per SM a Pagie-1 1M x 2048 gradient pass took 245 ms, at 32 warps
-// 159 ms, at 8 warps 410 ms.
-int info_grad() {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grad_kernel, kGradBlock, 0) != cudaSuccess)
-        return 0;
-    return n;
-}
-
-cudaError_t launch_grad(const GradArgs &a, int grid, int block, cudaStream_t st) {
-    (void)block;
-    grad_kernel<<<grid, kGradBlock, 0, st>>>(a);
+template <int RPT, int WARPS, int CAP, int NSLOT, int MINB, bool XREG>
+cudaError_t launch_grad_t(const GradArgs &a, int sms, cudaStream_t st, int *occ_out) {
+    constexpr size_t smem = grad_smem_bytes<RPT, WARPS, CAP, NSLOT>();
+    auto k = grad_kernel<RPT, WARPS, CAP, NSLOT, MINB, XREG>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, WARPS * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ_out) {
+        *occ_out = occ;
+        return cudaSuccess;
+    }
+    k<<<sms * (occ > 0 ? occ : 1), WARPS * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
+
+// One row per lane (a tape row per word per lane; two rows per lane halved
+// the resident warps and ran 33% slower).  Buckets 0-3 (compiled depth <=
+// 8, 7 adjoint slots): 8, 8, 8 and 4 warps per block, as many blocks as
+// the tape and registers allow; bucket 4 (up to 256 words or deeper
+// stacks): 2 warps and 19 slots.
+#define GP_GRAD_LAUNCH(R, W, C, S, M) \
+    (xreg ? launch_grad_t<R, W, C, S, M, true>(a, sms, st, occ) \
+          : launch_grad_t<R, W, C, S, M, false>(a, sms, st, occ))
+cudaError_t launch_grad(const GradArgs &a, int sms, cudaStream_t st, int *occ) {
+    const bool xreg = a.n_feat <= 2;
+    switch (a.bucket) {
+    case 0: return GP_GRAD_LAUNCH(1, 8, kGradCap0, kSmallDepth - 1, 5);
+    case 1: return GP_GRAD_LAUNCH(1, 8, kGradCap1, kSmallDepth - 1, 4);
+    case 2: return GP_GRAD_LAUNCH(1, 8, kGradCap2, kSmallDepth - 1, 2);
+    case 3: return GP_GRAD_LAUNCH(1, 4, kGradCap3, kSmallDepth - 1, 2);
+    default: return GP_GRAD_LAUNCH(1, 2, kCodeStride, kDeepSlots, 3);
+    }
+}
+#undef GP_GRAD_LAUNCH
 
 // Adam: one thread per program walks its prefix list; the k-th CONST node
 // takes slot k of grad / m / v.

@@ -100,6 +100,23 @@ __host__ __device__ inline int prog_class(int depth, int ext) {
     return depth > kSmallDepth ? kClassDeep : (ext ? kClassShallowExt : kClassShallow);
 }
 
+// Length buckets of the constant gradient (the compiled gradient form):
+// its per-warp tape holds one value per word and row, so each bucket is one
+// launch with a tape sized for its longest program; programs of compiled
+// depth at most kSmallDepth need 7 adjoint slots, the others (last bucket)
+// 19.
+constexpr int kGradBuckets = 5;
+constexpr int kGradCap0 = 24, kGradCap1 = 48, kGradCap2 = 96, kGradCap3 = 160;
+__host__ __device__ inline int grad_bucket(int n_ins, int depth) {
+    if (depth > kSmallDepth) return 4;
+    return n_ins <= kGradCap0 ? 0
+         : n_ins <= kGradCap1 ? 1
+         : n_ins <= kGradCap2 ? 2
+         : n_ins <= kGradCap3 ? 3 : 4;
+}
+// classes of the program order (evaluator classes or gradient buckets)
+constexpr int kOrderClasses = 5;
+
 // Workspace carved out of one device allocation (all offsets 256-aligned).
 struct Workspace {
     unsigned long long *counters;  // [8] work-queue counters
@@ -108,7 +125,7 @@ struct Workspace {
     uint2 *code;                   // [P][kCodeStride]
     ProgMeta *meta;                // [P]
     int32_t *order;                // [P] program ids, by class then length
-    int32_t *class_count;          // [kNumClasses + 2]
+    int32_t *class_count;          // [kOrderClasses + 2]
     float *part;                   // [P][n_chunks] per-item partial sums
     // correlation extras (may be null)
     double *ystat;                 // [4]: ybar, sum w yc, sum w yc^2, (float) ybar
@@ -157,6 +174,12 @@ struct CompileArgs {
     const float *X;
     int64_t ld;
     float *shift;
+    // gradient form: no constant-only subtree is folded (every constant
+    // keeps a word of its own or an operand place), and bits 24-31 of a
+    // word carry its auxiliary byte -- the constant's slot (k-th constant
+    // in prefix order) on words that read a constant, and on words that
+    // pop a stack slot the index of the word whose result was spilled there
+    int grad;
 };
 cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st);
 // weighted mean of y and the moments of yc = fl(y - fl(ybar)) (FP64,
@@ -164,7 +187,7 @@ cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st);
 cudaError_t launch_ystats(const float *y, const float *w, int64_t n_rows, const double *sumw,
                           double *part, double *ystat, cudaStream_t st);
 cudaError_t launch_order(const ProgMeta *meta, int n_progs, int32_t *order,
-                         int32_t *class_count, cudaStream_t st);
+                         int32_t *class_count, cudaStream_t st, int mode = 0);
 cudaError_t launch_sumw(const float *w, int64_t n_rows, double *part,
                         double *sumw, cudaStream_t st);
 
@@ -265,30 +288,28 @@ struct TournArgs {
 cudaError_t launch_tournament(const TournArgs &a, cudaStream_t st);
 
 struct GradArgs {
-    const gp_node *progs;
-    const int32_t *offsets;
+    const uint2 *code;          // gradient form (CompileArgs::grad), [P][kCodeStride]
     const ProgMeta *meta;
-    const int32_t *order;
-    const uint8_t *rchild;
-    const int8_t *kslot;
+    const int32_t *order;       // by length bucket, then length
+    const int32_t *class_count; // programs per bucket
+    int bucket;                 // the launch's length bucket (grad_bucket)
     const float *X;
     int64_t ld;
     int64_t n_rows;
+    int n_feat;
     const float *y;
     const float *w;
-    int n_progs;
     int metric;
     int64_t chunk_rows;
     int n_chunks;
-    unsigned long long *counter;
+    unsigned long long *counter;  // [kGradBuckets] work-queue counters, one per bucket
     float *part;   // [P][n_chunks] loss sums
     float *gpart;  // [P][n_chunks][16]
     unsigned int *dev_status;
 };
-cudaError_t launch_grad(const GradArgs &a, int grid, int block,
-                        cudaStream_t st);
-// resident blocks of grad_kernel per SM (its launch fills them all)
-int info_grad();
+// one launch of bucket a.bucket filling every SM; with occ non-null only
+// reports the resident blocks per SM (no launch)
+cudaError_t launch_grad(const GradArgs &a, int sms, cudaStream_t st, int *occ = nullptr);
 struct GradFinalizeArgs {
     const float *part;
     const float *gpart;
