@@ -64,9 +64,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-generation", action="store_true",
                     help="skip the whole-generation (evaluate, select, mutate) timing")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip gp_autotune and run the library's default tunables")
     ap.add_argument("--rows-per-thread", type=int, default=0,
                     help="evaluator rows per thread (4, 8 or 16; 0: the library's default)")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the accumulator-error block (oracle on 16 sampled programs)")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="resident evaluator blocks per SM (0: as many as fit)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -111,6 +114,53 @@ def op_counts(nodes):
     for code, fn in SFU_OF_OP.items():
         sfu[fn] = sfu.get(fn, 0) + int((op == code).sum())
     return int((op >= 2).sum()), sfu, int(len(op))
+
+
+def folded_op_counts(nodes, offsets):
+    """The pre-pass folds every maximal constant-only subtree (no variable
+    below it) into one constant.  Returns (function nodes left, {mufu
+    function: nodes left}, nodes folded away) -- the work the evaluator
+    actually does."""
+    from paper_2110_11226_gb300 import synth
+    op = nodes["op"].astype(np.int64)
+    var, const = synth.OP["var"], synth.OP["const"]
+    n_fn = 0
+    sfu = {}
+    folded = 0
+    for p in range(len(offsets) - 1):
+        a, b = int(offsets[p]), int(offsets[p + 1])
+        ops = op[a:b]
+        kon = np.zeros(b - a, bool)
+        size = np.ones(b - a, np.int64)
+        st = []
+        for j in range(b - a - 1, -1, -1):
+            ar = synth.ARITY.get(int(ops[j]), -1)
+            if ar == 0:
+                kon[j] = ops[j] == const
+            elif ar == 1:
+                s1, k1 = st.pop()
+                kon[j], size[j] = k1, 1 + s1
+            elif ar == 2:
+                s1, k1 = st.pop()
+                s2, k2 = st.pop()
+                kon[j], size[j] = k1 and k2, 1 + s1 + s2
+            else:
+                break
+            st.append((size[j], kon[j]))
+        inside = np.zeros(b - a, bool)
+        j = 0
+        while j < b - a:
+            if kon[j] and ops[j] not in (var, const):  # a folded subtree: its root becomes a constant
+                inside[j:j + size[j]] = True
+                folded += int(size[j]) - 1
+                j += int(size[j])
+            else:
+                j += 1
+        live = ops[~inside]
+        n_fn += int((live >= 2).sum())
+        for code, fn in SFU_OF_OP.items():
+            sfu[fn] = sfu.get(fn, 0) + int((live == code).sum())
+    return n_fn, sfu, folded
 
 
 def _code_only(text):
@@ -242,6 +292,44 @@ def cpu_baseline(wl, seconds, n_threads=0):
             "kind": "oracle",
             "sample": f"first {p0} programs x first {n_s} rows of {wl.name}, FP64 C oracle, OpenMP over programs",
             "seconds": round(dt, 2)}
+
+
+def precision_block(wl, pn, po, dX, dy, dw, opts, k=16):
+    """Error of the fitness against the FP64 oracle over every row, for each
+    cross-chunk accumulator (FP64, Kahan FP32), on k sampled programs whose
+    oracle fitness is finite."""
+    import oracle
+    from paper_2110_11226_gb300 import gp
+    d = wl.data
+    P = len(wl.offsets) - 1
+    res = {}
+    fits = {}
+    for acc in ("fp64", "kahan32"):
+        o = gp.make_opts(rows_per_thread=opts.rows_per_thread, chunk_rows=opts.chunk_rows,
+                         blocks_per_sm=opts.blocks_per_sm, accum=acc)
+        fits[acc] = gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=wl.metric, opts=o).cpu().numpy()
+    idx = np.sort(np.random.default_rng(17).choice(P, size=min(k, P), replace=False))
+    progs = [wl.nodes[wl.offsets[i]:wl.offsets[i + 1]] for i in idx]
+    sn = np.concatenate(progs)
+    so = np.zeros(len(idx) + 1, np.int32)
+    so[1:] = np.cumsum([len(x) for x in progs])
+    f64, _ = oracle.fitness(sn, so, d.X, d.y, d.w, wl.metric)
+    fin = np.isfinite(f64) & np.isfinite(fits["fp64"][idx])
+    for acc, f in fits.items():
+        with np.errstate(all="ignore"):
+            rel = np.abs(f[idx][fin] - f64[fin]) / np.maximum(np.abs(f64[fin]), 1e-300)
+        res[acc] = {"max_rel": float(rel.max()) if rel.size else None,
+                    "median_rel": float(np.median(rel)) if rel.size else None}
+    with np.errstate(all="ignore"):
+        both = np.isfinite(fits["fp64"]) & np.isfinite(fits["kahan32"])
+        diff = np.abs(fits["fp64"][both] - fits["kahan32"][both]) / \
+            np.maximum(np.abs(fits["fp64"][both]), 1e-300)
+    res["fp64_vs_kahan32_max_rel"] = float(diff.max()) if diff.size else None
+    res["programs_compared"] = int(fin.sum())
+    res["reference"] = (f"FP64 C oracle over all {d.n_rows} rows of {len(idx)} sampled programs "
+                        f"(finite ones compared); GPU rows in FP32, per-lane Kahan FP32, chunk "
+                        f"sums in FP64 or Kahan FP32")
+    return res
 
 
 def run_reference(args):
@@ -385,9 +473,20 @@ def main():
     from paper_2110_11226_gb300.dist import gather_fitness
     stream = torch.cuda.current_stream()
     pipes = gp.gp_probe_pipes()
+    # the tunables: gp_autotune's choice for this shape (on the first 2^21
+    # rows) unless asked otherwise; the defaults are timed beside it below
     tuned = None
-    if args.autotune:
+    tune_s = None
+    # the library defaults for this shape, taken before any tuning record
+    # exists (blocks_per_sm 32 = as many as fit; no length split)
+    dflt_used = gp.gp_resolve_opts(P, N, d.n_feat, None)
+    dflt_used.blocks_per_sm = 32
+    dflt_used.long_edge = -1
+    dflt_used.long_blocks_per_sm = 32
+    if not args.no_autotune and not args.rows_per_thread and not args.blocks_per_sm:
+        t0 = time.perf_counter()
         tuned = gp.gp_autotune(pn, po, dX, dy, dw, metric=wl.metric)
+        tune_s = time.perf_counter() - t0
 
     # the generation step: batched evaluation (pre-pass, persistent
     # evaluator, FP64 finalize) and tournament selection, captured once as a
@@ -444,6 +543,29 @@ def main():
         step_eager(2000 + s)
     eval_ms, n_eval_calls = gp.gp_timing_read()
     gp.gp_timing_enable(False)
+    # the library defaults on the same step (eager launches), for comparison
+    untuned = None
+    if tuned is not None:
+        dws = torch.empty(gp.gp_workspace_size(P, N, d.n_feat, dflt_used), dtype=torch.uint8,
+                          device=dev)
+
+        def step_default(seed):
+            gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=wl.metric, opts=dflt_used, out=fit, ws=dws)
+            gp.gp_tournament_ex(fit, ws * P, wl.tourn_size, seed, out=win)
+
+        step_default(5)
+        torch.cuda.synchronize()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kd = max(1, min(args.steps, 3))
+        a_.record(stream)
+        for s_ in range(kd):
+            step_default(3000 + s_)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        untuned = {"ms_per_step": a_.elapsed_time(b_) / kd,
+                   "opts": {"rows_per_thread": dflt_used.rows_per_thread,
+                            "chunk_rows": dflt_used.chunk_rows, "long_edge": None},
+                   "step": "eager launches, library defaults"}
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([total_ms], device=dev)
@@ -483,6 +605,22 @@ def main():
         roof = {"bound": "alu", "pipe": bound, "achieved": ops / t_kernel / 1e12,
                 "peak": pk / 1e12, "unit": "Tlane-op/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    # the same on the work left after constant folding (the folded nodes are
+    # evaluated once per program, not per row)
+    n_fn_e, sfu_e, n_folded = folded_op_counts(wl.nodes, wl.offsets)
+    for fn, kk in LOSS_SFU[wl.metric].items():
+        sfu_e[fn] = sfu_e.get(fn, 0) + kk * P
+    if bound != "hbm":
+        if bound == "fp32":
+            ops_e = N * (n_fn_e + LOSS_FP32[wl.metric] * P)
+        else:
+            ops_e = N * sum(sfu_e.values())
+            t_sfu_e = sum(N * kk / pipes[fn] for fn, kk in sfu_e.items())
+            pk = ops_e / t_sfu_e if t_sfu_e > 0 else pk
+        roof["achieved_evaluated"] = ops_e / t_kernel / 1e12
+        roof["peak_evaluated"] = pk / 1e12
+        roof["frac_evaluated"] = roof["achieved_evaluated"] / roof["peak_evaluated"]
+    roof["folded_nodes"] = n_folded
     tpr = recorded_traffic(wl.name)
     roof["traffic"] = None if tpr is None else tpr * N
     roof["algorithmic_bytes"] = bytes_alg
@@ -505,13 +643,19 @@ def main():
                        "parallelism": f"program shards x{ws} + fitness all-gather" if ws > 1 else "single GPU",
                        "opts": {"rows_per_thread": used.rows_per_thread, "chunk_rows": used.chunk_rows,
                                 "blocks_per_sm": used.blocks_per_sm or "max resident",
-                                "class_1_2_rows_per_thread": 4, "autotuned": tuned is not None}},
+                                "long_edge": used.long_edge if used.long_edge > 0 else None,
+                                "long_rows_per_thread": used.long_rows_per_thread if used.long_edge > 0 else None,
+                                "long_blocks_per_sm": (used.long_blocks_per_sm or "max resident")
+                                if used.long_edge > 0 else None,
+                                "class_1_2_rows_per_thread": 4, "autotuned": tuned is not None,
+                                "autotune_seconds": tune_s, "untuned": untuned}},
             "node_evals_per_s": value * (n_nodes / P),
             "finite_fitness_frac": fin,
             "clocks": clocks,
             # per step: compile, order, weight sum (+1 with weights), three
-            # evaluator launches (program classes), finalize, tournament
-            "gpu_launches": (8 + (d.w is not None)) * args.steps,
+            # evaluator launches (program classes; +1 when the common class is
+            # split by length), finalize, tournament
+            "gpu_launches": (8 + (d.w is not None) + (used.long_edge > 0)) * args.steps,
             "roofline": roof,
             "pipes": pipes}
 
@@ -607,6 +751,9 @@ def main():
         line["e2e"] = {"value": rows_evals * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "steps": ksteps,
                        "api": "gp_evaluate_host + gp_tournament_ex (host buffers, pinned)"}
+
+    if rank == 0 and not args.no_precision:
+        line["precision"] = precision_block(wl, pn, po, dX, dy, dw, opts)
 
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)

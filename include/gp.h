@@ -126,15 +126,25 @@ enum gp_accum { GP_ACCUM_FP64 = 0, GP_ACCUM_KAHAN32 = 1 };
 
 /* Tunables of the batched evaluator; zero means "choose".  The choice is
  * the autotuned one for this problem shape when gp_autotune has run,
- * otherwise a fixed default.  Results are bit-identical for every choice
- * with the same rows_per_thread and chunk_rows (fixed reduction
- * partition); blocks_per_sm never changes them. */
+ * otherwise a fixed default.
+ * Length buckets: with long_edge > 0 the programs of the common class
+ * (compiled stack of at most 8 values, no extended function) whose compiled
+ * form is longer than long_edge words run in a launch of their own, with
+ * long_rows_per_thread and long_blocks_per_sm (0: rows_per_thread and
+ * blocks_per_sm), before the shorter ones; long_edge = -1 asks for no split
+ * (the default when nothing is tuned).
+ * A program's fitness is bit-identical for every choice that gives it the
+ * same rows per thread and the same chunk_rows (fixed reduction partition);
+ * blocks_per_sm and the bucket it lands in never change it. */
 typedef struct gp_eval_opts {
-    int rows_per_thread;  /* 4, 8 or 16 (default 4)                       */
-    int chunk_rows;       /* rows per work item, multiple of 256          */
-    int blocks_per_sm;    /* resident blocks per SM of the persistent grid */
-    int accum;            /* gp_accum                                     */
-    int reserved[4];      /* must be 0                                    */
+    int rows_per_thread;       /* 4, 8 or 16 (default 4)                      */
+    int chunk_rows;            /* rows per work item, multiple of 256         */
+    int blocks_per_sm;         /* resident blocks per SM of the persistent grid */
+    int accum;                 /* gp_accum                                    */
+    int long_edge;             /* compiled words; -1 no split, 1..255 split    */
+    int long_rows_per_thread;  /* 4, 8 or 16 for the long bucket              */
+    int long_blocks_per_sm;    /* resident blocks per SM of the long bucket   */
+    int reserved[1];           /* must be 0                                   */
 } gp_eval_opts;
 
 /* ---- information ------------------------------------------------------- */
@@ -378,10 +388,14 @@ int gp_set_consts(gp_node *progs, const int32_t *offsets, int n_progs,
  * the last call into *flags and clears them. */
 int gp_last_device_status(void *stream, uint32_t *flags);
 
-/* Times the candidate tunables of the batched evaluator on these inputs
- * (CUDA events on `stream`, synchronising) and remembers the fastest for
- * this problem shape; writes it to *best (may be NULL).  Later calls with
- * zero opts fields use it. */
+/* Searches the tunables of the batched evaluator on these inputs and
+ * remembers the fastest for this problem shape; writes it to *best (may be
+ * NULL).  Later calls with zero opts fields use it.  The search is staged:
+ * rows_per_thread x chunk_rows, then blocks_per_sm, then the length-bucket
+ * edge (none, 12, 16, 24, 32 compiled words) with the long bucket's rows per
+ * thread; every candidate is timed as the median of three calls after one
+ * warm-up (CUDA events on `stream`, synchronising), on the first 2^21 rows
+ * when there are more.  GP_ERR_ARG for GP_SPEARMAN. */
 int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs,
                 const float *X, int64_t n_rows, int n_feat, const float *y,
                 const float *w, int metric, gp_eval_opts *best, void *stream);
@@ -407,29 +421,40 @@ int gp_timing_read(double *total_ms, int *n_calls);
  * serving process whose device memory is handed out at start-up to another
  * allocator, code that must not call cudaMalloc/cudaFree because those can
  * synchronise the device, or a caller with no allocator of its own.
- * gp_evaluate_static computes exactly what gp_evaluate computes (same
- * arguments, same results) but uses a fixed scratch array of
- * GP_STATIC_SCRATCH_BYTES that is part of the library's device image, which
- * every GPU that loads the library holds until the process exits; it calls
- * no allocating routine.  When the workspace of the default tunables
- * exceeds that size, the call uses longer row chunks (65536 rows, then 4x
- * longer each time) until it fits -- its fitness then equals gp_evaluate_ex
- * with that chunk_rows, and gp_evaluate's within the FP32 summation order;
- * at P = 4096 programs and 16M rows that is 65536-row chunks in about
- * 12 MiB.  A problem that fits with none gets GP_ERR_WORKSPACE and nothing
- * is launched.  The
- * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's
- * contents: calls that overlap on the GPU (different streams, or host
- * threads without ordering) race; serialise them. */
+ * gp_evaluate_static takes gp_evaluate's arguments and, for the fused
+ * metrics (GP_MAE ... GP_PEARSON), computes what gp_evaluate computes; it
+ * returns GP_ERR_ARG for GP_SPEARMAN, whose scratch grows with the batch.
+ * It uses a fixed scratch array of GP_STATIC_SCRATCH_BYTES that is part of
+ * the library's device image, which every GPU that loads the library holds
+ * until the process exits; it calls no allocating routine.  When the
+ * workspace of the default tunables fits, the fitness is gp_evaluate's,
+ * bit for bit.  When it does not, the call uses longer row chunks (65536
+ * rows, then 4x longer each time) until it fits -- its fitness then equals
+ * gp_evaluate_ex with the opts gp_static_opts reports, bit for bit, and
+ * gp_evaluate's within the FP32 summation order; at P = 4096 programs and
+ * 16M rows that is 65536-row chunks in about 12 MiB.  A problem that fits
+ * with none gets GP_ERR_WORKSPACE and nothing is launched.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and keeps it for the life of that device's context (gp_shutdown forgets
+ * it), so make that first call before any stream capture.  All calls share
+ * the one array and it keeps the last call's contents: calls that overlap
+ * on the GPU (different streams, or host threads without ordering) race;
+ * serialise them. */
 #define GP_STATIC_SCRATCH_BYTES (16u << 20)
 int gp_evaluate_static(const gp_node *progs, const int32_t *offsets,
                        int n_progs, const float *X, int64_t n_rows, int n_feat,
                        const float *y, const float *w, int metric,
                        float *out_fitness, void *stream);
 
-/* Frees the library's cached device scratch on every device. */
+/* The tunables gp_evaluate_static uses for this problem (chunk_rows 0: the
+ * defaults; otherwise the longer row chunks it falls back to), without any
+ * device work.  GP_ERR_WORKSPACE when no chunk length fits the array,
+ * GP_ERR_ARG for bad arguments or GP_SPEARMAN. */
+int gp_static_opts(int n_progs, int64_t n_rows, int n_feat, int metric,
+                   gp_eval_opts *out);
+
+/* Frees the library's cached device scratch on every device and forgets the
+ * device addresses gp_evaluate_static looked up. */
 void gp_shutdown(void);
 
 #ifdef __cplusplus

@@ -165,17 +165,24 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
                  gp_eval_opts *out) {
     gp_eval_opts o{};
     if (in) o = *in;
-    for (int i = 0; i < 4; ++i)
-        if (o.reserved[i] != 0) return GP_ERR_ARG;
-    if (o.rows_per_thread == 0 || o.chunk_rows == 0 || o.blocks_per_sm == 0) {
+    if (o.reserved[0] != 0) return GP_ERR_ARG;
+    if (o.rows_per_thread == 0 || o.chunk_rows == 0 || o.blocks_per_sm == 0 || o.long_edge == 0) {
         std::lock_guard<std::mutex> g(g_mu);
         auto it = c->tuned.find(ShapeKey{n_progs, n_rows, n_feat});
         if (it != c->tuned.end()) {
             if (o.rows_per_thread == 0) o.rows_per_thread = it->second.rows_per_thread;
             if (o.chunk_rows == 0) o.chunk_rows = it->second.chunk_rows;
             if (o.blocks_per_sm == 0) o.blocks_per_sm = it->second.blocks_per_sm;
+            if (o.long_edge == 0) {
+                o.long_edge = it->second.long_edge;
+                o.long_rows_per_thread = it->second.long_rows_per_thread;
+                o.long_blocks_per_sm = it->second.long_blocks_per_sm;
+            }
         }
     }
+    // length buckets: none unless asked for or tuned
+    if (o.long_edge == 0) o.long_edge = -1;
+    if (o.long_edge != -1 && (o.long_edge < 1 || o.long_edge > 255)) return GP_ERR_ARG;
     // 4 rows per thread: 48 registers, 5 blocks (40 warps) per SM, measured
     // 7% faster than 8 rows (79 registers, 3 blocks) on Pagie-1 x 4096
     if (o.rows_per_thread == 0) o.rows_per_thread = 4;
@@ -185,6 +192,10 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
     if (o.chunk_rows < 256 || o.chunk_rows % 256 != 0) return GP_ERR_ARG;
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 32) return GP_ERR_ARG;
     if (o.accum != GP_ACCUM_FP64 && o.accum != GP_ACCUM_KAHAN32) return GP_ERR_ARG;
+    if (o.long_rows_per_thread == 0) o.long_rows_per_thread = o.rows_per_thread;
+    if (o.long_rows_per_thread != 4 && o.long_rows_per_thread != 8 && o.long_rows_per_thread != 16)
+        return GP_ERR_ARG;
+    if (o.long_blocks_per_sm < 0 || o.long_blocks_per_sm > 32) return GP_ERR_ARG;
     *out = o;
     return GP_OK;
 }
@@ -221,33 +232,40 @@ int make_plan(const gp_eval_opts *opts, int n_progs, int64_t n_rows, int n_feat,
 }
 
 // the batched evaluation sequence on a carved workspace
+// ld: the column stride of X (n_rows, or more when the rows are a prefix)
 int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, const float *X,
                  int64_t n_rows, int n_feat, const float *y, const float *w, int metric,
                  const Plan &pl, const Workspace &W, DevCtx *c, float *out, double *out64,
-                 int32_t *out_status, cudaStream_t st) {
+                 int32_t *out_status, cudaStream_t st, int64_t ld = -1) {
+    if (ld < 0) ld = n_rows;
     const bool mom = metric == GP_PEARSON;
     GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
     CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
                    nullptr, nullptr, nullptr, c->status, nullptr};
     if (mom) {
         ca.X = X;
-        ca.ld = n_rows;
+        ca.ld = ld;
         ca.shift = W.shift;
     }
     GP_CUDA(launch_compile(ca, st));
-    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st));
+    const bool split = pl.o.long_edge > 0;
+    GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st, 0, split ? pl.o.long_edge : 0));
     GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
     if (mom) GP_CUDA(launch_ystats(y, w, n_rows, W.sumw, W.ystat_part, W.ystat, st));
     const int fmode = (n_feat <= 2) ? 2 : 0;
     // the moment epilogue has instances for 4 and 8 rows per thread
     const int rpt = (mom && pl.o.rows_per_thread == 16) ? 8 : pl.o.rows_per_thread;
-    const bool vec = aligned16(X) && aligned16(y) && (!w || aligned16(w)) && (n_rows % 4 == 0);
+    const bool vec = aligned16(X) && aligned16(y) && (!w || aligned16(w)) && (n_rows % 4 == 0) &&
+                     (ld % 4 == 0);
     std::pair<cudaEvent_t, cudaEvent_t> tev{nullptr, nullptr};
     if (g_timing.on) {
         tev = timing_pair();
         GP_CUDA(cudaEventRecord(tev.first, st));
     }
-    for (int cls = 0; cls < kNumClasses; ++cls) {
+    // launches: class 0 (or, split by length, its long then its short
+    // programs), class 1, class 2
+    for (int launch = split ? -1 : 0; launch < kNumClasses; ++launch) {
+        const int cls = launch < 0 ? 0 : launch;
         EvalArgs ea{};
         ea.code = W.code;
         ea.meta = W.meta;
@@ -255,7 +273,7 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
         ea.class_count = W.class_count;
         ea.cls = cls;
         ea.X = X;
-        ea.ld = (fmode == 2) ? (n_feat == 2 ? n_rows : 0) : n_rows;
+        ea.ld = (fmode == 2) ? (n_feat == 2 ? ld : 0) : ld;
         ea.n_rows = n_rows;
         ea.y = y;
         ea.w = w;
@@ -263,7 +281,8 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
         ea.metric = metric;
         ea.chunk_rows = pl.o.chunk_rows;
         ea.n_chunks = pl.n_chunks;
-        ea.counter = W.counters + cls;
+        ea.sub = split && cls == kClassShallow ? (launch < 0 ? 1 : 2) : 0;
+        ea.counter = W.counters + (ea.sub == 1 ? kNumClasses : cls);
         ea.part = W.part;
         ea.dev_status = c->status;
         ea.vec_ok = vec ? 1 : 0;
@@ -275,11 +294,13 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
         // classes 1 and 2 keep 4 rows per thread (the 19-slot stack would
         // otherwise leave room for one block per SM; class 2 is rare); the
         // same chunk partition serves all three
-        const int rpt_c = (cls == kClassShallow) ? rpt : 4;
+        const int rpt_long = (mom && pl.o.long_rows_per_thread == 16) ? 8 : pl.o.long_rows_per_thread;
+        const int rpt_c = (cls == kClassShallow) ? (ea.sub == 1 ? rpt_long : rpt) : 4;
+        const int want = ea.sub == 1 ? pl.o.long_blocks_per_sm : pl.o.blocks_per_sm;
         const int block = kEvalBlockThreads;
         int occ = eval_info(rpt_c, fmode, cls, block, nullptr, mom);
         if (occ < 1) occ = 1;
-        int bps = pl.o.blocks_per_sm > 0 ? std::min(pl.o.blocks_per_sm, occ) : occ;
+        int bps = want > 0 ? std::min(want, occ) : occ;
         GP_CUDA(eval_launch(ea, rpt_c, fmode, c->sms * bps, block, st));
     }
     if (tev.second) GP_CUDA(cudaEventRecord(tev.second, st));
@@ -844,54 +865,105 @@ int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs, const
     DevCtx *c = nullptr;
     if ((rc = ctx_of_current(&c))) return rc;
     cudaStream_t st = S(stream);
+    // candidates are timed on the first rows only (the column stride stays
+    // n_rows): enough work items for the queue to balance, a short search
+    const int64_t n_tune = std::min<int64_t>(n_rows, (int64_t)1 << 21);
     float *out = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
     GP_CUDA(cudaMalloc(&out, (size_t)n_progs * sizeof(float)));
-    const int64_t base_chunk = default_chunk(n_progs, n_rows, n_feat, c->sms);
-    std::vector<gp_eval_opts> cands;
-    const int fmode = (n_feat <= 2) ? 2 : 0;
-    for (int rpt : {4, 8, 16}) {
-        const int occ = eval_info(rpt, fmode, 0, kEvalBlockThreads, nullptr);
-        for (int64_t ch : {base_chunk, std::max<int64_t>(base_chunk / 4, 1024)}) {
-            const int64_t chr = round_up(std::min<int64_t>(ch, 65536), 256);
-            for (int bps = 1; bps <= std::max(occ, 1); ++bps) {
-                gp_eval_opts o{};
-                o.rows_per_thread = rpt;
-                o.chunk_rows = (int)chr;
-                o.blocks_per_sm = bps;
-                cands.push_back(o);
-            }
-        }
-    }
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best_ms = 1e30f;
-    gp_eval_opts best_o = cands.front();
-    for (const gp_eval_opts &o : cands) {
-        // one warm-up, then the time of one call
-        rc = gp_evaluate_ex(progs, offsets, n_progs, X, n_rows, n_feat, y, w, metric, &o, out,
-                            nullptr, nullptr, nullptr, 0, stream);
-        if (rc) break;
-        cudaEventRecord(e0, st);
-        rc = gp_evaluate_ex(progs, offsets, n_progs, X, n_rows, n_feat, y, w, metric, &o, out,
-                            nullptr, nullptr, nullptr, 0, stream);
-        cudaEventRecord(e1, st);
-        if (rc) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = GP_ERR_CUDA;
-            break;
+    // one evaluation with explicit opts on the tuning rows
+    auto run = [&](const gp_eval_opts &o) -> int {
+        Plan pl;
+        int r = make_plan(&o, n_progs, n_tune, n_feat, c, &pl, metric == GP_PEARSON);
+        if (r) return r;
+        if (pl.L.total > ws_bytes) {
+            if (ws) cudaFree(ws);
+            ws = nullptr;
+            if (cudaMalloc(&ws, pl.L.total) != cudaSuccess) {
+                cudaGetLastError();
+                ws_bytes = 0;
+                return GP_ERR_NOMEM;
+            }
+            ws_bytes = pl.L.total;
         }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
+        Workspace W = carve(ws, pl.L, false);
+        return run_evaluate(progs, offsets, n_progs, X, n_tune, n_feat, y, w, metric, pl, W, c,
+                            out, nullptr, nullptr, st, n_rows);
+    };
+    // median of three timed calls after one warm-up; +inf if a call fails
+    auto time_of = [&](const gp_eval_opts &o, int *err) -> float {
+        if ((*err = run(o))) return 3.4e38f;
+        float t[3];
+        for (int k = 0; k < 3; ++k) {
+            cudaEventRecord(e0, st);
+            if ((*err = run(o))) return 3.4e38f;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                *err = GP_ERR_CUDA;
+                return 3.4e38f;
+            }
+            cudaEventElapsedTime(&t[k], e0, e1);
+        }
+        std::sort(t, t + 3);
+        return t[1];
+    };
+    const int fmode = (n_feat <= 2) ? 2 : 0;
+    const int64_t base_chunk = default_chunk(n_progs, n_tune, n_feat, c->sms);
+    gp_eval_opts best_o{};
+    best_o.long_edge = -1;
+    float best_ms = 3.4e38f;
+    int err = GP_OK;
+    auto consider = [&](const gp_eval_opts &o) {
+        if (err) return;
+        const float ms = time_of(o, &err);
+        if (!err && ms < best_ms) {
             best_ms = ms;
             best_o = o;
         }
+    };
+    // stage 1: rows per thread x chunk length, as many blocks as fit
+    for (int rpt : {4, 8})
+        for (int64_t ch : {base_chunk, std::max<int64_t>(base_chunk / 4, 1024)}) {
+            gp_eval_opts o{};
+            o.rows_per_thread = rpt;
+            o.chunk_rows = (int)round_up(std::min<int64_t>(ch, 65536), 256);
+            o.long_edge = -1;
+            consider(o);
+        }
+    // stage 2: fewer resident blocks
+    if (!err) {
+        const gp_eval_opts b1 = best_o;
+        const int occ = eval_info(b1.rows_per_thread, fmode, 0, kEvalBlockThreads, nullptr);
+        for (int bps = 1; bps < occ; ++bps) {
+            gp_eval_opts o = b1;
+            o.blocks_per_sm = bps;
+            consider(o);
+        }
+    }
+    // stage 3: a length-bucket edge, the long bucket with its own rows per
+    // thread
+    if (!err) {
+        const gp_eval_opts b2 = best_o;
+        for (int edge : {12, 16, 24, 32})
+            for (int lrpt : {4, 8}) {
+                gp_eval_opts o = b2;
+                o.long_edge = edge;
+                o.long_rows_per_thread = lrpt;
+                o.long_blocks_per_sm = 0;
+                consider(o);
+            }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(out);
-    if (rc) return rc;
+    if (ws) cudaFree(ws);
+    if (err) return err;
+    if (best_o.long_rows_per_thread == 0) best_o.long_rows_per_thread = best_o.rows_per_thread;
     {
         std::lock_guard<std::mutex> g(g_mu);
         c->tuned[ShapeKey{n_progs, n_rows, n_feat}] = best_o;
@@ -962,6 +1034,7 @@ void gp_shutdown(void) {
         c.tuned.clear();
     }
     cudaSetDevice(cur);
+    static_scratch_forget();
 }
 
 }  // extern "C"

@@ -345,7 +345,7 @@ __device__ __forceinline__ int order_class(const ProgMeta &m, int mode) {
 
 __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n_progs,
                                                      int32_t *order, int32_t *class_count,
-                                                     int mode) {
+                                                     int mode, int edge) {
     __shared__ int hist[kOrderBins];
     __shared__ int cursor[kOrderBins];
     for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x) hist[i] = 0;
@@ -367,7 +367,11 @@ __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n
                 prev = run;
             }
         }
-        class_count[kOrderClasses] = 0;
+        // class-0 programs longer than edge: keys 0 .. 255 - edge (n_ins > edge)
+        int n_long = 0;
+        if (edge > 0)
+            for (int k = 0; k < 256 - edge; ++k) n_long += hist[k];
+        class_count[kOrderClasses] = n_long;
         class_count[kOrderClasses + 1] = 0;
     }
     __syncthreads();
@@ -381,8 +385,8 @@ __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n
 }
 
 cudaError_t launch_order(const ProgMeta *meta, int n_progs, int32_t *order,
-                         int32_t *class_count, cudaStream_t st, int mode) {
-    order_kernel<<<1, 1024, 0, st>>>(meta, n_progs, order, class_count, mode);
+                         int32_t *class_count, cudaStream_t st, int mode, int edge) {
+    order_kernel<<<1, 1024, 0, st>>>(meta, n_progs, order, class_count, mode, edge);
     return cudaGetLastError();
 }
 

@@ -152,6 +152,9 @@ struct Layout {
 Layout make_layout(int n_progs, int n_chunks, bool grad, bool moments = false);
 Workspace carve(void *base, const Layout &L, bool grad);
 
+// forget the cached device addresses of gp_evaluate_static's array
+void static_scratch_forget();
+
 // workspace bytes of one batched evaluation with this metric (0 for bad
 // arguments); gp_workspace_size reports the largest over all metrics
 size_t workspace_bytes_for(int n_progs, int64_t n_rows, int n_feat, const gp_eval_opts *opts,
@@ -186,8 +189,11 @@ cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st);
 // fixed partition); needs the total weight already in *sumw
 cudaError_t launch_ystats(const float *y, const float *w, int64_t n_rows, const double *sumw,
                           double *part, double *ystat, cudaStream_t st);
+// mode 0 with edge > 0 also writes to class_count[kOrderClasses] how many
+// class-0 programs have more than `edge` compiled words (the long bucket,
+// which the order puts first)
 cudaError_t launch_order(const ProgMeta *meta, int n_progs, int32_t *order,
-                         int32_t *class_count, cudaStream_t st, int mode = 0);
+                         int32_t *class_count, cudaStream_t st, int mode = 0, int edge = 0);
 cudaError_t launch_sumw(const float *w, int64_t n_rows, double *part,
                         double *sumw, cudaStream_t st);
 
@@ -206,6 +212,9 @@ struct EvalArgs {
     int metric;
     int64_t chunk_rows;
     int n_chunks;
+    // 0: the whole class; 1, 2: the long, the short programs of class 0
+    // (class_count[kOrderClasses] long ones first)
+    int sub;
     unsigned long long *counter;
     float *part;       // eval mode
     float *pred;       // predict mode

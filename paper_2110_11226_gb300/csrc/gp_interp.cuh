@@ -437,8 +437,14 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32,
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     float4 *stk = stack_all + (size_t)warp * NSLOT * (RPT / 4) * 32 + lane;
-    const int cls_begin = (a.cls == 0) ? 0 : a.class_count[0] + (a.cls == 2 ? a.class_count[1] : 0);
-    const int n_cls = a.class_count[a.cls];
+    int cls_begin = (a.cls == 0) ? 0 : a.class_count[0] + (a.cls == 2 ? a.class_count[1] : 0);
+    int n_cls = a.class_count[a.cls];
+    if (a.sub == 1) {  // the long programs of class 0 (first in its order)
+        n_cls = a.class_count[kOrderClasses];
+    } else if (a.sub == 2) {  // the rest of class 0
+        cls_begin = a.class_count[kOrderClasses];
+        n_cls -= cls_begin;
+    }
     const unsigned long long total = (unsigned long long)n_cls * (unsigned long long)a.n_chunks;
     const bool vec = a.vec_ok != 0;
     const bool two_feat = FMODE == 2 && a.ld > 0;

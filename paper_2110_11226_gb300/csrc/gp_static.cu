@@ -44,12 +44,21 @@ int static_scratch(void **out) {
 
 }  // namespace
 
-extern "C" int gp_evaluate_static(const gp_node *progs, const int32_t *offsets, int n_progs,
-                                  const float *X, int64_t n_rows, int n_feat, const float *y,
-                                  const float *w, int metric, float *out_fitness, void *stream) {
-    if (n_progs < 1 || n_rows < 1 || n_feat < 1) return GP_ERR_ARG;
-    // the default tunables, or, when their workspace does not fit, longer
-    // row chunks (fewer per-chunk partial sums)
+namespace gpk {
+// the device addresses are good for the life of each device's context;
+// gp_shutdown forgets them (a later call looks them up again)
+void static_scratch_forget() {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    for (int d = 0; d < kMaxStaticDevices; ++d) g_static_ptr[d] = nullptr;
+}
+}  // namespace gpk
+
+// The default tunables, or, when their workspace does not fit the array,
+// longer row chunks (fewer per-chunk partial sums): 65536 rows, then 4x
+// longer each time.  opts->chunk_rows = 0 means the defaults.
+extern "C" int gp_static_opts(int n_progs, int64_t n_rows, int n_feat, int metric,
+                              gp_eval_opts *out) {
+    if (n_progs < 1 || n_rows < 1 || n_feat < 1 || !out) return GP_ERR_ARG;
     gp_eval_opts opts{};
     size_t need = gpk::workspace_bytes_for(n_progs, n_rows, n_feat, nullptr, metric);
     if (need == 0) return GP_ERR_ARG;
@@ -60,8 +69,18 @@ extern "C" int gp_evaluate_static(const gp_node *progs, const int32_t *offsets, 
         if (need == 0) return GP_ERR_ARG;
     }
     if (need > (size_t)GP_STATIC_SCRATCH_BYTES) return GP_ERR_WORKSPACE;
+    *out = opts;
+    return GP_OK;
+}
+
+extern "C" int gp_evaluate_static(const gp_node *progs, const int32_t *offsets, int n_progs,
+                                  const float *X, int64_t n_rows, int n_feat, const float *y,
+                                  const float *w, int metric, float *out_fitness, void *stream) {
+    gp_eval_opts opts{};
+    int rc = gp_static_opts(n_progs, n_rows, n_feat, metric, &opts);
+    if (rc != GP_OK) return rc;
     void *ws = nullptr;
-    const int rc = static_scratch(&ws);
+    rc = static_scratch(&ws);
     if (rc != GP_OK) return rc;
     // the evaluator clears the one region that must start at zero (the work
     // queue counters) on every call and writes every other region before

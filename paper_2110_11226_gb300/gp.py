@@ -69,7 +69,8 @@ def make_mut_params(p_crossover=0.7, p_subtree=0.1, p_hoist=0.05, p_point=0.1,
 class EvalOpts(C.Structure):
     _fields_ = [("rows_per_thread", C.c_int), ("chunk_rows", C.c_int),
                 ("blocks_per_sm", C.c_int), ("accum", C.c_int),
-                ("reserved", C.c_int * 4)]
+                ("long_edge", C.c_int), ("long_rows_per_thread", C.c_int),
+                ("long_blocks_per_sm", C.c_int), ("reserved", C.c_int * 1)]
 
 
 def _load():
@@ -106,6 +107,7 @@ def _load():
         "gp_autotune": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
         "gp_probe_pipes": (i32, [P, P]),
         "gp_evaluate_static": (i32, [P, P, i32, P, i64, i32, P, P, i32, P, P]),
+        "gp_static_opts": (i32, [i32, i64, i32, i32, P]),
         "gp_timing_enable": (i32, [i32]),
         "gp_timing_read": (i32, [P, P]),
         "gp_shutdown": (None, []),
@@ -231,12 +233,16 @@ def gp_evaluate_static(progs, offsets, X, y, w=None, metric="mse", out=None, str
     return out
 
 
-def make_opts(rows_per_thread=0, chunk_rows=0, blocks_per_sm=0, accum="fp64") -> EvalOpts:
+def make_opts(rows_per_thread=0, chunk_rows=0, blocks_per_sm=0, accum="fp64", long_edge=0,
+              long_rows_per_thread=0, long_blocks_per_sm=0) -> EvalOpts:
     o = EvalOpts()
     o.rows_per_thread = rows_per_thread
     o.chunk_rows = chunk_rows
     o.blocks_per_sm = blocks_per_sm
     o.accum = ACCUM[accum] if isinstance(accum, str) else int(accum)
+    o.long_edge = long_edge
+    o.long_rows_per_thread = long_rows_per_thread
+    o.long_blocks_per_sm = long_blocks_per_sm
     return o
 
 
@@ -267,6 +273,14 @@ def gp_resolve_opts(n_progs, n_rows, n_feat, opts: Optional[EvalOpts] = None) ->
     _check("gp_resolve_opts", _lib.gp_resolve_opts(int(n_progs), int(n_rows), int(n_feat),
                                                    None if opts is None else C.byref(opts),
                                                    C.byref(out)))
+    return out
+
+
+def gp_static_opts(n_progs, n_rows, n_feat, metric="mse") -> EvalOpts:
+    """The tunables gp_evaluate_static uses for this problem."""
+    out = EvalOpts()
+    _check("gp_static_opts", _lib.gp_static_opts(int(n_progs), int(n_rows), int(n_feat),
+                                                 _metric(metric), C.byref(out)))
     return out
 
 

@@ -83,16 +83,52 @@ class FitStats:
     max_rel_strict: float
 
 
-def check_fitness(gpu_fit, nodes, off, X, y, w, metric, row0=0, n_eval=None, v=None, e=None,
-                  fl=None):
-    gpu_fit = np.asarray(gpu_fit, np.float64)
-    f64, st = oracle.fitness(nodes, off, X, y, w, metric, row0=row0, n_eval=n_eval)
-    if v is None:
-        v, e, fl = oracle.predict_bound(nodes, off, X, row0=row0, n_eval=n_eval, ulps_fn=ULPS)
-    ys = y[row0:row0 + v.shape[1]]
-    ws = None if w is None else w[row0:row0 + v.shape[1]]
+def _bound_terms(nodes, off, X, y, w, metric, row0, n_eval, block):
+    """Per program: the propagated FP32 bound on the metric's mean (before
+    the root of RMSE), whether any row is flagged, and the largest and the
+    total weighted row loss, over rows [row0, row0 + n_eval) taken in blocks
+    of rows (memory stays bounded at full size)."""
+    P = len(off) - 1
+    wv_all = None if w is None else w.astype(np.float64)
+    sw = float(n_eval) if wv_all is None else wv_all[row0:row0 + n_eval].sum()
+    bsum = np.zeros(P)
+    flag = np.zeros(P, bool)
+    lmax = np.zeros(P)
+    lsum = np.zeros(P)
     mse_metric = "mse" if metric == "rmse" else metric
-    b = fitness_bound(mse_metric, v, e, ys, ws)
+    for r in range(row0, row0 + n_eval, block):
+        m = min(block, row0 + n_eval - r)
+        v, e, fl = oracle.predict_bound(nodes, off, X, row0=r, n_eval=m, ulps_fn=ULPS)
+        ys = y[r:r + m]
+        ws = None if wv_all is None else wv_all[r:r + m]
+        wsum = float(m) if ws is None else ws.sum()
+        bsum += fitness_bound(mse_metric, v, e, ys, ws) * wsum
+        flag |= (fl != 0).any(axis=1)
+        with np.errstate(all="ignore"):
+            yy = ys.astype(np.float64)[None, :]
+            if metric == "mae":
+                rl = np.abs(v - yy)
+            elif metric == "logloss":
+                rl = np.abs(v) + np.log(2.0)
+            else:
+                rl = (v - yy) ** 2
+            wl = rl if ws is None else rl * ws[None, :]
+            lmax = np.fmax(lmax, np.nanmax(wl, axis=1))
+            lsum += np.nansum(wl, axis=1)
+    return bsum / sw, flag, lmax, lsum
+
+
+def check_fitness(gpu_fit, nodes, off, X, y, w, metric, row0=0, n_eval=None, block=1 << 18):
+    """Fitness against the FP64 oracle: programs whose rows are all
+    unflagged and whose propagated FP32 bound is below a quarter of 1e-4 of
+    the fitness ("strict") must match within 1e-4 relative; the others
+    ("conditioning") within 1.5 x the bound + 1e-4; flagged ones (a
+    protected decision may flip, a value or loss leaves the float range)
+    are counted.  The bound is accumulated over blocks of rows."""
+    gpu_fit = np.asarray(gpu_fit, np.float64)
+    n_eval = X.shape[1] - row0 if n_eval is None else n_eval
+    f64, st = oracle.fitness(nodes, off, X, y, w, metric, row0=row0, n_eval=n_eval)
+    b, fl_any, lmax, lsum = _bound_terms(nodes, off, X, y, w, metric, row0, n_eval, block)
     f_cmp = f64
     g_cmp = gpu_fit
     if metric == "rmse":  # compare squares: the bound is on the MSE
@@ -103,17 +139,8 @@ def check_fitness(gpu_fit, nodes, off, X, y, w, metric, row0=0, n_eval=None, v=N
     # FP64 oracle stays finite (all losses are >= 0, so the total bounds
     # every partial sum)
     FMAX = float(np.finfo(np.float32).max)
-    with np.errstate(all="ignore"):
-        yy = ys.astype(np.float64)[None, :]
-        if metric == "mae":
-            rl = np.abs(v - yy)
-        elif metric == "logloss":
-            rl = np.abs(v) + np.log(2.0)
-        else:
-            rl = (v - yy) ** 2
-        wl = rl if ws is None else rl * ws.astype(np.float64)[None, :]
-        loss_range = (np.nanmax(wl, axis=1) > 0.5 * FMAX) | (np.nansum(wl, axis=1) > 0.5 * FMAX)
-    flagged = (fl != 0).any(axis=1) | (st != 0) | loss_range
+    loss_range = (lmax > 0.5 * FMAX) | (lsum > 0.5 * FMAX)
+    flagged = fl_any | (st != 0) | loss_range
     with np.errstate(invalid="ignore"):
         strict = ~flagged & np.isfinite(f64) & (b <= 0.25 * REL_FIT * np.abs(f_cmp))
         rel = np.abs(gpu_fit - f64) / np.maximum(np.abs(f64), 1e-300)
@@ -172,3 +199,11 @@ def check_pearson(gpu_fit, nodes, off, X, y, w):
     assert np.all(np.isnan(gpu_fit[st != 0]))
     mr = float(np.max(err[strict] / np.abs(f64[strict]))) if strict.any() else 0.0
     return FitStats(len(f64), int(strict.sum()), int(cond.sum()), int(flagged.sum()), mr), f64
+
+
+def check_fitness_sampled(gpu_fit, nodes, off, X, y, w, metric):
+    """Full-size fitness of sampled programs: check_fitness over every row,
+    its bound accumulated in blocks.  Returns (strict, conditioning,
+    flagged) counts."""
+    st, _ = check_fitness(gpu_fit, nodes, off, X, y, w, metric)
+    return st.strict, st.conditioning, st.flagged

@@ -104,3 +104,20 @@ def test_clock_sampler_reads_clocks_and_throttle_reasons(monkeypatch, tmp_path):
     with bench.ClockSampler(0) as c:
         pass
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_folded_op_counts_follow_the_pre_pass_folding():
+    """Constant-only subtrees fold to one constant: their function nodes
+    leave the count, and the folded-away nodes are counted."""
+    import bench
+    from helpers import pack, parse_prefix
+    progs = ["sin add 0.5 0.25",            # all constant: 3 nodes folded, no function left
+             "mul x0 exp 0.5",               # exp(0.5) folds: 1 node folded, mul left
+             "add sqrt x0 div x1 0.5",       # nothing constant-only above a terminal
+             "sub log mul 2 3 x0"]           # log(mul(2,3)) folds: 3 nodes folded
+    nodes, off = pack([parse_prefix(p) for p in progs])
+    n_fn, sfu, folded = bench.folded_op_counts(nodes, off)
+    assert folded == 3 + 1 + 0 + 3
+    assert n_fn == 0 + 1 + 3 + 1
+    assert sfu.get("sin", 0) == 0 and sfu.get("ex2", 0) == 0 and sfu.get("lg2", 0) == 0
+    assert sfu["rsqrt"] == 1 and sfu["rcp"] == 1

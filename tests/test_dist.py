@@ -39,17 +39,17 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, out_dir):
+def _worker(rank, world, port, out_dir, n_progs):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     d = synth.pagie_data(512, 3)
-    nodes, off = synth.ramped_half_and_half(64, 2, 6, synth.FULL_SET, 2, seed=8)
+    nodes, off = synth.ramped_half_and_half(n_progs, 2, 6, synth.FULL_SET, 2, seed=8)
     progs = synth.unpack(nodes, off)
     a, b = shard_bounds(len(progs), world, rank)
     sn, so = synth.pack(progs[a:b])
     fit_local, _ = oracle.fitness(sn, so, d.X, d.y, None, "rmse")
-    fit = gather_fitness(torch.from_numpy(fit_local.astype(np.float32)))
+    fit = gather_fitness(torch.from_numpy(fit_local.astype(np.float32)), n_total=len(progs))
     win = oracle.tournament(fit.numpy(), len(progs), 20, 42)
     t = max_over_ranks(float(rank + 1))
     np.save(os.path.join(out_dir, f"win{rank}.npy"), win)
@@ -59,13 +59,15 @@ def _worker(rank, world, port, out_dir):
     dist.destroy_process_group()
 
 
-def test_two_rank_generation_matches_single_process(tmp_path):
+@pytest.mark.parametrize("n_progs", [64, 65])
+def test_two_rank_generation_matches_single_process(tmp_path, n_progs):
+    """Even shards (64 programs) and uneven ones (65: 33 and 32)."""
     world = 2
-    mp.spawn(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    mp.spawn(_worker, args=(world, _free_port(), str(tmp_path), n_progs), nprocs=world, join=True)
     d = synth.pagie_data(512, 3)
-    nodes, off = synth.ramped_half_and_half(64, 2, 6, synth.FULL_SET, 2, seed=8)
+    nodes, off = synth.ramped_half_and_half(n_progs, 2, 6, synth.FULL_SET, 2, seed=8)
     fit, _ = oracle.fitness(nodes, off, d.X, d.y, None, "rmse")
-    want = oracle.tournament(fit.astype(np.float32), 64, 20, 42)
+    want = oracle.tournament(fit.astype(np.float32), n_progs, 20, 42)
     for r in range(world):
         np.testing.assert_array_equal(np.load(tmp_path / f"fit{r}.npy"), fit.astype(np.float32))
         np.testing.assert_array_equal(np.load(tmp_path / f"win{r}.npy"), want)
