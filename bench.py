@@ -47,7 +47,7 @@ UNIT = "program-row evals/s"
 SFU_OF_OP = {5: "rcp", 14: "rcp", 6: "rsqrt", 7: "lg2", 8: "ex2", 9: "sin", 10: "sin", 11: "sin"}
 LOSS_FP32 = {"mae": 3, "mse": 3, "rmse": 3, "logloss": 6}
 LOSS_SFU = {"mae": {}, "mse": {}, "rmse": {}, "logloss": {"ex2": 1, "lg2": 1}}
-KERNEL_SOURCES = ("gp_interp.cuh", "gp_math.cuh", "gp_internal.cuh", "gp_compile.cu")
+KERNEL_SOURCES = ("gp_interp.cuh", "gp_fast.cuh", "gp_math.cuh", "gp_internal.cuh", "gp_compile.cu")
 
 
 def parse():
@@ -70,6 +70,9 @@ def parse():
                     help="evaluator rows per thread (4, 8 or 16; 0: the library's default)")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the accumulator-error block (oracle on 16 sampled programs)")
+    ap.add_argument("--long-edge", type=int, default=0,
+                    help="length-bucket edge in compiled words (0: the library's choice)")
+    ap.add_argument("--long-rows-per-thread", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="resident evaluator blocks per SM (0: as many as fit)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -194,9 +197,18 @@ DATA_DESC = {
 }
 
 
-def recorded_traffic(workload):
+def traffic_opts_key(used):
+    """The launch shape a recorded traffic figure holds for: rows per
+    thread, length-bucket edge (0: no split) and the long bucket's rows per
+    thread (each evaluator launch reads the inputs once)."""
+    edge = used.long_edge if used.long_edge > 0 else 0
+    return f"{used.rows_per_thread}/{edge}/{used.long_rows_per_thread if edge else 0}"
+
+
+def recorded_traffic(workload, opts_key):
     """DRAM bytes per row of the evaluator from the committed ncu summary, if
-    it was taken on the current kernel sources (else None)."""
+    it was taken on the current kernel sources and launch shape (else
+    None)."""
     path = os.path.join(ROOT, "profiles", "eval_kernel_pagie1_traffic.md")
     if not os.path.exists(path):
         return None
@@ -206,7 +218,8 @@ def recorded_traffic(workload):
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_sources_sha256_16") != kernel_hash() or vals.get("workload") != workload:
+    if vals.get("kernel_sources_sha256_16") != kernel_hash() or vals.get("workload") != workload \
+            or vals.get("launch_shape") != opts_key:
         return None
     try:
         return float(vals["dram_bytes_per_row"])
@@ -483,7 +496,8 @@ def main():
     dflt_used.blocks_per_sm = 32
     dflt_used.long_edge = -1
     dflt_used.long_blocks_per_sm = 32
-    if not args.no_autotune and not args.rows_per_thread and not args.blocks_per_sm:
+    explicit = args.rows_per_thread or args.blocks_per_sm or args.long_edge
+    if not args.no_autotune and not explicit:
         t0 = time.perf_counter()
         tuned = gp.gp_autotune(pn, po, dX, dy, dw, metric=wl.metric)
         tune_s = time.perf_counter() - t0
@@ -493,8 +507,9 @@ def main():
     # CUDA graph on a preallocated workspace and replayed (or launched
     # eagerly with --no-graph); with several ranks the fitness all-gather
     # sits between the two and the step runs eagerly
-    opts = tuned if tuned is not None else gp.make_opts(rows_per_thread=args.rows_per_thread,
-                                                        blocks_per_sm=args.blocks_per_sm)
+    opts = tuned if tuned is not None else gp.make_opts(
+        rows_per_thread=args.rows_per_thread, blocks_per_sm=args.blocks_per_sm,
+        long_edge=args.long_edge, long_rows_per_thread=args.long_rows_per_thread)
     ws_buf = torch.empty(gp.gp_workspace_size(P, N, d.n_feat, opts), dtype=torch.uint8, device=dev)
     used = gp.gp_resolve_opts(P, N, d.n_feat, opts)
 
@@ -621,7 +636,7 @@ def main():
         roof["peak_evaluated"] = pk / 1e12
         roof["frac_evaluated"] = roof["achieved_evaluated"] / roof["peak_evaluated"]
     roof["folded_nodes"] = n_folded
-    tpr = recorded_traffic(wl.name)
+    tpr = recorded_traffic(wl.name, traffic_opts_key(used))
     roof["traffic"] = None if tpr is None else tpr * N
     roof["algorithmic_bytes"] = bytes_alg
     roof["kernel_ms"] = t_kernel * 1e3

@@ -20,8 +20,8 @@ int b = 2; /* inline */ int c = 3;
 
 
 def test_hash_follows_code_not_comments(monkeypatch, tmp_path):
-    files = {"gp_interp.cuh": "int f() { return 1; }  // one\n", "gp_math.cuh": "",
-             "gp_internal.cuh": "", "gp_compile.cu": ""}
+    files = {k: "" for k in bench.KERNEL_SOURCES}
+    files["gp_interp.cuh"] = "int f() { return 1; }  // one\n"
     csrc = tmp_path / "paper_2110_11226_gb300" / "csrc"
     csrc.mkdir(parents=True)
     for k, v in files.items():
@@ -37,18 +37,28 @@ def test_hash_follows_code_not_comments(monkeypatch, tmp_path):
 def test_recorded_traffic_is_keyed_by_the_hash(monkeypatch, tmp_path):
     csrc = tmp_path / "paper_2110_11226_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    for k in ("gp_interp.cuh", "gp_math.cuh", "gp_internal.cuh", "gp_compile.cu"):
+    for k in bench.KERNEL_SOURCES:
         (csrc / k).write_text("int x;\n")
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h = bench.kernel_hash()
     prof = tmp_path / "profiles" / "eval_kernel_pagie1_traffic.md"
-    prof.write_text(f"- workload: pagie_large\n- kernel_sources_sha256_16: {h}\n"
-                    "- dram_bytes_per_row: 13.5\n")
-    assert bench.recorded_traffic("pagie_large") == 13.5
-    assert bench.recorded_traffic("tabular") is None
+    prof.write_text(f"- workload: pagie_large\n- launch_shape: 8/32/8\n"
+                    f"- kernel_sources_sha256_16: {h}\n- dram_bytes_per_row: 13.5\n")
+    assert bench.recorded_traffic("pagie_large", "8/32/8") == 13.5
+    assert bench.recorded_traffic("tabular", "8/32/8") is None
+    # another launch shape reads the inputs another number of times
+    assert bench.recorded_traffic("pagie_large", "4/0/0") is None
     (csrc / "gp_compile.cu").write_text("int y;\n")
-    assert bench.recorded_traffic("pagie_large") is None
+    assert bench.recorded_traffic("pagie_large", "8/32/8") is None
+
+
+def test_traffic_launch_shape_key():
+    import types
+    split = types.SimpleNamespace(rows_per_thread=8, long_edge=32, long_rows_per_thread=8)
+    plain = types.SimpleNamespace(rows_per_thread=4, long_edge=-1, long_rows_per_thread=8)
+    assert bench.traffic_opts_key(split) == "8/32/8"
+    assert bench.traffic_opts_key(plain) == "4/0/0"
 
 
 def test_reference_arm_prints_the_contract_line():
