@@ -241,7 +241,7 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
     const bool mom = metric == GP_PEARSON;
     GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
     CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
-                   nullptr, nullptr, nullptr, c->status, nullptr};
+                   c->status, nullptr};
     if (mom) {
         ca.X = X;
         ca.ld = ld;
@@ -401,7 +401,7 @@ int compile_all(const gp_node *progs, const int32_t *offsets, int n_progs, int n
     }
     *W = carve(c->ws, L, false);
     CompileArgs ca{progs, offsets, n_progs, n_feat, W->code, W->meta,
-                   nullptr, nullptr, nullptr, c->status, out_status};
+                   c->status, out_status};
     GP_CUDA(launch_compile(ca, st));
     return GP_OK;
 }
@@ -568,7 +568,7 @@ int gp_evaluate_plain(const gp_node *progs, const int32_t *offsets, int n_progs,
     Workspace W = carve(c->ws, L, false);
     cudaStream_t st = S(stream);
     CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
-                   nullptr, nullptr, nullptr, c->status, nullptr};
+                   c->status, nullptr};
     GP_CUDA(launch_compile(ca, st));
     GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
     PlainArgs pa{progs, offsets, W.meta, X, n_rows, n_rows, y, w, metric, n_blocks, W.part};
@@ -712,12 +712,14 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, con
     cudaStream_t st = S(stream);
     GP_CUDA(cudaMemsetAsync(W.counters, 0, 8 * sizeof(unsigned long long), st));
     CompileArgs ca{progs, offsets, n_progs, n_feat, W.code, W.meta,
-                   W.rchild, W.kslot, W.cnode, c->status, nullptr};
-    ca.grad = 1;  // the gradient form: no constant folding, slots and spill sources
+                   c->status, nullptr};
+    ca.grad = 1;  // the gradient form: no constant folding, marker words
     GP_CUDA(launch_compile(ca, st));
     GP_CUDA(launch_order(W.meta, n_progs, W.order, W.class_count, st, 1));
     GP_CUDA(launch_sumw(w, n_rows, W.sumw_part, W.sumw, st));
-    // one launch per length bucket of the compiled programs
+    // one launch per bucket (constants, stack depth) of the compiled programs
+    const bool vec = aligned16(X) && aligned16(y) && (!w || aligned16(w)) && (n_rows % 4 == 0) &&
+                     (chunk % 4 == 0);
     for (int bucket = 0; bucket < kGradBuckets; ++bucket) {
         GradArgs ga{};
         ga.code = W.code;
@@ -738,6 +740,7 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, con
         ga.part = W.part;
         ga.gpart = W.gpart;
         ga.dev_status = c->status;
+        ga.vec_ok = vec ? 1 : 0;
         GP_CUDA(launch_grad(ga, c->sms, st));
     }
     GradFinalizeArgs fa{W.part, W.gpart, n_chunks, n_progs, W.meta, W.sumw, metric,
@@ -751,7 +754,7 @@ int gp_adam_step(gp_node *progs, const int32_t *offsets, int n_progs, const floa
     if (!progs || !offsets || !grad || !m || !v || n_progs < 1 || step < 1) return GP_ERR_ARG;
     if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f))
         return GP_ERR_ARG;
-    AdamArgs a{progs, offsets, nullptr, nullptr, n_progs, grad, m, v, step, lr, beta1, beta2, eps};
+    AdamArgs a{progs, offsets, nullptr, n_progs, grad, m, v, step, lr, beta1, beta2, eps};
     GP_CUDA(launch_adam(a, S(stream)));
     return GP_OK;
 }

@@ -25,7 +25,7 @@ Layout make_layout(int n_progs, int n_chunks, bool grad, bool moments) {
     L.counters = o;    o = align256(o + 8 * sizeof(unsigned long long));
     L.sumw = o;        o = align256(o + sizeof(double));
     L.sumw_part = o;   o = align256(o + kSumwBlocks * sizeof(double));
-    L.code = o;        o = align256(o + P * kCodeStride * sizeof(uint2));
+    L.code = o;        o = align256(o + P * (grad ? kGradCodeStride : kCodeStride) * sizeof(uint2));
     L.meta = o;        o = align256(o + P * sizeof(ProgMeta));
     L.order = o;       o = align256(o + P * sizeof(int32_t));
     L.class_count = o; o = align256(o + (kOrderClasses + 2) * sizeof(int32_t));
@@ -37,9 +37,6 @@ Layout make_layout(int n_progs, int n_chunks, bool grad, bool moments) {
         L.mom = o;        o = align256(o + P * C * 3 * sizeof(double));
     }
     if (grad) {
-        L.rchild = o;  o = align256(o + P * kCodeStride);
-        L.kslot = o;   o = align256(o + P * kCodeStride);
-        L.cnode = o;   o = align256(o + P * GP_MAX_CONSTS * sizeof(int16_t));
         L.gpart = o;   o = align256(o + P * C * GP_MAX_CONSTS * sizeof(float));
     }
     L.total = o;
@@ -63,12 +60,7 @@ Workspace carve(void *base, const Layout &L, bool grad) {
         w.shift = reinterpret_cast<float *>(b + L.shift);
         w.mom = reinterpret_cast<double *>(b + L.mom);
     }
-    if (grad) {
-        w.rchild = reinterpret_cast<uint8_t *>(b + L.rchild);
-        w.kslot = reinterpret_cast<int8_t *>(b + L.kslot);
-        w.cnode = reinterpret_cast<int16_t *>(b + L.cnode);
-        w.gpart = reinterpret_cast<float *>(b + L.gpart);
-    }
+    if (grad) w.gpart = reinterpret_cast<float *>(b + L.gpart);
     w.bytes = L.total;
     return w;
 }
@@ -125,7 +117,7 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
     if (p >= a.n_progs) return;
     const int off = a.offsets[p];
     const int len = a.offsets[p + 1] - off;
-    uint2 *out = a.code + (size_t)p * kCodeStride;
+    uint2 *out = a.code + (size_t)p * (a.grad ? kGradCodeStride : kCodeStride);
     const gp_node *prog = a.progs + off;
 
     uint8_t size[GP_MAX_LEN];
@@ -224,41 +216,34 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
         }
     }
 
-    // auxiliary tables for the adjoint (right child offset, constant slot)
-    if (a.rchild) {
-        uint8_t *rc = a.rchild + (size_t)p * kCodeStride;
-        int8_t *ks = a.kslot + (size_t)p * kCodeStride;
-        int16_t *cn = a.cnode + (size_t)p * GP_MAX_CONSTS;
-        int k = 0;
-        for (int j = 0; j < len; ++j) {
-            const int op = prog[j].op;
-            rc[j] = (op_arity(op) == 2) ? (uint8_t)(1 + size[j + 1]) : 0;
-            ks[j] = -1;
-            if (op == GP_CONST) {
-                if (k < GP_MAX_CONSTS) cn[k] = (int16_t)j;
-                ks[j] = (int8_t)(k < GP_MAX_CONSTS ? k : -1);
-                ++k;
-            }
-        }
-        for (; k < GP_MAX_CONSTS; ++k) cn[k] = -1;
-    }
-
-    // gradient form: the slot of each constant (k-th CONST in prefix order)
-    // and, per stack slot, the word whose result was spilled into it
-    uint8_t cslot[GP_MAX_LEN];
-    uint8_t spill_src[GP_MAX_STACK];
+    // gradient form: the number of constants before each node in prefix
+    // order; the constants under node j are [cpre[j], cpre[j + size[j]])
+    uint8_t cpre[GP_MAX_LEN + 1];
     if (a.grad) {
         int k = 0;
         for (int j = 0; j < len; ++j) {
-            cslot[j] = (uint8_t)(k < GP_MAX_CONSTS ? k : GP_MAX_CONSTS);
+            cpre[j] = (uint8_t)min(k, GP_MAX_CONSTS);
             k += prog[j].op == GP_CONST;
         }
+        cpre[len] = (uint8_t)min(k, GP_MAX_CONSTS);
     }
-    auto aux = [&](uint32_t v) { return a.grad ? (v << 24) : 0u; };
-
     // pass 3: emit in reverse-scan order
     int n = 0, depth = 0;
     bool ext = false;  // an extended-set instruction was emitted
+    // gradient form: a marker word before the next word when one of its
+    // operands holds constants (j_top: the node whose value is the top
+    // operand, j_other: the other operand's node; -1 where the partial
+    // derivative is 1 and leaves the tangents as they are)
+    auto mark = [&](int j_top, int j_other, bool fresh) {
+        if (!a.grad) return;
+        const uint32_t tlo = j_top >= 0 ? cpre[j_top] : 0u;
+        const uint32_t thi = j_top >= 0 ? cpre[j_top + size[j_top]] : 0u;
+        const uint32_t olo = j_other >= 0 ? cpre[j_other] : 0u;
+        const uint32_t ohi = j_other >= 0 ? cpre[j_other + size[j_other]] : 0u;
+        if (tlo == thi && olo == ohi) return;
+        out[n++] = make_uint2(kGradMark, tlo | (thi << 5) | (olo << 10) | (ohi << 15) |
+                                             ((fresh ? 1u : 0u) << 20));
+    };
     sp = 0;
     for (int j = len - 1; j >= 0; --j) {
         if (mode[j] == 3) continue;  // inside a folded constant subtree
@@ -275,30 +260,31 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
             const bool spill = sp > 0;  // the old top goes to slot sp-1
             const uint32_t op = (spill ? (x ? OP_PUSH_X_SP : OP_PUSH_C_SP) : (x ? OP_PUSH_X : OP_PUSH_C)) |
                                 ((x && nd.feat == 1) ? kOpCol1 : 0u);
-            if (spill && a.grad) spill_src[sp - 1] = (uint8_t)(n - 1);
-            const uint32_t w = x ? make_ins(op, spill ? sp - 1 : 0, (uint32_t)(uint16_t)nd.feat)
-                                 : (make_ins(op, spill ? sp - 1 : 0, 0) | aux(a.grad ? cslot[j] : 0u));
+            if (!x) mark(-1, j, true);  // the constant's own tangent starts at 1
+            const uint32_t w = make_ins(op, spill ? sp - 1 : 0, x ? (uint32_t)(uint16_t)nd.feat : 0u);
             out[n++] = make_uint2(w, __float_as_uint(nd.c));
             ++sp;
         } else if (ar == 1) {
             const bool e = nd.op > GP_INV;  // extended function: its number in the feature field
             ext |= e;
+            mark(j + 1, -1, false);
             out[n++] = make_uint2(e ? make_ins(OP_EXT1, 0, (uint32_t)(nd.op - GP_SQ))
                                     : make_ins(OP_SQRT + (nd.op - GP_SQRT), 0, 0),
                                   0u);
         } else {
             // add, sub, mul, div, max, min
             const int b = nd.op <= GP_DIV ? nd.op - GP_ADD : 4 + (nd.op - GP_MAX);
+            const int lc = j + 1, rc = j + 1 + size[j + 1];
             if (mode[j] == 0) {
-                // right operand in slot sp-2, left operand is t
+                // right operand in slot sp-2, left operand is t (add: both
+                // partials 1; sub: 1 for t)
                 const uint32_t ops[6] = {OP_ADD_S, OP_SUB_S, OP_MUL_S, OP_DIV_S, OP_EXT2, OP_EXT2};
                 ext |= b >= 4;
-                out[n++] = make_uint2(make_ins(ops[b], sp - 2, b >= 4 ? (uint32_t)(b - 4) : 0u) |
-                                          aux(a.grad ? spill_src[sp - 2] : 0u),
-                                      0u);
+                if (b != 0) mark(b == 1 ? -1 : lc, rc, false);
+                out[n++] = make_uint2(make_ins(ops[b], sp - 2, b >= 4 ? (uint32_t)(b - 4) : 0u), 0u);
                 --sp;
             } else {
-                const int tj = (mode[j] == 1) ? j + 1 + size[j + 1] : j + 1;
+                const int tj = (mode[j] == 1) ? rc : lc;  // the inline terminal
                 gp_node t = prog[tj];
                 if (kon[tj]) {
                     t.op = GP_CONST;
@@ -307,12 +293,15 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
                 }
                 const int x = (t.op == GP_VAR) ? 0 : 1;  // X or C variant
                 // right terminal: t = op(t, u); left terminal: t = op(u, t)
+                // (add, and sub with the terminal on the right, leave the
+                // top's tangents as they are)
                 const uint32_t fwd[4] = {OP_ADD_X, OP_SUB_X, OP_MUL_X, OP_DIV_X};
                 const uint32_t rev[4] = {OP_ADD_X, OP_RSUB_X, OP_MUL_X, OP_RDIV_X};
+                const int jt = (mode[j] == 1) ? lc : rc;  // the top operand's node
+                mark((b == 0 || (b == 1 && mode[j] == 1)) ? -1 : jt, tj, x == 1);
                 const uint32_t op = (((mode[j] == 1) ? fwd[b] : rev[b]) + x) |
                                     ((x == 0 && t.feat == 1) ? kOpCol1 : 0u);
-                const uint32_t w = x == 0 ? make_ins(op, 0, (uint32_t)(uint16_t)t.feat)
-                                          : (make_ins(op, 0, 0) | aux(a.grad ? cslot[tj] : 0u));
+                const uint32_t w = make_ins(op, 0, x == 0 ? (uint32_t)(uint16_t)t.feat : 0u);
                 out[n++] = make_uint2(w, __float_as_uint(t.c));
             }
         }
@@ -334,13 +323,14 @@ cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st) {
 // classes follow one another (0, 1, 2) and, inside a class, longer programs
 // come first (longest-processing-time order for the dynamic work queue).
 // mode 0: the evaluator's classes (stack depth, extended functions); mode
-// 1: the gradient's length buckets.
+// 1: the gradient's buckets (constants, stack depth), whose programs with
+// their marker words may exceed 256 words (those share the first key).
 // Invalid programs (n_ins = 1) land at the end of class 0.  Order inside
 // one key is arbitrary; results do not depend on it.
 constexpr int kOrderBins = kOrderClasses * 256;
 
 __device__ __forceinline__ int order_class(const ProgMeta &m, int mode) {
-    return mode == 0 ? prog_class(m.depth, m.ext) : grad_bucket(m.n_ins, m.depth);
+    return mode == 0 ? prog_class(m.depth, m.ext) : grad_bucket(m.n_consts, m.depth);
 }
 
 __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n_progs,
@@ -353,7 +343,7 @@ __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n
     for (int p = threadIdx.x; p < n_progs; p += blockDim.x) {
         const ProgMeta m = meta[p];
         const int cls = order_class(m, mode);
-        const int key = cls * 256 + (256 - m.n_ins);
+        const int key = cls * 256 + (256 - min(m.n_ins, 256));
         atomicAdd(&hist[key], 1);
     }
     __syncthreads();
@@ -378,7 +368,7 @@ __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n
     for (int p = threadIdx.x; p < n_progs; p += blockDim.x) {
         const ProgMeta m = meta[p];
         const int cls = order_class(m, mode);
-        const int key = cls * 256 + (256 - m.n_ins);
+        const int key = cls * 256 + (256 - min(m.n_ins, 256));
         const int pos = atomicAdd(&cursor[key], 1);
         order[pos] = p;
     }

@@ -1,28 +1,30 @@
 // gp_grad.cu -- gradients of fitness with respect to the ephemeral
-// constants (reverse mode), and one Adam step on the constants.  Neither
+// constants (forward mode), and one Adam step on the constants.  Neither
 // has a counterpart in the paper; they serve constant tuning between
 // generations.
 //
-// The adjoint runs on the compiled stack form of the evaluator
+// Forward mode on the compiled stack form of the evaluator
 // (gp_internal.cuh), in its gradient variant: no constant-only subtree is
-// folded, every word that reads a constant names the constant's slot, and
-// every word that pops a stack slot names the word whose result was spilled
-// into it.  A block takes one (program, row chunk) item; its warps run the
-// program over their own sub-tiles of 32 * RPT rows:
-//   forward   the words in order, as the evaluator runs them (the same FP32
-//             operations, so the fitness equals gp_evaluate's), each word's
-//             result written to the warp's tape in shared memory -- one float
-//             per word and row, nothing of size programs x rows x nodes;
-//   adjoint   the words in reverse: the adjoint of the top of the stack in
-//             registers, the adjoints of spilled values in the warp's stack
-//             slots (the forward values there are dead by then); a word's
-//             input is the previous word's result on the tape, a popped
-//             slot's value the spilled word's result; a word that reads a
-//             constant adds its share to that constant's per-lane sum.
-// Programs are bucketed by compiled length (kGradCap0, 1, 2, 256 words) and
-// depth, one launch per bucket with a tape sized for its longest program.
-// Per-lane sums are FP32 (the loss Kahan-compensated), warp sums
-// fixed-order, chunk sums FP64 in order (gp_reduce.cu).
+// folded, and a marker word precedes every word whose operands hold
+// constants, naming the constants under each operand (they form contiguous
+// ranges of the prefix-order numbering).  Each row carries one tangent per
+// constant, dt[k] = d(value holding c_k)/d(c_k): a pushed constant starts
+// at 1, and a marked word multiplies the tangents under each operand by
+// its partial derivative with respect to that operand, so after the root
+// dt[k] is d(program)/d(c_k).  Every constant is a leaf used once, so a
+// row costs the forward pass plus one multiply per (constant, ancestor)
+// pair -- no tape and no reverse sweep: the values and tangents live in
+// registers and a few shared-memory slots per row.
+//
+// A block takes one (program, row chunk) item; its warps run the program
+// over their own sub-tiles of 128 rows (4 per lane) with the evaluator's
+// fast loop (the same FP32 operations, so the fitness equals
+// gp_evaluate's), which hands each marked word back to grad_word.  The
+// loss derivative per row times the tangents gives each constant's share.
+// Programs are bucketed by their number of constants (the tangent slots
+// per row) and stack depth, one launch per bucket.  Per-lane sums are FP32
+// (the loss Kahan-compensated), warp sums fixed-order, chunk sums FP64 in
+// order (gp_reduce.cu).
 #include "gp_internal.cuh"
 #include "gp_interp.cuh"
 
@@ -76,22 +78,6 @@ __device__ __forceinline__ float d_unary(uint32_t op, uint32_t ext, float u, flo
     }
 }
 
-// v into constant k's per-lane sum (k uniform over the warp).  Plain FP32:
-// a lane adds at most 512 terms per 16K-row chunk (then FP64 across
-// chunks); compensated sums had cost 16 registers and a resident block.
-__device__ __forceinline__ void gadd(float (&gs)[GP_MAX_CONSTS], uint32_t k, float v) {
-#define GP_GADD_CASE(q) \
-    case q: gs[q] = __fadd_rn(gs[q], v); break;
-    switch (k) {
-        GP_GADD_CASE(0) GP_GADD_CASE(1) GP_GADD_CASE(2) GP_GADD_CASE(3)
-        GP_GADD_CASE(4) GP_GADD_CASE(5) GP_GADD_CASE(6) GP_GADD_CASE(7)
-        GP_GADD_CASE(8) GP_GADD_CASE(9) GP_GADD_CASE(10) GP_GADD_CASE(11)
-        GP_GADD_CASE(12) GP_GADD_CASE(13) GP_GADD_CASE(14) GP_GADD_CASE(15)
-        default: break;
-    }
-#undef GP_GADD_CASE
-}
-
 // the extended unary functions of one row (the evaluator's, so the forward
 // values are its values)
 __device__ __forceinline__ float f_ext1(uint32_t fn, float x) {
@@ -108,32 +94,195 @@ __device__ __forceinline__ float f_ext1(uint32_t fn, float x) {
 
 }  // namespace
 
-// shared memory of one block: the program's words, then per warp the tape
-// [CAP words][RPT rows][32 lanes] and the adjoint slots [NSLOT][RPT][32]
-template <int RPT, int WARPS, int CAP, int NSLOT>
-constexpr size_t grad_smem_bytes() {
-    return ((size_t)(CAP + 2) * sizeof(uint2) + 15) / 16 * 16 +
-           (size_t)WARPS * (CAP + NSLOT) * RPT * 32 * sizeof(float);
+// One word of the gradient form that the fast loop handed back (a marked
+// word, or one the loop does not run): its value with the evaluator's
+// operations and, after a marker (mk != 0), its partial derivatives with
+// respect to the top operand t (pt) and the other operand (po), applied to
+// the tangents of the constants under each (kGradMark).  Four rows per
+// lane; the stack slot of this lane's rows is one float4 (sb + slot * 512
+// bytes), the tangent of constant k one float4 at dts[k * 32].
+template <int NSLOT, int KT, bool XREG>
+__device__ __forceinline__ void grad_word(uint32_t w, float c, uint32_t mk, float (&t)[4],
+                                          const float (&x0)[4], const float (&x1)[4],
+                                          const float *__restrict__ X, int64_t ld, int64_t r0,
+                                          int64_t re, bool vec, uint32_t sb, float4 *dts) {
+    constexpr int R = 4;
+    const uint32_t op = w & 31u;
+    const uint32_t fn = (w >> 16) & 7u;
+    const uint32_t sa = sb + min((w >> 8) & 255u, (uint32_t)NSLOT - 1u) * 32u * 16u;
+    // the other operand: a stack slot (S forms, EXT2), a column (X forms,
+    // PUSH_X), else the word's constant
+    float o[R];
+    const bool from_slot = (op >= OP_ADD_S && op <= OP_DIV_S) || op == OP_EXT2;
+    const bool from_col = op == OP_PUSH_X || op == OP_PUSH_X_SP ||
+                          (op >= OP_ADD_X && op <= OP_RDIV_X && ((op - OP_ADD_X) & 1u) == 0u);
+    if (from_slot) {
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3])
+                     : "r"(sa));
+    } else if (from_col) {
+        const int feat = (int)(w >> 16);
+        if (XREG) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) o[j] = feat ? x1[j] : x0[j];
+        } else {
+            load_rows<R>(o, X + (int64_t)feat * ld, r0, re, vec);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) o[j] = c;
+    }
+    if (op == OP_PUSH_X_SP || op == OP_PUSH_C_SP)
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(sa), "f"(t[0]), "f"(t[1]),
+                     "f"(t[2]), "f"(t[3])
+                     : "memory");
+    float v[R];
+#define GP_ROWS(stmt) _Pragma("unroll") for (int j = 0; j < R; ++j) { stmt; }
+    switch (op) {
+    case OP_ADD_S: case OP_ADD_X: case OP_ADD_C: GP_ROWS(v[j] = f_add(t[j], o[j])) break;
+    case OP_SUB_S: case OP_SUB_X: case OP_SUB_C: GP_ROWS(v[j] = f_sub(t[j], o[j])) break;
+    case OP_RSUB_X: case OP_RSUB_C: GP_ROWS(v[j] = f_sub(o[j], t[j])) break;
+    case OP_MUL_S: case OP_MUL_X: case OP_MUL_C: GP_ROWS(v[j] = f_mul(t[j], o[j])) break;
+    case OP_DIV_S: case OP_DIV_X: case OP_DIV_C: GP_ROWS(v[j] = f_div(t[j], o[j])) break;
+    case OP_RDIV_X: case OP_RDIV_C: GP_ROWS(v[j] = f_div(o[j], t[j])) break;
+    case OP_SQRT: GP_ROWS(v[j] = f_sqrt(t[j])) break;
+    case OP_LOG: GP_ROWS(v[j] = f_log(t[j])) break;
+    case OP_EXP: GP_ROWS(v[j] = f_exp(t[j])) break;
+    case OP_SIN: case OP_COS: case OP_TAN:
+        GP_ROWS(v[j] = t[j])
+        trig_rows<R>(v, (int)(op - OP_SIN));
+        break;
+    case OP_ABS: GP_ROWS(v[j] = f_abs(t[j])) break;
+    case OP_NEG: GP_ROWS(v[j] = f_neg(t[j])) break;
+    case OP_INV: GP_ROWS(v[j] = f_inv(t[j])) break;
+    case OP_EXT1: GP_ROWS(v[j] = f_ext1(fn, t[j])) break;
+    case OP_EXT2:
+        if (fn == EXT_MAX) { GP_ROWS(v[j] = f_max(t[j], o[j])) }
+        else { GP_ROWS(v[j] = f_min(t[j], o[j])) }
+        break;
+    default: GP_ROWS(v[j] = o[j]) break;  // the pushes (OP_END never gets here)
+    }
+    if (mk != 0u) {
+        float pt[R], po[R];
+        GP_ROWS(pt[j] = 1.0f; po[j] = 1.0f)
+        switch (op) {
+        case OP_SUB_S: case OP_SUB_X: case OP_SUB_C: GP_ROWS(po[j] = -1.0f) break;
+        case OP_RSUB_X: case OP_RSUB_C: GP_ROWS(pt[j] = -1.0f) break;
+        case OP_MUL_S: case OP_MUL_X: case OP_MUL_C: GP_ROWS(pt[j] = o[j]; po[j] = t[j]) break;
+        case OP_DIV_S: case OP_DIV_X: case OP_DIV_C:
+            GP_ROWS(const bool p0 = fabsf(o[j]) < kThr;
+                    pt[j] = p0 ? 0.0f : __frcp_rn(o[j]);
+                    po[j] = p0 ? 0.0f : -__fdiv_rn(v[j], o[j]))
+            break;
+        case OP_RDIV_X: case OP_RDIV_C:
+            GP_ROWS(const bool p0 = fabsf(t[j]) < kThr;
+                    pt[j] = p0 ? 0.0f : -__fdiv_rn(v[j], t[j]);
+                    po[j] = p0 ? 0.0f : __frcp_rn(t[j]))
+            break;
+        case OP_EXT2:
+            GP_ROWS(const bool left = (fn == EXT_MAX) ? (t[j] > o[j] || t[j] != t[j])
+                                                      : (t[j] < o[j] || t[j] != t[j]);
+                    pt[j] = left ? 1.0f : 0.0f; po[j] = left ? 0.0f : 1.0f)
+            break;
+        case OP_SQRT: case OP_LOG: case OP_EXP: case OP_SIN: case OP_COS: case OP_TAN:
+        case OP_ABS: case OP_NEG: case OP_INV: case OP_EXT1:
+            GP_ROWS(pt[j] = d_unary(op, fn, t[j], v[j]))
+            break;
+        default: break;  // add and the pushes: both partials 1
+        }
+        const int tlo = (int)(mk & 31u), thi = min((int)((mk >> 5) & 31u), KT);
+        const int olo = (int)((mk >> 10) & 31u), ohi = min((int)((mk >> 15) & 31u), KT);
+        const bool fresh = ((mk >> 20) & 1u) != 0u;
+        for (int k = tlo; k < thi; ++k) {
+            float4 d = dts[k * 32];
+            d.x = __fmul_rn(d.x, pt[0]);
+            d.y = __fmul_rn(d.y, pt[1]);
+            d.z = __fmul_rn(d.z, pt[2]);
+            d.w = __fmul_rn(d.w, pt[3]);
+            dts[k * 32] = d;
+        }
+        for (int k = olo; k < ohi; ++k) {
+            float4 d = fresh ? make_float4(1.0f, 1.0f, 1.0f, 1.0f) : dts[k * 32];
+            d.x = __fmul_rn(d.x, po[0]);
+            d.y = __fmul_rn(d.y, po[1]);
+            d.z = __fmul_rn(d.z, po[2]);
+            d.w = __fmul_rn(d.w, po[3]);
+            dts[k * 32] = d;
+        }
+    }
+    GP_ROWS(t[j] = v[j])
+#undef GP_ROWS
 }
 
-template <int RPT, int WARPS, int CAP, int NSLOT, int MINB, bool XREG>
+// Runs one program of the gradient form over the lane's four rows: the
+// evaluator's fast loop runs the unmarked words, and each word it hands
+// back -- a marker with the word after it, or a word it does not run --
+// runs in grad_word.  Returns the prediction in t and leaves each
+// constant's tangent d(prediction)/d(c_k) in dts[k * 32].
+template <int NSLOT, int KT, bool XREG>
+__device__ __forceinline__ void grad_run(float (&t)[4], const uint2 *cbuf, const float (&x0)[4],
+                                         const float (&x1)[4], const float *__restrict__ X,
+                                         int64_t ld, int64_t r0, int64_t re, bool vec,
+                                         float4 *stk, float4 *dts) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = 0.0f;
+    uint32_t pa = (uint32_t)__cvta_generic_to_shared(cbuf);
+    const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stk);
+    const uint64_t x0p[2] = {pack2(x0[0], x0[1]), pack2(x0[2], x0[3])};
+    const uint64_t x1p[2] = {pack2(x1[0], x1[1]), pack2(x1[2], x1[3])};
+#pragma unroll 1
+    for (;;) {
+        uint64_t tp[2] = {pack2(t[0], t[1]), pack2(t[2], t[3])};
+        uint32_t hw;
+        float hc;
+        run_fast<4, NSLOT, true, XREG>(pa, tp, x0p, x1p, sb, hw, hc);
+        unpack2(tp[0], t[0], t[1]);
+        unpack2(tp[1], t[2], t[3]);
+        uint32_t w = __shfl_sync(0xffffffffu, hw, 0);
+        float c = hc;
+        uint32_t mk = 0u;
+        if ((w & 63u) == kGradMark) {
+            mk = __shfl_sync(0xffffffffu, __float_as_uint(hc), 0);
+            uint32_t w2, c2;
+            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(w2), "=r"(c2) : "r"(pa));
+            pa += 8u;
+            w = __shfl_sync(0xffffffffu, w2, 0);
+            c = __uint_as_float(c2);
+        }
+        if ((w & 31u) == OP_END) break;
+        grad_word<NSLOT, KT, XREG>(w, c, mk, t, x0, x1, X, ld, r0, re, vec, sb, dts);
+    }
+}
+
+// shared memory of one block: the program's words (through the buffer's
+// end OP_END), then per warp the value stack [NSLOT][32 lanes] and the
+// tangents [KT][32 lanes], one float4 (four rows) per entry
+template <int WARPS, int NSLOT, int KT>
+constexpr size_t grad_smem_bytes() {
+    return (size_t)(kGradCodeStride + 2) * sizeof(uint2) +
+           (size_t)WARPS * (NSLOT + KT) * 32 * sizeof(float4);
+}
+
+template <int WARPS, int NSLOT, int KT, int MINB, bool XREG>
 __global__ void __launch_bounds__(WARPS * 32, MINB) grad_kernel(const GradArgs a) {
+    constexpr int R = 4;
+    static_assert((kGradCodeStride + 2) * sizeof(uint2) % 16 == 0, "stack alignment");
     extern __shared__ float4 smem_grad[];
     uint2 *cbuf = reinterpret_cast<uint2 *>(smem_grad);
-    float *tape_all = reinterpret_cast<float *>(smem_grad + ((CAP + 2) * sizeof(uint2) + 15) / 16);
-    float *slot_all = tape_all + (size_t)WARPS * CAP * RPT * 32;
+    float4 *stack_all = smem_grad + (kGradCodeStride + 2) * sizeof(uint2) / 16;
+    float4 *tan_all = stack_all + (size_t)WARPS * NSLOT * 32;
     __shared__ float wsum[WARPS];
     __shared__ float wgrad[WARPS][GP_MAX_CONSTS];
     __shared__ unsigned long long s_item;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    // element (word i, row j) of this lane: tape[(i * RPT + j) * 32]
-    float *tape = tape_all + (size_t)warp * CAP * RPT * 32 + lane;
-    float *adjs = slot_all + (size_t)warp * NSLOT * RPT * 32 + lane;
+    float4 *stk = stack_all + (size_t)warp * NSLOT * 32 + lane;
+    float4 *dts = tan_all + (size_t)warp * KT * 32 + lane;
     int cls_begin = 0;
     for (int b = 0; b < a.bucket; ++b) cls_begin += a.class_count[b];
     const int n_cls = a.class_count[a.bucket];
     const unsigned long long total = (unsigned long long)n_cls * (unsigned long long)a.n_chunks;
+    const bool vec = a.vec_ok != 0;
     const bool two_feat = XREG && a.n_feat == 2;
 
     for (unsigned long long it = 0; it <= total; ++it) {
@@ -149,7 +298,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) grad_kernel(const GradArgs a
         const int p = a.order[cls_begin + rank];
         const ProgMeta m = a.meta[p];
         float *gp = a.gpart + ((size_t)p * a.n_chunks + chunk) * GP_MAX_CONSTS;
-        if (m.status != GP_PROG_OK || m.n_consts > GP_MAX_CONSTS || m.n_ins > CAP) {
+        if (m.status != GP_PROG_OK || m.n_consts > KT || m.n_ins > kGradCodeStride) {
             if (threadIdx.x == 0) {
                 a.part[(size_t)p * a.n_chunks + chunk] = __int_as_float(0x7fc00000);
                 if (m.n_consts > GP_MAX_CONSTS) atomicOr(a.dev_status, GP_DEV_TOO_MANY_CONSTS);
@@ -159,183 +308,67 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) grad_kernel(const GradArgs a
             continue;
         }
         const int n_ins = m.n_ins;
-        for (int i = threadIdx.x; i < n_ins; i += WARPS * 32) cbuf[i] = a.code[(size_t)p * kCodeStride + i];
+        const uint2 *src = a.code + (size_t)p * kGradCodeStride;
+        for (int i = threadIdx.x; i < kGradCodeStride + 2; i += WARPS * 32)
+            cbuf[i] = (i < n_ins) ? src[i] : make_uint2(make_ins(OP_END, 0, 0), 0u);
         __syncthreads();
 
+        const int nc = m.n_consts;
         const int64_t rb = (int64_t)chunk * a.chunk_rows;
         const int64_t re = min(a.n_rows, rb + a.chunk_rows);
         const int n_in = (int)(re - rb);
-        float gs[GP_MAX_CONSTS];
+        float gs[KT];
 #pragma unroll
-        for (int k = 0; k < GP_MAX_CONSTS; ++k) gs[k] = 0.0f;
+        for (int k = 0; k < KT; ++k) gs[k] = 0.0f;
         float ls = 0.0f, lc = 0.0f;
-        for (int base = warp * 32 * RPT; base < n_in; base += WARPS * 32 * RPT) {
-            const int o = base + lane * RPT;
-            const bool full = __all_sync(0xffffffffu, o + RPT <= n_in);
-            const int nv = full ? RPT : n_in - o;
-            const int64_t r0 = rb + o;
-            float x0[RPT], x1[RPT];
+        for (int base = warp * 32 * R; base < n_in; base += WARPS * 32 * R) {
+            const int o = base + lane * R;
+            const bool full = __all_sync(0xffffffffu, o + R <= n_in);
+            const int nv = full ? R : n_in - o;
+            float x0[R], x1[R];
             if (XREG) {
+                load_chunk_rows<R>(x0, a.X + (rb + o), full && vec, nv);
+                if (two_feat) load_chunk_rows<R>(x1, a.X + (a.ld + rb + o), full && vec, nv);
+                else {
 #pragma unroll
-                for (int j = 0; j < RPT; ++j) {
-                    x0[j] = (j < nv) ? __ldg(a.X + r0 + j) : 0.0f;
-                    x1[j] = two_feat ? ((j < nv) ? __ldg(a.X + a.ld + r0 + j) : 0.0f) : x0[j];
+                    for (int j = 0; j < R; ++j) x1[j] = x0[j];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < R; ++j) x0[j] = x1[j] = 0.0f;
+            }
+            float t[R];
+            grad_run<NSLOT, KT, XREG>(t, cbuf, x0, x1, a.X, a.ld, rb + o, re, vec, stk, dts);
+            // the loss and its derivative per row
+            float yv[R], wv[R];
+            load_chunk_rows<R>(yv, a.y + (rb + o), full && vec, nv);
+            if (a.w) load_chunk_rows<R>(wv, a.w + (rb + o), full && vec, nv);
+            else {
+#pragma unroll
+                for (int j = 0; j < R; ++j) wv[j] = 1.0f;
+            }
+            float e = 0.0f, at[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const bool in = j < nv;
+                float l = row_loss(a.metric, t[j], yv[j]);
+                if (a.w) l = __fmul_rn(wv[j], l);
+                e = in ? __fadd_rn(e, l) : e;
+                at[j] = in ? __fmul_rn(wv[j], g_dloss(a.metric, t[j], yv[j])) : 0.0f;
+            }
+            kahan_add(ls, lc, e);
+            // each constant's share: the rows' loss derivatives times its tangents
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if (k < nc) {
+                    const float4 d = dts[k * 32];
+                    const float dd[R] = {d.x, d.y, d.z, d.w};
+                    float s = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < R; ++j) s = (j < nv) ? __fadd_rn(s, __fmul_rn(at[j], dd[j])) : s;
+                    gs[k] = __fadd_rn(gs[k], s);
                 }
             }
-            // the value of column feat on the lane's rows
-            auto column = [&](uint32_t feat, float (&u)[RPT]) {
-                if (XREG) {
-#pragma unroll
-                    for (int j = 0; j < RPT; ++j) u[j] = feat ? x1[j] : x0[j];
-                } else {
-#pragma unroll
-                    for (int j = 0; j < RPT; ++j)
-                        u[j] = (j < nv) ? __ldg(a.X + (int64_t)feat * a.ld + r0 + j) : 0.0f;
-                }
-            };
-            // ---- forward: every word's result onto the tape (one switch
-            // per word over its operation, each case with its operands)
-            float t[RPT];
-#pragma unroll
-            for (int j = 0; j < RPT; ++j) t[j] = 0.0f;
-            for (int i = 0; i < n_ins - 1; ++i) {
-                const uint2 ins = cbuf[i];
-                const uint32_t w = __shfl_sync(0xffffffffu, ins.x, 0);
-                const float c = __uint_as_float(ins.y);
-                float u[RPT];
-#define GP_TAPE(q) tape[((q) * RPT + j) * 32]
-#define GP_ROWS(stmt) _Pragma("unroll") for (int j = 0; j < RPT; ++j) { stmt; }
-                switch (w & 31u) {
-                case OP_PUSH_X: case OP_PUSH_X_SP: column(w >> 16, u); GP_ROWS(t[j] = u[j]) break;
-                case OP_PUSH_C: case OP_PUSH_C_SP: GP_ROWS(t[j] = c) break;
-                case OP_ADD_S: GP_ROWS(t[j] = f_add(t[j], GP_TAPE(w >> 24))) break;
-                case OP_SUB_S: GP_ROWS(t[j] = f_sub(t[j], GP_TAPE(w >> 24))) break;
-                case OP_MUL_S: GP_ROWS(t[j] = f_mul(t[j], GP_TAPE(w >> 24))) break;
-                case OP_DIV_S: GP_ROWS(t[j] = f_div(t[j], GP_TAPE(w >> 24))) break;
-                case OP_ADD_X: column(w >> 16, u); GP_ROWS(t[j] = f_add(t[j], u[j])) break;
-                case OP_ADD_C: GP_ROWS(t[j] = f_add(t[j], c)) break;
-                case OP_SUB_X: column(w >> 16, u); GP_ROWS(t[j] = f_sub(t[j], u[j])) break;
-                case OP_SUB_C: GP_ROWS(t[j] = f_sub(t[j], c)) break;
-                case OP_RSUB_X: column(w >> 16, u); GP_ROWS(t[j] = f_sub(u[j], t[j])) break;
-                case OP_RSUB_C: GP_ROWS(t[j] = f_sub(c, t[j])) break;
-                case OP_MUL_X: column(w >> 16, u); GP_ROWS(t[j] = f_mul(t[j], u[j])) break;
-                case OP_MUL_C: GP_ROWS(t[j] = f_mul(t[j], c)) break;
-                case OP_DIV_X: column(w >> 16, u); GP_ROWS(t[j] = f_div(t[j], u[j])) break;
-                case OP_DIV_C: GP_ROWS(t[j] = f_div(t[j], c)) break;
-                case OP_RDIV_X: column(w >> 16, u); GP_ROWS(t[j] = f_div(u[j], t[j])) break;
-                case OP_RDIV_C: GP_ROWS(t[j] = f_div(c, t[j])) break;
-                case OP_SQRT: GP_ROWS(t[j] = f_sqrt(t[j])) break;
-                case OP_LOG: GP_ROWS(t[j] = f_log(t[j])) break;
-                case OP_EXP: GP_ROWS(t[j] = f_exp(t[j])) break;
-                case OP_SIN: case OP_COS: case OP_TAN: trig_rows<RPT>(t, (int)((w & 31u) - OP_SIN)); break;
-                case OP_ABS: GP_ROWS(t[j] = f_abs(t[j])) break;
-                case OP_NEG: GP_ROWS(t[j] = f_neg(t[j])) break;
-                case OP_INV: GP_ROWS(t[j] = f_inv(t[j])) break;
-                case OP_EXT1: GP_ROWS(t[j] = f_ext1((w >> 16) & 7u, t[j])) break;
-                case OP_EXT2:
-                    if (((w >> 16) & 7u) == EXT_MAX) { GP_ROWS(t[j] = f_max(t[j], GP_TAPE(w >> 24))) }
-                    else { GP_ROWS(t[j] = f_min(t[j], GP_TAPE(w >> 24))) }
-                    break;
-                default: break;  // OP_END is never reached here
-                }
-                GP_ROWS(GP_TAPE(i) = t[j])
-            }
-            // ---- the loss and its derivative per row
-            float at[RPT];
-            {
-                float e = 0.0f;
-#pragma unroll
-                for (int j = 0; j < RPT; ++j) {
-                    const bool in = j < nv;
-                    const float yv = in ? __ldg(a.y + r0 + j) : 0.0f;
-                    const float wv = (a.w && in) ? __ldg(a.w + r0 + j) : 1.0f;
-                    float l = row_loss(a.metric, t[j], yv);
-                    if (a.w) l = __fmul_rn(wv, l);
-                    e = in ? __fadd_rn(e, l) : e;
-                    at[j] = in ? __fmul_rn(wv, g_dloss(a.metric, t[j], yv)) : 0.0f;
-                }
-                kahan_add(ls, lc, e);
-            }
-            // the lane's share of constant k: its rows' adjoints times d
-#define GP_SHARE(k, d)                                                     \
-    {                                                                      \
-        float s_ = 0.0f;                                                   \
-        _Pragma("unroll") for (int j = 0; j < RPT; ++j)                    \
-            s_ = (j < nv) ? __fadd_rn(s_, __fmul_rn(at[j], (d))) : s_;     \
-        gadd(gs, (k), s_);                                                 \
-    }
-            // ---- adjoint: the words in reverse, one switch per word; the
-            // word's input is the previous word's result (tin), its output
-            // its own (v); a popped slot's value is the spilled word's result
-            for (int i = n_ins - 2; i >= 0; --i) {
-                const uint2 ins = cbuf[i];
-                const uint32_t w = __shfl_sync(0xffffffffu, ins.x, 0);
-                const float c = __uint_as_float(ins.y);
-                const uint32_t slot = min((w >> 8) & 255u, (uint32_t)NSLOT - 1u);
-                const uint32_t aux = w >> 24;
-#define GP_ADJ(j) adjs[(slot * RPT + (j)) * 32]
-#define GP_TIN GP_TAPE(i - 1)
-#define GP_V GP_TAPE(i)
-                float u[RPT];
-                switch (w & 31u) {
-                case OP_PUSH_X: break;
-                case OP_PUSH_X_SP: GP_ROWS(at[j] = GP_ADJ(j)) break;
-                case OP_PUSH_C: GP_SHARE(aux, 1.0f) break;
-                case OP_PUSH_C_SP: GP_SHARE(aux, 1.0f) GP_ROWS(at[j] = GP_ADJ(j)) break;
-                case OP_ADD_S: GP_ROWS(GP_ADJ(j) = at[j]) break;
-                case OP_SUB_S: GP_ROWS(GP_ADJ(j) = -at[j]) break;
-                case OP_MUL_S:
-                    GP_ROWS(GP_ADJ(j) = __fmul_rn(at[j], GP_TIN); at[j] = __fmul_rn(at[j], GP_TAPE(aux)))
-                    break;
-                case OP_DIV_S:
-                    GP_ROWS(const float r = GP_TAPE(aux); const bool p0 = fabsf(r) < kThr;
-                            GP_ADJ(j) = p0 ? 0.0f : __fmul_rn(at[j], -__fdiv_rn(GP_V, r));
-                            at[j] = p0 ? 0.0f : __fmul_rn(at[j], __frcp_rn(r)))
-                    break;
-                case OP_ADD_X: case OP_SUB_X: break;
-                case OP_ADD_C: GP_SHARE(aux, 1.0f) break;
-                case OP_SUB_C: GP_SHARE(aux, -1.0f) break;
-                case OP_RSUB_X: GP_ROWS(at[j] = -at[j]) break;
-                case OP_RSUB_C: GP_SHARE(aux, 1.0f) GP_ROWS(at[j] = -at[j]) break;
-                case OP_MUL_X: column(w >> 16, u); GP_ROWS(at[j] = __fmul_rn(at[j], u[j])) break;
-                case OP_MUL_C: GP_SHARE(aux, GP_TIN) GP_ROWS(at[j] = __fmul_rn(at[j], c)) break;
-                case OP_DIV_X:
-                    column(w >> 16, u);
-                    GP_ROWS(at[j] = fabsf(u[j]) < kThr ? 0.0f : __fmul_rn(at[j], __frcp_rn(u[j])))
-                    break;
-                case OP_DIV_C:
-                    if (fabsf(c) < kThr) { GP_ROWS(at[j] = 0.0f) }
-                    else {
-                        GP_SHARE(aux, -__fdiv_rn(GP_V, c))
-                        GP_ROWS(at[j] = __fmul_rn(at[j], __frcp_rn(c)))
-                    }
-                    break;
-                case OP_RDIV_X:
-                    GP_ROWS(const float r = GP_TIN;
-                            at[j] = fabsf(r) < kThr ? 0.0f : __fmul_rn(at[j], -__fdiv_rn(GP_V, r)))
-                    break;
-                case OP_RDIV_C:
-                    GP_SHARE(aux, fabsf(GP_TIN) < kThr ? 0.0f : __frcp_rn(GP_TIN))
-                    GP_ROWS(const float r = GP_TIN;
-                            at[j] = fabsf(r) < kThr ? 0.0f : __fmul_rn(at[j], -__fdiv_rn(GP_V, r)))
-                    break;
-                case OP_EXT2:
-                    GP_ROWS(const float l = GP_TIN; const float r = GP_TAPE(aux);
-                            const bool left = (((w >> 16) & 7u) == EXT_MAX) ? (l > r || l != l)
-                                                                             : (l < r || l != l);
-                            GP_ADJ(j) = left ? 0.0f : at[j]; at[j] = left ? at[j] : 0.0f)
-                    break;
-                default:  // the unary functions
-                    GP_ROWS(at[j] = __fmul_rn(at[j], d_unary(w & 31u, (w >> 16) & 7u, GP_TIN, GP_V)))
-                    break;
-                }
-#undef GP_ADJ
-#undef GP_TIN
-#undef GP_V
-            }
-#undef GP_SHARE
-#undef GP_ROWS
-#undef GP_TAPE
         }
         // fixed butterfly per warp, then the warps in order
         float lv = __fsub_rn(ls, lc);
@@ -344,9 +377,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) grad_kernel(const GradArgs a
         if (lane == 0) wsum[warp] = lv;
 #pragma unroll
         for (int k = 0; k < GP_MAX_CONSTS; ++k) {
-            float v = gs[k];
+            float v = 0.0f;
+            if (k < KT) {
+                v = gs[k < KT ? k : 0];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
+                for (int off = 16; off > 0; off >>= 1)
+                    v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
+            }
             if (lane == 0) wgrad[warp][k] = v;
         }
         __syncthreads();
@@ -364,10 +401,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) grad_kernel(const GradArgs a
     }
 }
 
-template <int RPT, int WARPS, int CAP, int NSLOT, int MINB, bool XREG>
+template <int WARPS, int NSLOT, int KT, int MINB, bool XREG>
 cudaError_t launch_grad_t(const GradArgs &a, int sms, cudaStream_t st, int *occ_out) {
-    constexpr size_t smem = grad_smem_bytes<RPT, WARPS, CAP, NSLOT>();
-    auto k = grad_kernel<RPT, WARPS, CAP, NSLOT, MINB, XREG>;
+    constexpr size_t smem = grad_smem_bytes<WARPS, NSLOT, KT>();
+    auto k = grad_kernel<WARPS, NSLOT, KT, MINB, XREG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -381,22 +418,19 @@ cudaError_t launch_grad_t(const GradArgs &a, int sms, cudaStream_t st, int *occ_
     return cudaGetLastError();
 }
 
-// One row per lane (a tape row per word per lane; two rows per lane halved
-// the resident warps and ran 33% slower).  Buckets 0-3 (compiled depth <=
-// 8, 7 adjoint slots): 8, 8, 8 and 4 warps per block, as many blocks as
-// the tape and registers allow; bucket 4 (up to 256 words or deeper
-// stacks): 2 warps and 19 slots.
-#define GP_GRAD_LAUNCH(R, W, C, S, M) \
-    (xreg ? launch_grad_t<R, W, C, S, M, true>(a, sms, st, occ) \
-          : launch_grad_t<R, W, C, S, M, false>(a, sms, st, occ))
+// Four rows per lane.  Bucket 0 (at most kGradTan0 constants, compiled
+// depth <= 8): 8 warps, 7 stack slots and 4 tangent slots per row, 4
+// blocks per SM; bucket 1 (up to 16 constants): 16 tangent slots, 2
+// blocks; bucket 2 (deeper stacks): 4 warps, 19 slots, 3 blocks.
+#define GP_GRAD_LAUNCH(W, S, K, M) \
+    (xreg ? launch_grad_t<W, S, K, M, true>(a, sms, st, occ) \
+          : launch_grad_t<W, S, K, M, false>(a, sms, st, occ))
 cudaError_t launch_grad(const GradArgs &a, int sms, cudaStream_t st, int *occ) {
     const bool xreg = a.n_feat <= 2;
     switch (a.bucket) {
-    case 0: return GP_GRAD_LAUNCH(1, 8, kGradCap0, kSmallDepth - 1, 5);
-    case 1: return GP_GRAD_LAUNCH(1, 8, kGradCap1, kSmallDepth - 1, 4);
-    case 2: return GP_GRAD_LAUNCH(1, 8, kGradCap2, kSmallDepth - 1, 2);
-    case 3: return GP_GRAD_LAUNCH(1, 4, kGradCap3, kSmallDepth - 1, 2);
-    default: return GP_GRAD_LAUNCH(1, 2, kCodeStride, kDeepSlots, 3);
+    case 0: return GP_GRAD_LAUNCH(8, kSmallDepth - 1, kGradTan0, 4);
+    case 1: return GP_GRAD_LAUNCH(8, kSmallDepth - 1, GP_MAX_CONSTS, 2);
+    default: return GP_GRAD_LAUNCH(4, kDeepSlots, GP_MAX_CONSTS, 3);
     }
 }
 #undef GP_GRAD_LAUNCH

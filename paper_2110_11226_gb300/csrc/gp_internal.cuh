@@ -55,6 +55,27 @@ enum : uint32_t {
     OP_EXT1 = 30, OP_EXT2 = 31
 };
 constexpr uint32_t kOpCol1 = 32;  // bit 5: a column read of column 1
+
+// Gradient form of a program (forward-mode derivatives with respect to its
+// constants).  The constants are numbered 0, 1, ... in prefix order, so the
+// constants under any node form a contiguous range of numbers, and those
+// of a binary node's left subtree come just before those of its right one.
+// The tangent of constant k on a row, dt[k], is the derivative with
+// respect to c_k of the stack value whose subtree holds c_k; a word that
+// combines its operands multiplies the tangents under each operand by the
+// word's partial derivative with respect to that operand, so at the end
+// dt[k] is d(program)/d(c_k).  Each word whose operands hold constants is
+// preceded by a marker word: x = kGradMark, y = the ranges
+//   bits 0-4 / 5-9    [tlo, thi): constants under the top operand t
+//   bits 10-14 / 15-19 [olo, ohi): constants under the other operand (the
+//                      popped slot, the inline terminal, or for a push of a
+//                      constant the constant itself)
+//   bit 20            fresh: the other operand is a constant terminal, its
+//                      tangent starts at 1 here
+// The marker's low five bits read as OP_END, and the fast loop hands it
+// back like any word it does not run.
+constexpr uint32_t kGradMark = OP_END | kOpCol1;
+constexpr int kGradCodeStride = 512;  // words of the gradient form (<= 2 per node + END)
 enum : uint32_t { EXT_SQ = 0, EXT_CUBE, EXT_CBRT, EXT_TANH, EXT_ATAN, EXT_SINH, EXT_COSH };
 enum : uint32_t { EXT_MAX = 0, EXT_MIN = 1 };
 
@@ -100,19 +121,15 @@ __host__ __device__ inline int prog_class(int depth, int ext) {
     return depth > kSmallDepth ? kClassDeep : (ext ? kClassShallowExt : kClassShallow);
 }
 
-// Length buckets of the constant gradient (the compiled gradient form):
-// its per-warp tape holds one value per word and row, so each bucket is one
-// launch with a tape sized for its longest program; programs of compiled
-// depth at most kSmallDepth need 7 adjoint slots, the others (last bucket)
-// 19.
-constexpr int kGradBuckets = 5;
-constexpr int kGradCap0 = 24, kGradCap1 = 48, kGradCap2 = 96, kGradCap3 = 160;
-__host__ __device__ inline int grad_bucket(int n_ins, int depth) {
-    if (depth > kSmallDepth) return 4;
-    return n_ins <= kGradCap0 ? 0
-         : n_ins <= kGradCap1 ? 1
-         : n_ins <= kGradCap2 ? 2
-         : n_ins <= kGradCap3 ? 3 : 4;
+// Buckets of the constant gradient, one launch each: the tangents of a
+// warp's rows take kGradTan0 (bucket 0) or GP_MAX_CONSTS (buckets 1, 2)
+// shared-memory slots per row, the value stack 7 (buckets 0, 1) or 19
+// (bucket 2).
+constexpr int kGradBuckets = 3;
+constexpr int kGradTan0 = 4;
+__host__ __device__ inline int grad_bucket(int n_consts, int depth) {
+    if (depth > kSmallDepth) return 2;
+    return n_consts <= kGradTan0 ? 0 : 1;
 }
 // classes of the program order (evaluator classes or gradient buckets)
 constexpr int kOrderClasses = 5;
@@ -122,7 +139,7 @@ struct Workspace {
     unsigned long long *counters;  // [8] work-queue counters
     double *sumw;                  // [1] total weight
     double *sumw_part;             // [kSumwBlocks]
-    uint2 *code;                   // [P][kCodeStride]
+    uint2 *code;                   // [P][kCodeStride], the gradient form [P][kGradCodeStride]
     ProgMeta *meta;                // [P]
     int32_t *order;                // [P] program ids, by class then length
     int32_t *class_count;          // [kOrderClasses + 2]
@@ -132,10 +149,7 @@ struct Workspace {
     double *ystat_part;            // [kSumwBlocks][2]
     float *shift;                  // [P] program value at row 0
     double *mom;                   // [P][n_chunks][3] per-item moment sums
-    // constant-gradient extras (may be null)
-    uint8_t *rchild;               // [P][256] right child offset per node
-    int8_t *kslot;                 // [P][256] constant slot per node or -1
-    int16_t *cnode;                // [P][16] node index of constant k
+    // constant-gradient extra (may be null)
     float *gpart;                  // [P][n_chunks][16]
     size_t bytes;
 };
@@ -145,7 +159,7 @@ constexpr int kSumwBlocks = 512;
 struct Layout {
     size_t counters, sumw, sumw_part, code, meta, order, class_count, part;
     size_t ystat, ystat_part, shift, mom;
-    size_t rchild, kslot, cnode, gpart, total;
+    size_t gpart, total;
 };
 
 // moments: reserve the correlation extras (GP_PEARSON)
@@ -168,20 +182,16 @@ struct CompileArgs {
     int n_feat;
     uint2 *code;
     ProgMeta *meta;
-    uint8_t *rchild;   // optional
-    int8_t *kslot;     // optional
-    int16_t *cnode;    // optional
     unsigned int *dev_status;
     int32_t *out_prog_status;  // optional, caller's
     // optional: each program's value at row 0 of X (column stride ld)
     const float *X;
     int64_t ld;
     float *shift;
-    // gradient form: no constant-only subtree is folded (every constant
-    // keeps a word of its own or an operand place), and bits 24-31 of a
-    // word carry its auxiliary byte -- the constant's slot (k-th constant
-    // in prefix order) on words that read a constant, and on words that
-    // pop a stack slot the index of the word whose result was spilled there
+    // gradient form (code stride kGradCodeStride): no constant-only subtree
+    // is folded, so every constant keeps a word of its own or an operand
+    // place, and a marker word (kGradMark) precedes each word whose
+    // operands carry constants (see kGradMark)
     int grad;
 };
 cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st);
@@ -297,11 +307,11 @@ struct TournArgs {
 cudaError_t launch_tournament(const TournArgs &a, cudaStream_t st);
 
 struct GradArgs {
-    const uint2 *code;          // gradient form (CompileArgs::grad), [P][kCodeStride]
+    const uint2 *code;          // gradient form (CompileArgs::grad), [P][kGradCodeStride]
     const ProgMeta *meta;
-    const int32_t *order;       // by length bucket, then length
+    const int32_t *order;       // by bucket, then length
     const int32_t *class_count; // programs per bucket
-    int bucket;                 // the launch's length bucket (grad_bucket)
+    int bucket;                 // the launch's bucket (grad_bucket)
     const float *X;
     int64_t ld;
     int64_t n_rows;
@@ -312,6 +322,7 @@ struct GradArgs {
     int64_t chunk_rows;
     int n_chunks;
     unsigned long long *counter;  // [kGradBuckets] work-queue counters, one per bucket
+    int vec_ok;                   // X, y, w and the row counts allow 16-byte row loads
     float *part;   // [P][n_chunks] loss sums
     float *gpart;  // [P][n_chunks][16]
     unsigned int *dev_status;
@@ -336,7 +347,6 @@ struct AdamArgs {
     gp_node *progs;
     const int32_t *offsets;
     const ProgMeta *meta;
-    const int16_t *cnode;
     int n_progs;
     const float *grad;
     float *m;
