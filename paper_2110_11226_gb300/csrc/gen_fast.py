@@ -71,14 +71,16 @@ def kp(name, neg=False):
 
 
 class Gen:
-    def __init__(self, rpt, divs, xreg):
-        self.rpt, self.divs, self.xreg = rpt, divs, xreg
+    def __init__(self, rpt, divs, xreg, grad=False):
+        self.rpt, self.divs, self.xreg, self.grad = rpt, divs, xreg, grad
         self.np = rpt // 2               # pairs per lane
         p = self.np
         self.T = [f"%{1 + i}" for i in range(p)]
         self.HW, self.HC, self.SB, self.NSM1 = f"%{p + 1}", f"%{p + 2}", f"%{p + 3}", f"%{p + 4}"
         self.X = [[f"%{p + 5 + i}" for i in range(p)], [f"%{2 * p + 5 + i}" for i in range(p)]]
         self.THR = f"%{3 * p + 5}"
+        # gradient variant: the lane's tangent slot 0 and the tangent slots
+        self.DB, self.KT = f"%{3 * p + 6}", f"%{3 * p + 7}"
         self.slot_bytes = (rpt // 4) * 512
         self.lines = []
 
@@ -90,7 +92,9 @@ class Gen:
         self.lines.append(f"{name}%=:")
 
     def nxt(self):
-        self.e("bra.uni N%=;")
+        # the gradient variant returns through ret: 0 = the next word, else
+        # the partial-derivative body of the marked word just run
+        self.e("brx.idx.uni %%ret, TR%=;" if self.grad else "bra.uni N%=;")
 
     def unpack(self, i, a, b, src=None):
         self.e(f"mov.b64 {{{a}, {b}}}, {src or self.T[i]};")
@@ -150,15 +154,24 @@ class Gen:
     # both, the kind (0 sin, 1 cos) from the dispatch index.  j = the
     # integer nearest x/pi - kind/2, r = x - (j + kind/2) pi, then one odd
     # polynomial, negated when j + kind is odd (a sign-bit flip)
-    def trig(self):
-        self.range_check("trig_fast")
-        self.e(f"sub.u32 %%kd, %%i, {OPS['SIN']};")
-        self.e("setp.ne.u32 %%p, %%kd, 0;")
-        self.e("selp.b64 %%KM, 0xBF000000BF000000, 0x8000000080000000, %%p;")  # -kind/2
-        self.e("selp.b64 %%F, 0x3F0000003F000000, 0x0000000000000000, %%p;")   # +kind/2
-        self.e("shl.b32 %%kd, %%kd, 31;")
+    def trig(self, src=None, dst=None, kind=None):
+        """sin/cos of the pairs src(i) into dst(i) (default: the rows, in
+        place, after the range test, the kind from the dispatch index); a
+        static kind (0 sin, 1 cos) skips the test and the index"""
+        src = src or (lambda i: self.T[i])
+        if kind is None:
+            self.range_check("trig_fast")
+            self.e(f"sub.u32 %%kd, %%i, {OPS['SIN']};")
+            self.e("setp.ne.u32 %%p, %%kd, 0;")
+            self.e("selp.b64 %%KM, 0xBF000000BF000000, 0x8000000080000000, %%p;")  # -kind/2
+            self.e("selp.b64 %%F, 0x3F0000003F000000, 0x0000000000000000, %%p;")   # +kind/2
+            self.e("shl.b32 %%kd, %%kd, 31;")
+        else:
+            self.e("mov.b64 %%KM, " + ("0xBF000000BF000000;" if kind else "0x8000000080000000;"))
+            self.e("mov.b64 %%F, " + ("0x3F0000003F000000;" if kind else "0x0000000000000000;"))
+            self.e(f"mov.b32 %%kd, {0x80000000 if kind else 0};")
         for i in range(self.np):
-            t = self.T[i]
+            t = src(i)
             self.e(f"mov.b64 %%K0, {kp('inv_pi')};")
             self.e(f"fma.rn.f32x2 %%JM, {t}, %%K0, %%KM;")
             self.e(f"mov.b64 %%K1, {kp('magic')};")
@@ -191,7 +204,7 @@ class Gen:
                 self.e(f"mov.b32 %%a, {v};")
                 self.e(f"xor.b32 %%a, %%a, {n};")
                 self.e(f"mov.b32 {v}, %%a;")
-            self.pack(i, "%%v0", "%%v1")
+            self.pack(i, "%%v0", "%%v1", dst(i) if dst else None)
 
     # log of every row (f_log: the logarithm of max(|t|, thr), 0 below the
     # threshold, inf and NaN passed through)
@@ -345,6 +358,184 @@ class Gen:
                 self.e(f"selp.f32 {v}, 0f3F800000, {q}, %%p;")
             self.pack(i, "%%v0", "%%v1")
 
+    # -- the gradient variant: marked words --------------------------------
+    # A marker word (index END|COL1) announces that the next word's operands
+    # hold constants; its constant field packs the constant ranges (the
+    # format of gp_internal.cuh).  The loop runs the marked word's value
+    # body with ret = its index + 1, so the body returns through TR into
+    # the word's partial-derivative body (pt with respect to the rows t,
+    # po with respect to the other operand, as pairs), and the tangent tail
+    # scales the tangents of the two ranges.  Marked words the loop does
+    # not run, and those whose value body gives up, are handed back as
+    # their marker with the address at the marked word.
+    PARTIAL = dict(PC="PONE", PCS="PONE", AC="PONE", AS="PONE", SS="PSUB", SC="PSUB",
+                   RC="PRSUB", MS="PMS", MC="PMC", DS="PDIV", DC="PDIV", RDC="PRDIV",
+                   SQ="PSQ", IV="PIV", LG="PLG", XP="PXP", AB="PAB", NG="PNG",
+                   PX0="PONE", PX1="PONE", PXS0="PONE", PXS1="PONE", AX0="PONE", AX1="PONE",
+                   SX0="PSUB", SX1="PSUB", RX0="PRSUB", RX1="PRSUB", MX0="PMX0", MX1="PMX1",
+                   DX0="PDIV", DX1="PDIV", RDX0="PRDIV", RDX1="PRDIV")
+
+    def partial_labels(self, ent):
+        """per dispatch index: the partial-derivative body, or EX where the
+        loop does not run the word"""
+        out = []
+        for i, lab in enumerate(ent):
+            if lab == "TRG":
+                out.append("PSIN" if i == OPS["SIN"] else "PCOS")
+            else:
+                out.append(self.PARTIAL.get(lab, "EX"))
+        return out
+
+    def marked_entry(self):
+        e = self.e
+        e("mov.b32 %%mk, %%cb;")
+        e("ld.shared.v2.b32 {%%w2, %%c2}, [%0];")
+        e("and.b32 %%i2, %%w2, 63;")
+        e("brx.idx.uni %%i2, TM%=;")
+        self.label("MKS")
+        e("add.u32 %0, %0, 8;")
+        e("mov.b32 %%w, %%w2;")
+        e("mov.b32 %%cb, %%c2;")
+        e("mov.b32 %%cf, %%c2;")
+        e("mov.b32 %%i, %%i2;")
+        e("add.u32 %%ret, %%i2, 1;")
+        for i in range(self.np):
+            e(f"mov.b64 %%TO{i}, {self.T[i]};")
+        e("brx.idx.uni %%i, T%=;")
+
+    def partial_bodies(self, part):
+        e, p = self.e, self.np
+        ONES, MONES = "0x3F8000003F800000", "0xBF800000BF800000"
+        for lab in sorted(set(part) - {"EX"}):
+            self.label(lab)
+            if lab in ("PONE", "PSUB", "PRSUB", "PNG"):
+                pt = MONES if lab in ("PRSUB", "PNG") else ONES
+                po = MONES if lab == "PSUB" else ONES
+                for i in range(p):
+                    e(f"mov.b64 %%PT{i}, {pt};")
+                    e(f"mov.b64 %%PO{i}, {po};")
+            elif lab in ("PMS", "PMC", "PMX0", "PMX1"):
+                for i in range(p):
+                    src = {"PMS": f"%%U{i}", "PMC": "%%C"}.get(lab) or self.X[int(lab[-1])][i]
+                    e(f"mov.b64 %%PT{i}, {src};")
+                    e(f"mov.b64 %%PO{i}, %%TO{i};")
+            elif lab in ("PDIV", "PRDIV"):
+                # divisor b in U, quotient v in the rows: r = 1/b, -v r; both 0
+                # where |b| < thr (the protected branch is constant)
+                for i in range(p):
+                    self.rcp_pair(f"%%U{i}", f"%%A{i}")
+                    e(f"mov.b64 %%K0, {MONES};")
+                    e(f"mul.rn.f32x2 %%S, {self.T[i]}, %%K0;")
+                    e(f"mul.rn.f32x2 %%S, %%S, %%A{i};")
+                    e(f"mov.b64 {{%%s0, %%s1}}, %%U{i};")
+                    e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
+                    e("mov.b64 {%%v0, %%v1}, %%S;")
+                    for r in (0, 1):
+                        e(f"abs.f32 %%m, %%s{r};")
+                        e(f"setp.lt.f32 %%p, %%m, {self.THR};")
+                        e(f"selp.f32 %%c{r}, 0f00000000, %%c{r}, %%p;")
+                        e(f"selp.f32 %%v{r}, 0f00000000, %%v{r}, %%p;")
+                    r_, nv = ("%%PT", "%%PO") if lab == "PDIV" else ("%%PO", "%%PT")
+                    e(f"mov.b64 {r_}{i}, {{%%c0, %%c1}};")
+                    e(f"mov.b64 {nv}{i}, {{%%v0, %%v1}};")
+            elif lab == "PSQ":
+                # d sqrt|t| = sign(t) / (2 sqrt|t|) (t = 0 is handed back)
+                for i in range(p):
+                    self.rcp_pair(self.T[i], f"%%A{i}")
+                    e(f"mov.b64 %%K0, {kp('half')};")
+                    e(f"mul.rn.f32x2 %%A{i}, %%A{i}, %%K0;")
+                    e(f"mov.b64 {{%%s0, %%s1}}, %%TO{i};")
+                    e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
+                    for r in (0, 1):
+                        e(f"copysign.f32 %%c{r}, %%s{r}, %%c{r};")
+                    e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
+            elif lab == "PIV":
+                # d (1/t) = -v^2 (0 on the protected branch, where v = 0)
+                for i in range(p):
+                    e(f"mov.b64 %%K0, {MONES};")
+                    e(f"mul.rn.f32x2 %%S, {self.T[i]}, %%K0;")
+                    e(f"mul.rn.f32x2 %%PT{i}, %%S, {self.T[i]};")
+            elif lab == "PLG":
+                # d log|t| = 1/t, 0 where |t| < thr
+                for i in range(p):
+                    self.rcp_pair(f"%%TO{i}", f"%%A{i}")
+                    e(f"mov.b64 {{%%s0, %%s1}}, %%TO{i};")
+                    e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
+                    for r in (0, 1):
+                        e(f"abs.f32 %%m, %%s{r};")
+                        e(f"setp.lt.f32 %%p, %%m, {self.THR};")
+                        e(f"selp.f32 %%c{r}, 0f00000000, %%c{r}, %%p;")
+                    e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
+            elif lab == "PXP":
+                for i in range(p):
+                    e(f"mov.b64 %%PT{i}, {self.T[i]};")
+            elif lab == "PAB":
+                # sign(t): 1, -1, or 0 (at 0 and NaN)
+                for i in range(p):
+                    e(f"mov.b64 {{%%s0, %%s1}}, %%TO{i};")
+                    for r in (0, 1):
+                        e(f"setp.gt.f32 %%p, %%s{r}, 0f00000000;")
+                        e(f"selp.f32 %%c{r}, 0f3F800000, 0f00000000, %%p;")
+                        e(f"setp.lt.f32 %%p, %%s{r}, 0f00000000;")
+                        e(f"selp.f32 %%c{r}, 0fBF800000, %%c{r}, %%p;")
+                    e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
+            elif lab in ("PSIN", "PCOS"):
+                # d sin t = cos t; d cos t = -sin t (the value's range test
+                # already passed on these rows)
+                self.trig(src=lambda i: f"%%TO{i}", dst=lambda i: f"%%PT{i}",
+                          kind=1 if lab == "PSIN" else 0)
+                if lab == "PCOS":
+                    for i in range(p):
+                        e(f"mov.b64 %%K0, {MONES};")
+                        e(f"mul.rn.f32x2 %%PT{i}, %%PT{i}, %%K0;")
+            else:
+                raise ValueError(lab)
+            e("bra.uni TT%=;")
+
+    def tangent_tail(self):
+        """dt[k] *= pt for k in [tlo, thi); dt[k] = (fresh ? 1 : dt[k]) * po
+        for k in [olo, ohi); both ranges clamped to the KT slots"""
+        e, p = self.e, self.np
+        assert p == 2, "one float4 of tangents per (constant, lane): 4 rows"
+
+        def loop(lab, factor):
+            self.label(lab)
+            e("ld.shared.v2.b64 {%%A0, %%A1}, [%%da];")
+            for i in range(p):
+                e(f"mul.rn.f32x2 %%A{i}, %%A{i}, {factor}{i};")
+            e("st.shared.v2.b64 [%%da], {%%A0, %%A1};")
+            e("add.u32 %%da, %%da, 512;")
+            e("setp.lt.u32 %%p, %%da, %%de;")
+            e(f"@%%p bra {lab}%=;")
+
+        def bounds(lo_bit, hi_bit, skip):
+            e(f"bfe.u32 %%lo, %%mk, {lo_bit}, 5;")
+            e(f"bfe.u32 %%hi, %%mk, {hi_bit}, 5;")
+            e(f"min.u32 %%hi, %%hi, {self.KT};")
+            e("setp.ge.u32 %%p, %%lo, %%hi;")
+            e(f"@%%p bra {skip}%=;")
+            e(f"mad.lo.u32 %%da, %%lo, 512, {self.DB};")
+            e(f"mad.lo.u32 %%de, %%hi, 512, {self.DB};")
+
+        self.label("TT")
+        bounds(0, 5, "TTO")
+        loop("TTL", "%%PT")
+        self.label("TTO")
+        bounds(10, 15, "TTE")
+        e("bfe.u32 %%a, %%mk, 20, 1;")
+        e("setp.ne.u32 %%p, %%a, 0;")
+        e("@%%p bra TTF%=;")
+        loop("TTM", "%%PO")
+        e("bra.uni TTE%=;")
+        self.label("TTF")   # fresh: the tangent starts at 1, so it is po
+        e("st.shared.v2.b64 [%%da], {%%PO0, %%PO1};")
+        e("add.u32 %%da, %%da, 512;")
+        e("setp.lt.u32 %%p, %%da, %%de;")
+        e("@%%p bra TTF%=;")
+        self.label("TTE")
+        e("mov.u32 %%ret, 0;")
+        e("bra.uni N%=;")
+
     # -- the loop -----------------------------------------------------------
     def table(self):
         """64 branch targets; a label names one body (ops sharing a body say so
@@ -366,6 +557,8 @@ class Gen:
             for k, v in xops.items():
                 ent[OPS[k]] = v + "0"
                 ent[OPS[k] | COL1] = v + "1"
+        if self.grad:
+            ent[OPS["END"] | COL1] = "MK"
         owner = {}
         for op, lab in enumerate(ent):
             base = op & (COL1 - 1)
@@ -386,6 +579,14 @@ class Gen:
         e(".reg .f32 %%cf, %%q, %%m, %%mx, %%mn, %%v<2>, %%u<2>, %%s<2>, %%c<2>;")
         e(f".reg .b64 %%C, %%U<{p}>, %%K<2>, %%KM, %%JM, %%JJ, %%R, %%S, %%P, %%Q, %%F;")
         e("T%=: .branchtargets " + ", ".join(f"{x}%=" for x in ent) + ";")
+        if self.grad:
+            part = self.partial_labels(ent)
+            e(".reg .b32 %%ret, %%mk, %%i2, %%w2, %%c2, %%lo, %%hi, %%da, %%de;")
+            e(f".reg .b64 %%TO<{p}>, %%PT<{p}>, %%PO<{p}>, %%A<{p}>;")
+            tm = ["MKS" if part[i] != "EX" else "EX" for i in range(64)]
+            e("TM%=: .branchtargets " + ", ".join(f"{x}%=" for x in tm) + ";")
+            e("TR%=: .branchtargets " + ", ".join(f"{x}%=" for x in ["N"] + part) + ";")
+            e("mov.u32 %%ret, 0;")
         self.label("N")
         e("ld.shared.v2.b32 {%%w, %%cb}, [%0];")
         e("mov.b32 %%cf, %%cb;")
@@ -395,6 +596,9 @@ class Gen:
         X = self.X
         for name in used:
             self.label(name)
+            if name == "MK":
+                self.marked_entry()
+                continue
             col = int(name[-1]) if name[-1] in "01" and name not in ("PC",) else None
             stem = name[:-1] if col is not None else name
             if stem == "PX" or stem == "PXS":
@@ -477,7 +681,17 @@ class Gen:
             self.label("DTU")
             self.div_body()
             self.nxt()
+        if self.grad:
+            self.partial_bodies(part)
+            self.tangent_tail()
         self.label("EX")
+        if self.grad:
+            # a marked word whose value body gave up (a range test): hand
+            # back its marker, the address at the marked word
+            e("setp.ne.u32 %%p, %%ret, 0;")
+            e(f"@%%p mov.b32 %%w, {OPS['END'] | COL1};")
+            e("@%%p mov.b32 %%cf, %%mk;")
+            e("@%%p sub.u32 %0, %0, 8;")
         e(f"mov.b32 {self.HW}, %%w;")
         e(f"mov.f32 {self.HC}, %%cf;")
         e("}")
@@ -485,19 +699,21 @@ class Gen:
 
 
 
-def function(rpt, divs, xreg):
-    g = Gen(rpt, divs, xreg)
+def function(rpt, divs, xreg, grad=False):
+    g = Gen(rpt, divs, xreg, grad)
     lines = g.generate()
     p = rpt // 2
-    name = f"fast_r{rpt}_{'divs' if divs else 'nodivs'}_{'x' if xreg else 'nox'}"
+    name = f"fast_r{rpt}_{'divs' if divs else 'nodivs'}_{'x' if xreg else 'nox'}" + \
+        ("_grad" if grad else "")
     body = "\n".join(f'        "{ln}\\n\\t"' for ln in lines)
     outs = ", ".join(['"+r"(pa)'] + [f'"+l"(t[{i}])' for i in range(p)] + ['"=r"(hw)', '"=f"(hc)'])
     ins = ", ".join(['"r"(sb)', '"n"(NSLOT - 1)'] + [f'"l"(x0[{i}])' for i in range(p)]
-                    + [f'"l"(x1[{i}])' for i in range(p)] + ['"f"(kThr)'])
-    return (f"template <int NSLOT>\n"
+                    + [f'"l"(x1[{i}])' for i in range(p)] + ['"f"(kThr)']
+                    + (['"r"(db)', '"n"(KT)'] if grad else []))
+    return (f"template <int NSLOT{', int KT' if grad else ''}>\n"
             f"__device__ __forceinline__ void {name}(uint32_t &pa, uint64_t (&t)[{p}],\n"
             f"        const uint64_t (&x0)[{p}], const uint64_t (&x1)[{p}], uint32_t sb,\n"
-            f"        uint32_t &hw, float &hc) {{\n"
+            f"        {'uint32_t db, ' if grad else ''}uint32_t &hw, float &hc) {{\n"
             f"    asm volatile(\n{body}\n"
             f"        : {outs}\n"
             f"        : {ins});\n}}\n")
@@ -536,6 +752,10 @@ def main():
             for xreg in (True, False):
                 parts.append(function(rpt, divs, xreg))
                 parts.append("\n")
+    # the constant gradient's loop (4 rows per lane, the division set)
+    for xreg in (True, False):
+        parts.append(function(4, True, xreg, grad=True))
+        parts.append("\n")
     parts.append("}  // namespace gpk\n")
     with open(os.path.join(HERE, "gp_fast.cuh"), "w") as f:
         f.write("".join(parts))

@@ -94,18 +94,36 @@ __device__ __forceinline__ float f_ext1(uint32_t fn, float x) {
 
 }  // namespace
 
+// The tangents of a lane's four rows: one float4 per constant k at the
+// shared-memory address db + k * 512.  They are read and written only by
+// volatile asm statements (here and in the fast loop, which declares no
+// memory clobber), so their order is kept.
+__device__ __forceinline__ float4 tan_load(uint32_t a) {
+    float4 d;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(d.x), "=f"(d.y), "=f"(d.z), "=f"(d.w)
+                 : "r"(a));
+    return d;
+}
+__device__ __forceinline__ void tan_store(uint32_t a, float4 d) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(d.x), "f"(d.y),
+                 "f"(d.z), "f"(d.w)
+                 : "memory");
+}
+
 // One word of the gradient form that the fast loop handed back (a marked
-// word, or one the loop does not run): its value with the evaluator's
-// operations and, after a marker (mk != 0), its partial derivatives with
-// respect to the top operand t (pt) and the other operand (po), applied to
-// the tangents of the constants under each (kGradMark).  Four rows per
-// lane; the stack slot of this lane's rows is one float4 (sb + slot * 512
-// bytes), the tangent of constant k one float4 at dts[k * 32].
+// word it does not run or whose fast path gave up, or an unmarked word it
+// does not run): its value with the evaluator's operations and, after a
+// marker (mk != 0), its partial derivatives with respect to the top
+// operand t (pt) and the other operand (po), applied to the tangents of
+// the constants under each (kGradMark).  Four rows per lane; the stack
+// slot of this lane's rows is one float4 (sb + slot * 512 bytes), the
+// tangent of constant k one float4 at db + k * 512.
 template <int NSLOT, int KT, bool XREG>
 __device__ __forceinline__ void grad_word(uint32_t w, float c, uint32_t mk, float (&t)[4],
                                           const float (&x0)[4], const float (&x1)[4],
                                           const float *__restrict__ X, int64_t ld, int64_t r0,
-                                          int64_t re, bool vec, uint32_t sb, float4 *dts) {
+                                          int64_t re, bool vec, uint32_t sb, uint32_t db) {
     constexpr int R = 4;
     const uint32_t op = w & 31u;
     const uint32_t fn = (w >> 16) & 7u;
@@ -194,20 +212,20 @@ __device__ __forceinline__ void grad_word(uint32_t w, float c, uint32_t mk, floa
         const int olo = (int)((mk >> 10) & 31u), ohi = min((int)((mk >> 15) & 31u), KT);
         const bool fresh = ((mk >> 20) & 1u) != 0u;
         for (int k = tlo; k < thi; ++k) {
-            float4 d = dts[k * 32];
+            float4 d = tan_load(db + (uint32_t)k * 512u);
             d.x = __fmul_rn(d.x, pt[0]);
             d.y = __fmul_rn(d.y, pt[1]);
             d.z = __fmul_rn(d.z, pt[2]);
             d.w = __fmul_rn(d.w, pt[3]);
-            dts[k * 32] = d;
+            tan_store(db + (uint32_t)k * 512u, d);
         }
         for (int k = olo; k < ohi; ++k) {
-            float4 d = fresh ? make_float4(1.0f, 1.0f, 1.0f, 1.0f) : dts[k * 32];
+            float4 d = fresh ? make_float4(1.0f, 1.0f, 1.0f, 1.0f) : tan_load(db + (uint32_t)k * 512u);
             d.x = __fmul_rn(d.x, po[0]);
             d.y = __fmul_rn(d.y, po[1]);
             d.z = __fmul_rn(d.z, po[2]);
             d.w = __fmul_rn(d.w, po[3]);
-            dts[k * 32] = d;
+            tan_store(db + (uint32_t)k * 512u, d);
         }
     }
     GP_ROWS(t[j] = v[j])
@@ -215,15 +233,16 @@ __device__ __forceinline__ void grad_word(uint32_t w, float c, uint32_t mk, floa
 }
 
 // Runs one program of the gradient form over the lane's four rows: the
-// evaluator's fast loop runs the unmarked words, and each word it hands
-// back -- a marker with the word after it, or a word it does not run --
-// runs in grad_word.  Returns the prediction in t and leaves each
-// constant's tangent d(prediction)/d(c_k) in dts[k * 32].
+// gradient variant of the fast loop runs the words it can, marked ones
+// with their tangent updates, and each word it hands back -- a marker with
+// the word after it, or a word it does not run -- runs in grad_word.
+// Returns the prediction in t and leaves each constant's tangent
+// d(prediction)/d(c_k) at db + k * 512.
 template <int NSLOT, int KT, bool XREG>
 __device__ __forceinline__ void grad_run(float (&t)[4], const uint2 *cbuf, const float (&x0)[4],
                                          const float (&x1)[4], const float *__restrict__ X,
                                          int64_t ld, int64_t r0, int64_t re, bool vec,
-                                         float4 *stk, float4 *dts) {
+                                         float4 *stk, uint32_t db) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) t[j] = 0.0f;
     uint32_t pa = (uint32_t)__cvta_generic_to_shared(cbuf);
@@ -235,7 +254,8 @@ __device__ __forceinline__ void grad_run(float (&t)[4], const uint2 *cbuf, const
         uint64_t tp[2] = {pack2(t[0], t[1]), pack2(t[2], t[3])};
         uint32_t hw;
         float hc;
-        run_fast<4, NSLOT, true, XREG>(pa, tp, x0p, x1p, sb, hw, hc);
+        if constexpr (XREG) fast_r4_divs_x_grad<NSLOT, KT>(pa, tp, x0p, x1p, sb, db, hw, hc);
+        else fast_r4_divs_nox_grad<NSLOT, KT>(pa, tp, x0p, x1p, sb, db, hw, hc);
         unpack2(tp[0], t[0], t[1]);
         unpack2(tp[1], t[2], t[3]);
         uint32_t w = __shfl_sync(0xffffffffu, hw, 0);
@@ -250,7 +270,7 @@ __device__ __forceinline__ void grad_run(float (&t)[4], const uint2 *cbuf, const
             c = __uint_as_float(c2);
         }
         if ((w & 31u) == OP_END) break;
-        grad_word<NSLOT, KT, XREG>(w, c, mk, t, x0, x1, X, ld, r0, re, vec, sb, dts);
+        grad_word<NSLOT, KT, XREG>(w, c, mk, t, x0, x1, X, ld, r0, re, vec, sb, db);
     }
 }
 
@@ -277,7 +297,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) grad_kernel(const GradArgs a
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     float4 *stk = stack_all + (size_t)warp * NSLOT * 32 + lane;
-    float4 *dts = tan_all + (size_t)warp * KT * 32 + lane;
+    const uint32_t db = (uint32_t)__cvta_generic_to_shared(tan_all + (size_t)warp * KT * 32 + lane);
     int cls_begin = 0;
     for (int b = 0; b < a.bucket; ++b) cls_begin += a.class_count[b];
     const int n_cls = a.class_count[a.bucket];
@@ -338,7 +358,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) grad_kernel(const GradArgs a
                 for (int j = 0; j < R; ++j) x0[j] = x1[j] = 0.0f;
             }
             float t[R];
-            grad_run<NSLOT, KT, XREG>(t, cbuf, x0, x1, a.X, a.ld, rb + o, re, vec, stk, dts);
+            grad_run<NSLOT, KT, XREG>(t, cbuf, x0, x1, a.X, a.ld, rb + o, re, vec, stk, db);
             // the loss and its derivative per row
             float yv[R], wv[R];
             load_chunk_rows<R>(yv, a.y + (rb + o), full && vec, nv);
@@ -361,7 +381,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) grad_kernel(const GradArgs a
 #pragma unroll
             for (int k = 0; k < KT; ++k) {
                 if (k < nc) {
-                    const float4 d = dts[k * 32];
+                    const float4 d = tan_load(db + (uint32_t)k * 512u);
                     const float dd[R] = {d.x, d.y, d.z, d.w};
                     float s = 0.0f;
 #pragma unroll
