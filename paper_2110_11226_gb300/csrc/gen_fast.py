@@ -387,110 +387,111 @@ class Gen:
         return out
 
     def marked_entry(self):
+        """the marked word is loaded and dispatched through TV: a copy of a
+        cheap body, a shared body (which returns through ret), or EX when
+        the loop does not run it (EX then hands back the marker)"""
         e = self.e
         e("mov.b32 %%mk, %%cb;")
-        e("ld.shared.v2.b32 {%%w2, %%c2}, [%0];")
-        e("and.b32 %%i2, %%w2, 63;")
-        e("brx.idx.uni %%i2, TM%=;")
-        self.label("MKS")
+        e("ld.shared.v2.b32 {%%w, %%cb}, [%0];")
         e("add.u32 %0, %0, 8;")
-        e("mov.b32 %%w, %%w2;")
-        e("mov.b32 %%cb, %%c2;")
-        e("mov.b32 %%cf, %%c2;")
-        e("mov.b32 %%i, %%i2;")
-        e("add.u32 %%ret, %%i2, 1;")
+        e("mov.b32 %%cf, %%cb;")
+        e("and.b32 %%i, %%w, 63;")
+        e("add.u32 %%ret, %%i, 1;")
         for i in range(self.np):
             e(f"mov.b64 %%TO{i}, {self.T[i]};")
-        e("brx.idx.uni %%i, T%=;")
+        e("brx.idx.uni %%i, TV%=;")
 
-    def partial_bodies(self, part):
+    def partial_bodies(self, labels):
+        for lab in labels:
+            self.label(lab)
+            self.partial_code(lab)
+            self.e("bra.uni TT%=;")
+
+    def partial_code(self, lab):
         e, p = self.e, self.np
         ONES, MONES = "0x3F8000003F800000", "0xBF800000BF800000"
-        for lab in sorted(set(part) - {"EX"}):
-            self.label(lab)
-            if lab in ("PONE", "PSUB", "PRSUB", "PNG"):
-                pt = MONES if lab in ("PRSUB", "PNG") else ONES
-                po = MONES if lab == "PSUB" else ONES
+        if lab in ("PONE", "PSUB", "PRSUB", "PNG"):
+            pt = MONES if lab in ("PRSUB", "PNG") else ONES
+            po = MONES if lab == "PSUB" else ONES
+            for i in range(p):
+                e(f"mov.b64 %%PT{i}, {pt};")
+                e(f"mov.b64 %%PO{i}, {po};")
+        elif lab in ("PMS", "PMC", "PMX0", "PMX1"):
+            for i in range(p):
+                src = {"PMS": f"%%U{i}", "PMC": "%%C"}.get(lab) or self.X[int(lab[-1])][i]
+                e(f"mov.b64 %%PT{i}, {src};")
+                e(f"mov.b64 %%PO{i}, %%TO{i};")
+        elif lab in ("PDIV", "PRDIV"):
+            # divisor b in U, quotient v in the rows: r = 1/b, -v r; both 0
+            # where |b| < thr (the protected branch is constant)
+            for i in range(p):
+                self.rcp_pair(f"%%U{i}", f"%%A{i}")
+                e(f"mov.b64 %%K0, {MONES};")
+                e(f"mul.rn.f32x2 %%S, {self.T[i]}, %%K0;")
+                e(f"mul.rn.f32x2 %%S, %%S, %%A{i};")
+                e(f"mov.b64 {{%%s0, %%s1}}, %%U{i};")
+                e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
+                e("mov.b64 {%%v0, %%v1}, %%S;")
+                for r in (0, 1):
+                    e(f"abs.f32 %%m, %%s{r};")
+                    e(f"setp.lt.f32 %%p, %%m, {self.THR};")
+                    e(f"selp.f32 %%c{r}, 0f00000000, %%c{r}, %%p;")
+                    e(f"selp.f32 %%v{r}, 0f00000000, %%v{r}, %%p;")
+                r_, nv = ("%%PT", "%%PO") if lab == "PDIV" else ("%%PO", "%%PT")
+                e(f"mov.b64 {r_}{i}, {{%%c0, %%c1}};")
+                e(f"mov.b64 {nv}{i}, {{%%v0, %%v1}};")
+        elif lab == "PSQ":
+            # d sqrt|t| = sign(t) / (2 sqrt|t|) (t = 0 is handed back)
+            for i in range(p):
+                self.rcp_pair(self.T[i], f"%%A{i}")
+                e(f"mov.b64 %%K0, {kp('half')};")
+                e(f"mul.rn.f32x2 %%A{i}, %%A{i}, %%K0;")
+                e(f"mov.b64 {{%%s0, %%s1}}, %%TO{i};")
+                e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
+                for r in (0, 1):
+                    e(f"copysign.f32 %%c{r}, %%s{r}, %%c{r};")
+                e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
+        elif lab == "PIV":
+            # d (1/t) = -v^2 (0 on the protected branch, where v = 0)
+            for i in range(p):
+                e(f"mov.b64 %%K0, {MONES};")
+                e(f"mul.rn.f32x2 %%S, {self.T[i]}, %%K0;")
+                e(f"mul.rn.f32x2 %%PT{i}, %%S, {self.T[i]};")
+        elif lab == "PLG":
+            # d log|t| = 1/t, 0 where |t| < thr
+            for i in range(p):
+                self.rcp_pair(f"%%TO{i}", f"%%A{i}")
+                e(f"mov.b64 {{%%s0, %%s1}}, %%TO{i};")
+                e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
+                for r in (0, 1):
+                    e(f"abs.f32 %%m, %%s{r};")
+                    e(f"setp.lt.f32 %%p, %%m, {self.THR};")
+                    e(f"selp.f32 %%c{r}, 0f00000000, %%c{r}, %%p;")
+                e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
+        elif lab == "PXP":
+            for i in range(p):
+                e(f"mov.b64 %%PT{i}, {self.T[i]};")
+        elif lab == "PAB":
+            # sign(t): 1, -1, or 0 (at 0 and NaN)
+            for i in range(p):
+                e(f"mov.b64 {{%%s0, %%s1}}, %%TO{i};")
+                for r in (0, 1):
+                    e(f"setp.gt.f32 %%p, %%s{r}, 0f00000000;")
+                    e(f"selp.f32 %%c{r}, 0f3F800000, 0f00000000, %%p;")
+                    e(f"setp.lt.f32 %%p, %%s{r}, 0f00000000;")
+                    e(f"selp.f32 %%c{r}, 0fBF800000, %%c{r}, %%p;")
+                e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
+        elif lab in ("PSIN", "PCOS"):
+            # d sin t = cos t; d cos t = -sin t (the value's range test
+            # already passed on these rows)
+            self.trig(src=lambda i: f"%%TO{i}", dst=lambda i: f"%%PT{i}",
+                      kind=1 if lab == "PSIN" else 0)
+            if lab == "PCOS":
                 for i in range(p):
-                    e(f"mov.b64 %%PT{i}, {pt};")
-                    e(f"mov.b64 %%PO{i}, {po};")
-            elif lab in ("PMS", "PMC", "PMX0", "PMX1"):
-                for i in range(p):
-                    src = {"PMS": f"%%U{i}", "PMC": "%%C"}.get(lab) or self.X[int(lab[-1])][i]
-                    e(f"mov.b64 %%PT{i}, {src};")
-                    e(f"mov.b64 %%PO{i}, %%TO{i};")
-            elif lab in ("PDIV", "PRDIV"):
-                # divisor b in U, quotient v in the rows: r = 1/b, -v r; both 0
-                # where |b| < thr (the protected branch is constant)
-                for i in range(p):
-                    self.rcp_pair(f"%%U{i}", f"%%A{i}")
                     e(f"mov.b64 %%K0, {MONES};")
-                    e(f"mul.rn.f32x2 %%S, {self.T[i]}, %%K0;")
-                    e(f"mul.rn.f32x2 %%S, %%S, %%A{i};")
-                    e(f"mov.b64 {{%%s0, %%s1}}, %%U{i};")
-                    e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
-                    e("mov.b64 {%%v0, %%v1}, %%S;")
-                    for r in (0, 1):
-                        e(f"abs.f32 %%m, %%s{r};")
-                        e(f"setp.lt.f32 %%p, %%m, {self.THR};")
-                        e(f"selp.f32 %%c{r}, 0f00000000, %%c{r}, %%p;")
-                        e(f"selp.f32 %%v{r}, 0f00000000, %%v{r}, %%p;")
-                    r_, nv = ("%%PT", "%%PO") if lab == "PDIV" else ("%%PO", "%%PT")
-                    e(f"mov.b64 {r_}{i}, {{%%c0, %%c1}};")
-                    e(f"mov.b64 {nv}{i}, {{%%v0, %%v1}};")
-            elif lab == "PSQ":
-                # d sqrt|t| = sign(t) / (2 sqrt|t|) (t = 0 is handed back)
-                for i in range(p):
-                    self.rcp_pair(self.T[i], f"%%A{i}")
-                    e(f"mov.b64 %%K0, {kp('half')};")
-                    e(f"mul.rn.f32x2 %%A{i}, %%A{i}, %%K0;")
-                    e(f"mov.b64 {{%%s0, %%s1}}, %%TO{i};")
-                    e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
-                    for r in (0, 1):
-                        e(f"copysign.f32 %%c{r}, %%s{r}, %%c{r};")
-                    e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
-            elif lab == "PIV":
-                # d (1/t) = -v^2 (0 on the protected branch, where v = 0)
-                for i in range(p):
-                    e(f"mov.b64 %%K0, {MONES};")
-                    e(f"mul.rn.f32x2 %%S, {self.T[i]}, %%K0;")
-                    e(f"mul.rn.f32x2 %%PT{i}, %%S, {self.T[i]};")
-            elif lab == "PLG":
-                # d log|t| = 1/t, 0 where |t| < thr
-                for i in range(p):
-                    self.rcp_pair(f"%%TO{i}", f"%%A{i}")
-                    e(f"mov.b64 {{%%s0, %%s1}}, %%TO{i};")
-                    e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
-                    for r in (0, 1):
-                        e(f"abs.f32 %%m, %%s{r};")
-                        e(f"setp.lt.f32 %%p, %%m, {self.THR};")
-                        e(f"selp.f32 %%c{r}, 0f00000000, %%c{r}, %%p;")
-                    e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
-            elif lab == "PXP":
-                for i in range(p):
-                    e(f"mov.b64 %%PT{i}, {self.T[i]};")
-            elif lab == "PAB":
-                # sign(t): 1, -1, or 0 (at 0 and NaN)
-                for i in range(p):
-                    e(f"mov.b64 {{%%s0, %%s1}}, %%TO{i};")
-                    for r in (0, 1):
-                        e(f"setp.gt.f32 %%p, %%s{r}, 0f00000000;")
-                        e(f"selp.f32 %%c{r}, 0f3F800000, 0f00000000, %%p;")
-                        e(f"setp.lt.f32 %%p, %%s{r}, 0f00000000;")
-                        e(f"selp.f32 %%c{r}, 0fBF800000, %%c{r}, %%p;")
-                    e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
-            elif lab in ("PSIN", "PCOS"):
-                # d sin t = cos t; d cos t = -sin t (the value's range test
-                # already passed on these rows)
-                self.trig(src=lambda i: f"%%TO{i}", dst=lambda i: f"%%PT{i}",
-                          kind=1 if lab == "PSIN" else 0)
-                if lab == "PCOS":
-                    for i in range(p):
-                        e(f"mov.b64 %%K0, {MONES};")
-                        e(f"mul.rn.f32x2 %%PT{i}, %%PT{i}, %%K0;")
-            else:
-                raise ValueError(lab)
-            e("bra.uni TT%=;")
+                    e(f"mul.rn.f32x2 %%PT{i}, %%PT{i}, %%K0;")
+        else:
+            raise ValueError(lab)
 
     def tangent_tail(self):
         """dt[k] *= pt for k in [tlo, thi); dt[k] = (fresh ? 1 : dt[k]) * po
@@ -535,6 +536,99 @@ class Gen:
         self.label("TTE")
         e("mov.u32 %%ret, 0;")
         e("bra.uni N%=;")
+
+    # cheap bodies (no range test, a handful of instructions) end with a
+    # plain branch to the next word; in the gradient variant the others
+    # return through ret, and the marked words of the cheap ones run a copy
+    # of the body that goes on to its partial-derivative body directly
+    CHEAP = ("PX", "PXS", "PC", "PCS", "AS", "SS", "MS", "AX", "SX", "MX", "RX", "AC", "SC",
+             "MC", "RC", "AB", "NG")
+
+    @staticmethod
+    def stem(name):
+        col = int(name[-1]) if name[-1] in "01" and name not in ("PC",) else None
+        return (name[:-1] if col is not None else name), col
+
+    def body(self, name):
+        """the value body of one dispatch label; True when it ends with its
+        own branch (the divisions go on to the shared division body)"""
+        e, p, X = self.e, self.np, self.X
+        stem, col = self.stem(name)
+        if stem == "PX" or stem == "PXS":
+            if stem == "PXS":
+                self.spill()
+            for i in range(p):
+                e(f"mov.b64 {self.T[i]}, {X[col][i]};")
+        elif stem in ("PC", "PCS"):
+            if stem == "PCS":
+                self.spill()
+            self.cpair()
+            for i in range(p):
+                e(f"mov.b64 {self.T[i]}, %%C;")
+        elif stem in ("AS", "SS", "MS"):
+            self.slot_load()
+            op = dict(AS="add", SS="sub", MS="mul")[stem]
+            self.pairwise(op, lambda i: (self.T[i], f"%%U{i}"))
+        elif stem in ("AX", "SX", "MX"):
+            op = dict(AX="add", SX="sub", MX="mul")[stem]
+            self.pairwise(op, lambda i, c=col: (self.T[i], X[c][i]))
+        elif stem == "RX":
+            self.pairwise("sub", lambda i, c=col: (X[c][i], self.T[i]))
+        elif stem in ("AC", "SC", "MC"):
+            self.cpair()
+            op = dict(AC="add", SC="sub", MC="mul")[stem]
+            self.pairwise(op, lambda i: (self.T[i], "%%C"))
+        elif stem == "RC":
+            self.cpair()
+            self.pairwise("sub", lambda i: ("%%C", self.T[i]))
+        elif stem == "AB" or stem == "NG":
+            op = "abs" if stem == "AB" else "neg"
+            for i in range(p):
+                self.unpack(i, "%%v0", "%%v1")
+                e(f"{op}.f32 %%v0, %%v0;")
+                e(f"{op}.f32 %%v1, %%v1;")
+                self.pack(i, "%%v0", "%%v1")
+        elif stem == "DS":
+            # the divisor pairs into U, then the shared body
+            self.slot_load()
+            e("bra.uni DTU%=;")
+            return True
+        elif stem in ("DC", "DX"):
+            src = "%%C" if stem == "DC" else None
+            if stem == "DC":
+                self.cpair()
+            for i in range(p):
+                e(f"mov.b64 %%U{i}, {src or X[col][i]};")
+            e("bra.uni DTU%=;")
+            return True
+        elif stem in ("RDC", "RDX"):
+            # u / t: the range test on these operands first (a word
+            # handed back must leave the rows untouched), then the rows
+            # become the divisor and the operand the dividend, and the
+            # shared body divides (rare: 0.13 words per program of the
+            # Pagie-1 population)
+            if stem == "RDC":
+                self.cpair()
+            opnd = (lambda i: "%%C") if stem == "RDC" else (lambda i, c=col: X[c][i])
+            self.div_check(num=opnd, den=lambda i: self.T[i])
+            for i in range(p):
+                e(f"mov.b64 %%U{i}, {self.T[i]};")
+                e(f"mov.b64 {self.T[i]}, {opnd(i)};")
+            e("bra.uni DTUX%=;")
+            return True
+        elif stem == "SQ":
+            self.sqrt()
+        elif stem == "IV":
+            self.inv()
+        elif stem == "TRG":
+            self.trig()
+        elif stem == "LG":
+            self.log()
+        elif stem == "XP":
+            self.exp()
+        else:
+            raise ValueError(name)
+        return False
 
     # -- the loop -----------------------------------------------------------
     def table(self):
@@ -581,11 +675,17 @@ class Gen:
         e("T%=: .branchtargets " + ", ".join(f"{x}%=" for x in ent) + ";")
         if self.grad:
             part = self.partial_labels(ent)
-            e(".reg .b32 %%ret, %%mk, %%i2, %%w2, %%c2, %%lo, %%hi, %%da, %%de;")
+            e(".reg .b32 %%ret, %%mk, %%lo, %%hi, %%da, %%de;")
             e(f".reg .b64 %%TO<{p}>, %%PT<{p}>, %%PO<{p}>, %%A<{p}>;")
-            tm = ["MKS" if part[i] != "EX" else "EX" for i in range(64)]
-            e("TM%=: .branchtargets " + ", ".join(f"{x}%=" for x in tm) + ";")
-            e("TR%=: .branchtargets " + ", ".join(f"{x}%=" for x in ["N"] + part) + ";")
+            cheap = [self.stem(lab)[0] in self.CHEAP for lab in ent]
+            # a marked word's value body: the copy of a cheap body (its
+            # partial derivatives follow inline), else the shared one, which
+            # returns through ret into the partial-derivative body
+            tv = [("V" + lab if cheap[i] else lab) if part[i] != "EX" else "EX"
+                  for i, lab in enumerate(ent)]
+            e("TV%=: .branchtargets " + ", ".join(f"{x}%=" for x in tv) + ";")
+            tr = ["N"] + [("EX" if cheap[i] else part[i]) for i in range(64)]
+            e("TR%=: .branchtargets " + ", ".join(f"{x}%=" for x in tr) + ";")
             e("mov.u32 %%ret, 0;")
         self.label("N")
         e("ld.shared.v2.b32 {%%w, %%cb}, [%0];")
@@ -599,90 +699,26 @@ class Gen:
             if name == "MK":
                 self.marked_entry()
                 continue
-            col = int(name[-1]) if name[-1] in "01" and name not in ("PC",) else None
-            stem = name[:-1] if col is not None else name
-            if stem == "PX" or stem == "PXS":
-                if stem == "PXS":
-                    self.spill()
-                for i in range(p):
-                    e(f"mov.b64 {self.T[i]}, {X[col][i]};")
-            elif stem in ("PC", "PCS"):
-                if stem == "PCS":
-                    self.spill()
-                self.cpair()
-                for i in range(p):
-                    e(f"mov.b64 {self.T[i]}, %%C;")
-            elif stem in ("AS", "SS", "MS"):
-                self.slot_load()
-                op = dict(AS="add", SS="sub", MS="mul")[stem]
-                self.pairwise(op, lambda i: (self.T[i], f"%%U{i}"))
-            elif stem in ("AX", "SX", "MX"):
-                op = dict(AX="add", SX="sub", MX="mul")[stem]
-                self.pairwise(op, lambda i, c=col: (self.T[i], X[c][i]))
-            elif stem == "RX":
-                self.pairwise("sub", lambda i, c=col: (X[c][i], self.T[i]))
-            elif stem in ("AC", "SC", "MC"):
-                self.cpair()
-                op = dict(AC="add", SC="sub", MC="mul")[stem]
-                self.pairwise(op, lambda i: (self.T[i], "%%C"))
-            elif stem == "RC":
-                self.cpair()
-                self.pairwise("sub", lambda i: ("%%C", self.T[i]))
-            elif stem == "AB" or stem == "NG":
-                op = "abs" if stem == "AB" else "neg"
-                for i in range(p):
-                    self.unpack(i, "%%v0", "%%v1")
-                    e(f"{op}.f32 %%v0, %%v0;")
-                    e(f"{op}.f32 %%v1, %%v1;")
-                    self.pack(i, "%%v0", "%%v1")
-            elif stem == "DS":
-                # the divisor pairs into U, then the shared body
-                self.slot_load()
-                e("bra.uni DTU%=;")
+            if self.body(name):
                 continue
-            elif stem in ("DC", "DX"):
-                src = "%%C" if stem == "DC" else None
-                if stem == "DC":
-                    self.cpair()
-                for i in range(p):
-                    e(f"mov.b64 %%U{i}, {src or X[col][i]};")
-                e("bra.uni DTU%=;")
-                continue
-            elif stem in ("RDC", "RDX"):
-                # u / t: the range test on these operands first (a word
-                # handed back must leave the rows untouched), then the rows
-                # become the divisor and the operand the dividend, and the
-                # shared body divides (rare: 0.13 words per program of the
-                # Pagie-1 population)
-                if stem == "RDC":
-                    self.cpair()
-                opnd = (lambda i: "%%C") if stem == "RDC" else (lambda i, c=col: X[c][i])
-                self.div_check(num=opnd, den=lambda i: self.T[i])
-                for i in range(p):
-                    e(f"mov.b64 %%U{i}, {self.T[i]};")
-                    e(f"mov.b64 {self.T[i]}, {opnd(i)};")
-                e("bra.uni DTUX%=;")
-                continue
-            elif stem == "SQ":
-                self.sqrt()
-            elif stem == "IV":
-                self.inv()
-            elif stem == "TRG":
-                self.trig()
-            elif stem == "LG":
-                self.log()
-            elif stem == "XP":
-                self.exp()
+            if self.grad and self.stem(name)[0] in self.CHEAP:
+                e("bra.uni N%=;")
             else:
-                raise ValueError(name)
-            self.nxt()
+                self.nxt()
+        if self.grad:
+            for name in used:
+                if self.stem(name)[0] in self.CHEAP and self.PARTIAL.get(name, "EX") != "EX":
+                    self.label("V" + name)
+                    self.body(name)
+                    self.partial_code(self.PARTIAL[name])
+                    e("bra.uni TT%=;")
         if self.divs:
             # t = t / u with the protection, the divisor pairs in U
             self.label("DTU")
             self.div_body()
             self.nxt()
         if self.grad:
-            self.partial_bodies(part)
+            self.partial_bodies(sorted(set(tr[1:]) - {"EX"}))
             self.tangent_tail()
         self.label("EX")
         if self.grad:

@@ -438,10 +438,10 @@ cudaError_t launch_grad_t(const GradArgs &a, int sms, cudaStream_t st, int *occ_
     return cudaGetLastError();
 }
 
-// Four rows per lane.  Bucket 0 (at most kGradTan0 constants, compiled
-// depth <= 8): 8 warps, 7 stack slots and 4 tangent slots per row, 4
-// blocks per SM; bucket 1 (up to 16 constants): 16 tangent slots, 2
-// blocks; bucket 2 (deeper stacks): 4 warps, 19 slots, 3 blocks.
+// Four rows per lane.  Buckets 0-2 (compiled depth <= 8, 7 stack slots):
+// 8 warps with 4, 8 or 16 tangent slots per row, 4, 3 or 2 blocks per SM
+// (shared memory allows no more); bucket 3 (deeper stacks): 4 warps, 19
+// slots, 3 blocks.
 #define GP_GRAD_LAUNCH(W, S, K, M) \
     (xreg ? launch_grad_t<W, S, K, M, true>(a, sms, st, occ) \
           : launch_grad_t<W, S, K, M, false>(a, sms, st, occ))
@@ -449,7 +449,8 @@ cudaError_t launch_grad(const GradArgs &a, int sms, cudaStream_t st, int *occ) {
     const bool xreg = a.n_feat <= 2;
     switch (a.bucket) {
     case 0: return GP_GRAD_LAUNCH(8, kSmallDepth - 1, kGradTan0, 4);
-    case 1: return GP_GRAD_LAUNCH(8, kSmallDepth - 1, GP_MAX_CONSTS, 2);
+    case 1: return GP_GRAD_LAUNCH(8, kSmallDepth - 1, kGradTan1, 3);
+    case 2: return GP_GRAD_LAUNCH(8, kSmallDepth - 1, GP_MAX_CONSTS, 2);
     default: return GP_GRAD_LAUNCH(4, kDeepSlots, GP_MAX_CONSTS, 3);
     }
 }

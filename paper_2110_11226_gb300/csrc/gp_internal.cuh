@@ -122,14 +122,15 @@ __host__ __device__ inline int prog_class(int depth, int ext) {
 }
 
 // Buckets of the constant gradient, one launch each: the tangents of a
-// warp's rows take kGradTan0 (bucket 0) or GP_MAX_CONSTS (buckets 1, 2)
-// shared-memory slots per row, the value stack 7 (buckets 0, 1) or 19
-// (bucket 2).
-constexpr int kGradBuckets = 3;
-constexpr int kGradTan0 = 4;
+// warp's rows take kGradTan0 (bucket 0), kGradTan1 (bucket 1) or
+// GP_MAX_CONSTS (buckets 2, 3) shared-memory slots per row, the value
+// stack 7 (buckets 0-2) or 19 (bucket 3); fewer tangent slots leave room
+// for more resident warps.
+constexpr int kGradBuckets = 4;
+constexpr int kGradTan0 = 4, kGradTan1 = 8;
 __host__ __device__ inline int grad_bucket(int n_consts, int depth) {
-    if (depth > kSmallDepth) return 2;
-    return n_consts <= kGradTan0 ? 0 : 1;
+    if (depth > kSmallDepth) return 3;
+    return n_consts <= kGradTan0 ? 0 : (n_consts <= kGradTan1 ? 1 : 2);
 }
 // classes of the program order (evaluator classes or gradient buckets)
 constexpr int kOrderClasses = 5;
