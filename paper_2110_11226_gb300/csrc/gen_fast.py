@@ -392,6 +392,7 @@ class Gen:
         the loop does not run it (EX then hands back the marker)"""
         e = self.e
         e("mov.b32 %%mk, %%cb;")
+        e("bfe.u32 %%tl, %%w, 8, 2;")      # the marker's shape: its tangent tail
         e("ld.shared.v2.b32 {%%w, %%cb}, [%0];")
         e("add.u32 %0, %0, 8;")
         e("mov.b32 %%cf, %%cb;")
@@ -405,7 +406,7 @@ class Gen:
         for lab in labels:
             self.label(lab)
             self.partial_code(lab)
-            self.e("bra.uni TT%=;")
+            self.e("brx.idx.uni %%tl, TQ%=;")
 
     def partial_code(self, lab):
         e, p = self.e, self.np
@@ -534,6 +535,25 @@ class Gen:
         e("setp.lt.u32 %%p, %%da, %%de;")
         e("@%%p bra TTF%=;")
         self.label("TTE")
+        e("mov.u32 %%ret, 0;")
+        e("bra.uni N%=;")
+        # shape 1: dt[tlo] *= pt; shape 2: dt[olo] = po (fresh); the index
+        # clamped to the KT slots like the ranges above
+        self.label("TT1")
+        e("and.b32 %%lo, %%mk, 31;")
+        e(f"min.u32 %%lo, %%lo, {self.KT} - 1;")
+        e(f"mad.lo.u32 %%da, %%lo, 512, {self.DB};")
+        e("ld.shared.v2.b64 {%%A0, %%A1}, [%%da];")
+        for i in range(p):
+            e(f"mul.rn.f32x2 %%A{i}, %%A{i}, %%PT{i};")
+        e("st.shared.v2.b64 [%%da], {%%A0, %%A1};")
+        e("mov.u32 %%ret, 0;")
+        e("bra.uni N%=;")
+        self.label("TTF1")
+        e("bfe.u32 %%lo, %%mk, 10, 5;")
+        e(f"min.u32 %%lo, %%lo, {self.KT} - 1;")
+        e(f"mad.lo.u32 %%da, %%lo, 512, {self.DB};")
+        e("st.shared.v2.b64 [%%da], {%%PO0, %%PO1};")
         e("mov.u32 %%ret, 0;")
         e("bra.uni N%=;")
 
@@ -675,7 +695,8 @@ class Gen:
         e("T%=: .branchtargets " + ", ".join(f"{x}%=" for x in ent) + ";")
         if self.grad:
             part = self.partial_labels(ent)
-            e(".reg .b32 %%ret, %%mk, %%lo, %%hi, %%da, %%de;")
+            e(".reg .b32 %%ret, %%mk, %%tl, %%lo, %%hi, %%da, %%de;")
+            e("TQ%=: .branchtargets TT%=, TT1%=, TTF1%=, TT%=;")
             e(f".reg .b64 %%TO<{p}>, %%PT<{p}>, %%PO<{p}>, %%A<{p}>;")
             cheap = [self.stem(lab)[0] in self.CHEAP for lab in ent]
             # a marked word's value body: the copy of a cheap body (its
@@ -711,7 +732,7 @@ class Gen:
                     self.label("V" + name)
                     self.body(name)
                     self.partial_code(self.PARTIAL[name])
-                    e("bra.uni TT%=;")
+                    e("brx.idx.uni %%tl, TQ%=;")
         if self.divs:
             # t = t / u with the protection, the divisor pairs in U
             self.label("DTU")

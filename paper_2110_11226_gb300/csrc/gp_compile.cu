@@ -241,8 +241,11 @@ __global__ void __launch_bounds__(128) compile_kernel(CompileArgs a) {
         const uint32_t olo = j_other >= 0 ? cpre[j_other] : 0u;
         const uint32_t ohi = j_other >= 0 ? cpre[j_other + size[j_other]] : 0u;
         if (tlo == thi && olo == ohi) return;
-        out[n++] = make_uint2(kGradMark, tlo | (thi << 5) | (olo << 10) | (ohi << 15) |
-                                             ((fresh ? 1u : 0u) << 20));
+        // the two common shapes get tails of their own in the fast loop
+        const uint32_t shape = (thi == tlo + 1 && olo == ohi) ? 1u
+                             : (tlo == thi && ohi == olo + 1 && fresh) ? 2u : 0u;
+        out[n++] = make_uint2(kGradMark | (shape << 8),
+                              tlo | (thi << 5) | (olo << 10) | (ohi << 15) | ((fresh ? 1u : 0u) << 20));
     };
     sp = 0;
     for (int j = len - 1; j >= 0; --j) {

@@ -65,7 +65,9 @@ constexpr uint32_t kOpCol1 = 32;  // bit 5: a column read of column 1
 // combines its operands multiplies the tangents under each operand by the
 // word's partial derivative with respect to that operand, so at the end
 // dt[k] is d(program)/d(c_k).  Each word whose operands hold constants is
-// preceded by a marker word: x = kGradMark, y = the ranges
+// preceded by a marker word: x = kGradMark | shape << 8 (shape 1: one
+// constant under t and none under the other operand; 2: none under t and
+// one fresh constant; 0: anything else), y = the ranges
 //   bits 0-4 / 5-9    [tlo, thi): constants under the top operand t
 //   bits 10-14 / 15-19 [olo, ohi): constants under the other operand (the
 //                      popped slot, the inline terminal, or for a push of a

@@ -859,13 +859,14 @@ def _subset(nodes, off, idx):
                                          ("wide", 500_000)])
 def test_full_size_fitness_sampled(name, n_rows):
     """64 sampled programs of each full-size workload, in the bench's launch
-    configuration, against the FP64 oracle over every row (parity.py:
-    check_fitness_sampled)."""
+    configuration (the tunables gp_autotune picks for it), against the FP64
+    oracle over every row (parity.py: check_fitness_sampled)."""
     k = 64
     wl = synth.workload(name, n_rows=n_rows)
     d = wl.data
     pn, po, dX, dy, dw = put(wl.nodes, wl.offsets, d.X, d.y, d.w)
-    fit = gp.gp_evaluate(pn, po, dX, dy, dw, metric=wl.metric).cpu().numpy()
+    opts = gp.gp_autotune(pn, po, dX, dy, dw, metric=wl.metric)
+    fit = gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=wl.metric, opts=opts).cpu().numpy()
     assert np.isfinite(fit).mean() > 0.5
     idx = _sample(wl.offsets, k, 5)
     sn, so = _subset(wl.nodes, wl.offsets, idx)
