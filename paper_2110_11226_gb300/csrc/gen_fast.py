@@ -55,7 +55,7 @@ K = dict(inv_pi=0x3EA2F983, magic=0x4B400000, pi_hi=0x40490FDB, pi_mid=0xB3BBBD2
          e6=0x3AB57078, log2e=0x3FB8AA3B, exp_fast=0x42AE0000, one=0x3F800000,
          mhalf=0xBF000000, flt_max=0x7F7FFFFF, half=0x3F000000, mone=0xBF800000,
          inf=0x7F800000, two_m100=0x0D800000, two_126=0x7E800000, two_60=0x5D800000,
-         two_m60=0x21800000)
+         two_m60=0x21800000, exp_inf=0x42B20000, exp_zero=0xC2DC0000)
 NEG = 0x80000000
 
 
@@ -83,6 +83,8 @@ class Gen:
         self.DB, self.KT = f"%{3 * p + 6}", f"%{3 * p + 7}"
         self.slot_bytes = (rpt // 4) * 512
         self.lines = []
+        self.nsv = 0          # special-value paths emitted so far
+        self.deferred = []    # their blocks, emitted after the bodies
 
     # -- emission helpers -------------------------------------------------
     def e(self, s):
@@ -128,11 +130,18 @@ class Gen:
             a, b = srcs(i)
             self.e(f"{op}.rn.f32x2 {self.T[i]}, {a}, {b};")
 
-    # A warp-wide test of every row before any row changes: bra EX unless
-    # every |v| < hi (NaN fails) and, with lo, every |v| >= lo.  Each group
-    # is (hi, lo or None, vals) with vals(i) the pair register of rows 2i
-    # and 2i+1; the groups share one vote.
-    def range_check(self, hi, lo=None, vals=None, groups=None):
+    # A warp-wide test of every row before any row changes: unless every
+    # |v| < hi (NaN fails) and, with lo, every |v| >= lo, the warp leaves
+    # the fast path -- to EX, or with special (a callable emitting a per-row
+    # test that sets %%p on rows the body cannot take) to a second test
+    # that lets the special values through (NaN, inf, zero) and bails only
+    # on the rest.  Past that test the warp goes back into the body, or,
+    # with body, runs body (a copy of the computation that also gives the
+    # special rows the C++ functions' results) and ends there; the copy
+    # sits out of the hot path and keeps nothing live across it.
+    # Each group is (hi, lo or None, vals) with vals(i) the pair register
+    # of rows 2i and 2i+1; the groups share one vote.
+    def range_check(self, hi, lo=None, vals=None, groups=None, special=None, body=None):
         groups = groups or [(hi, lo, vals or (lambda i: self.T[i]))]
         self.e("setp.ne.u32 %%ps, 0, 0;")
         for hi, lo, vals in groups:
@@ -148,7 +157,50 @@ class Gen:
             if lo:
                 self.e(f"setp.lt.or.f32 %%ps, %%mn, {kf(lo)}, %%ps;")
         self.e("vote.sync.any.pred %%ps, %%ps, 0xffffffff;")
-        self.e("@%%ps bra EX%=;")
+        if special is None:
+            self.e("@%%ps bra EX%=;")
+            return None
+        k = self.nsv
+        self.nsv += 1
+        self.e(f"@%%ps bra SV{k}%=;")
+        self.label(f"SC{k}")
+
+        def block():
+            self.label(f"SV{k}")
+            self.e("setp.ne.u32 %%ps, 0, 0;")
+            special()
+            self.e("vote.sync.any.pred %%ps, %%ps, 0xffffffff;")
+            self.e("@%%ps bra EX%=;")
+            if body is None:
+                self.e(f"bra.uni SC{k}%=;")
+            else:
+                body()
+                self.nxt()
+        self.deferred.append(block)
+        return k
+
+    def fix_rows(self, i, rows):
+        """pair i of the rows after a computation whose input pair is in Y:
+        rows(s, v) per row (s the input, v the result)"""
+        self.unpack(i, "%%v0", "%%v1")
+        self.e("mov.b64 {%%s0, %%s1}, %%Y;")
+        for r in (0, 1):
+            rows(f"%%s{r}", f"%%v{r}")
+        self.pack(i, "%%v0", "%%v1")
+
+    def rows_test(self, vals, test):
+        """per row of vals: test(v) emits code setting %%p; %%ps |= %%p"""
+        for i in range(self.np):
+            self.e(f"mov.b64 {{%%v0, %%v1}}, {vals(i)};")
+            for v in ("%%v0", "%%v1"):
+                test(v)
+                self.e("or.pred %%ps, %%ps, %%p;")
+
+    def beyond(self, lo, v):
+        """%%p = lo <= |v| < inf (NaN and inf pass)"""
+        self.e(f"abs.f32 %%m, {v};")
+        self.e(f"setp.ge.f32 %%p, %%m, {kf(lo)};")
+        self.e(f"setp.lt.and.f32 %%p, %%m, {kf('inf')}, %%p;")
 
     # sin or cos of every row (the steps of sincos_fast): one body for
     # both, the kind (0 sin, 1 cos) from the dispatch index.  j = the
@@ -160,7 +212,8 @@ class Gen:
         static kind (0 sin, 1 cos) skips the test and the index"""
         src = src or (lambda i: self.T[i])
         if kind is None:
-            self.range_check("trig_fast")
+            self.range_check("trig_fast", special=lambda: self.rows_test(
+                lambda i: self.T[i], lambda v: self.beyond("trig_fast", v)))
             self.e(f"sub.u32 %%kd, %%i, {OPS['SIN']};")
             self.e("setp.ne.u32 %%p, %%kd, 0;")
             self.e("selp.b64 %%KM, 0xBF000000BF000000, 0x8000000080000000, %%p;")  # -kind/2
@@ -250,29 +303,53 @@ class Gen:
 
     # exp of every row when all |t| < 87 (exp_fast), else handed back
     def exp(self):
-        self.range_check("exp_fast")
+        # special: NaN goes through the steps (NaN); x >= 89 (inf too) is
+        # +inf and x <= -110 is +0, as expf gives them; only 87 <= |x| and
+        # -110 < x < 89 leave
+        def test(v):
+            self.e(f"abs.f32 %%m, {v};")
+            self.e(f"setp.ge.f32 %%p, %%m, {kf('exp_fast')};")
+            self.e(f"setp.lt.and.f32 %%p, {v}, {kf('exp_inf')}, %%p;")
+            self.e(f"setp.gt.and.f32 %%p, {v}, {kf('exp_zero')}, %%p;")
+
+        def fix(sv, v):
+            self.e(f"setp.ge.f32 %%p, {sv}, {kf('exp_inf')};")
+            self.e(f"selp.f32 {v}, {kf('inf')}, {v}, %%p;")
+            self.e(f"setp.le.f32 %%p, {sv}, {kf('exp_zero')};")
+            self.e(f"selp.f32 {v}, 0f00000000, {v}, %%p;")
+
+        def special_body():
+            for i in range(self.np):
+                self.e(f"mov.b64 %%Y, {self.T[i]};")
+                self.exp_pair(i)
+                self.fix_rows(i, fix)
+        self.range_check("exp_fast", special=lambda: self.rows_test(lambda i: self.T[i], test),
+                         body=special_body)
         for i in range(self.np):
-            t = self.T[i]
-            self.e(f"mov.b64 %%K0, {kp('log2e')};")
-            self.e(f"mov.b64 %%K1, {kp('magic')};")
-            self.e(f"fma.rn.f32x2 %%JM, {t}, %%K0, %%K1;")
-            self.e("sub.rn.f32x2 %%JJ, %%JM, %%K1;")
-            self.e(f"mov.b64 %%K0, {kp('ln2_hi', True)};")
-            self.e(f"fma.rn.f32x2 %%R, %%JJ, %%K0, {t};")
-            self.e(f"mov.b64 %%K0, {kp('ln2_lo', True)};")
-            self.e("fma.rn.f32x2 %%R, %%JJ, %%K0, %%R;")
-            self.e(f"mov.b64 %%K0, {kp('e6')};")
-            self.e(f"mov.b64 %%K1, {kp('e5')};")
-            self.e("fma.rn.f32x2 %%P, %%K0, %%R, %%K1;")
-            for c in ("e4", "e3", "e2", "e1", "one"):
-                self.e(f"mov.b64 %%K0, {kp(c)};")
-                self.e("fma.rn.f32x2 %%P, %%P, %%R, %%K0;")
-            self.unpack(i, "%%n0", "%%n1", "%%JM")
-            for r in (0, 1):
-                # 2^j: the low bits of the rounded sum are j, shifted into the exponent
-                self.e(f"mad.lo.u32 %%n{r}, %%n{r}, 8388608, 0x3F800000;")
-            self.e("mov.b64 %%S, {%%n0, %%n1};")
-            self.e(f"mul.rn.f32x2 {t}, %%P, %%S;")
+            self.exp_pair(i)
+
+    def exp_pair(self, i):
+        t = self.T[i]
+        self.e(f"mov.b64 %%K0, {kp('log2e')};")
+        self.e(f"mov.b64 %%K1, {kp('magic')};")
+        self.e(f"fma.rn.f32x2 %%JM, {t}, %%K0, %%K1;")
+        self.e("sub.rn.f32x2 %%JJ, %%JM, %%K1;")
+        self.e(f"mov.b64 %%K0, {kp('ln2_hi', True)};")
+        self.e(f"fma.rn.f32x2 %%R, %%JJ, %%K0, {t};")
+        self.e(f"mov.b64 %%K0, {kp('ln2_lo', True)};")
+        self.e("fma.rn.f32x2 %%R, %%JJ, %%K0, %%R;")
+        self.e(f"mov.b64 %%K0, {kp('e6')};")
+        self.e(f"mov.b64 %%K1, {kp('e5')};")
+        self.e("fma.rn.f32x2 %%P, %%K0, %%R, %%K1;")
+        for c in ("e4", "e3", "e2", "e1", "one"):
+            self.e(f"mov.b64 %%K0, {kp(c)};")
+            self.e("fma.rn.f32x2 %%P, %%P, %%R, %%K0;")
+        self.unpack(i, "%%n0", "%%n1", "%%JM")
+        for r in (0, 1):
+            # 2^j: the low bits of the rounded sum are j, shifted into the exponent
+            self.e(f"mad.lo.u32 %%n{r}, %%n{r}, 8388608, 0x3F800000;")
+        self.e("mov.b64 %%S, {%%n0, %%n1};")
+        self.e(f"mul.rn.f32x2 {t}, %%P, %%S;")
 
     # The IEEE reciprocal, square root and quotient, correctly rounded, from
     # the hardware estimates and Newton-Raphson steps with FMA (P. Markstein,
@@ -300,40 +377,91 @@ class Gen:
         self.e(f"fma.rn.f32x2 {dst}, %%P, %%Q, %%P;")     # e + e (1 - b e)
 
     def inv(self):
-        # |t| < thr ? 0 : 1 / t
-        self.range_check("two_126")
+        # |t| < thr ? 0 : 1 / t; special: NaN goes through the steps (NaN),
+        # +-inf gives +-0, as rcp.rn does; 2^126 <= |t| < inf leaves
+        def fix(sv, v):
+            self.e(f"abs.f32 %%m, {sv};")
+            self.e(f"setp.eq.f32 %%p, %%m, {kf('inf')};")
+            self.e(f"copysign.f32 %%q, {sv}, 0f00000000;")
+            self.e(f"selp.f32 {v}, %%q, {v}, %%p;")
+
+        def special_body():
+            for i in range(self.np):
+                self.e(f"mov.b64 %%Y, {self.T[i]};")
+                self.inv_pair(i)
+                self.fix_rows(i, fix)
+        self.range_check("two_126", body=special_body, special=lambda: self.rows_test(
+            lambda i: self.T[i], lambda v: self.beyond("two_126", v)))
         for i in range(self.np):
-            self.rcp_pair(self.T[i], f"%%U{i}")
-        for i in range(self.np):
-            self.unpack(i, "%%v0", "%%v1")
-            self.e(f"mov.b64 {{%%u0, %%u1}}, %%U{i};")
-            for v, u in (("%%v0", "%%u0"), ("%%v1", "%%u1")):
-                self.e(f"abs.f32 %%m, {v};")
-                self.e(f"setp.lt.f32 %%p, %%m, {self.THR};")
-                self.e(f"selp.f32 {v}, 0f00000000, {u}, %%p;")
-            self.pack(i, "%%v0", "%%v1")
+            self.inv_pair(i)
+
+    def inv_pair(self, i):
+        self.rcp_pair(self.T[i], f"%%U{i}")
+        self.unpack(i, "%%v0", "%%v1")
+        self.e(f"mov.b64 {{%%u0, %%u1}}, %%U{i};")
+        for v, u in (("%%v0", "%%u0"), ("%%v1", "%%u1")):
+            self.e(f"abs.f32 %%m, {v};")
+            self.e(f"setp.lt.f32 %%p, %%m, {self.THR};")
+            self.e(f"selp.f32 {v}, 0f00000000, {u}, %%p;")
+        self.pack(i, "%%v0", "%%v1")
 
     def sqrt(self):
-        # sqrt |t|
-        self.range_check("inf", lo="two_m100")
+        # sqrt |t|; special: NaN goes through the steps (NaN), |t| = 0 gives
+        # +0 and |t| = inf +inf, as sqrt.rn does; 0 < |t| < 2^-100 leaves
+        def test(v):
+            self.e(f"abs.f32 %%m, {v};")
+            self.e("setp.gt.f32 %%p, %%m, 0f00000000;")
+            self.e(f"setp.lt.and.f32 %%p, %%m, {kf('two_m100')}, %%p;")
+
+        def fix(sv, v):
+            self.e(f"abs.f32 %%m, {sv};")
+            self.e("setp.eq.f32 %%p, %%m, 0f00000000;")
+            self.e(f"setp.eq.or.f32 %%p, %%m, {kf('inf')}, %%p;")
+            self.e(f"selp.f32 {v}, %%m, {v}, %%p;")
+
+        def special_body():
+            for i in range(self.np):
+                self.e(f"mov.b64 %%Y, {self.T[i]};")
+                self.sqrt_pair(i)
+                self.fix_rows(i, fix)
+        self.range_check("inf", lo="two_m100", body=special_body,
+                         special=lambda: self.rows_test(lambda i: self.T[i], test))
         for i in range(self.np):
-            self.unpack(i, "%%v0", "%%v1")
-            self.e("abs.f32 %%v0, %%v0;")
-            self.e("abs.f32 %%v1, %%v1;")
-            self.e("rsqrt.approx.ftz.f32 %%u0, %%v0;")
-            self.e("rsqrt.approx.ftz.f32 %%u1, %%v1;")
-            self.e("mov.b64 %%F, {%%v0, %%v1};")            # x
-            self.e("mov.b64 %%P, {%%u0, %%u1};")            # e
-            self.e("mul.rn.f32x2 %%S, %%F, %%P;")           # g = x e
-            self.e(f"mov.b64 %%K0, {kp('half')};")
-            self.e("mul.rn.f32x2 %%Q, %%P, %%K0;")          # h = e / 2
-            self.e(f"mov.b64 %%K1, {kp('mone')};")
-            self.e("mul.rn.f32x2 %%R, %%S, %%K1;")          # -g
-            self.e("fma.rn.f32x2 %%R, %%R, %%S, %%F;")      # x - g g
-            self.e(f"fma.rn.f32x2 {self.T[i]}, %%R, %%Q, %%S;")
+            self.sqrt_pair(i)
+
+    def sqrt_pair(self, i):
+        self.unpack(i, "%%v0", "%%v1")
+        self.e("abs.f32 %%v0, %%v0;")
+        self.e("abs.f32 %%v1, %%v1;")
+        self.e("rsqrt.approx.ftz.f32 %%u0, %%v0;")
+        self.e("rsqrt.approx.ftz.f32 %%u1, %%v1;")
+        self.e("mov.b64 %%F, {%%v0, %%v1};")            # x
+        self.e("mov.b64 %%P, {%%u0, %%u1};")            # e
+        self.e("mul.rn.f32x2 %%S, %%F, %%P;")           # g = x e
+        self.e(f"mov.b64 %%K0, {kp('half')};")
+        self.e("mul.rn.f32x2 %%Q, %%P, %%K0;")          # h = e / 2
+        self.e(f"mov.b64 %%K1, {kp('mone')};")
+        self.e("mul.rn.f32x2 %%R, %%S, %%K1;")          # -g
+        self.e("fma.rn.f32x2 %%R, %%R, %%S, %%F;")      # x - g g
+        self.e(f"fma.rn.f32x2 {self.T[i]}, %%R, %%Q, %%S;")
 
     def div_check(self, num, den):
-        self.range_check(None, groups=[("two_60", None, den), ("two_60", "two_m60", num)])
+        # special: a row with a NaN operand goes through the steps (NaN, or
+        # 1 on the protected branch, as the C++ division gives); the others
+        # must be in range
+        def special():
+            for i in range(self.np):
+                self.e(f"mov.b64 {{%%v0, %%v1}}, {num(i)};")
+                self.e(f"mov.b64 {{%%u0, %%u1}}, {den(i)};")
+                for r in (0, 1):
+                    self.e(f"abs.f32 %%m, %%u{r};")
+                    self.e(f"setp.ge.f32 %%p, %%m, {kf('two_60')};")
+                    self.e(f"abs.f32 %%m, %%v{r};")
+                    self.e(f"setp.ge.or.f32 %%p, %%m, {kf('two_60')}, %%p;")
+                    self.e(f"setp.lt.or.f32 %%p, %%m, {kf('two_m60')}, %%p;")
+                    self.e("or.pred %%ps, %%ps, %%p;")
+        self.range_check(None, groups=[("two_60", None, den), ("two_60", "two_m60", num)],
+                         special=special)
 
     def div_body(self):
         """t = t / u for the divisor pairs in U, with the protection
@@ -442,7 +570,8 @@ class Gen:
                 e(f"mov.b64 {r_}{i}, {{%%c0, %%c1}};")
                 e(f"mov.b64 {nv}{i}, {{%%v0, %%v1}};")
         elif lab == "PSQ":
-            # d sqrt|t| = sign(t) / (2 sqrt|t|) (t = 0 is handed back)
+            # d sqrt|t| = sign(t) / (2 sqrt|t|); 0 at t = 0 (the protected
+            # convention) and at |t| = inf
             for i in range(p):
                 self.rcp_pair(self.T[i], f"%%A{i}")
                 e(f"mov.b64 %%K0, {kp('half')};")
@@ -451,6 +580,10 @@ class Gen:
                 e(f"mov.b64 {{%%c0, %%c1}}, %%A{i};")
                 for r in (0, 1):
                     e(f"copysign.f32 %%c{r}, %%s{r}, %%c{r};")
+                    e(f"abs.f32 %%m, %%s{r};")
+                    e("setp.eq.f32 %%p, %%m, 0f00000000;")
+                    e(f"setp.eq.or.f32 %%p, %%m, {kf('inf')}, %%p;")
+                    e(f"selp.f32 %%c{r}, 0f00000000, %%c{r}, %%p;")
                 e(f"mov.b64 %%PT{i}, {{%%c0, %%c1}};")
         elif lab == "PIV":
             # d (1/t) = -v^2 (0 on the protected branch, where v = 0)
@@ -692,6 +825,8 @@ class Gen:
         e(".reg .b32 %%w, %%cb, %%i, %%a, %%kd, %%n<2>, %%m<2>, %%k<2>;")
         e(".reg .f32 %%cf, %%q, %%m, %%mx, %%mn, %%v<2>, %%u<2>, %%s<2>, %%c<2>;")
         e(f".reg .b64 %%C, %%U<{p}>, %%K<2>, %%KM, %%JM, %%JJ, %%R, %%S, %%P, %%Q, %%F;")
+        if self.divs:
+            e(".reg .b64 %%Y;")
         e("T%=: .branchtargets " + ", ".join(f"{x}%=" for x in ent) + ";")
         if self.grad:
             part = self.partial_labels(ent)
@@ -741,6 +876,8 @@ class Gen:
         if self.grad:
             self.partial_bodies(sorted(set(tr[1:]) - {"EX"}))
             self.tangent_tail()
+        for block in self.deferred:
+            block()
         self.label("EX")
         if self.grad:
             # a marked word whose value body gave up (a range test): hand

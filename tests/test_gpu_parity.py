@@ -148,6 +148,66 @@ def test_constant_subtrees_fold_to_the_per_row_value():
     assert st.ok > 0.5 * st.rows, st
 
 
+def _edge_arguments():
+    """Arguments at and around every edge of the fast loop's paths: zero,
+    subnormals, the protection threshold, the square root's and the
+    division's range limits, exp's fast range (87), its overflow and
+    underflow ends (89, -110), the trigonometric range (65536), the
+    reciprocal's (2^126), huge values, infinities and NaN."""
+    v = [0.0, 1e-40, 2.0 ** -101, 2.0 ** -99, 2.0 ** -61, 2.0 ** -59, 0.000999, 0.001, 0.0011,
+         0.5, 1.0, 3.25, 86.9, 87.0, 88.0, 88.72, 88.73, 89.0, 100.0, 103.9, 104.0, 109.9,
+         110.0, 120.0, 65535.0, 65536.0, 70000.0, 2.0 ** 59, 2.0 ** 61, 2.0 ** 125, 2.0 ** 126,
+         2.0 ** 127, 3e38, np.inf]
+    v = np.array(v, np.float64)
+    return np.concatenate([v, -v, [np.nan]]).astype(np.float32)
+
+
+@pytest.mark.parametrize("rpt", [4, 8])
+def test_fast_loop_matches_the_folded_value_at_edge_arguments(rpt):
+    """Every operation the fast loop runs gives, on every edge argument, the
+    bits of the C++ function the pre-pass folds constants with (NaN where
+    it gives NaN): unary functions f(x0) on the rows against f(c) folded,
+    and the division both ways against c1 / c2 folded."""
+    V, C = synth.OP["var"], synth.OP["const"]
+    e = _edge_arguments()
+    n = len(e)
+    progs = []
+    unary = ("sqrt", "log", "exp", "sin", "cos", "inv", "abs", "neg")
+    for f in unary:
+        progs.append([(synth.OP[f], 0, 0.0), (V, 0, 0.0)])
+        progs += [[(synth.OP[f], 0, 0.0), (C, 0, float(c))] for c in e]
+    # div x0 x1 over the grid of edge pairs; the folded c1 / c2 for each
+    a, b = np.meshgrid(e, e, indexing="ij")
+    X = np.stack([a.ravel(), b.ravel()]).astype(np.float32)
+    progs.append([(synth.OP["div"], 0, 0.0), (V, 0, 0.0), (V, 1, 0.0)])
+    progs.append([(synth.OP["div"], 0, 0.0), (V, 0, 0.0), (C, 0, 0.75)])
+    progs.append([(synth.OP["div"], 0, 0.0), (C, 0, -2.5), (V, 1, 0.0)])
+    folded = [[(synth.OP["div"], 0, 0.0), (C, 0, float(x)), (C, 0, float(y))]
+              for x, y in zip(a.ravel(), b.ravel())]
+    folded += [[(synth.OP["div"], 0, 0.0), (C, 0, float(x)), (C, 0, 0.75)] for x in e]
+    folded += [[(synth.OP["div"], 0, 0.0), (C, 0, -2.5), (C, 0, float(y))] for y in e]
+    nodes, off = pack(progs + folded)
+    pn, po, dX, _, _ = put(nodes, off, X)
+    got = gp.gp_predict_ex(pn, po, dX, gp.make_opts(rows_per_thread=rpt)).cpu().numpy()
+
+    def same(x, y, what):
+        nan = np.isnan(y)
+        np.testing.assert_array_equal(np.isnan(x), nan, err_msg=what)
+        np.testing.assert_array_equal(x[~nan].view(np.uint32), y[~nan].view(np.uint32),
+                                      err_msg=what)
+
+    # X[0] holds the edge values on rows i * n (the grid's first column)
+    rows = np.arange(n) * n
+    for k, f in enumerate(unary):
+        base = k * (n + 1)
+        same(got[base, rows], got[base + 1:base + 1 + n, 0], f)
+    d0 = len(unary) * (n + 1)
+    fb = len(progs)
+    same(got[d0], got[fb:fb + n * n, 0], "div x0 x1")
+    same(got[d0 + 1, rows], got[fb + n * n:fb + n * n + n, 0], "div x0 0.75")
+    same(got[d0 + 2, :n], got[fb + n * n + n:fb + n * n + 2 * n, 0], "div -2.5 x1")
+
+
 def _special_rows(X, seed):
     """Overwrite a scattering of rows with values that reach the protected
     branches and the slow paths: zero, both sides of the threshold,
