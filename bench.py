@@ -70,6 +70,8 @@ def parse():
                     help="evaluator rows per thread (4, 8 or 16; 0: the library's default)")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the accumulator-error block (oracle on 16 sampled programs)")
+    ap.add_argument("--chunk-rows", type=int, default=0,
+                    help="rows per work item (0: the library's choice)")
     ap.add_argument("--long-edge", type=int, default=0,
                     help="length-bucket edge in compiled words (0: the library's choice)")
     ap.add_argument("--long-rows-per-thread", type=int, default=0)
@@ -496,7 +498,7 @@ def main():
     dflt_used.blocks_per_sm = 32
     dflt_used.long_edge = -1
     dflt_used.long_blocks_per_sm = 32
-    explicit = args.rows_per_thread or args.blocks_per_sm or args.long_edge
+    explicit = args.rows_per_thread or args.blocks_per_sm or args.long_edge or args.chunk_rows
     if not args.no_autotune and not explicit:
         t0 = time.perf_counter()
         tuned = gp.gp_autotune(pn, po, dX, dy, dw, metric=wl.metric)
@@ -509,7 +511,8 @@ def main():
     # sits between the two and the step runs eagerly
     opts = tuned if tuned is not None else gp.make_opts(
         rows_per_thread=args.rows_per_thread, blocks_per_sm=args.blocks_per_sm,
-        long_edge=args.long_edge, long_rows_per_thread=args.long_rows_per_thread)
+        chunk_rows=args.chunk_rows, long_edge=args.long_edge,
+        long_rows_per_thread=args.long_rows_per_thread)
     ws_buf = torch.empty(gp.gp_workspace_size(P, N, d.n_feat, opts), dtype=torch.uint8, device=dev)
     used = gp.gp_resolve_opts(P, N, d.n_feat, opts)
 

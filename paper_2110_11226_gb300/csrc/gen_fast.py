@@ -306,15 +306,10 @@ class Gen:
 
     # exp of every row when all |t| < 87 (exp_fast), else handed back
     def exp(self):
-        # special: NaN goes through the steps (NaN); x >= 89 (inf too) is
-        # +inf and x <= -110 is +0, as expf gives them; only 87 <= |x| and
-        # -110 < x < 89 leave
-        def test(v):
-            self.e(f"abs.f32 %%m, {v};")
-            self.e(f"setp.ge.f32 %%p, %%m, {kf('exp_fast')};")
-            self.e(f"setp.lt.and.f32 %%p, {v}, {kf('exp_inf')}, %%p;")
-            self.e(f"setp.gt.and.f32 %%p, {v}, {kf('exp_zero')}, %%p;")
-
+        # special: a warp with |x| >= 87 (or NaN) in any row runs a copy
+        # whose scaling by 2^j is two exact halves (exp_wide: subnormal
+        # results round once, large ones overflow), x >= 89 giving +inf and
+        # x <= -110 +0, as f_exp does; NaN gives NaN
         def fix(sv, v):
             self.e(f"setp.ge.f32 %%p, {sv}, {kf('exp_inf')};")
             self.e(f"selp.f32 {v}, {kf('inf')}, {v}, %%p;")
@@ -324,14 +319,13 @@ class Gen:
         def special_body():
             for i in range(self.np):
                 self.e(f"mov.b64 %%Y, {self.T[i]};")
-                self.exp_pair(i)
+                self.exp_pair(i, wide=True)
                 self.fix_rows(i, fix)
-        self.range_check("exp_fast", special=lambda: self.rows_test(lambda i: self.T[i], test),
-                         body=special_body)
+        self.range_check("exp_fast", special=lambda: None, body=special_body)
         for i in range(self.np):
             self.exp_pair(i)
 
-    def exp_pair(self, i):
+    def exp_pair(self, i, wide=False):
         t = self.T[i]
         self.e(f"mov.b64 %%K0, {kp('log2e')};")
         self.e(f"mov.b64 %%K1, {kp('magic')};")
@@ -348,11 +342,26 @@ class Gen:
             self.e(f"mov.b64 %%K0, {kp(c)};")
             self.e("fma.rn.f32x2 %%P, %%P, %%R, %%K0;")
         self.unpack(i, "%%n0", "%%n1", "%%JM")
+        if not wide:
+            for r in (0, 1):
+                # 2^j: the low bits of the rounded sum are j, shifted into the exponent
+                self.e(f"mad.lo.u32 %%n{r}, %%n{r}, 8388608, 0x3F800000;")
+            self.e("mov.b64 %%S, {%%n0, %%n1};")
+            self.e(f"mul.rn.f32x2 {t}, %%P, %%S;")
+            return
         for r in (0, 1):
-            # 2^j: the low bits of the rounded sum are j, shifted into the exponent
-            self.e(f"mad.lo.u32 %%n{r}, %%n{r}, 8388608, 0x3F800000;")
-        self.e("mov.b64 %%S, {%%n0, %%n1};")
+            # j = the sum's bits - the magic's; 2^(j >> 1) into n, the rest into m
+            self.e(f"sub.s32 %%n{r}, %%n{r}, {K['magic']};")
+            self.e(f"shr.s32 %%m{r}, %%n{r}, 1;")
+            self.e(f"sub.s32 %%n{r}, %%n{r}, %%m{r};")
+            self.e(f"add.s32 %%m{r}, %%m{r}, 127;")
+            self.e(f"shl.b32 %%m{r}, %%m{r}, 23;")
+            self.e(f"add.s32 %%n{r}, %%n{r}, 127;")
+            self.e(f"shl.b32 %%n{r}, %%n{r}, 23;")
+        self.e("mov.b64 %%S, {%%m0, %%m1};")
         self.e(f"mul.rn.f32x2 {t}, %%P, %%S;")
+        self.e("mov.b64 %%S, {%%n0, %%n1};")
+        self.e(f"mul.rn.f32x2 {t}, {t}, %%S;")
 
     # The IEEE reciprocal, square root and quotient, correctly rounded, from
     # the hardware estimates and Newton-Raphson steps with FMA (P. Markstein,
@@ -454,31 +463,46 @@ class Gen:
         self.e("fma.rn.f32x2 %%R, %%R, %%S, %%F;")      # x - g g
         self.e(f"fma.rn.f32x2 {self.T[i]}, %%R, %%Q, %%S;")
 
-    def div_check(self, num, den):
-        # special: a row with a NaN operand goes through the steps (NaN, or
-        # 1 on the protected branch, as the C++ division gives); the others
-        # must be in range
+    def div_check(self, num, den, pre=None):
+        """the division's range test; a special row -- a NaN operand, an
+        infinite one, a zero dividend -- is let through to a copy of the
+        division (pre: the reversed forms' swap first) that gives it the
+        IEEE quotient; finite operands out of range still leave"""
         def special():
             for i in range(self.np):
                 self.e(f"mov.b64 {{%%v0, %%v1}}, {num(i)};")
                 self.e(f"mov.b64 {{%%u0, %%u1}}, {den(i)};")
                 for r in (0, 1):
-                    self.e(f"abs.f32 %%m, %%u{r};")
-                    self.e(f"setp.ge.f32 %%p, %%m, {kf('two_60')};")
-                    self.e(f"abs.f32 %%m, %%v{r};")
-                    self.e(f"setp.ge.or.f32 %%p, %%m, {kf('two_60')}, %%p;")
-                    self.e(f"setp.lt.or.f32 %%p, %%m, {kf('two_m60')}, %%p;")
+                    self.beyond("two_60", f"%%u{r}")
                     self.e("or.pred %%ps, %%ps, %%p;")
+                    self.beyond("two_60", f"%%v{r}")
+                    self.e("or.pred %%ps, %%ps, %%p;")
+                    self.e(f"abs.f32 %%m, %%v{r};")
+                    self.e("setp.gt.f32 %%p, %%m, 0f00000000;")
+                    self.e(f"setp.lt.and.f32 %%p, %%m, {kf('two_m60')}, %%p;")
+                    self.e("or.pred %%ps, %%ps, %%p;")
+
+        def body():
+            if pre:
+                pre()
+            self.div_compute(fix=True)
         self.range_check(None, groups=[("two_60", None, den), ("two_60", "two_m60", num)],
-                         special=special)
+                         special=special, body=body)
 
     def div_body(self):
         """t = t / u for the divisor pairs in U, with the protection
         |divisor| < thr -> 1; DTUX: the same after the range test"""
+        self.div_check(lambda i: self.T[i], lambda i: f"%%U{i}")
+        self.label("DTUX")
+        self.div_compute()
+
+    def div_compute(self, fix=False):
+        """the rows (dividends) over U (divisors); with fix, a zero or
+        infinite dividend over a divisor that is not NaN gives dividend *
+        sign(divisor) and an infinite divisor dividend * (+-0), the IEEE
+        quotients the Newton steps miss"""
         num = lambda i: self.T[i]
         den = lambda i: f"%%U{i}"
-        self.div_check(num, den)
-        self.label("DTUX")
         for i in range(self.np):
             # y = 1 / b, q = a y, then q + (a - b q) y
             self.rcp_pair(den(i), "%%JJ")
@@ -489,6 +513,22 @@ class Gen:
             self.e("fma.rn.f32x2 %%JM, %%R, %%JJ, %%JM;")
             self.e(f"mov.b64 {{%%s0, %%s1}}, {den(i)};")
             self.e("mov.b64 {%%c0, %%c1}, %%JM;")
+            if fix:
+                self.e(f"mov.b64 {{%%u0, %%u1}}, {num(i)};")
+                for r in (0, 1):
+                    a, b, q = f"%%u{r}", f"%%s{r}", f"%%c{r}"
+                    self.e(f"abs.f32 %%m, {a};")
+                    self.e(f"setp.eq.f32 %%p, %%m, {kf('inf')};")
+                    self.e(f"setp.eq.or.f32 %%p, {a}, 0f00000000, %%p;")
+                    self.e(f"setp.num.and.f32 %%p, {b}, {b}, %%p;")   # a NaN divisor: NaN
+                    self.e(f"copysign.f32 %%q, {b}, 0f3F800000;")
+                    self.e(f"mul.rn.f32 %%q, {a}, %%q;")
+                    self.e(f"selp.f32 {q}, %%q, {q}, %%p;")
+                    self.e(f"abs.f32 %%m, {b};")
+                    self.e(f"setp.eq.f32 %%p, %%m, {kf('inf')};")
+                    self.e(f"copysign.f32 %%q, {b}, 0f00000000;")
+                    self.e(f"mul.rn.f32 %%q, {a}, %%q;")
+                    self.e(f"selp.f32 {q}, %%q, {q}, %%p;")
             for v, b, q in (("%%v0", "%%s0", "%%c0"), ("%%v1", "%%s1", "%%c1")):
                 self.e(f"abs.f32 %%m, {b};")
                 self.e(f"setp.lt.f32 %%p, %%m, {self.THR};")
@@ -772,10 +812,13 @@ class Gen:
             if stem == "RDC":
                 self.cpair()
             opnd = (lambda i: "%%C") if stem == "RDC" else (lambda i, c=col: X[c][i])
-            self.div_check(num=opnd, den=lambda i: self.T[i])
-            for i in range(p):
-                e(f"mov.b64 %%U{i}, {self.T[i]};")
-                e(f"mov.b64 {self.T[i]}, {opnd(i)};")
+
+            def swap():
+                for i in range(p):
+                    e(f"mov.b64 %%U{i}, {self.T[i]};")
+                    e(f"mov.b64 {self.T[i]}, {opnd(i)};")
+            self.div_check(num=opnd, den=lambda i: self.T[i], pre=swap)
+            swap()
             e("bra.uni DTUX%=;")
             return True
         elif stem == "SQ":

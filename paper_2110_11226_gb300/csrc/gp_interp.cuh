@@ -65,7 +65,9 @@ __device__ __forceinline__ float f_log(float a) {
     return b < kThr ? 0.0f : (b <= 3.40282347e38f ? l : b);
 }
 __device__ __forceinline__ float f_exp(float a) {
-    return fabsf(a) < kExpFast ? exp_fast(a) : expf(a);
+    if (fabsf(a) < kExpFast) return exp_fast(a);
+    if (a >= kExpInf) return __int_as_float(0x7f800000);
+    return a <= kExpZero ? 0.0f : exp_wide(a);  // NaN: NaN
 }
 __device__ __forceinline__ float f_abs(float a) { return fabsf(a); }
 __device__ __forceinline__ float f_neg(float a) { return -a; }

@@ -19,9 +19,10 @@
 // max(|a|, 0.001), so no zero, negative or subnormal argument reaches it.
 // exp: for |x| < 87, 2^j e^r with j the integer nearest x log2(e), the
 // Cody-Waite reduction r = x - j ln2 in two FMAs and a degree-6 polynomial
-// (coefficients from fit_exp.py: 1.04 ulp); other arguments go to CUDA's
-// expf.  The inline-PTX loop of the evaluator transcribes the same steps
-// and constants, so both give the same bits.
+// (coefficients from fit_exp.py: 1.04 ulp); beyond |x| = 87 the same
+// steps scale by 2^j in two exact halves (exp_wide), x >= 89 gives +inf
+// and x <= -110 gives +0.  The inline-PTX loop of the evaluator
+// transcribes the same steps and constants, so both give the same bits.
 #pragma once
 
 #include <cstdint>
@@ -108,6 +109,7 @@ constexpr float kExpE1 = 1.0f, kExpE2 = 0.4999999403953552f, kExpE3 = 0.16666421
                 kExpE6 = 0.001384272240102291f;
 constexpr float kLog2e = 1.4426950216293335f;
 constexpr float kExpFast = 87.0f;
+constexpr float kExpInf = 89.0f, kExpZero = -110.0f;  // e^x is +inf / +0 beyond
 static_assert(__builtin_bit_cast(uint32_t, kLogP0) == 0xBEFFFFFDu, "log constant");
 static_assert(__builtin_bit_cast(uint32_t, kLogP1) == 0x3EAAAB7Au, "log constant");
 static_assert(__builtin_bit_cast(uint32_t, kLogP2) == 0xBE80024Du, "log constant");
@@ -126,6 +128,8 @@ static_assert(__builtin_bit_cast(uint32_t, kExpE5) == 0x3C09371Cu, "exp constant
 static_assert(__builtin_bit_cast(uint32_t, kExpE6) == 0x3AB57078u, "exp constant");
 static_assert(__builtin_bit_cast(uint32_t, kLog2e) == 0x3FB8AA3Bu, "exp constant");
 static_assert(__builtin_bit_cast(uint32_t, kExpFast) == 0x42AE0000u, "exp constant");
+static_assert(__builtin_bit_cast(uint32_t, kExpInf) == 0x42B20000u, "exp constant");
+static_assert(__builtin_bit_cast(uint32_t, kExpZero) == 0xC2DC0000u, "exp constant");
 
 // log x for x >= 0.001 (finite; the caller selects inf and NaN itself)
 __device__ __forceinline__ float log_pos(float x) {
@@ -160,6 +164,28 @@ __device__ __forceinline__ float exp_fast(float x) {
     p = __fmaf_rn(p, r, 1.0f);
     const float s = __int_as_float((int32_t)(((uint32_t)__float_as_int(jm) << 23) + 0x3F800000u));
     return __fmul_rn(p, s);
+}
+
+// e^x over the whole float range: exp_fast's steps with 2^j applied as two
+// exact powers of two (2^(j >> 1), then the rest), so a product beyond the
+// normal range rounds once, to a subnormal or to inf; the same bits as
+// exp_fast where |x| < 87.  For -110 < x < 89 (j in [-159, 129], both
+// factors normal); NaN gives NaN.
+__device__ __forceinline__ float exp_wide(float x) {
+    const float jm = __fmaf_rn(x, kLog2e, kRoundMagic);
+    const float jf = __fsub_rn(jm, kRoundMagic);
+    float r = __fmaf_rn(jf, -kLn2Hi, x);
+    r = __fmaf_rn(jf, -kLn2Lo, r);
+    float p = __fmaf_rn(kExpE6, r, kExpE5);
+    p = __fmaf_rn(p, r, kExpE4);
+    p = __fmaf_rn(p, r, kExpE3);
+    p = __fmaf_rn(p, r, kExpE2);
+    p = __fmaf_rn(p, r, kExpE1);
+    p = __fmaf_rn(p, r, 1.0f);
+    const int32_t j = __float_as_int(jm) - __float_as_int(kRoundMagic);
+    const int32_t ja = j >> 1, jb = j - ja;
+    return __fmul_rn(__fmul_rn(p, __int_as_float((ja + 127) << 23)),
+                     __int_as_float((jb + 127) << 23));
 }
 
 // sin (kind 0) or cos (kind 1) of |x| < 65536: j = the integer nearest
