@@ -563,10 +563,14 @@ class Gen:
                 out.append(self.PARTIAL.get(lab, "EX"))
         return out
 
+    # partials that read the rows as they were before the word
+    NEEDS_TO = ("PMS", "PMC", "PMX0", "PMX1", "PAB", "PSQ", "PLG", "PSIN", "PCOS")
+
     def marked_entry(self):
         """the marked word is loaded and dispatched through TV: a copy of a
-        cheap body, a shared body (which returns through ret), or EX when
-        the loop does not run it (EX then hands back the marker)"""
+        cheap body, a stub into a shared body (which returns through ret),
+        or MKX when the loop does not run it (EX then hands back the
+        marker, as it does when ret is set)"""
         e = self.e
         e("mov.b32 %%mk, %%cb;")
         e("bfe.u32 %%tl, %%w, 8, 2;")      # the marker's shape: its tangent tail
@@ -574,10 +578,15 @@ class Gen:
         e("add.u32 %0, %0, 8;")
         e("mov.b32 %%cf, %%cb;")
         e("and.b32 %%i, %%w, 63;")
-        e("add.u32 %%ret, %%i, 1;")
-        for i in range(self.np):
-            e(f"mov.b64 %%TO{i}, {self.T[i]};")
         e("brx.idx.uni %%i, TV%=;")
+        self.label("MKX")
+        e("mov.u32 %%ret, 1;")
+        e("bra.uni EX%=;")
+
+    def save_rows(self, part):
+        if part in self.NEEDS_TO:
+            for i in range(self.np):
+                self.e(f"mov.b64 %%TO{i}, {self.T[i]};")
 
     def partial_bodies(self, labels):
         for lab in labels:
@@ -889,7 +898,7 @@ class Gen:
             # a marked word's value body: the copy of a cheap body (its
             # partial derivatives follow inline), else the shared one, which
             # returns through ret into the partial-derivative body
-            tv = [("V" + lab if cheap[i] else lab) if part[i] != "EX" else "EX"
+            tv = [("V" + lab if cheap[i] else "S" + lab) if part[i] != "EX" else "MKX"
                   for i, lab in enumerate(ent)]
             e("TV%=: .branchtargets " + ", ".join(f"{x}%=" for x in tv) + ";")
             tr = ["N"] + [("EX" if cheap[i] else part[i]) for i in range(64)]
@@ -917,6 +926,7 @@ class Gen:
             for name in used:
                 if self.stem(name)[0] in self.CHEAP and self.PARTIAL.get(name, "EX") != "EX":
                     self.label("V" + name)
+                    self.save_rows(self.PARTIAL[name])
                     self.body(name)
                     self.partial_code(self.PARTIAL[name])
                     e("brx.idx.uni %%tl, TQ%=;")
@@ -926,6 +936,16 @@ class Gen:
             self.div_body()
             self.nxt()
         if self.grad:
+            # stubs into the shared bodies: ret = the word's index + 1 (TR)
+            done = set()
+            for i, lab in enumerate(tv):
+                if not lab.startswith("S") or lab in done:
+                    continue
+                done.add(lab)
+                self.label(lab)
+                e("add.u32 %%ret, %%i, 1;")
+                self.save_rows(part[i])
+                e(f"bra.uni {lab[1:]}%=;")
             self.partial_bodies(sorted(set(tr[1:]) - {"EX"}))
             self.tangent_tail()
         for block in self.deferred:

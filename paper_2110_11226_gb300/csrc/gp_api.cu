@@ -743,6 +743,34 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, con
         ga.vec_ok = vec ? 1 : 0;
         GP_CUDA(launch_grad(ga, c->sms, st));
     }
+    // the programs without constants: their loss partials from the
+    // evaluator (no tangents; their gradient slots are 0)
+    {
+        EvalArgs ea{};
+        ea.code = W.code;
+        ea.code_stride = kGradCodeStride;
+        ea.meta = W.meta;
+        ea.order = W.order;
+        ea.class_count = W.class_count;
+        ea.cls = kClassShallow;
+        ea.qcls = kGradBuckets + 1;
+        ea.X = X;
+        ea.ld = n_rows;
+        ea.n_rows = n_rows;
+        ea.y = y;
+        ea.w = w;
+        ea.n_progs = n_progs;
+        ea.metric = metric;
+        ea.chunk_rows = chunk;
+        ea.n_chunks = n_chunks;
+        ea.counter = W.counters + kGradBuckets;
+        ea.part = W.part;
+        ea.dev_status = c->status;
+        ea.vec_ok = vec ? 1 : 0;
+        const int fmode = (n_feat <= 2) ? 2 : 0;
+        const int occ = eval_info(4, fmode, kClassShallow, kEvalBlockThreads, nullptr);
+        GP_CUDA(eval_launch(ea, 4, fmode, c->sms * std::max(occ, 1), kEvalBlockThreads, st));
+    }
     GradFinalizeArgs fa{W.part, W.gpart, n_chunks, n_progs, W.meta, W.sumw, metric,
                         out_grad, out_fitness};
     GP_CUDA(launch_grad_finalize(fa, st));

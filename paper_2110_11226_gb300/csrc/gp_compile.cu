@@ -333,7 +333,7 @@ cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st) {
 constexpr int kOrderBins = kOrderClasses * 256;
 
 __device__ __forceinline__ int order_class(const ProgMeta &m, int mode) {
-    return mode == 0 ? prog_class(m.depth, m.ext) : grad_bucket(m.n_consts, m.depth);
+    return mode == 0 ? prog_class(m.depth, m.ext) : grad_bucket(m.n_consts, m.depth, m.ext);
 }
 
 __global__ void __launch_bounds__(1024) order_kernel(const ProgMeta *meta, int n_progs,

@@ -128,10 +128,14 @@ __host__ __device__ inline int prog_class(int depth, int ext) {
 // GP_MAX_CONSTS (buckets 2, 3) shared-memory slots per row, the value
 // stack 7 (buckets 0-2) or 19 (bucket 3); fewer tangent slots leave room
 // for more resident warps.
+// Programs without constants (and without the extended functions, stack
+// depth <= 8) need no tangents: they form order class kGradBuckets and
+// run through the evaluator, which writes their loss partials.
 constexpr int kGradBuckets = 4;
 constexpr int kGradTan0 = 4, kGradTan1 = 8;
-__host__ __device__ inline int grad_bucket(int n_consts, int depth) {
+__host__ __device__ inline int grad_bucket(int n_consts, int depth, int ext) {
     if (depth > kSmallDepth) return 3;
+    if (n_consts == 0 && !ext) return kGradBuckets;
     return n_consts <= kGradTan0 ? 0 : (n_consts <= kGradTan1 ? 1 : 2);
 }
 // classes of the program order (evaluator classes or gradient buckets)
@@ -238,6 +242,11 @@ struct EvalArgs {
     double *mom;
     const float *shift;
     const double *ystat;
+    // 0: programs' words every kCodeStride entries; else this stride
+    int code_stride;
+    // 0: the programs of class cls; k + 1: those of order class k (the
+    // constant gradient's buckets: its constant-free programs)
+    int qcls;
 };
 // One launcher per (rows per thread, feature mode) instance; a.cls picks
 // the program class (stack slots, extended functions).  fmode 2: columns 0 and 1 held in

@@ -439,8 +439,10 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32,
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     float4 *stk = stack_all + (size_t)warp * NSLOT * (RPT / 4) * 32 + lane;
-    int cls_begin = (a.cls == 0) ? 0 : a.class_count[0] + (a.cls == 2 ? a.class_count[1] : 0);
-    int n_cls = a.class_count[a.cls];
+    const int qc = a.qcls ? a.qcls - 1 : a.cls;  // the span of the program order
+    int cls_begin = 0;
+    for (int b = 0; b < qc; ++b) cls_begin += a.class_count[b];
+    int n_cls = a.class_count[qc];
     if (a.sub == 1) {  // the long programs of class 0 (first in its order)
         n_cls = a.class_count[kOrderClasses];
     } else if (a.sub == 2) {  // the rest of class 0
@@ -484,9 +486,9 @@ __global__ void __launch_bounds__(eval_warps<RPT>() * 32,
         // the program, then OP_END through the buffer's last entry (the last
         // one stored apart: as a third pass of the loop it cost the kernel
         // 15 registers)
+        const uint2 *src = a.code + (size_t)p * (a.code_stride ? a.code_stride : kCodeStride);
         for (int i = threadIdx.x; i <= kCodeStride; i += kEvalBlock)
-            cbuf[i] = (i < m.n_ins) ? a.code[(size_t)p * kCodeStride + i]
-                                    : make_uint2(make_ins(OP_END, 0, 0), 0u);
+            cbuf[i] = (i < m.n_ins) ? src[i] : make_uint2(make_ins(OP_END, 0, 0), 0u);
         if (threadIdx.x == 0) cbuf[kCodeStride + 1] = make_uint2(make_ins(OP_END, 0, 0), 0u);
         __syncthreads();
 
