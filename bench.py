@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pagie_large")
-    ap.add_argument("--n-rows", type=int, default=1 << 24)
+    ap.add_argument("--n-rows", type=int, default=0,
+                    help="rows (0: the workload's own size; 16,777,216 for pagie_large)")
     ap.add_argument("--n-progs", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -98,7 +99,7 @@ def dist_info():
 
 def make_workload(args, rank):
     from paper_2110_11226_gb300 import synth
-    wl = synth.workload(args.workload, n_rows=args.n_rows, n_progs=args.n_progs or None)
+    wl = synth.workload(args.workload, n_rows=args.n_rows or None, n_progs=args.n_progs or None)
     if rank:
         # program shard of rank r: its own P programs, same data
         nodes, off = synth.ramped_half_and_half(len(wl.offsets) - 1, *_depths(args.workload),
@@ -214,18 +215,24 @@ def recorded_traffic(workload, opts_key):
     path = os.path.join(ROOT, "profiles", "eval_kernel_pagie1_traffic.md")
     if not os.path.exists(path):
         return None
-    vals = {}
+    vals, per_shape, shape = {}, {}, None
     with open(path) as fh:
         for line in fh:
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
-                vals[k.strip()] = v.strip().strip("`")
+                k, v = k.strip(), v.strip().strip("`")
+                vals[k] = v
+                # each launch shape's figure follows its own launch_shape line
+                if k == "launch_shape":
+                    shape = v
+                elif k == "dram_bytes_per_row" and shape is not None:
+                    per_shape[shape] = v
     if vals.get("kernel_sources_sha256_16") != kernel_hash() or vals.get("workload") != workload \
-            or vals.get("launch_shape") != opts_key:
+            or opts_key not in per_shape:
         return None
     try:
-        return float(vals["dram_bytes_per_row"])
-    except (KeyError, ValueError):
+        return float(per_shape[opts_key])
+    except ValueError:
         return None
 
 
@@ -410,8 +417,6 @@ def run_const_tune(args):
     import torch
     from paper_2110_11226_gb300 import gp
     args.workload = "const_tune"
-    if args.n_rows == 1 << 24:
-        args.n_rows = 0  # the workload's own 1M rows
     wl = make_workload(args, 0)
     d = wl.data
     P, N = len(wl.offsets) - 1, d.n_rows

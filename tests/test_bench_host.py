@@ -49,8 +49,15 @@ def test_recorded_traffic_is_keyed_by_the_hash(monkeypatch, tmp_path):
     assert bench.recorded_traffic("tabular", "8/32/8") is None
     # another launch shape reads the inputs another number of times
     assert bench.recorded_traffic("pagie_large", "4/0/0") is None
+    # several launch shapes, each figure after its own launch_shape line
+    prof.write_text(f"- workload: pagie_large\n- kernel_sources_sha256_16: {h}\n"
+                    f"- launch_shape: 4/0/0\n- dram_bytes_per_row: 12.5\n"
+                    f"- launch_shape: 8/32/8\n- dram_bytes_per_row: 12.75\n")
+    assert bench.recorded_traffic("pagie_large", "4/0/0") == 12.5
+    assert bench.recorded_traffic("pagie_large", "8/32/8") == 12.75
+    assert bench.recorded_traffic("pagie_large", "8/0/0") is None
     (csrc / "gp_compile.cu").write_text("int y;\n")
-    assert bench.recorded_traffic("pagie_large", "8/32/8") is None
+    assert bench.recorded_traffic("pagie_large", "4/0/0") is None
 
 
 def test_traffic_launch_shape_key():
