@@ -675,10 +675,10 @@ def main():
             "node_evals_per_s": value * (n_nodes / P),
             "finite_fitness_frac": fin,
             "clocks": clocks,
-            # per step: compile, order, weight sum (+1 with weights), three
+            # per step: compile, order, weight sum (+1 with weights), four
             # evaluator launches (program classes; +1 when the common class is
             # split by length), finalize, tournament
-            "gpu_launches": (8 + (d.w is not None) + (used.long_edge > 0)) * args.steps,
+            "gpu_launches": (9 + (d.w is not None) + (used.long_edge > 0)) * args.steps,
             "roofline": roof,
             "pipes": pipes}
 

@@ -128,7 +128,7 @@ enum gp_accum { GP_ACCUM_FP64 = 0, GP_ACCUM_KAHAN32 = 1 };
  * the autotuned one for this problem shape when gp_autotune has run,
  * otherwise a fixed default.
  * Length buckets: with long_edge > 0 the programs of the common class
- * (compiled stack of at most 8 values, no extended function) whose compiled
+ * (compiled stack of at most 7 values, no extended function) whose compiled
  * form is longer than long_edge words run in a launch of their own, with
  * long_rows_per_thread and long_blocks_per_sm (0: rows_per_thread and
  * blocks_per_sm), before the shorter ones; long_edge = -1 asks for no split
@@ -228,7 +228,7 @@ int gp_predict(const gp_node *progs, const int32_t *offsets, int n_progs,
 
 /* Predictions as gp_predict, with the evaluator's rows per thread taken
  * from opts (NULL: the defaults; only rows_per_thread is read, 4 or 8, and
- * it applies to the programs of the common class -- stack of at most 8
+ * it applies to the programs of the common class -- stack of at most 7
  * values, no extended function -- the others always run 4 rows per
  * thread).  Every prediction is the same bits whatever rows_per_thread
  * says: the per-row operations do not depend on how rows are grouped.

@@ -263,7 +263,7 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
         GP_CUDA(cudaEventRecord(tev.first, st));
     }
     // launches: class 0 (or, split by length, its long then its short
-    // programs), class 1, class 2
+    // programs), classes 1, 2 and 3
     for (int launch = split ? -1 : 0; launch < kNumClasses; ++launch) {
         const int cls = launch < 0 ? 0 : launch;
         EvalArgs ea{};
@@ -291,9 +291,9 @@ int run_evaluate(const gp_node *progs, const int32_t *offsets, int n_progs, cons
             ea.shift = W.shift;
             ea.ystat = W.ystat;
         }
-        // classes 1 and 2 keep 4 rows per thread (the 19-slot stack would
-        // otherwise leave room for one block per SM; class 2 is rare); the
-        // same chunk partition serves all three
+        // classes 1-3 keep 4 rows per thread (the 19-slot stack would
+        // otherwise leave room for one block per SM; classes 2 and 3 are
+        // rare); the same chunk partition serves all four
         const int rpt_long = (mom && pl.o.long_rows_per_thread == 16) ? 8 : pl.o.long_rows_per_thread;
         const int rpt_c = (cls == kClassShallow) ? (ea.sub == 1 ? rpt_long : rpt) : 4;
         const int want = ea.sub == 1 ? pl.o.long_blocks_per_sm : pl.o.blocks_per_sm;
@@ -752,7 +752,8 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, con
         ea.meta = W.meta;
         ea.order = W.order;
         ea.class_count = W.class_count;
-        ea.cls = kClassShallow;
+        // compiled stacks of up to kSmallDepth values: the 7-slot instance
+        ea.cls = kClassShallow8;
         ea.qcls = kGradBuckets + 1;
         ea.X = X;
         ea.ld = n_rows;
@@ -768,7 +769,7 @@ int gp_const_grad(const gp_node *progs, const int32_t *offsets, int n_progs, con
         ea.dev_status = c->status;
         ea.vec_ok = vec ? 1 : 0;
         const int fmode = (n_feat <= 2) ? 2 : 0;
-        const int occ = eval_info(4, fmode, kClassShallow, kEvalBlockThreads, nullptr);
+        const int occ = eval_info(4, fmode, kClassShallow8, kEvalBlockThreads, nullptr);
         GP_CUDA(eval_launch(ea, 4, fmode, c->sms * std::max(occ, 1), kEvalBlockThreads, st));
     }
     GradFinalizeArgs fa{W.part, W.gpart, n_chunks, n_progs, W.meta, W.sumw, metric,

@@ -323,7 +323,7 @@ cudaError_t launch_compile(const CompileArgs &a, cudaStream_t st) {
 }
 
 // Counting sort of program ids: key = class * 256 + (256 - n_ins), so the
-// classes follow one another (0, 1, 2) and, inside a class, longer programs
+// classes follow one another (0, 1, 2, 3) and, inside a class, longer programs
 // come first (longest-processing-time order for the dynamic work queue).
 // mode 0: the evaluator's classes (stack depth, extended functions); mode
 // 1: the gradient's buckets (constants, stack depth), whose programs with

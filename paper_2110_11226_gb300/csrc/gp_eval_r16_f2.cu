@@ -1,15 +1,16 @@
 // gp_eval_r16_f2.cu -- instance of the batched evaluator: 16 rows per thread
 // in blocks of 4 warps, feature mode 2 (columns 0 and 1 held in registers),
-// program class 0 only (classes 1 and 2 always run 4 rows per thread).
+// program class 0 only (6 stack slots; the other classes always run 4 rows
+// per thread).
 #include "gp_interp.cuh"
 
 namespace gpk {
 cudaError_t launch_eval_r16_f2(const EvalArgs &a, int grid, int block, cudaStream_t st) {
     if (a.cls != kClassShallow || a.mom) return cudaErrorInvalidValue;
-    return launch_eval_t<16, kSmallDepth - 1, 2, kEpiLoss, false>(a, grid, block, st);
+    return launch_eval_t<16, kShallowDepth - 1, 2, kEpiLoss, false>(a, grid, block, st);
 }
 int info_eval_r16_f2(int cls, int block, int *regs, bool moments) {
     if (cls != kClassShallow || moments) return 0;
-    return info_t<16, kSmallDepth - 1, 2, kEpiLoss, false>(block, regs);
+    return info_t<16, kShallowDepth - 1, 2, kEpiLoss, false>(block, regs);
 }
 }  // namespace gpk

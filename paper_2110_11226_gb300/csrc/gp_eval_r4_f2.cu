@@ -1,8 +1,9 @@
 // gp_eval_r4_f2.cu -- instances of the batched evaluator: 4 rows per
 // thread, feature mode 2 (columns 0 and 1 held in registers),
-// all three program classes (7 shared-memory stack slots without or with the
-// extended functions, 19 slots with every function), with the loss
-// epilogue or the moment epilogue of the correlation fitness.
+// all four program classes (6 shared-memory stack slots for class 0, 7 for
+// class 3 and for class 2 with the extended functions, 19 slots with every
+// function), with the loss epilogue or the moment epilogue of the
+// correlation fitness.
 #include "gp_interp.cuh"
 
 namespace gpk {
@@ -10,6 +11,8 @@ namespace {
 template <int EPI>
 cudaError_t launch_cls(const EvalArgs &a, int grid, int block, cudaStream_t st) {
     if (a.cls == kClassShallow)
+        return launch_eval_t<4, kShallowDepth - 1, 2, EPI, false>(a, grid, block, st);
+    if (a.cls == kClassShallow8)
         return launch_eval_t<4, kSmallDepth - 1, 2, EPI, false>(a, grid, block, st);
     if (a.cls == kClassShallowExt)
         return launch_eval_t<4, kSmallDepth - 1, 2, EPI, true>(a, grid, block, st);
@@ -17,7 +20,8 @@ cudaError_t launch_cls(const EvalArgs &a, int grid, int block, cudaStream_t st) 
 }
 template <int EPI>
 int info_cls(int cls, int block, int *regs) {
-    if (cls == kClassShallow) return info_t<4, kSmallDepth - 1, 2, EPI, false>(block, regs);
+    if (cls == kClassShallow) return info_t<4, kShallowDepth - 1, 2, EPI, false>(block, regs);
+    if (cls == kClassShallow8) return info_t<4, kSmallDepth - 1, 2, EPI, false>(block, regs);
     if (cls == kClassShallowExt) return info_t<4, kSmallDepth - 1, 2, EPI, true>(block, regs);
     return info_t<4, kDeepSlots, 2, EPI, true>(block, regs);
 }

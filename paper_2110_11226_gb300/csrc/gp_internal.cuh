@@ -111,16 +111,22 @@ struct ProgMeta {
     int32_t n_consts;  // CONST nodes
 };
 
-// Program classes, one evaluator instance each.  Programs whose compiled
-// stack fits kSmallDepth run with a 7-slot shared-memory stack (more blocks
-// per SM): class 0 without the extended functions, class 2 with them (their
-// dispatch entries would slow class 0 down); deeper programs run in class 1
-// (19 slots, every function).
+// Program classes, one evaluator instance each.  Programs without the
+// extended functions whose compiled stack fits kShallowDepth form class 0,
+// the common one: a 6-slot shared-memory stack, so that at 8 rows per
+// thread 4 blocks of 8 warps fit per SM (a 7-slot stack fits 3).  Those of
+// depth kSmallDepth form class 3 (7 slots, 4 rows per thread); programs
+// with the extended functions and a stack of at most kSmallDepth, class 2
+// (7 slots; their dispatch entries would slow class 0 down); deeper
+// programs, class 1 (19 slots, every function).
 constexpr int kSmallDepth = 8;     // 7 stack slots + t
-constexpr int kNumClasses = 3;
-constexpr int kClassShallow = 0, kClassDeep = 1, kClassShallowExt = 2;
+constexpr int kShallowDepth = 7;   // 6 stack slots + t
+constexpr int kNumClasses = 4;
+constexpr int kClassShallow = 0, kClassDeep = 1, kClassShallowExt = 2, kClassShallow8 = 3;
 __host__ __device__ inline int prog_class(int depth, int ext) {
-    return depth > kSmallDepth ? kClassDeep : (ext ? kClassShallowExt : kClassShallow);
+    if (depth > kSmallDepth) return kClassDeep;
+    if (ext) return kClassShallowExt;
+    return depth > kShallowDepth ? kClassShallow8 : kClassShallow;
 }
 
 // Buckets of the constant gradient, one launch each: the tangents of a

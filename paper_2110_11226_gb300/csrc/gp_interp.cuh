@@ -414,9 +414,10 @@ constexpr size_t eval_smem_bytes() {
 }
 
 // epilogues: the weighted loss sum, the predictions, or the moment sums
-// of the correlation fitness.  At 8 rows per thread every epilogue asks for
-// 3 resident blocks (at most 80 registers; left alone the loss epilogue
-// took 81 and fit 2).  At 4 rows the moment epilogue asks for 5 (at most 48
+// of the correlation fitness.  At 8 rows per thread the loss and store
+// epilogues ask for 4 resident blocks (at most 64 registers, with the
+// 6-slot stack of class 0: 295 against 312 ms at 3 blocks on Pagie-1 16M
+// x 4096), the moment epilogue for 3 (at most 85 registers).  At 4 rows the moment epilogue asks for 5 (at most 48
 // registers, a few spilled words: 4% faster than 4 blocks at 59 registers
 // on Pagie-1 16M x 4096); the others are left alone (46 registers: 5 fit),
 // because asking for 5 blocks there changed their schedule and cost 7%.
@@ -424,7 +425,8 @@ constexpr int kEpiLoss = 0, kEpiPred = 1, kEpiMom = 2;
 
 template <int RPT, int NSLOT, int FMODE, int EPI, bool EXT>
 __global__ void __launch_bounds__(eval_warps<RPT>() * 32,
-                                  RPT == 8 ? 3 : (EPI == kEpiMom && RPT == 4 ? 5 : 0))
+                                  RPT == 8 ? (EPI == kEpiMom ? 3 : 4)
+                                           : (EPI == kEpiMom && RPT == 4 ? 5 : 0))
     eval_kernel(const EvalArgs a) {
     constexpr bool PRED = EPI == kEpiPred;
     constexpr bool MOM = EPI == kEpiMom;

@@ -274,15 +274,16 @@ def test_deep_and_long_programs():
 
 def _class_mix(n_feat, seed):
     """Programs for each evaluator class: the usual set with a compiled stack
-    of at most 8 (class 0), the extended set likewise (class 2) and left
-    spines whose right operands are subtrees, which keep d + 1 values on the
-    stack, over both sets (class 1)."""
+    of at most 7 (class 0), the extended set with at most 8 (class 2), and
+    left spines whose right operands are subtrees, which keep d + 1 values on
+    the stack, over both sets: d = 6 and 7 at the edges of classes 0 and 3
+    (the usual set at exactly 8) and class 2, deeper ones in class 1."""
     V, Cn = synth.OP["var"], synth.OP["const"]
     usual = synth.unpack(*synth.ramped_half_and_half(150, 2, 6, synth.FULL_SET, n_feat, seed=seed))
     ext = synth.unpack(*synth.ramped_half_and_half(150, 2, 6, synth.EXTENDED_SET, n_feat,
                                                    seed=seed + 1))
     deep = []
-    for d in (9, 12, 19):
+    for d in (6, 7, 9, 12, 19):
         deep.append([(synth.OP["max"], 0, 0.0)] * d + [(V, 1 % n_feat, 0.0)] +
                     [(synth.OP["tanh"], 0, 0.0), (V, 0, 0.0)] * d)
         deep.append([(synth.OP["add"], 0, 0.0)] * d + [(V, 1 % n_feat, 0.0)] +
@@ -295,9 +296,10 @@ def _class_mix(n_feat, seed):
 @pytest.mark.parametrize("n_feat", [2, 9])
 @pytest.mark.parametrize("metric", ["rmse", "pearson"])
 def test_fitness_in_every_program_class(n_feat, metric):
-    """One population, interleaved, whose programs fall into all three
-    evaluator classes (7-slot stack without and with the extended functions,
-    19-slot stack): every fitness matches the oracle's, and equals, bit for
+    """One population, interleaved, whose programs fall into all four
+    evaluator classes (6-slot stack, 7-slot stack without and with the
+    extended functions, 19-slot stack): at 4 and at 8 rows per thread for
+    the common class, every fitness matches the oracle's, and equals, bit for
     bit, the fitness of the same programs evaluated one group at a time with
     the same row chunks (each class reads its own span of the program
     order)."""
@@ -316,21 +318,23 @@ def test_fitness_in_every_program_class(n_feat, metric):
     progs = [progs[i] for i in perm]
     where = [where[i] for i in perm]
     nodes, off = pack(progs)
-    opts = gp.make_opts(chunk_rows=2048)
     pn, po, dX, dy, dw = put(nodes, off, X, y, w)
-    fit = gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=metric, opts=opts).cpu().numpy()
-    if metric == "pearson":
-        st, _ = check_pearson(fit, nodes, off, X, y, w)
-    else:
-        st, _ = check_fitness(fit, nodes, off, X, y, w, metric)
-    assert st.flagged < 0.3 * st.programs, st
-    for g, grp in enumerate(groups):
-        gn, go = pack(grp)
-        gpn, gpo = gp.nodes_to_device(gn), dev(go.astype(np.int32))
-        alone = gp.gp_evaluate_ex(gpn, gpo, dX, dy, dw, metric=metric, opts=opts).cpu().numpy()
-        mixed = np.array([fit[k] for k in range(len(progs)) if where[k][0] == g])
-        idx = [where[k][1] for k in range(len(progs)) if where[k][0] == g]
-        np.testing.assert_array_equal(mixed.view(np.uint32), alone[idx].view(np.uint32))
+    for rpt in (4, 8):
+        opts = gp.make_opts(rows_per_thread=rpt, chunk_rows=2048)
+        fit = gp.gp_evaluate_ex(pn, po, dX, dy, dw, metric=metric, opts=opts).cpu().numpy()
+        if metric == "pearson":
+            st, _ = check_pearson(fit, nodes, off, X, y, w)
+        else:
+            st, _ = check_fitness(fit, nodes, off, X, y, w, metric)
+        assert st.flagged < 0.3 * st.programs, st
+        for g, grp in enumerate(groups):
+            gn, go = pack(grp)
+            gpn, gpo = gp.nodes_to_device(gn), dev(go.astype(np.int32))
+            alone = gp.gp_evaluate_ex(gpn, gpo, dX, dy, dw, metric=metric,
+                                      opts=opts).cpu().numpy()
+            mixed = np.array([fit[k] for k in range(len(progs)) if where[k][0] == g])
+            idx = [where[k][1] for k in range(len(progs)) if where[k][0] == g]
+            np.testing.assert_array_equal(mixed.view(np.uint32), alone[idx].view(np.uint32))
 
 
 # --------------------------------------------------------------------------
