@@ -137,7 +137,7 @@ enum gp_accum { GP_ACCUM_FP64 = 0, GP_ACCUM_KAHAN32 = 1 };
  * same rows per thread and the same chunk_rows (fixed reduction partition);
  * blocks_per_sm and the bucket it lands in never change it. */
 typedef struct gp_eval_opts {
-    int rows_per_thread;       /* 4, 8 or 16 (default 4)                      */
+    int rows_per_thread;       /* 4, 8 or 16 (default 8)                      */
     int chunk_rows;            /* rows per work item, multiple of 256         */
     int blocks_per_sm;         /* resident blocks per SM of the persistent grid */
     int accum;                 /* gp_accum                                    */

@@ -144,7 +144,7 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // moment work on one or two chunks; the L2 holds 129 MB)
 constexpr int64_t kChunkL2Bytes = 48ll << 20;
 
-int64_t default_chunk(int n_progs, int64_t n_rows, int n_feat, int sms) {
+int64_t default_chunk(int n_progs, int64_t n_rows, int n_feat, int sms, int64_t pass_rows = 1024) {
     // enough items for dynamic balancing (about 16 per resident warp),
     // chunks of at most 16K rows (measured on Pagie-1 x 4096 programs at
     // 1M and 16M rows: 16K-row chunks beat 64K by 4%, 8K and 32K by 1%),
@@ -154,10 +154,10 @@ int64_t default_chunk(int n_progs, int64_t n_rows, int n_feat, int sms) {
     int64_t c = (int64_t)((double)n_rows * (double)n_progs / items_wanted);
     c = std::min<int64_t>(c, 16384);
     c = std::min<int64_t>(c, kChunkL2Bytes / (4 * ((int64_t)n_feat + 2)));
-    // whole passes of a block (8 warps x 32 lanes x 4 rows): a partial last
-    // pass idles warps (measured on 500K x 2000: 6400-row chunks 5% slower
-    // than 6144)
-    c = std::max<int64_t>(c / 1024 * 1024, 1024);
+    // whole passes of a block (8 warps x 32 lanes x 4 rows, or 8 rows:
+    // pass_rows): a partial last pass idles warps (measured on 500K x 2000:
+    // 6400-row chunks 5% slower than 6144)
+    c = std::max<int64_t>(c / pass_rows * pass_rows, pass_rows);
     return std::min<int64_t>(c, round_up(n_rows, 256));
 }
 
@@ -183,12 +183,16 @@ int resolve_opts(const gp_eval_opts *in, int n_progs, int64_t n_rows, int n_feat
     // length buckets: none unless asked for or tuned
     if (o.long_edge == 0) o.long_edge = -1;
     if (o.long_edge != -1 && (o.long_edge < 1 || o.long_edge > 255)) return GP_ERR_ARG;
-    // 4 rows per thread: 48 registers, 5 blocks (40 warps) per SM, measured
-    // 7% faster than 8 rows (79 registers, 3 blocks) on Pagie-1 x 4096
-    if (o.rows_per_thread == 0) o.rows_per_thread = 4;
+    // 8 rows per thread: 64 registers, 4 blocks (32 warps) per SM, measured
+    // 5% faster than 4 rows (48 registers, 5 blocks) on Pagie-1 16M x 4096
+    // with RMSE, 0.5% with Pearson; the autotuner picks it on every
+    // benchmark workload
+    if (o.rows_per_thread == 0) o.rows_per_thread = 8;
     if (o.rows_per_thread != 4 && o.rows_per_thread != 8 && o.rows_per_thread != 16)
         return GP_ERR_ARG;
-    if (o.chunk_rows == 0) o.chunk_rows = (int)default_chunk(n_progs, n_rows, n_feat, c->sms);
+    if (o.chunk_rows == 0)
+        o.chunk_rows = (int)default_chunk(n_progs, n_rows, n_feat, c->sms,
+                                          o.rows_per_thread == 4 ? 1024 : 2048);
     if (o.chunk_rows < 256 || o.chunk_rows % 256 != 0) return GP_ERR_ARG;
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 32) return GP_ERR_ARG;
     if (o.accum != GP_ACCUM_FP64 && o.accum != GP_ACCUM_KAHAN32) return GP_ERR_ARG;
