@@ -169,7 +169,8 @@ constexpr bool kBallotPeers = true;
 // that neighbouring threads store to neighbouring addresses.  Padding
 // beyond a ragged tile's end takes digit 255 and, being last in key order,
 // sorted positions >= the tile length, which are not written.  Pass 0
-// reads float values and produces the row index as the payload.  Two
+// reads float values and produces the payload: the row index, or, when
+// vals is given, vals[row] (a per-row table shared by the segments).  Two
 // blocks per SM (64 registers); three, at 40 registers with spills, ran
 // the rank fitness 3% slower.
 template <bool FROM_FLOAT>
@@ -198,7 +199,8 @@ __global__ void __launch_bounds__(kScatThreads, 2) scatter_kernel(
         const int i = warp * (kScatItems * 32) + r * 32 + lane;
         const bool in = i < tl;
         kk[r] = in ? load_key<FROM_FLOAT>(src, so + t0 + i) : 0xffffffffu;
-        vv[r] = FROM_FLOAT ? (uint32_t)(t0 + i) : (in ? vals[so + t0 + i] : 0u);
+        if (FROM_FLOAT) vv[r] = vals ? (in ? vals[t0 + i] : 0u) : (uint32_t)(t0 + i);
+        else vv[r] = in ? vals[so + t0 + i] : 0u;
     }
     // global position of this tile's first item of digit t: the digit's
     // start in the segment plus the same digit in earlier tiles
@@ -309,13 +311,15 @@ __global__ void __launch_bounds__(256) edges_kernel(const uint32_t *__restrict__
 // constant program, and sums without the cancellation of uncentred squares.
 // mode 0 (the target): r2[row] = rank, and part = (sum w, sum w b,
 // sum w b^2) of the tile; mode 1 (programs): part = (sum w a, sum w a^2,
-// sum w a b), b = the target's centred rank of the row.  Unweighted and
+// sum w a b), b = the target's centred rank of the row, read from r2y by
+// the row in vals or, with vals_are_ranks (unweighted rows), carried in
+// vals itself by the sort.  Unweighted and
 // with n <= 2^29 a thread's sums are exact 64-bit integers; otherwise FP64.
 // One FP64 triple per (segment, tile), added in a fixed order.
 __global__ void __launch_bounds__(kTileThreads) rank_kernel(
     const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n, int n_tiles,
     int mode, const int2 *__restrict__ edge, uint32_t *r2, const uint32_t *__restrict__ r2y,
-    const float *__restrict__ w, double *part) {
+    const float *__restrict__ w, double *part, int vals_are_ranks) {
     constexpr int kSegs = kTile / 32;  // 32-position segments of the tile
     __shared__ uint32_t sk[kTile];
     __shared__ int16_t sfirst[kTile], slast[kTile];
@@ -351,7 +355,7 @@ __global__ void __launch_bounds__(kTileThreads) rank_kernel(
 #pragma unroll
     for (int it = 0; it < kTileItems; ++it) {
         const int q = it * kTileThreads + t;
-        rb[it] = (mode == 1 && q < tl) ? r2y[rows[it]] : 0u;
+        rb[it] = (mode == 1 && q < tl) ? (vals_are_ranks ? rows[it] : r2y[rows[it]]) : 0u;
     }
     __syncthreads();
     // tie groups inside the tile: the warp's 32 positions q = it * 256 + t
@@ -506,11 +510,12 @@ __global__ void __launch_bounds__(256) spearman_final_kernel(
 }
 
 // Sorts each of n_seg segments of n float values into keys (order-preserving
-// integers) with the row index as payload; the result is in keys/vals.
+// integers) with the row index as payload, or payload[row] when a per-row
+// table is given; the result is in keys/vals.
 // hist holds n_seg * 256 * n_tiles counts, tot n_seg * 256.
 cudaError_t radix_sort_values(const float *v, uint32_t *keys, uint32_t *vals, uint32_t *keys2,
                               uint32_t *vals2, int n_seg, int64_t n, int32_t *hist, int32_t *tot,
-                              uint32_t *nan_flag, cudaStream_t st) {
+                              uint32_t *nan_flag, const uint32_t *payload, cudaStream_t st) {
     const int n_tiles = (int)((n + kSortTile - 1) / kSortTile);
     const dim3 grid(n_tiles, n_seg);
     const int scan_rows = n_seg * kBins;
@@ -529,7 +534,7 @@ cudaError_t radix_sort_values(const float *v, uint32_t *keys, uint32_t *vals, ui
         }
         tile_scan_kernel<<<scan_blocks, 256, 0, st>>>(hist, tot, scan_rows, n_tiles);
         if (pass == 0) {
-            scatter_kernel<true><<<grid, kScatThreads, 0, st>>>(v, nullptr, n, n_tiles, shift, hist,
+            scatter_kernel<true><<<grid, kScatThreads, 0, st>>>(v, payload, n, n_tiles, shift, hist,
                                                                 tot, ko, vo);
         } else {
             scatter_kernel<false><<<grid, kScatThreads, 0, st>>>(ki, vi, n, n_tiles, shift, hist,
@@ -586,11 +591,12 @@ cudaError_t target_ranks(const float *y, const float *w, int64_t n, void *scratc
     const RankScratch r = carve_rank(scratch, 1, n);
     cudaError_t e = cudaMemsetAsync(r.nan_flag, 0, 4, st);
     if (e != cudaSuccess) return e;
-    e = radix_sort_values(y, r.keys, r.vals, r.keys2, r.vals2, 1, n, r.hist, r.tot, r.nan_flag, st);
+    e = radix_sort_values(y, r.keys, r.vals, r.keys2, r.vals2, 1, n, r.hist, r.tot, r.nan_flag,
+                          nullptr, st);
     if (e != cudaSuccess) return e;
     edges_kernel<<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(r.keys, n, (int)n_tiles, 1, r.edge);
     rank_kernel<<<dim3((unsigned)n_tiles, 1), kTileThreads, 0, st>>>(
-        r.keys, r.vals, n, (int)n_tiles, 0, r.edge, r2y, nullptr, w, tpart);
+        r.keys, r.vals, n, (int)n_tiles, 0, r.edge, r2y, nullptr, w, tpart, 0);
     return cudaGetLastError();
 }
 
@@ -601,13 +607,17 @@ cudaError_t spearman_batch(const float *pred, int n_seg, int64_t n, const uint32
     const RankScratch r = carve_rank(scratch, n_seg, n);
     cudaError_t e = cudaMemsetAsync(r.nan_flag, 0, (size_t)n_seg * 4, st);
     if (e != cudaSuccess) return e;
+    // unweighted rows need only the target's rank of each row: the sort
+    // carries it as the payload, so the rank pass reads it in sorted order
+    // instead of gathering it by row
+    const bool carry_ranks = w == nullptr;
     e = radix_sort_values(pred, r.keys, r.vals, r.keys2, r.vals2, n_seg, n, r.hist, r.tot,
-                          r.nan_flag, st);
+                          r.nan_flag, carry_ranks ? r2y : nullptr, st);
     if (e != cudaSuccess) return e;
     edges_kernel<<<(unsigned)((n_tiles * n_seg + 255) / 256), 256, 0, st>>>(r.keys, n, (int)n_tiles,
                                                                            n_seg, r.edge);
     rank_kernel<<<dim3((unsigned)n_tiles, n_seg), kTileThreads, 0, st>>>(
-        r.keys, r.vals, n, (int)n_tiles, 1, r.edge, nullptr, r2y, w, r.part);
+        r.keys, r.vals, n, (int)n_tiles, 1, r.edge, nullptr, r2y, w, r.part, carry_ranks ? 1 : 0);
     spearman_final_kernel<<<(n_seg + 7) / 8, 256, 0, st>>>(r.part, tpart, n_seg, (int)n_tiles,
                                                            r.nan_flag, out, out64);
     return cudaGetLastError();
