@@ -138,3 +138,15 @@ def test_folded_op_counts_follow_the_pre_pass_folding():
     assert n_fn == 0 + 1 + 3 + 1
     assert sfu.get("sin", 0) == 0 and sfu.get("ex2", 0) == 0 and sfu.get("lg2", 0) == 0
     assert sfu["rsqrt"] == 1 and sfu["rcp"] == 1
+
+
+def test_workloads_run_at_their_own_size_by_default(monkeypatch):
+    """Without --n-rows each workload keeps the row count it is defined
+    with (16,777,216 only for pagie_large); --n-rows overrides it."""
+    import sys
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "pagie_small"])
+    args = bench.parse()
+    assert args.n_rows == 0
+    assert bench.make_workload(args, 0).data.n_rows == 4096
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "pagie_small", "--n-rows", "1000"])
+    assert bench.make_workload(bench.parse(), 0).data.n_rows == 1000
