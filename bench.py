@@ -670,7 +670,7 @@ def main():
                                 "long_rows_per_thread": used.long_rows_per_thread if used.long_edge > 0 else None,
                                 "long_blocks_per_sm": (used.long_blocks_per_sm or "max resident")
                                 if used.long_edge > 0 else None,
-                                "class_1_2_rows_per_thread": 4, "autotuned": tuned is not None,
+                                "classes_1_to_3_rows_per_thread": 4, "autotuned": tuned is not None,
                                 "autotune_seconds": tune_s, "untuned": untuned}},
             "node_evals_per_s": value * (n_nodes / P),
             "finite_fitness_frac": fin,
