@@ -393,7 +393,8 @@ int gp_last_device_status(void *stream, uint32_t *flags);
  * NULL).  Later calls with zero opts fields use it.  The search is staged:
  * rows_per_thread x chunk_rows, then blocks_per_sm, then the length-bucket
  * edge (none, 12, 16, 24, 32 compiled words) with the long bucket's rows per
- * thread; every candidate is timed as the median of three calls after one
+ * thread, a split being taken only when it is at least 1% faster than one
+ * launch; every candidate is timed as the median of three calls after one
  * warm-up (CUDA events on `stream`, synchronising), on the first 2^21 rows
  * when there are more.  GP_ERR_ARG for GP_SPEARMAN. */
 int gp_autotune(const gp_node *progs, const int32_t *offsets, int n_progs,
